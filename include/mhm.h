@@ -1,0 +1,192 @@
+/*
+ * mhm.h -- C ABI of the GB300 MHM local-problem pipeline.
+ *
+ * The Multiscale Hybrid-Mixed method (paper Sec. 2) splits -div(kappa grad u) = f
+ * on (0,1)^2 into one independent local problem per coarse triangle K of T_H
+ * and a global saddle-point problem on the skeleton (Eq. "global").  This
+ * library runs the local problems and the skeleton assembly on one GPU:
+ *
+ *   mhm_create_mesh        splitProblem (Alg. 1): T_H, faces, normals, the
+ *                          multiplier space Lambda_H^{m,l}, per-K records
+ *   mhm_local_solve_batch  solveLocalProblem (Alg. 1, Sec. 3, Eqs. "etaf",
+ *                          "etai", "etaf_comb", "source_term") for every K:
+ *                          assembly of a(.,.)_K on the refined submesh, the
+ *                          zero-mean Neumann factorisation, the N_I + 1 solves
+ *                          and the face integrals (psi_j, eta_i), (psi_j, eta_f)
+ *   mhm_assemble_skeleton  reduceLocalProblems' gather (Eq. "mat_global"):
+ *                          the global matrix A (CSR) and right-hand side E
+ *   mhm_solve_global       reduceLocalProblems' solve of Eq. "mat_global"
+ *   mhm_reconstruct        computeSolution (Eq. "u_Hh") and error norms
+ *
+ * Conventions (the paper fixes only "globally indexed" elements and faces):
+ *  - Vertex (i,j) of the grid has id j(nx+1)+i; square (i,j) is split along its
+ *    (i,j)-(i+1,j+1) diagonal into K = 2(j nx + i) = [(i,j),(i+1,j),(i+1,j+1)]
+ *    and K+1 = [(i,j),(i+1,j+1),(i,j+1)], counter-clockwise.
+ *  - Local face a of K is opposite local vertex a.  Global faces are numbered
+ *    in order of first encounter (K ascending, a = 0,1,2).
+ *  - Face normal n: outward on the boundary; on an interior face with vertex
+ *    ids g0 < g1, n = (t_y, -t_x) for the unit tangent t from g0 to g1.  The
+ *    sign seen from K is s = n . n_F^K = +-1.
+ *  - Lambda_H^{m,l}: m subfaces per face counted from the lower-id vertex,
+ *    Legendre P_p (p = 0..l) of the subface coordinate in [-1,1]; global index
+ *    offset(face) + q(l+1) + p; local index inside K runs over a = 0,1,2.
+ *  - Submesh: N = 2^r segments per face, local degree P (1 or 2); lattice
+ *    point (i,j), i+j <= PN, is local DOF sum_{j'<j}(PN+1-j') + i.  kappa is
+ *    given per fine triangle, per K in ascending order, and inside K row by
+ *    row: the N-j "up" triangles then the N-1-j "down" triangles of row j.
+ *
+ * Memory: every pointer named *_dev is device memory owned by the caller; the
+ * library keeps no reference to it after the call returns.  Host pointers
+ * (*_host, descriptors) are read during the call only.  The mesh object owns
+ * its own device tables until mhm_destroy_mesh.
+ *
+ * Execution: calls taking a stream are asynchronous and stream-ordered; their
+ * status covers argument checks and launch errors.  Per-element outcomes of
+ * the local solves (convergence) are written to status_dev.
+ *
+ * There is no CPU fallback: without an sm_103 device every compute call
+ * returns MHM_ERR_UNSUPPORTED.
+ */
+#ifndef MHM_H
+#define MHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mhm_status;
+#define MHM_OK 0
+#define MHM_ERR_INVALID_ARG 1
+#define MHM_ERR_OOM 2
+#define MHM_ERR_CUDA 3
+#define MHM_ERR_NOT_CONVERGED 4
+#define MHM_ERR_TIMEOUT 5
+#define MHM_ERR_UNSUPPORTED 6
+
+/* Arithmetic of the local solves. */
+#define MHM_FP64 0   /* factorisation, solves and face integrals in FP64 */
+#define MHM_MIXED 1  /* FP32 factorisation and solves, FP64 residuals and refinement */
+
+/* Source term f of -div(kappa grad u) = f. */
+#define MHM_SRC_CONST 0   /* f = value */
+#define MHM_SRC_SINSIN 1  /* f = value * 2 (freq pi)^2 sin(freq pi x) sin(freq pi y) */
+
+typedef struct mhm_mesh mhm_mesh;
+
+/* Description of T_H and of the local spaces (paper Sec. 2 and Sec. 5's
+ * parameters H, m, l, k and the submesh size). */
+typedef struct {
+    int32_t nx, ny;   /* coarse squares on (0,1)^2, each split into two triangles */
+    int32_t r;        /* refinement level of every K (2^r segments per face), 0..7 */
+    int32_t degree;   /* local Lagrange degree P: 1 or 2 */
+    int32_t m, l;     /* subfaces per face (>= 1) and multiplier degree (>= 0) */
+} mhm_mesh_desc;
+
+typedef struct {
+    int32_t kind;     /* MHM_SRC_* */
+    double value;
+    double freq;
+} mhm_source;
+
+/* Dirichlet data g = c[0] + c[1] x + c[2] y + c[3] x^2 + c[4] x y + c[5] y^2 on
+ * the boundary (the paper treats g = 0; a polynomial g adds (g, psi_j)_F on the
+ * boundary faces to the right-hand side). */
+typedef struct {
+    double c[6];
+} mhm_dirichlet;
+
+/* Options of the local solves. */
+typedef struct {
+    int32_t it_max;   /* MIXED: maximum refinement passes (>= 1) */
+    double tol;       /* MIXED: stop when max_c |dz_c| <= tol * max_c |z_c| */
+    int64_t K_begin;  /* process K in [K_begin, K_end); K_end <= 0 means n_K */
+    int64_t K_end;
+} mhm_solve_opts;
+
+/* ------------------------------------------------------------------ mesh --- */
+
+/* splitProblem (Alg. 1, first step; Sec. 3): builds T_H, the skeleton, normals,
+ * signs, multiplier offsets and the per-K records on the host and uploads them
+ * to `device`.  *out receives a mesh handle; free it with mhm_destroy_mesh.
+ * Errors: INVALID_ARG (sizes out of range), OOM, CUDA, UNSUPPORTED (device is
+ * not sm_103). */
+mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device, mhm_mesh** out);
+void mhm_destroy_mesh(mhm_mesh* mesh);
+
+/* Queries for sizes and for the integer structure (bit-exact parity). */
+#define MHM_Q_SIZES 0          /* int64[8]: n_K, n_faces, n_vertices, n_lambda, n_fine per K,
+                                  n_local per K, N_I per K, skeleton nnz */
+#define MHM_Q_TRI_VERTS 1      /* int32[n_K*3] vertex ids, CCW */
+#define MHM_Q_TRI_FACES 2      /* int32[n_K*3] face id of local face a */
+#define MHM_Q_TRI_SIGNS 3      /* int8[n_K*3]  s = n . n_F^K */
+#define MHM_Q_FACE_VERTS 4     /* int32[n_faces*2] vertex ids, lower first */
+#define MHM_Q_LAMBDA_OFFSET 5  /* int64[n_faces+1] first global multiplier of each face */
+#define MHM_Q_K_LAMBDA 6       /* int32[n_K*N_I] global multiplier id of each local one */
+#define MHM_Q_CSR_ROWPTR 7     /* int32[n_lambda+1] skeleton CSR row pointers */
+#define MHM_Q_CSR_COLS 8       /* int32[nnz] skeleton CSR column ids */
+#define MHM_Q_VERTEX_XY 9      /* double[n_vertices*2] */
+#define MHM_Q_FACE_NORMALS 10  /* double[n_faces*2] */
+/* Copies the queried table into host_out (bytes must be >= its size).
+ * Errors: INVALID_ARG (unknown query, short buffer). */
+mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, size_t bytes);
+
+/* ---------------------------------------------------------- local solves --- */
+
+/* Bytes of device scratch memory mhm_local_solve_batch needs for `precision`
+ * (0 for MHM_FP64, whose factors live in shared memory only). */
+mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes);
+
+/* solveLocalProblem for K in [opts->K_begin, opts->K_end) (all K by default):
+ * for each K, assembles A = [a(phi_j, phi_i)] with a(u,w) = (kappa grad u,
+ * grad w)_K on the submesh (Eq. "source_term"), the loads (f, phi_w)_K and
+ * N_i = -(s psi_i, phi_w)_{dK} (Eqs. "etaf", "etai"), solves the Neumann
+ * problems in the zero-mean space V_h(K) inside V_0^perp(K) (Sec. 2, item 2),
+ * and writes the local contributions to Eq. "mat_global":
+ *   AK_dev[K*N_I*N_I + j*N_I + i] = (s psi_j, eta_i)_{dK}   (row-major, symmetric)
+ *   EK_dev[K*N_I + j]             = -(s psi_j, eta_f)_{dK}
+ *   BK_dev[K*N_I + j]             = (s psi_j, 1)_{dK}
+ *   FK_dev[K]                     = (f, 1)_K
+ *   status_dev[K]                 = 0, or MHM_ERR_NOT_CONVERGED (MIXED refinement
+ *                                   hit it_max), or MHM_ERR_INVALID_ARG (non-positive pivot)
+ *   iters_dev[K]                  = refinement passes taken (1 for FP64); may be NULL
+ * Arrays are indexed by absolute K; entries outside the range are untouched.
+ * kappa_dev: n_K * 4^r doubles, > 0.  workspace_dev: at least
+ * mhm_local_workspace_size bytes (may be NULL when that size is 0).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID_ARG (NULL pointers, bad options, workspace too small),
+ * UNSUPPORTED, CUDA (launch failure). */
+mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
+                                 int32_t precision, const mhm_solve_opts* opts, double* AK_dev,
+                                 double* EK_dev, double* BK_dev, double* FK_dev, int32_t* status_dev,
+                                 int32_t* iters_dev, void* workspace_dev, size_t workspace_bytes,
+                                 void* stream);
+
+/* -------------------------------------------------------------- skeleton --- */
+
+/* reduceLocalProblems' gather (Eq. "mat_global"): sums the per-K blocks into
+ * the global skeleton matrix A (CSR pattern from MHM_Q_CSR_ROWPTR/COLS; the two
+ * contributions to a face's diagonal block are added in ascending K order, no
+ * atomics) and the right-hand side E_j = sum_K EK[K, local j] + (g, psi_j)_F.
+ * A_vals_dev: nnz doubles; E_dev: n_lambda doubles; g may be NULL (g = 0).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+mhm_status mhm_assemble_skeleton(const mhm_mesh* mesh, const double* AK_dev, const double* EK_dev,
+                                 const mhm_dirichlet* g, double* A_vals_dev, double* E_dev,
+                                 void* stream);
+
+/* ------------------------------------------------------------------ misc --- */
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* mhm_last_error(void);
+
+/* Micro-benchmark of the arithmetic pipes on `device` (used for roofline
+ * denominators): out[0] = FP64 FMA GFLOP/s, out[1] = FP32 FMA GFLOP/s, each
+ * over the whole GPU, 2 flops per FMA.  Synchronous. */
+mhm_status mhm_measure_pipes(int32_t device, double* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHM_H */

@@ -1,0 +1,159 @@
+// C ABI entry points: argument checks, error reporting and dispatch to the
+// kernels.  No entry point falls back to the CPU.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <string>
+
+#include "mhm_internal.h"
+
+namespace mhm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+mhm_status fail(mhm_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+mhm_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MHM_ERR_OOM : MHM_ERR_CUDA;
+}
+
+bool device_supported(int device) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return false;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    return major == 10 && minor == 3;
+}
+
+// Makes the mesh's device current; fails for host-only meshes.
+static mhm_status enter(const mhm_mesh* mesh, const char* who) {
+    if (!mesh) return fail(MHM_ERR_INVALID_ARG, std::string(who) + ": NULL mesh");
+    if (mesh->device < 0)
+        return fail(MHM_ERR_UNSUPPORTED, std::string(who) + ": mesh was created without a device");
+    cudaError_t e = cudaSetDevice(mesh->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return MHM_OK;
+}
+
+}  // namespace mhm
+
+using namespace mhm;
+
+extern "C" const char* mhm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes) {
+    if (!mesh || !bytes) return fail(MHM_ERR_INVALID_ARG, "mhm_local_workspace_size: NULL argument");
+    if (precision == MHM_FP64) {
+        *bytes = 0;
+        return MHM_OK;
+    }
+    if (precision == MHM_MIXED) {
+        *bytes = mixed_workspace_bytes(mesh);
+        return MHM_OK;
+    }
+    return fail(MHM_ERR_INVALID_ARG, "mhm_local_workspace_size: unknown precision");
+}
+
+extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa, const mhm_source* f,
+                                            int32_t precision, const mhm_solve_opts* opts, double* AK,
+                                            double* EK, double* BK, double* FK, int32_t* status,
+                                            int32_t* iters, void* workspace, size_t ws_bytes, void* stream) {
+    mhm_status st = enter(mesh, "mhm_local_solve_batch");
+    if (st) return st;
+    if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: NULL pointer argument");
+    if (f->kind != MHM_SRC_CONST && f->kind != MHM_SRC_SINSIN)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown source kind");
+    mhm_solve_opts o{};
+    o.it_max = 8;
+    o.tol = 1e-14;
+    o.K_begin = 0;
+    o.K_end = 0;
+    if (opts) o = *opts;
+    const int64_t K0 = o.K_begin, K1 = o.K_end > 0 ? o.K_end : mesh->nK;
+    if (K0 < 0 || K1 > mesh->nK || K0 > K1)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: K range out of bounds");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == MHM_FP64)
+        return launch_local_fp64(mesh, kappa, *f, K0, K1, AK, EK, BK, FK, status, iters, s);
+    if (precision == MHM_MIXED) {
+        if (o.it_max < 1 || !(o.tol > 0.0))
+            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: it_max >= 1 and tol > 0 required");
+        const size_t need = mixed_workspace_bytes(mesh);
+        if (ws_bytes < need || (need > 0 && !workspace))
+            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
+        return launch_local_mixed(mesh, kappa, *f, o, K0, K1, AK, EK, BK, FK, status, iters, workspace, ws_bytes, s);
+    }
+    return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown precision");
+}
+
+extern "C" mhm_status mhm_assemble_skeleton(const mhm_mesh* mesh, const double* AK, const double* EK,
+                                            const mhm_dirichlet* g, double* A_vals, double* E, void* stream) {
+    mhm_status st = enter(mesh, "mhm_assemble_skeleton");
+    if (st) return st;
+    if (!AK || !EK || !A_vals || !E) return fail(MHM_ERR_INVALID_ARG, "mhm_assemble_skeleton: NULL pointer argument");
+    return launch_skeleton(mesh, AK, EK, g, A_vals, E, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ pipe peaks ---
+
+namespace {
+
+template <typename T, int CHAINS>
+__global__ void k_fma_peak(T* out, int iters, T a, T b) {
+    T x[CHAINS];
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) x[c] = (T)(threadIdx.x + c);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) x[c] = x[c] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += x[c];
+    if (s == (T)12345.678) out[threadIdx.x] = s;  // keeps the chains alive
+}
+
+template <typename T, int CHAINS>
+double time_fma(int sms, int iters) {
+    T* out = nullptr;
+    cudaMalloc(&out, 1024 * sizeof(T));
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_peak<T, CHAINS><<<blocks, threads>>>(out, iters / 10, (T)0.999, (T)0.001);
+    cudaEventRecord(e0);
+    k_fma_peak<T, CHAINS><<<blocks, threads>>>(out, iters, (T)0.999, (T)0.001);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    const double flops = 2.0 * CHAINS * (double)iters * blocks * threads;
+    return flops / (ms * 1e-3) / 1e9;
+}
+
+}  // namespace
+
+extern "C" mhm_status mhm_measure_pipes(int32_t device, double* out) {
+    if (!out) return fail(MHM_ERR_INVALID_ARG, "mhm_measure_pipes: NULL output");
+    if (!device_supported(device)) return fail(MHM_ERR_UNSUPPORTED, "mhm_measure_pipes: not an sm_103 device");
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    out[0] = time_fma<double, 8>(sms, 1 << 12);
+    out[1] = time_fma<float, 16>(sms, 1 << 16);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mhm_measure_pipes");
+    return MHM_OK;
+}

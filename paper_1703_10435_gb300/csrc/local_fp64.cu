@@ -1,0 +1,412 @@
+// solveLocalProblem in FP64 (Alg. 1; Sec. 3, Eqs. "etaf", "etai", "etaf_comb";
+// Sec. 4.2, Eq. "source_term"), one thread block per coarse triangle K.
+//
+// What is computed.  With A the stiffness matrix of a(.,.)_K on the submesh,
+// m_w = int_K phi_w, and the loads N_i = -(s psi_i, phi_w)_{dK}, F = (f, phi_w)_K,
+// the zero-mean solutions are eta = z - (m^T z / |K|) 1 where z solves the
+// system pinned at DOF 0 with the compatible loads g~ = g - (1^T g / |K|) m.
+// The face integrals of Eq. "mat_global" then reduce to a Gram matrix:
+//     A_K = -N~^T A_p^{-1} N~ = -Y^T Y,   E_K = Y^T y_f,
+// with Y = L^{-1} N~, y_f = L^{-1} f~ and A_p = L L^T (Cholesky of the pinned
+// matrix).  Only the forward elimination is needed; no factor is stored.
+//
+// How.  A_p is block tridiagonal in the levels of the submesh (local_common.cuh).
+// The kernel slides a window over two consecutive levels held in shared memory:
+// rows [0, b) hold level lev (already reduced by the previous levels), rows
+// [b, b + b') the fresh level lev+1, the columns are the symmetric part (lower
+// triangle used) followed by the R = N_I + 1 right-hand sides.  It adds the
+// element matrices and loads of fine row lev (the only triangles touching both
+// levels), eliminates the b pivots of level lev by right-looking Cholesky on the
+// augmented rows (which produces L, W = L^{-1} C^T, the Schur complement of
+// level lev+1 and the forward-solved right-hand sides in one pass), accumulates
+// Y_lev^T Y_lev into the Gram matrix and moves the reduced level lev+1 to the
+// top of the window.
+#include <cuda_runtime.h>
+
+#include "local_common.cuh"
+
+namespace mhm {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+struct Fp64Args {
+    DeviceMesh dm;
+    const double* kappa;
+    int P, N, PN, M, L, dpf, NI, R;
+    int ld;        // leading dimension of the window (doubles)
+    int rhs0;      // first right-hand-side column of the window
+    int rows;      // window rows (largest b + b')
+    int src_kind;
+    double src_value, src_freq;
+    int64_t K0;
+    double *AK, *EK, *BK, *FK;
+    int32_t *status, *iters;
+};
+
+struct KCtx {
+    double X[3][2];      // coarse vertices
+    double Sup[36], Sdn[36];
+    double area_fine;    // |T| of every fine triangle
+    double area;         // |K|
+    double flen[3];      // face lengths
+    int sgn[3], rev[3];
+    double cproj[kMaxNI + 1];  // projection coefficient of each right-hand side
+    double FK;
+    int bad;             // first failing pivot (+1), 0 if none
+};
+
+// Sum over the block of one value per thread.
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        red[0] = s;
+    }
+    __syncthreads();
+    s = red[0];
+    __syncthreads();
+    return s;
+}
+
+// Cell integral of f phi_a over fine triangle (X0, X1, X2) by the collapsed
+// 4 x 4 Gauss rule; phi_a = -1 means the integral of f itself.
+__device__ double cell_source(const Fp64Args& g, const double X[3][2], int P, int a) {
+    const double* gx = g.dm.gauss_x + 3 * kMaxGauss;
+    const double* gw = g.dm.gauss_w + 3 * kMaxGauss;
+    const double adet = fabs((X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[2][0] - X[0][0]) * (X[1][1] - X[0][1]));
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            const double xi = gx[i], eta = gx[j] * (1.0 - gx[i]), w = gw[i] * gw[j] * (1.0 - gx[i]);
+            const double x = X[0][0] + xi * (X[1][0] - X[0][0]) + eta * (X[2][0] - X[0][0]);
+            const double y = X[0][1] + xi * (X[1][1] - X[0][1]) + eta * (X[2][1] - X[0][1]);
+            double phi = 1.0;
+            if (a >= 0) {
+                const double l0 = 1.0 - xi - eta, l1 = xi, l2 = eta;
+                if (P == 1) phi = a == 0 ? l0 : (a == 1 ? l1 : l2);
+                else {
+                    const double lam[3] = {l0, l1, l2};
+                    if (a < 3) phi = lam[a] * (2.0 * lam[a] - 1.0);
+                    else if (a == 3) phi = 4.0 * l1 * l2;
+                    else if (a == 4) phi = 4.0 * l2 * l0;
+                    else phi = 4.0 * l0 * l1;
+                }
+            }
+            s += w * adet * source_value(g.src_kind, g.src_value, g.src_freq, x, y) * phi;
+        }
+    return s;
+}
+
+// Vertices of fine triangle (up/down, i, j) in physical coordinates.
+__device__ __forceinline__ void fine_vertices(const KCtx& c, int N, bool up, int i, int j, double X[3][2]) {
+    const double e1x = (c.X[1][0] - c.X[0][0]) / N, e1y = (c.X[1][1] - c.X[0][1]) / N;
+    const double e2x = (c.X[2][0] - c.X[0][0]) / N, e2y = (c.X[2][1] - c.X[0][1]) / N;
+    int a[3][2];
+    if (up) { a[0][0] = i; a[0][1] = j; a[1][0] = i + 1; a[1][1] = j; a[2][0] = i; a[2][1] = j + 1; }
+    else    { a[0][0] = i + 1; a[0][1] = j; a[1][0] = i + 1; a[1][1] = j + 1; a[2][0] = i; a[2][1] = j + 1; }
+    for (int v = 0; v < 3; ++v) {
+        X[v][0] = c.X[0][0] + a[v][0] * e1x + a[v][1] * e2x;
+        X[v][1] = c.X[0][1] + a[v][0] * e1y + a[v][1] * e2y;
+    }
+}
+
+// Boundary loads N_i = -(s psi_i, phi_w) of the points of level `lev`, placed at
+// window row offset `row0`.
+__device__ void add_face_loads(const Fp64Args& g, const KCtx& c, const LevelGeom& lg, int lev, int row0,
+                               double* W) {
+    const int b = lg.size(lev);
+    const int work = b * 3 * g.dpf;
+    for (int t = threadIdx.x; t < work; t += blockDim.x) {
+        const int p = t / (3 * g.dpf), rem = t - p * 3 * g.dpf, a = rem / g.dpf, jf = rem - a * g.dpf;
+        int x, y;
+        lg.point(lev, p, &x, &y);
+        const int kl = face_position(g.PN, x, y, a);
+        if (kl < 0) continue;
+        const int k = c.rev[a] ? g.PN - kl : kl;
+        const double v = -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + k];
+        W[(row0 + p) * g.ld + g.rhs0 + a * g.dpf + jf] += v;
+    }
+}
+
+// Element contributions of fine row j (triangles touching levels j and j+1),
+// in four colour classes of pairwise disjoint triangles; level j at window rows
+// [0, b), level j+1 at [b, ...).
+__device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& lg, int j, int b,
+                             const double* kap, double* W) {
+    const int P = g.P, N = g.N, nb = P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
+    const int rowstart = j * (2 * N - j);
+    for (int cls = 0; cls < 4; ++cls) {
+        const bool up = cls < 2;
+        const int parity = cls & 1;
+        const int ntri = up ? N - j : N - 1 - j;
+        const int ncls = (ntri - parity + 1) / 2;
+        const int per = npair + nb * g.R;
+        for (int t = threadIdx.x; t < ncls * per; t += blockDim.x) {
+            const int ti = t / per, item = t - ti * per;
+            const int i = parity + 2 * ti;
+            int nx[6], ny[6];
+            element_nodes(P, up, i, j, nx, ny);
+            const double kt = kap[rowstart + (up ? i : (N - j) + i)];
+            const double* S = up ? c.Sup : c.Sdn;
+            if (item < npair) {
+                // pair (a <= bb) by row-major enumeration of the upper triangle
+                int a = 0, rem = item;
+                while (rem >= nb - a) { rem -= nb - a; ++a; }
+                const int bb = a + rem;
+                const int pa = lg.pos(nx[a], ny[a]), pb = lg.pos(nx[bb], ny[bb]);
+                if (pa < 0 || pb < 0) continue;  // pinned DOF
+                const int ra = pa + (lg.level_of_row(ny[a]) == j ? 0 : b);
+                const int rb = pb + (lg.level_of_row(ny[bb]) == j ? 0 : b);
+                const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+                W[hi * g.ld + lo] += kt * S[a * nb + bb];
+            } else {
+                const int it = item - npair, a = it / g.R, col = it - a * g.R;
+                const int pa = lg.pos(nx[a], ny[a]);
+                if (pa < 0) continue;
+                const int ra = pa + (lg.level_of_row(ny[a]) == j ? 0 : b);
+                const double mass = c.area_fine * element_mass_frac(P, a);
+                double v = -c.cproj[col] * mass;
+                if (col == g.NI) {
+                    if (g.src_kind == MHM_SRC_CONST) v += g.src_value * mass;
+                    else {
+                        double X[3][2];
+                        fine_vertices(c, N, up, i, j, X);
+                        v += cell_source(g, X, P, a);
+                    }
+                }
+                W[ra * g.ld + g.rhs0 + col] += v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_local_fp64(const Fp64Args g) {
+    extern __shared__ double smem[];
+    __shared__ KCtx c;
+    __shared__ double red[32];
+    const int64_t K = g.K0 + blockIdx.x;
+    const LevelGeom lg{g.P, g.N, g.PN};
+    const int R = g.R;
+    double* W = smem;                                 // window: rows x ld
+    double* gram = smem + (size_t)g.rows * g.ld;      // R x R, upper triangle used
+    const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+
+    // ---- per-K setup
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < 3; ++v) {
+            c.X[v][0] = g.dm.geom[6 * K + 2 * v];
+            c.X[v][1] = g.dm.geom[6 * K + 2 * v + 1];
+        }
+        c.area = 0.5 * fabs((c.X[1][0] - c.X[0][0]) * (c.X[2][1] - c.X[0][1]) -
+                            (c.X[2][0] - c.X[0][0]) * (c.X[1][1] - c.X[0][1]));
+        c.area_fine = c.area / ((double)g.N * g.N);
+        for (int a = 0; a < 3; ++a) {
+            const double* P0 = c.X[(a + 1) % 3];
+            const double* Q0 = c.X[(a + 2) % 3];
+            c.flen[a] = sqrt((Q0[0] - P0[0]) * (Q0[0] - P0[0]) + (Q0[1] - P0[1]) * (Q0[1] - P0[1]));
+            c.sgn[a] = g.dm.sign[3 * K + a];
+            c.rev[a] = g.dm.rev[3 * K + a];
+        }
+        double Xu[3][2], Xd[3][2];
+        fine_vertices(c, g.N, true, 0, 0, Xu);
+        fine_vertices(c, g.N, false, 0, 0, Xd);
+        element_stiffness(g.P, Xu, c.Sup);
+        element_stiffness(g.P, Xd, c.Sdn);
+        c.bad = 0;
+    }
+    __syncthreads();
+    // F_K = (f, 1)_K and the projection coefficients (1^T g) / |K| of every right-hand side
+    double FK;
+    if (g.src_kind == MHM_SRC_CONST) {
+        FK = g.src_value * c.area;
+    } else {
+        double s = 0.0;
+        for (int t = threadIdx.x; t < g.N * g.N; t += blockDim.x) {
+            // fine triangle t in kappa order: row j, then up/down, column i
+            int j = 0, rs = 0;
+            while (rs + 2 * (g.N - j) - 1 <= t) { rs += 2 * (g.N - j) - 1; ++j; }
+            const int o = t - rs;
+            const bool up = o < g.N - j;
+            const int i = up ? o : o - (g.N - j);
+            double X[3][2];
+            fine_vertices(c, g.N, up, i, j, X);
+            s += cell_source(g, X, g.P, -1);
+        }
+        FK = block_sum(s, red);
+    }
+    for (int col = threadIdx.x; col <= g.NI; col += blockDim.x) {
+        if (col == g.NI) c.cproj[col] = FK / c.area;
+        else {
+            const int a = col / g.dpf, jf = col - a * g.dpf;
+            c.cproj[col] = -c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf] / c.area;
+        }
+    }
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x) gram[t] = 0.0;
+    const int b0 = lg.size(0), b1 = lg.size(1);
+    for (int t = threadIdx.x; t < (b0 + b1) * g.ld; t += blockDim.x) W[t] = 0.0;
+    __syncthreads();
+    add_face_loads(g, c, lg, 0, 0, W);
+    __syncthreads();
+
+    // ---- level sweep
+    const int nlev = lg.n_levels();
+    for (int lev = 0; lev < nlev; ++lev) {
+        const int b = lg.size(lev);
+        const int bn = lev + 1 < nlev ? lg.size(lev + 1) : 0;
+        const int nr = b + bn;
+        if (bn > 0) {
+            add_face_loads(g, c, lg, lev + 1, b, W);
+            __syncthreads();
+            add_fine_row(g, c, lg, lev, b, kap, W);  // ends with a barrier
+        }
+        // pivot 0 of the level: scale column 0 and the right-hand sides of row 0
+        {
+            const double d = W[0];
+            const double inv = 1.0 / sqrt(d);
+            if (threadIdx.x == 0 && !(d > 0.0) && c.bad == 0) c.bad = 1;
+            __syncthreads();
+            for (int t = threadIdx.x; t < nr - 1 + R; t += blockDim.x) {
+                if (t < nr - 1) W[(t + 1) * g.ld] *= inv;
+                else W[g.rhs0 + (t - (nr - 1))] *= inv;
+            }
+            __syncthreads();
+        }
+        for (int k = 0; k < b; ++k) {
+            // trailing update by pivot k; rows/cols k+1.. in folded pairs, and, with
+            // look-ahead, the scaling of column k+1 and of row k+1's right-hand sides.
+            const int m = nr - k - 1;
+            if (m <= 0) break;
+            const double lkk1 = W[(k + 1) * g.ld + k];
+            const double dn = W[(k + 1) * g.ld + (k + 1)] - lkk1 * lkk1;  // new pivot k+1
+            const bool look = (k + 1 < b);
+            const double invn = look ? 1.0 / sqrt(dn) : 1.0;
+            if (look && threadIdx.x == 0 && !(dn > 0.0) && c.bad == 0) c.bad = k + 2;
+            const int H = (m + 1) / 2, Wd = m + 1 + 2 * R;
+            const int total = H * Wd;
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                const int p = e / Wd, cc = e - p * Wd;
+                const int ia = k + 1 + (m - 1 - p), ib = k + 1 + p;
+                int i, jcol;
+                bool rhs;
+                if (cc < m - p) { i = ia; jcol = k + 1 + cc; rhs = false; }
+                else if (cc < m + 1) { if (ia == ib) continue; i = ib; jcol = k + 1 + (cc - (m - p)); rhs = false; }
+                else if (cc < m + 1 + R) { i = ia; jcol = cc - (m + 1); rhs = true; }
+                else { if (ia == ib) continue; i = ib; jcol = cc - (m + 1 + R); rhs = true; }
+                const double lik = W[i * g.ld + k];
+                if (!rhs) {
+                    // the new pivot k+1 is recomputed by every thread above; its slot is not rewritten
+                    if (look && i == k + 1 && jcol == k + 1) continue;
+                    double v = W[i * g.ld + jcol] - lik * W[jcol * g.ld + k];
+                    if (look && jcol == k + 1 && i > k + 1) v *= invn;
+                    W[i * g.ld + jcol] = v;
+                } else {
+                    double v = W[i * g.ld + g.rhs0 + jcol] - lik * W[k * g.ld + g.rhs0 + jcol];
+                    if (look && i == k + 1) v *= invn;
+                    W[i * g.ld + g.rhs0 + jcol] = v;
+                }
+            }
+            __syncthreads();
+        }
+        // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
+        for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+            const int c1 = t / R, c2 = t - c1 * R;
+            if (c1 > c2) continue;
+            double s = 0.0;
+            for (int k = 0; k < b; ++k) s += W[k * g.ld + g.rhs0 + c1] * W[k * g.ld + g.rhs0 + c2];
+            gram[t] += s;
+        }
+        __syncthreads();
+        if (bn > 0) {
+            // move the reduced level lev+1 (rows/cols [b, nr)) to the top; clear the next rows
+            for (int t = threadIdx.x; t < bn * (bn + R); t += blockDim.x) {
+                const int i = t / (bn + R), jj = t - i * (bn + R);
+                if (jj < bn) {
+                    if (jj <= i) W[i * g.ld + jj] = W[(b + i) * g.ld + b + jj];
+                } else {
+                    W[i * g.ld + g.rhs0 + (jj - bn)] = W[(b + i) * g.ld + g.rhs0 + (jj - bn)];
+                }
+            }
+            __syncthreads();
+            const int bnn = lev + 2 < nlev ? lg.size(lev + 2) : 0;
+            for (int t = threadIdx.x; t < bnn * g.ld; t += blockDim.x) W[bn * g.ld + t] = 0.0;
+            __syncthreads();
+        }
+    }
+
+    // ---- outputs
+    const int NI = g.NI;
+    for (int t = threadIdx.x; t < NI * NI; t += blockDim.x) {
+        const int j = t / NI, i = t - j * NI;
+        const int lo = j < i ? j : i, hi = j < i ? i : j;
+        g.AK[K * NI * NI + t] = -gram[lo * R + hi];
+    }
+    for (int j = threadIdx.x; j < NI; j += blockDim.x) {
+        g.EK[K * NI + j] = gram[j * R + NI];
+        const int a = j / g.dpf, jf = j - a * g.dpf;
+        g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
+    }
+    if (threadIdx.x == 0) {
+        g.FK[K] = FK;
+        g.status[K] = c.bad ? MHM_ERR_INVALID_ARG : 0;
+        if (g.iters) g.iters[K] = 1;
+    }
+}
+
+}  // namespace
+
+int fp64_window_rows(const mhm_mesh* mesh) {
+    // largest b + b' over consecutive levels: levels 0 and 1
+    const int P = mesh->desc.degree, N = mesh->N;
+    auto size = [&](int lev) {
+        if (P == 1) return N + 1 - lev - (lev == 0);
+        if (lev == N) return 1;
+        return (2 * N - 2 * lev + 1) + (2 * N - 2 * lev) - (lev == 0);
+    };
+    return size(0) + (N >= 1 ? size(1) : 0);
+}
+
+mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mhm_source& f, int64_t K0,
+                             int64_t K1, double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                             int32_t* iters, cudaStream_t stream) {
+    Fp64Args g;
+    g.dm = mesh->dev();
+    g.kappa = kappa;
+    g.P = mesh->desc.degree;
+    g.N = mesh->N;
+    g.PN = mesh->PN;
+    g.M = mesh->desc.m;
+    g.L = mesh->desc.l;
+    g.dpf = mesh->dpf;
+    g.NI = (int)mesh->NI;
+    g.R = g.NI + 1;
+    const int rows = fp64_window_rows(mesh);
+    g.rows = rows;
+    g.rhs0 = rows;
+    g.ld = rows + g.R;
+    if (g.ld % 2 == 0) g.ld += 1;  // odd stride in doubles spreads rows over banks
+    g.src_kind = f.kind;
+    g.src_value = f.value;
+    g.src_freq = f.freq;
+    g.K0 = K0;
+    g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
+    g.status = status;
+    g.iters = iters;
+    const size_t smem = ((size_t)rows * g.ld + (size_t)g.R * g.R) * sizeof(double);
+    if (smem > 220 * 1024)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window exceeds shared memory (r too large)");
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t nblk = K1 - K0;
+    if (nblk <= 0) return MHM_OK;
+    k_local_fp64<<<(unsigned)nblk, kThreads, smem, stream>>>(g);
+    MHM_CUDA_TRY(cudaGetLastError());
+    return MHM_OK;
+}
+
+}  // namespace mhm

@@ -1,0 +1,364 @@
+// splitProblem (Alg. 1, first step): the coarse mesh T_H, its skeleton, face
+// normals and signs, the multiplier space Lambda_H^{m,l} and the tables the
+// kernels read, built on the host and uploaded once.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <utility>
+
+#include "mhm_internal.h"
+
+namespace {
+
+// Legendre P_n and its derivative at x by the three-term recurrence.
+void legendre_pd(int n, double x, double* p, double* dp) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+    }
+    *p = p1;
+    *dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// n-point Gauss-Legendre rule on [0,1]: roots of P_n by Newton from the
+// Chebyshev-like initial guesses cos(pi (i + 3/4) / (n + 1/2)).
+void gauss_legendre01(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double p = 0, dp = 1;
+        for (int it = 0; it < 100; ++it) {
+            legendre_pd(n, z, &p, &dp);
+            double dz = p / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        legendre_pd(n, z, &p, &dp);
+        x[n - 1 - i] = 0.5 * (z + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/((1-z^2) P'^2) on [-1,1], halved
+    }
+}
+
+double legendre_p(int p, double xi) {
+    if (p == 0) return 1.0;
+    double a = 1.0, b = xi;
+    for (int k = 1; k < p; ++k) {
+        double c = ((2 * k + 1) * xi * b - k * a) / (k + 1);
+        a = b;
+        b = c;
+    }
+    return b;
+}
+
+// 1-D Lagrange basis of degree P on one fine segment, local coordinate t in [0,1].
+void lagrange1d(int P, double t, double* v) {
+    if (P == 1) {
+        v[0] = 1.0 - t;
+        v[1] = t;
+    } else {
+        v[0] = 2.0 * (t - 0.5) * (t - 1.0);
+        v[1] = -4.0 * t * (t - 1.0);
+        v[2] = 2.0 * t * (t - 0.5);
+    }
+}
+
+template <typename T>
+mhm_status upload(const std::vector<T>& h, T** d) {
+    if (h.empty()) { *d = nullptr; return MHM_OK; }
+    cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) return mhm::fail(MHM_ERR_OOM, "cudaMalloc failed for mesh tables");
+    if (e != cudaSuccess) return mhm::cuda_fail(e, "cudaMalloc");
+    e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return mhm::cuda_fail(e, "cudaMemcpy");
+    return MHM_OK;
+}
+
+}  // namespace
+
+void free_mesh_device(mhm_mesh* m) {
+    void* ptrs[] = {m->d_geom, m->d_sign, m->d_rev, m->d_btab, m->d_btab_sum, m->d_gauss_x,
+                    m->d_gauss_w, m->d_face_v, m->d_face_K, m->d_tri_f, m->d_vxy, m->d_lam_off,
+                    m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device, mhm_mesh** out) {
+    if (!desc || !out) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: NULL argument");
+    *out = nullptr;
+    const mhm_mesh_desc d = *desc;
+    if (d.nx < 1 || d.ny < 1 || (int64_t)d.nx * d.ny > (1 << 26))
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: nx, ny out of range");
+    if (d.r < 0 || d.r > 7) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: r must be in 0..7");
+    if (d.degree != 1 && d.degree != 2) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: degree must be 1 or 2");
+    if (d.m < 1 || d.l < 0 || d.m * (d.l + 1) > mhm::kMaxFaceDofs)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: m >= 1, l >= 0 and m(l+1) <= 16 required");
+    // device < 0 builds the host tables only (queries work, compute calls return UNSUPPORTED).
+    if (device >= 0) {
+        if (!mhm::device_supported(device))
+            return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm_create_mesh: device is not an sm_103 GPU");
+        cudaError_t ce = cudaSetDevice(device);
+        if (ce != cudaSuccess) return mhm::cuda_fail(ce, "cudaSetDevice");
+    }
+
+    mhm_mesh* m = new mhm_mesh();
+    m->device = device;
+    m->desc = d;
+    const int nx = d.nx, ny = d.ny;
+    m->N = 1 << d.r;
+    m->PN = d.degree * m->N;
+    m->dpf = d.m * (d.l + 1);
+    m->nv = (int64_t)(nx + 1) * (ny + 1);
+    m->nK = 2LL * nx * ny;
+    m->nfine = (int64_t)m->N * m->N;
+    m->nloc = (int64_t)(m->PN + 1) * (m->PN + 2) / 2;
+    m->NI = 3LL * m->dpf;
+
+    // vertices and triangles
+    m->vxy.resize(m->nv * 2);
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            m->vxy[2 * (j * (nx + 1) + i)] = (double)i / nx;
+            m->vxy[2 * (j * (nx + 1) + i) + 1] = (double)j / ny;
+        }
+    auto vid = [nx](int i, int j) { return j * (nx + 1) + i; };
+    m->tri_v.resize(m->nK * 3);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int64_t K = 2LL * (j * nx + i);
+            int32_t* t = &m->tri_v[3 * K];
+            t[0] = vid(i, j); t[1] = vid(i + 1, j); t[2] = vid(i + 1, j + 1);
+            t[3] = vid(i, j); t[4] = vid(i + 1, j + 1); t[5] = vid(i, j + 1);
+        }
+
+    // faces in order of first encounter
+    std::map<std::pair<int32_t, int32_t>, int32_t> key;
+    m->tri_f.resize(m->nK * 3);
+    for (int64_t K = 0; K < m->nK; ++K)
+        for (int a = 0; a < 3; ++a) {
+            int32_t p = m->tri_v[3 * K + (a + 1) % 3], q = m->tri_v[3 * K + (a + 2) % 3];
+            auto k = std::make_pair(std::min(p, q), std::max(p, q));
+            auto it = key.find(k);
+            int32_t e;
+            if (it == key.end()) {
+                e = (int32_t)m->face_v.size() / 2;
+                key.emplace(k, e);
+                m->face_v.push_back(k.first);
+                m->face_v.push_back(k.second);
+                m->face_K.push_back((int32_t)K);
+                m->face_K.push_back(-1);
+            } else {
+                e = it->second;
+                m->face_K[2 * e + 1] = (int32_t)K;
+            }
+            m->tri_f[3 * K + a] = e;
+        }
+    m->ne = (int64_t)m->face_v.size() / 2;
+
+    // normals, signs, orientation flags
+    m->normals.resize(m->ne * 2);
+    auto outward = [&](int64_t K, int a, double* n) {
+        const double* P = &m->vxy[2 * m->tri_v[3 * K + (a + 1) % 3]];
+        const double* Q = &m->vxy[2 * m->tri_v[3 * K + (a + 2) % 3]];
+        double dx = Q[0] - P[0], dy = Q[1] - P[1], L = std::sqrt(dx * dx + dy * dy);
+        n[0] = dy / L;
+        n[1] = -dx / L;
+    };
+    for (int64_t e = 0; e < m->ne; ++e) {
+        if (m->face_K[2 * e + 1] < 0) {
+            int64_t K = m->face_K[2 * e];
+            int a = 0;
+            while (m->tri_f[3 * K + a] != e) ++a;
+            outward(K, a, &m->normals[2 * e]);
+        } else {
+            const double* A = &m->vxy[2 * m->face_v[2 * e]];
+            const double* B = &m->vxy[2 * m->face_v[2 * e + 1]];
+            double tx = B[0] - A[0], ty = B[1] - A[1], L = std::sqrt(tx * tx + ty * ty);
+            m->normals[2 * e] = ty / L;
+            m->normals[2 * e + 1] = -tx / L;
+        }
+    }
+    m->tri_s.resize(m->nK * 3);
+    m->tri_rev.resize(m->nK * 3);
+    for (int64_t K = 0; K < m->nK; ++K)
+        for (int a = 0; a < 3; ++a) {
+            double n[2];
+            outward(K, a, n);
+            int32_t e = m->tri_f[3 * K + a];
+            double s = n[0] * m->normals[2 * e] + n[1] * m->normals[2 * e + 1];
+            m->tri_s[3 * K + a] = s > 0 ? 1 : -1;
+            m->tri_rev[3 * K + a] = m->tri_v[3 * K + (a + 1) % 3] > m->tri_v[3 * K + (a + 2) % 3] ? 1 : 0;
+        }
+
+    // multiplier numbering
+    m->lam_off.resize(m->ne + 1);
+    for (int64_t e = 0; e <= m->ne; ++e) m->lam_off[e] = e * m->dpf;
+    m->nlam = m->lam_off[m->ne];
+    m->k_lambda.resize(m->nK * m->NI);
+    for (int64_t K = 0; K < m->nK; ++K)
+        for (int a = 0; a < 3; ++a)
+            for (int u = 0; u < m->dpf; ++u)
+                m->k_lambda[K * m->NI + a * m->dpf + u] = (int32_t)(m->lam_off[m->tri_f[3 * K + a]] + u);
+
+    // skeleton pattern: face e's rows couple with every face of its (one or two) K
+    m->nbr_ptr.assign(m->ne + 1, 0);
+    for (int64_t e = 0; e < m->ne; ++e) {
+        std::map<int32_t, mhm::FaceNbr> blocks;
+        for (int side = 0; side < 2; ++side) {
+            int32_t K = m->face_K[2 * e + side];
+            if (K < 0) continue;
+            int ae = 0;
+            while (m->tri_f[3 * K + ae] != e) ++ae;
+            for (int b = 0; b < 3; ++b) {
+                int32_t f = m->tri_f[3 * K + b];
+                auto it = blocks.find(f);
+                if (it == blocks.end()) {
+                    mhm::FaceNbr nb{f, 0, K, ae, b, -1, 0, 0};
+                    blocks.emplace(f, nb);
+                } else {  // f == e on an interior face: second K, larger id
+                    it->second.K1 = K;
+                    it->second.a1 = ae;
+                    it->second.b1 = b;
+                }
+            }
+        }
+        int32_t off = 0;
+        for (auto& kv : blocks) {
+            kv.second.col_off = off;
+            off += m->dpf;
+            m->nbrs.push_back(kv.second);
+        }
+        m->nbr_ptr[e + 1] = (int32_t)m->nbrs.size();
+    }
+    m->csr_rowptr.assign(m->nlam + 1, 0);
+    for (int64_t e = 0; e < m->ne; ++e) {
+        int32_t len = (m->nbr_ptr[e + 1] - m->nbr_ptr[e]) * m->dpf;
+        for (int u = 0; u < m->dpf; ++u) {
+            int64_t j = m->lam_off[e] + u;
+            m->csr_rowptr[j + 1] = m->csr_rowptr[j] + len;
+            for (int b = m->nbr_ptr[e]; b < m->nbr_ptr[e + 1]; ++b)
+                for (int v = 0; v < m->dpf; ++v) m->csr_cols.push_back((int32_t)(m->lam_off[m->nbrs[b].f] + v));
+        }
+    }
+    m->nnz = (int64_t)m->csr_cols.size();
+
+    // Gauss-Legendre tables, n = 1..kMaxGauss
+    m->gauss_x.assign(mhm::kMaxGauss * mhm::kMaxGauss, 0.0);
+    m->gauss_w.assign(mhm::kMaxGauss * mhm::kMaxGauss, 0.0);
+    for (int n = 1; n <= mhm::kMaxGauss; ++n)
+        gauss_legendre01(n, &m->gauss_x[(n - 1) * mhm::kMaxGauss], &m->gauss_w[(n - 1) * mhm::kMaxGauss]);
+
+    // face-load table: btab[jf][k] = int_0^1 psi_jf(tau) phi_k(tau) dtau, phi_k the 1-D
+    // Lagrange basis of degree P on N segments; pieces split at fine nodes and subfaces.
+    {
+        const int P = d.degree, N = m->N, PN = m->PN, M = d.m, L = d.l;
+        m->btab.assign((size_t)m->dpf * (PN + 1), 0.0);
+        m->btab_sum.assign(m->dpf, 0.0);
+        std::vector<double> cuts;
+        for (int k = 0; k <= N; ++k) cuts.push_back((double)k / N);
+        for (int q = 1; q < M; ++q) cuts.push_back((double)q / M);
+        std::sort(cuts.begin(), cuts.end());
+        const int ng = (P + L + 2) / 2 + 1;
+        const double* gx = &m->gauss_x[(ng - 1) * mhm::kMaxGauss];
+        const double* gw = &m->gauss_w[(ng - 1) * mhm::kMaxGauss];
+        for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+            double al = cuts[c], be = cuts[c + 1];
+            if (be - al < 1e-15) continue;
+            double mid = 0.5 * (al + be);
+            int seg = std::min(N - 1, (int)std::floor(mid * N));
+            int q = std::min(M - 1, (int)std::floor(mid * M));
+            for (int g = 0; g < ng; ++g) {
+                double tau = al + (be - al) * gx[g], w = (be - al) * gw[g];
+                double v[3];
+                lagrange1d(P, tau * N - seg, v);
+                double xi = 2.0 * (tau * M - q) - 1.0;
+                for (int p = 0; p <= L; ++p) {
+                    double psi = legendre_p(p, xi);
+                    int jf = q * (L + 1) + p;
+                    for (int b = 0; b <= P; ++b) m->btab[(size_t)jf * (PN + 1) + P * seg + b] += w * psi * v[b];
+                    m->btab_sum[jf] += w * psi;
+                }
+            }
+        }
+    }
+
+    // per-K geometry
+    std::vector<double> geom(m->nK * 6);
+    for (int64_t K = 0; K < m->nK; ++K)
+        for (int a = 0; a < 3; ++a) {
+            geom[6 * K + 2 * a] = m->vxy[2 * m->tri_v[3 * K + a]];
+            geom[6 * K + 2 * a + 1] = m->vxy[2 * m->tri_v[3 * K + a] + 1];
+        }
+
+    if (device < 0) {
+        *out = m;
+        return MHM_OK;
+    }
+    mhm_status st = MHM_OK;
+    if (!st) st = upload(geom, &m->d_geom);
+    if (!st) st = upload(m->tri_s, &m->d_sign);
+    if (!st) st = upload(m->tri_rev, &m->d_rev);
+    if (!st) st = upload(m->btab, &m->d_btab);
+    if (!st) st = upload(m->btab_sum, &m->d_btab_sum);
+    if (!st) st = upload(m->gauss_x, &m->d_gauss_x);
+    if (!st) st = upload(m->gauss_w, &m->d_gauss_w);
+    if (!st) st = upload(m->face_v, &m->d_face_v);
+    if (!st) st = upload(m->face_K, &m->d_face_K);
+    if (!st) st = upload(m->tri_f, &m->d_tri_f);
+    if (!st) st = upload(m->vxy, &m->d_vxy);
+    if (!st) st = upload(m->lam_off, &m->d_lam_off);
+    if (!st) st = upload(m->csr_rowptr, &m->d_csr_rowptr);
+    if (!st) st = upload(m->nbr_ptr, &m->d_nbr_ptr);
+    if (!st) st = upload(m->nbrs, &m->d_nbrs);
+    if (st) {
+        free_mesh_device(m);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return MHM_OK;
+}
+
+extern "C" void mhm_destroy_mesh(mhm_mesh* m) {
+    if (!m) return;
+    if (m->device < 0) {
+        delete m;
+        return;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m->device);
+    free_mesh_device(m);
+    cudaSetDevice(cur);
+    delete m;
+}
+
+template <typename T>
+static mhm_status copy_out(const std::vector<T>& v, void* out, size_t bytes) {
+    if (bytes < v.size() * sizeof(T)) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_mesh_query: buffer too small");
+    std::copy(v.begin(), v.end(), (T*)out);
+    return MHM_OK;
+}
+
+extern "C" mhm_status mhm_mesh_query(const mhm_mesh* m, int32_t what, void* out, size_t bytes) {
+    if (!m || !out) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_mesh_query: NULL argument");
+    switch (what) {
+        case MHM_Q_SIZES: {
+            std::vector<int64_t> s = {m->nK, m->ne, m->nv, m->nlam, m->nfine, m->nloc, m->NI, m->nnz};
+            return copy_out(s, out, bytes);
+        }
+        case MHM_Q_TRI_VERTS: return copy_out(m->tri_v, out, bytes);
+        case MHM_Q_TRI_FACES: return copy_out(m->tri_f, out, bytes);
+        case MHM_Q_TRI_SIGNS: return copy_out(m->tri_s, out, bytes);
+        case MHM_Q_FACE_VERTS: return copy_out(m->face_v, out, bytes);
+        case MHM_Q_LAMBDA_OFFSET: return copy_out(m->lam_off, out, bytes);
+        case MHM_Q_K_LAMBDA: return copy_out(m->k_lambda, out, bytes);
+        case MHM_Q_CSR_ROWPTR: return copy_out(m->csr_rowptr, out, bytes);
+        case MHM_Q_CSR_COLS: return copy_out(m->csr_cols, out, bytes);
+        case MHM_Q_VERTEX_XY: return copy_out(m->vxy, out, bytes);
+        case MHM_Q_FACE_NORMALS: return copy_out(m->normals, out, bytes);
+        default: return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_mesh_query: unknown query");
+    }
+}

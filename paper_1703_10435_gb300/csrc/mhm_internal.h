@@ -1,0 +1,111 @@
+// Internal declarations shared by the translation units of libmhm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mhm.h"
+
+namespace mhm {
+
+// Thread-local error text behind mhm_last_error().
+void set_error(const std::string& msg);
+mhm_status fail(mhm_status code, const std::string& msg);
+mhm_status cuda_fail(cudaError_t e, const char* what);
+
+#define MHM_CUDA_TRY(expr)                                              \
+    do {                                                                \
+        cudaError_t _e = (expr);                                        \
+        if (_e != cudaSuccess) return ::mhm::cuda_fail(_e, #expr);      \
+    } while (0)
+
+// Maximum number of Gauss points in the device tables.
+constexpr int kMaxGauss = 8;
+// Largest local degree and multiplier layout handled by the device kernels.
+constexpr int kMaxFaceDofs = 16;   // m (l + 1) per face
+constexpr int kMaxNI = 3 * kMaxFaceDofs;
+
+// One neighbour block (e, f) of face e's skeleton row: the K shared by e and f
+// (two K when f == e on an interior face) and the local faces of e and f in them.
+struct FaceNbr {
+    int32_t f;
+    int32_t col_off;   // offset of face f's columns inside the rows of face e
+    int32_t K0, a0, b0;
+    int32_t K1, a1, b1;  // K1 = -1 if only one contribution
+};
+
+// Per-K geometry and orientation record, device side (structure of arrays).
+struct DeviceMesh {
+    const double* geom;      // n_K * 6: v0, v1, v2
+    const int8_t* sign;      // n_K * 3
+    const int8_t* rev;       // n_K * 3: 1 if local face a runs from the higher-id vertex
+    const double* btab;      // face-load table: dofs_per_face * (PN+1): int psi_{q,p} phi_k over [0,1]
+    const double* btab_sum;  // dofs_per_face: int psi_{q,p} over [0,1]
+    const double* gauss_x;   // kMaxGauss * kMaxGauss: n-point Gauss-Legendre nodes on [0,1], row n-1
+    const double* gauss_w;
+};
+
+}  // namespace mhm
+
+struct mhm_mesh {
+    int device = 0;
+    mhm_mesh_desc desc{};
+    int64_t nK = 0, ne = 0, nv = 0, nlam = 0, nfine = 0, nloc = 0, NI = 0, nnz = 0;
+    int32_t N = 1, PN = 1, dpf = 1;  // 2^r, P*N, dofs per face m(l+1)
+
+    // host tables
+    std::vector<double> vxy;          // nv*2
+    std::vector<int32_t> tri_v;       // nK*3
+    std::vector<int32_t> tri_f;       // nK*3
+    std::vector<int8_t> tri_s;        // nK*3
+    std::vector<int8_t> tri_rev;      // nK*3
+    std::vector<int32_t> face_v;      // ne*2
+    std::vector<int32_t> face_K;      // ne*2 (second = -1 on the boundary)
+    std::vector<double> normals;      // ne*2
+    std::vector<int64_t> lam_off;     // ne+1
+    std::vector<int32_t> k_lambda;    // nK*NI
+    std::vector<int32_t> csr_rowptr;  // nlam+1
+    std::vector<int32_t> csr_cols;    // nnz
+    std::vector<int32_t> nbr_ptr;     // ne+1
+    std::vector<mhm::FaceNbr> nbrs;   // per face neighbour blocks
+    std::vector<double> btab, btab_sum, gauss_x, gauss_w;
+
+    // device copies (owned)
+    double* d_geom = nullptr;
+    int8_t* d_sign = nullptr;
+    int8_t* d_rev = nullptr;
+    double* d_btab = nullptr;
+    double* d_btab_sum = nullptr;
+    double* d_gauss_x = nullptr;
+    double* d_gauss_w = nullptr;
+    int32_t* d_face_v = nullptr;
+    int32_t* d_face_K = nullptr;
+    int32_t* d_tri_f = nullptr;
+    double* d_vxy = nullptr;
+    int64_t* d_lam_off = nullptr;
+    int32_t* d_csr_rowptr = nullptr;
+    int32_t* d_nbr_ptr = nullptr;
+    mhm::FaceNbr* d_nbrs = nullptr;
+
+    mhm::DeviceMesh dev() const {
+        return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w};
+    }
+};
+
+namespace mhm {
+// Launchers (defined in the .cu files).
+mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+                             int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
+                             int32_t* status, int32_t* iters, cudaStream_t stream);
+mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+                              const mhm_solve_opts& opts, int64_t K0, int64_t K1, double* AK,
+                              double* EK, double* BK, double* FK, int32_t* status, int32_t* iters,
+                              void* workspace, size_t ws_bytes, cudaStream_t stream);
+size_t mixed_workspace_bytes(const mhm_mesh* mesh);
+mhm_status launch_skeleton(const mhm_mesh* mesh, const double* AK, const double* EK,
+                           const mhm_dirichlet* g, double* A_vals, double* E, cudaStream_t stream);
+bool device_supported(int device);
+}  // namespace mhm

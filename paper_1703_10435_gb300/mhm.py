@@ -1,0 +1,167 @@
+"""Python binding of the C ABI in include/mhm.h (argument marshalling only).
+
+Functions keep the C names.  Device arrays are torch tensors on the mesh's
+device; their data pointers and the current CUDA stream are passed straight
+to the library, which runs every step of the pipeline in its own kernels.
+The library must be built (``paper_1703_10435_gb300.build.build()``); there
+is no fallback when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhm.so")
+
+MHM_OK = 0
+MHM_ERR_INVALID_ARG = 1
+MHM_ERR_OOM = 2
+MHM_ERR_CUDA = 3
+MHM_ERR_NOT_CONVERGED = 4
+MHM_ERR_TIMEOUT = 5
+MHM_ERR_UNSUPPORTED = 6
+
+MHM_FP64 = 0
+MHM_MIXED = 1
+MHM_SRC_CONST = 0
+MHM_SRC_SINSIN = 1
+
+Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q_K_LAMBDA, \
+    Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS = range(11)
+
+EXPORTED = [
+    "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
+    "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
+]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("m", ctypes.c_int32), ("l", ctypes.c_int32)]
+
+
+class Source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("freq", ctypes.c_double)]
+
+
+class Dirichlet(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double * 6)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("it_max", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("K_begin", ctypes.c_int64), ("K_end", ctypes.c_int64)]
+
+
+class MHMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mhm error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmhm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MHMError(MHM_ERR_UNSUPPORTED, "libmhm.so is not built; run paper_1703_10435_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        L.mhm_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), i32, ctypes.POINTER(vp)]
+        L.mhm_destroy_mesh.argtypes = [vp]
+        L.mhm_destroy_mesh.restype = None
+        L.mhm_mesh_query.argtypes = [vp, i32, vp, sz]
+        L.mhm_local_workspace_size.argtypes = [vp, i32, ctypes.POINTER(sz)]
+        L.mhm_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source), i32, ctypes.POINTER(SolveOpts),
+                                            vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.mhm_assemble_skeleton.argtypes = [vp, vp, vp, ctypes.POINTER(Dirichlet), vp, vp, vp]
+        L.mhm_last_error.restype = ctypes.c_char_p
+        L.mhm_measure_pipes.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
+                     "mhm_assemble_skeleton", "mhm_measure_pipes"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != MHM_OK:
+        raise MHMError(code, lib().mhm_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    """Owning handle of an mhm_mesh (splitProblem)."""
+
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0):
+        self.desc = MeshDesc(nx, ny, r, degree, m, l)
+        h = ctypes.c_void_p()
+        _check(lib().mhm_create_mesh(ctypes.byref(self.desc), device, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+        s = self.query(Q_SIZES, np.int64, 8)
+        (self.n_K, self.n_faces, self.n_vertices, self.n_lambda, self.n_fine, self.n_local,
+         self.n_I, self.nnz) = [int(v) for v in s]
+
+    def query(self, what, dtype, count):
+        out = np.empty(count, dtype=dtype)
+        _check(lib().mhm_mesh_query(self.handle, what, out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+        return out
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            _lib.mhm_destroy_mesh(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0) -> Mesh:
+    return Mesh(nx, ny, r, degree, m, l, device)
+
+
+def mhm_local_workspace_size(mesh: Mesh, precision: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().mhm_local_workspace_size(mesh.handle, precision, ctypes.byref(n)))
+    return int(n.value)
+
+
+def mhm_local_solve_batch(mesh: Mesh, kappa, source: Source, precision, opts: SolveOpts | None,
+                          AK, EK, BK, FK, status, iters=None, workspace=None, stream=None):
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().mhm_local_solve_batch(mesh.handle, _ptr(kappa), ctypes.byref(source), precision,
+                                       None if opts is None else ctypes.byref(opts),
+                                       _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters),
+                                       _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def mhm_assemble_skeleton(mesh: Mesh, AK, EK, dirichlet: Dirichlet | None, A_vals, E, stream=None):
+    _check(lib().mhm_assemble_skeleton(mesh.handle, _ptr(AK), _ptr(EK),
+                                       None if dirichlet is None else ctypes.byref(dirichlet),
+                                       _ptr(A_vals), _ptr(E), _stream(stream)))
+
+
+def mhm_measure_pipes(device: int = 0):
+    out = (ctypes.c_double * 2)()
+    _check(lib().mhm_measure_pipes(device, out))
+    return {"fp64_gflops": out[0], "fp32_gflops": out[1]}

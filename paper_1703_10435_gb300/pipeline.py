@@ -1,0 +1,78 @@
+"""Device buffers around the C calls: one object per mesh that owns the
+torch tensors the library writes into (per-K blocks, skeleton CSR values,
+right-hand side, status) and runs mhm_local_solve_batch followed by
+mhm_assemble_skeleton on a stream."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import mhm
+from .workloads import Workload
+
+
+def source_of(w: Workload) -> mhm.Source:
+    if w.source == "const":
+        return mhm.Source(mhm.MHM_SRC_CONST, w.source_value, 1.0)
+    return mhm.Source(mhm.MHM_SRC_SINSIN, w.source_value, w.source_freq)
+
+
+def dirichlet_of(w: Workload):
+    if w.dirichlet is None:
+        return None
+    c = list(w.dirichlet) + [0.0] * (6 - len(w.dirichlet))
+    return mhm.Dirichlet((mhm.ctypes.c_double * 6)(*c))
+
+
+class Pipeline:
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64):
+        self.mesh = mhm.Mesh(nx, ny, r, degree, m, l, device)
+        self.device = torch.device("cuda", device)
+        self.precision = precision
+        M = self.mesh
+        f64 = dict(dtype=torch.float64, device=self.device)
+        i32 = dict(dtype=torch.int32, device=self.device)
+        self.AK = torch.zeros(M.n_K * M.n_I * M.n_I, **f64)
+        self.EK = torch.zeros(M.n_K * M.n_I, **f64)
+        self.BK = torch.zeros(M.n_K * M.n_I, **f64)
+        self.FK = torch.zeros(M.n_K, **f64)
+        self.status = torch.zeros(M.n_K, **i32)
+        self.iters = torch.zeros(M.n_K, **i32)
+        self.A_vals = torch.zeros(M.nnz, **f64)
+        self.E = torch.zeros(M.n_lambda, **f64)
+        self.workspace = None
+        self.set_precision(precision)
+
+    @classmethod
+    def for_workload(cls, w: Workload, device: int = 0, precision: int = mhm.MHM_FP64):
+        return cls(w.nx, w.ny, w.r, w.degree, w.m, w.l, device, precision)
+
+    def set_precision(self, precision: int):
+        self.precision = precision
+        ws = mhm.mhm_local_workspace_size(self.mesh, precision)
+        if ws > 0 and (self.workspace is None or self.workspace.numel() < ws):
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+
+    def local(self, kappa, source: mhm.Source, opts: mhm.SolveOpts | None = None, stream=None):
+        mhm.mhm_local_solve_batch(self.mesh, kappa, source, self.precision, opts, self.AK, self.EK, self.BK,
+                                  self.FK, self.status, self.iters, self.workspace, stream)
+
+    def skeleton(self, dirichlet=None, stream=None):
+        mhm.mhm_assemble_skeleton(self.mesh, self.AK, self.EK, dirichlet, self.A_vals, self.E, stream)
+
+    def step(self, kappa, source, dirichlet=None, opts=None, stream=None):
+        self.local(kappa, source, opts, stream)
+        self.skeleton(dirichlet, stream)
+
+    # host-side views for tests and reports
+    def blocks(self):
+        M = self.mesh
+        return (self.AK.view(M.n_K, M.n_I, M.n_I).cpu().numpy(), self.EK.view(M.n_K, M.n_I).cpu().numpy(),
+                self.BK.view(M.n_K, M.n_I).cpu().numpy(), self.FK.cpu().numpy())
+
+    def skeleton_scipy(self):
+        import scipy.sparse
+        M = self.mesh
+        rowptr = M.query(mhm.Q_CSR_ROWPTR, np.int32, M.n_lambda + 1)
+        cols = M.query(mhm.Q_CSR_COLS, np.int32, M.nnz)
+        return scipy.sparse.csr_matrix((self.A_vals.cpu().numpy(), cols, rowptr), shape=(M.n_lambda, M.n_lambda))

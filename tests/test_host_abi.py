@@ -1,0 +1,84 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and its host mesh builder reproduces the oracle's
+connectivity, signs and multiplier numbering bit for bit (host-only meshes,
+no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.mesh import build_mesh
+from paper_1703_10435_gb300 import build, mhm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return mhm.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "mhm.h")).read()
+    declared = set(re.findall(r"\b(mhm_[a-z_0-9]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(mhm.EXPORTED) <= declared
+
+
+def _host_mesh(nx, ny, r=2, P=1, m=2, l=1):
+    return mhm.Mesh(nx, ny, r, P, m, l, device=-1)
+
+
+@pytest.mark.parametrize("nx,ny,m,l", [(1, 1, 1, 0), (4, 4, 1, 1), (3, 5, 2, 2), (8, 2, 3, 1)])
+def test_connectivity_bit_exact(lib, nx, ny, m, l):
+    M = _host_mesh(nx, ny, 2, 1, m, l)
+    o = build_mesh(nx, ny, m, l)
+    assert (M.n_K, M.n_faces, M.n_vertices, M.n_lambda) == (o.n_K, o.n_e, len(o.verts), o.n_lambda)
+    assert np.array_equal(M.query(mhm.Q_TRI_VERTS, np.int32, 3 * M.n_K).reshape(-1, 3), o.tris)
+    assert np.array_equal(M.query(mhm.Q_TRI_FACES, np.int32, 3 * M.n_K).reshape(-1, 3), o.tri_edges)
+    assert np.array_equal(M.query(mhm.Q_TRI_SIGNS, np.int8, 3 * M.n_K).reshape(-1, 3), o.signs)
+    assert np.array_equal(M.query(mhm.Q_FACE_VERTS, np.int32, 2 * M.n_faces).reshape(-1, 2), o.edges)
+    assert np.array_equal(M.query(mhm.Q_LAMBDA_OFFSET, np.int64, M.n_faces + 1), o.lam_offset)
+    kl = M.query(mhm.Q_K_LAMBDA, np.int32, M.n_K * M.n_I).reshape(M.n_K, M.n_I)
+    for K in range(M.n_K):
+        assert np.array_equal(kl[K], o.local_lambda(K))
+    assert np.array_equal(M.query(mhm.Q_VERTEX_XY, np.float64, 2 * M.n_vertices).reshape(-1, 2), o.verts)
+    assert np.array_equal(M.query(mhm.Q_FACE_NORMALS, np.float64, 2 * M.n_faces).reshape(-1, 2), o.normals)
+
+
+def test_skeleton_pattern_matches_oracle(lib):
+    import scipy.sparse
+    M = _host_mesh(3, 2, 2, 1, 2, 1)
+    o = build_mesh(3, 2, 2, 1)
+    rowptr = M.query(mhm.Q_CSR_ROWPTR, np.int32, M.n_lambda + 1)
+    cols = M.query(mhm.Q_CSR_COLS, np.int32, M.nnz)
+    assert np.all(np.diff(rowptr) > 0)
+    for j in range(M.n_lambda):
+        c = cols[rowptr[j]:rowptr[j + 1]]
+        assert np.all(np.diff(c) > 0)          # strictly ascending columns
+    # the oracle's pattern: (j, i) couple iff some K holds both
+    want = set()
+    for K in range(o.n_K):
+        ids = o.local_lambda(K)
+        want.update((int(a), int(b)) for a in ids for b in ids)
+    got = {(j, int(c)) for j in range(M.n_lambda) for c in cols[rowptr[j]:rowptr[j + 1]]}
+    assert got == want
+
+
+def test_errors_are_reported(lib):
+    with pytest.raises(mhm.MHMError) as e:
+        mhm.Mesh(0, 1, 2, 1, 1, 1, device=-1)
+    assert e.value.code == mhm.MHM_ERR_INVALID_ARG and "nx" in str(e.value)
+    with pytest.raises(mhm.MHMError) as e:
+        mhm.Mesh(1, 1, 2, 3, 1, 1, device=-1)
+    assert e.value.code == mhm.MHM_ERR_INVALID_ARG
+    M = _host_mesh(2, 2)
+    # compute calls on a host-only mesh fail loudly instead of falling back
+    code = lib.mhm_local_solve_batch(M.handle, None, None, 0, None, None, None, None, None, None, None,
+                                     None, 0, None)
+    assert code == mhm.MHM_ERR_UNSUPPORTED
