@@ -73,7 +73,7 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown source kind");
     mhm_solve_opts o{};
     o.it_max = 8;
-    o.tol = 1e-14;
+    o.tol = 1e-12;
     o.K_begin = 0;
     o.K_end = 0;
     if (opts) o = *opts;

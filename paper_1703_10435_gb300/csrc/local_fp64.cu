@@ -55,7 +55,23 @@ struct KCtx {
     double cproj[kMaxNI + 1];  // projection coefficient of each right-hand side
     double FK;
     int bad;             // first failing pivot (+1), 0 if none
+    double inv_piv;      // 1/sqrt of the current pivot
 };
+
+// 1/sqrt(d) in FP64 by two Newton-Raphson steps y <- y (3 - d y^2) / 2 from the
+// FP32 estimate (each step doubles the correct bits: ~24 -> 48 -> full).  Far
+// fewer FP64 operations than a correctly rounded sqrt followed by a division,
+// which matters where FP64 is 1/64 of the FP32 rate.  Outside the FP32 range,
+// or for d <= 0, the plain expression is used.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    double t = d * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    t = d * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    return y;
+}
 
 // Sum over the block of one value per thread.
 __device__ double block_sum(double v, double* red) {
@@ -266,61 +282,67 @@ __global__ void __launch_bounds__(kThreads) k_local_fp64(const Fp64Args g) {
             __syncthreads();
             add_fine_row(g, c, lg, lev, b, kap, W);  // ends with a barrier
         }
-        // pivot 0 of the level: scale column 0 and the right-hand sides of row 0
-        {
+        // Right-looking Cholesky of the level's b pivots on the augmented window rows.
+        // The inverse square root of each pivot is computed once, by the thread that
+        // finishes the pivot's diagonal entry, and read by everyone after a barrier.
+        if (threadIdx.x == 0) {
             const double d = W[0];
-            const double inv = 1.0 / sqrt(d);
-            if (threadIdx.x == 0 && !(d > 0.0) && c.bad == 0) c.bad = 1;
-            __syncthreads();
-            for (int t = threadIdx.x; t < nr - 1 + R; t += blockDim.x) {
-                if (t < nr - 1) W[(t + 1) * g.ld] *= inv;
-                else W[g.rhs0 + (t - (nr - 1))] *= inv;
+            if (!(d > 0.0) && c.bad == 0) c.bad = 1;
+            c.inv_piv = rsqrt_nr(d);
+        }
+        __syncthreads();
+        for (int k = 0; k < b; ++k) {
+            const int m = nr - k - 1;
+            // scale column k below the pivot and row k's right-hand sides: L(:,k), Y(k,:)
+            {
+                const double inv = c.inv_piv;
+                for (int t = threadIdx.x; t < m + R; t += blockDim.x) {
+                    if (t < m) W[(k + 1 + t) * g.ld + k] *= inv;
+                    else W[k * g.ld + g.rhs0 + (t - m)] *= inv;
+                }
             }
             __syncthreads();
-        }
-        for (int k = 0; k < b; ++k) {
-            // trailing update by pivot k; rows/cols k+1.. in folded pairs, and, with
-            // look-ahead, the scaling of column k+1 and of row k+1's right-hand sides.
-            const int m = nr - k - 1;
             if (m <= 0) break;
-            const double lkk1 = W[(k + 1) * g.ld + k];
-            const double dn = W[(k + 1) * g.ld + (k + 1)] - lkk1 * lkk1;  // new pivot k+1
-            const bool look = (k + 1 < b);
-            const double invn = look ? 1.0 / sqrt(dn) : 1.0;
-            if (look && threadIdx.x == 0 && !(dn > 0.0) && c.bad == 0) c.bad = k + 2;
+            // trailing update of rows/cols k+1..nr-1, lower triangle in folded row pairs
+            // (row k+1+(m-1-p) with row k+1+p), then both rows' right-hand sides
             const int H = (m + 1) / 2, Wd = m + 1 + 2 * R;
             const int total = H * Wd;
+            const bool next_pivot = k + 1 < b;
+            int p = threadIdx.x / Wd, cc = threadIdx.x - (threadIdx.x / Wd) * Wd;
             for (int e = threadIdx.x; e < total; e += blockDim.x) {
-                const int p = e / Wd, cc = e - p * Wd;
                 const int ia = k + 1 + (m - 1 - p), ib = k + 1 + p;
-                int i, jcol;
-                bool rhs;
-                if (cc < m - p) { i = ia; jcol = k + 1 + cc; rhs = false; }
-                else if (cc < m + 1) { if (ia == ib) continue; i = ib; jcol = k + 1 + (cc - (m - p)); rhs = false; }
+                int i = -1, jcol = 0;
+                bool rhs = false;
+                if (cc < m - p) { i = ia; jcol = k + 1 + cc; }
+                else if (cc < m + 1) { if (ia != ib) { i = ib; jcol = k + 1 + (cc - (m - p)); } }
                 else if (cc < m + 1 + R) { i = ia; jcol = cc - (m + 1); rhs = true; }
-                else { if (ia == ib) continue; i = ib; jcol = cc - (m + 1 + R); rhs = true; }
-                const double lik = W[i * g.ld + k];
-                if (!rhs) {
-                    // the new pivot k+1 is recomputed by every thread above; its slot is not rewritten
-                    if (look && i == k + 1 && jcol == k + 1) continue;
-                    double v = W[i * g.ld + jcol] - lik * W[jcol * g.ld + k];
-                    if (look && jcol == k + 1 && i > k + 1) v *= invn;
-                    W[i * g.ld + jcol] = v;
-                } else {
-                    double v = W[i * g.ld + g.rhs0 + jcol] - lik * W[k * g.ld + g.rhs0 + jcol];
-                    if (look && i == k + 1) v *= invn;
-                    W[i * g.ld + g.rhs0 + jcol] = v;
+                else if (ia != ib) { i = ib; jcol = cc - (m + 1 + R); rhs = true; }
+                if (i >= 0) {
+                    const double lik = W[i * g.ld + k];
+                    if (!rhs) {
+                        const double v = W[i * g.ld + jcol] - lik * W[jcol * g.ld + k];
+                        W[i * g.ld + jcol] = v;
+                        if (next_pivot && i == k + 1 && jcol == k + 1) {
+                            if (!(v > 0.0) && c.bad == 0) c.bad = k + 2;
+                            c.inv_piv = rsqrt_nr(v);
+                        }
+                    } else {
+                        W[i * g.ld + g.rhs0 + jcol] -= lik * W[k * g.ld + g.rhs0 + jcol];
+                    }
                 }
+                cc += blockDim.x;
+                while (cc >= Wd) { cc -= Wd; ++p; }
             }
             __syncthreads();
         }
         // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
-        for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
-            const int c1 = t / R, c2 = t - c1 * R;
-            if (c1 > c2) continue;
+        for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
+            int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
+            while (c2 >= R - c1) { c2 -= R - c1; ++c1; }
+            c2 += c1;
             double s = 0.0;
             for (int k = 0; k < b; ++k) s += W[k * g.ld + g.rhs0 + c1] * W[k * g.ld + g.rhs0 + c2];
-            gram[t] += s;
+            gram[c1 * R + c2] += s;
         }
         __syncthreads();
         if (bn > 0) {
