@@ -128,3 +128,176 @@ __device__ __forceinline__ int face_position(int PN, int x, int y, int a) {
 }
 
 }  // namespace mhm
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, non-tensor) global -> shared with an mbarrier.
+// Addresses and sizes must be multiples of 16 bytes.
+namespace mhm {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of `bar` with an iteration limit; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Orders this thread's earlier generic-proxy global writes before later async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+}  // namespace mhm
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky of the b pivots of a level window.
+namespace mhm {
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T d);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float d) { return rsqrtf(d); }
+// FP64: two Newton-Raphson steps y <- y (3 - d y^2) / 2 from the FP32 estimate
+// (each step doubles the correct bits), a handful of FP64 operations instead of
+// a correctly rounded sqrt and division; plain expression outside FP32 range.
+template <> __device__ __forceinline__ double rsqrt_t<double>(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    double t = d * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    t = d * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    return y;
+}
+
+// Loads the NB panel entries row[p0 .. p0+NB) (16-byte aligned) into registers.
+template <int NB> __device__ __forceinline__ void load_panel(const float* row, float (&v)[NB]) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(row + q);
+        v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
+    }
+}
+template <int NB> __device__ __forceinline__ void load_panel(const double* row, double (&v)[NB]) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(row + q);
+        v[q] = t.x; v[q + 1] = t.y;
+    }
+}
+
+// M (row-major, leading dimension ld, lower triangle used) holds the window rows
+// [0, nr): the b pivots of the current level first, then the next level.  Rhs
+// (row-major, ldr) holds ncols right-hand-side columns for rows [0, rhs_rows).
+// On return: rows [0, b) x cols [0, b) of M hold L (diagonal sqrt of the
+// pivots), rows [b, nr) x cols [0, b) hold L_{next,cur}, rows/cols [b, nr) the
+// Schur complement; Rhs rows [0, b) hold L^{-1} Rhs and rows [b, rhs_rows) are
+// reduced by -L_{next,cur} (L^{-1} Rhs).  Panels of NB pivots are factored by
+// warp 0 (warp-synchronous), then all threads apply the rank-NB update.
+// ld and ldr must keep every row 16-byte aligned; *bad gets the first
+// non-positive pivot (+1).  Ends with a block barrier.
+template <typename T, int NB>
+__device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int ldr, int rhs_rows, int ncols,
+                                       int* bad) {
+    for (int p0 = 0; p0 < b; p0 += NB) {
+        const int pe = min(p0 + NB, b);
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            for (int k = p0; k < pe; ++k) {
+                const T d = M[k * ld + k];
+                const T inv = rsqrt_t<T>(d);
+                if (lane == 0 && !(d > T(0)) && *bad == 0) *bad = k + 1;
+                for (int i = k + 1 + lane; i < nr; i += 32) M[i * ld + k] *= inv;
+                for (int c = lane; c < ncols; c += 32) Rhs[k * ldr + c] *= inv;
+                __syncwarp();
+                if (lane == 0) M[k * ld + k] = d * inv;
+                for (int j = k + 1; j < pe; ++j) {
+                    const T ljk = M[j * ld + k];
+                    for (int i = j + lane; i < nr; i += 32) M[i * ld + j] -= M[i * ld + k] * ljk;
+                }
+                for (int i = k + 1; i < pe; ++i) {
+                    const T lik = M[i * ld + k];
+                    for (int c = lane; c < ncols; c += 32) Rhs[i * ldr + c] -= lik * Rhs[k * ldr + c];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        const int nbk = pe - p0;
+        // symmetric part: rows/cols [pe, nr), folded row pairs (pe+m-1-p, pe+p)
+        const int m = nr - pe;
+        if (m > 0) {
+            const int H = (m + 1) / 2, Wd = m + 1, total = H * Wd;
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                const int p = e / Wd, cc = e - p * Wd;
+                const bool second = cc >= m - p;
+                const int i = pe + (second ? p : m - 1 - p);
+                const int j = pe + (second ? cc - (m - p) : cc);
+                if (second && m - 1 - p == p) continue;
+                T acc = M[i * ld + j];
+                if (nbk == NB) {
+                    T li[NB], lj[NB];
+                    load_panel<NB>(M + i * ld + p0, li);
+                    load_panel<NB>(M + j * ld + p0, lj);
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) acc -= li[q] * lj[q];
+                } else {
+                    for (int q = 0; q < nbk; ++q) acc -= M[i * ld + p0 + q] * M[j * ld + p0 + q];
+                }
+                M[i * ld + j] = acc;
+            }
+        }
+        // right-hand sides: rows [pe, rhs_rows)
+        const int rr = rhs_rows - pe;
+        if (rr > 0) {
+            for (int e = threadIdx.x; e < rr * ncols; e += blockDim.x) {
+                const int i = pe + e / ncols, c = e - (e / ncols) * ncols;
+                T acc = Rhs[i * ldr + c];
+                if (nbk == NB) {
+                    T li[NB];
+                    load_panel<NB>(M + i * ld + p0, li);
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) acc -= li[q] * Rhs[(p0 + q) * ldr + c];
+                } else {
+                    for (int q = 0; q < nbk; ++q) acc -= M[i * ld + p0 + q] * Rhs[(p0 + q) * ldr + c];
+                }
+                Rhs[i * ldr + c] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace mhm

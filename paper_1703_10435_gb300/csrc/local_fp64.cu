@@ -55,23 +55,7 @@ struct KCtx {
     double cproj[kMaxNI + 1];  // projection coefficient of each right-hand side
     double FK;
     int bad;             // first failing pivot (+1), 0 if none
-    double inv_piv;      // 1/sqrt of the current pivot
 };
-
-// 1/sqrt(d) in FP64 by two Newton-Raphson steps y <- y (3 - d y^2) / 2 from the
-// FP32 estimate (each step doubles the correct bits: ~24 -> 48 -> full).  Far
-// fewer FP64 operations than a correctly rounded sqrt followed by a division,
-// which matters where FP64 is 1/64 of the FP32 rate.  Outside the FP32 range,
-// or for d <= 0, the plain expression is used.
-__device__ __forceinline__ double rsqrt_nr(double d) {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
-    double t = d * y;
-    y = y * fma(-0.5 * t, y, 1.5);
-    t = d * y;
-    y = y * fma(-0.5 * t, y, 1.5);
-    return y;
-}
 
 // Sum over the block of one value per thread.
 __device__ double block_sum(double v, double* red) {
@@ -282,59 +266,9 @@ __global__ void __launch_bounds__(kThreads) k_local_fp64(const Fp64Args g) {
             __syncthreads();
             add_fine_row(g, c, lg, lev, b, kap, W);  // ends with a barrier
         }
-        // Right-looking Cholesky of the level's b pivots on the augmented window rows.
-        // The inverse square root of each pivot is computed once, by the thread that
-        // finishes the pivot's diagonal entry, and read by everyone after a barrier.
-        if (threadIdx.x == 0) {
-            const double d = W[0];
-            if (!(d > 0.0) && c.bad == 0) c.bad = 1;
-            c.inv_piv = rsqrt_nr(d);
-        }
-        __syncthreads();
-        for (int k = 0; k < b; ++k) {
-            const int m = nr - k - 1;
-            // scale column k below the pivot and row k's right-hand sides: L(:,k), Y(k,:)
-            {
-                const double inv = c.inv_piv;
-                for (int t = threadIdx.x; t < m + R; t += blockDim.x) {
-                    if (t < m) W[(k + 1 + t) * g.ld + k] *= inv;
-                    else W[k * g.ld + g.rhs0 + (t - m)] *= inv;
-                }
-            }
-            __syncthreads();
-            if (m <= 0) break;
-            // trailing update of rows/cols k+1..nr-1, lower triangle in folded row pairs
-            // (row k+1+(m-1-p) with row k+1+p), then both rows' right-hand sides
-            const int H = (m + 1) / 2, Wd = m + 1 + 2 * R;
-            const int total = H * Wd;
-            const bool next_pivot = k + 1 < b;
-            int p = threadIdx.x / Wd, cc = threadIdx.x - (threadIdx.x / Wd) * Wd;
-            for (int e = threadIdx.x; e < total; e += blockDim.x) {
-                const int ia = k + 1 + (m - 1 - p), ib = k + 1 + p;
-                int i = -1, jcol = 0;
-                bool rhs = false;
-                if (cc < m - p) { i = ia; jcol = k + 1 + cc; }
-                else if (cc < m + 1) { if (ia != ib) { i = ib; jcol = k + 1 + (cc - (m - p)); } }
-                else if (cc < m + 1 + R) { i = ia; jcol = cc - (m + 1); rhs = true; }
-                else if (ia != ib) { i = ib; jcol = cc - (m + 1 + R); rhs = true; }
-                if (i >= 0) {
-                    const double lik = W[i * g.ld + k];
-                    if (!rhs) {
-                        const double v = W[i * g.ld + jcol] - lik * W[jcol * g.ld + k];
-                        W[i * g.ld + jcol] = v;
-                        if (next_pivot && i == k + 1 && jcol == k + 1) {
-                            if (!(v > 0.0) && c.bad == 0) c.bad = k + 2;
-                            c.inv_piv = rsqrt_nr(v);
-                        }
-                    } else {
-                        W[i * g.ld + g.rhs0 + jcol] -= lik * W[k * g.ld + g.rhs0 + jcol];
-                    }
-                }
-                cc += blockDim.x;
-                while (cc >= Wd) { cc -= Wd; ++p; }
-            }
-            __syncthreads();
-        }
+        // Blocked right-looking Cholesky of the level's b pivots on the augmented window
+        // rows; the right-hand-side columns (all window rows) are forward-substituted.
+        blocked_cholesky_level<double, 8>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
         // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
         for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
             int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
@@ -412,7 +346,7 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mh
     g.rows = rows;
     g.rhs0 = rows;
     g.ld = rows + g.R;
-    if (g.ld % 2 == 0) g.ld += 1;  // odd stride in doubles spreads rows over banks
+    if (g.ld % 2 == 1) g.ld += 1;  // rows 16-byte aligned for the vector panel loads
     g.src_kind = f.kind;
     g.src_value = f.value;
     g.src_freq = f.freq;

@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kThreadsM = 256;
 constexpr int kWarpsM = kThreadsM / 32;
-constexpr int kMaxRowsPerLane = 4;   // levels up to 128 unknowns
 
 struct MixedArgs {
     DeviceMesh dm;
@@ -35,6 +34,9 @@ struct MixedArgs {
     int wrows, wld;               // FP32 window rows and leading dimension
     int wfloats;                  // floats reserved for the window (also holds R x R doubles)
     int yfloats;                  // floats reserved for the right-hand-side block (>= nunk R)
+    int bmax;                     // largest level size
+    int opmax;                    // floats of the largest level operator (multiple of 4)
+    int ldr;                      // leading dimension of the level right-hand sides (multiple of 4)
     int src_kind;
     double src_value, src_freq;
     int64_t K0, K1;
@@ -53,7 +55,6 @@ struct MCtx {
     double flen[3];
     int sgn[3], rev[3];
     double cproj[kMaxNI + 1];
-    float inv_piv;
     int bad;
     int col_done[kMaxNI + 1];
     double gamma[kMaxNI + 1];     // G_c^T M G_c per column
@@ -63,6 +64,9 @@ struct MCtx {
     int col_fail;
     double red[kWarpsM];
     double mz[kMaxNI + 1];
+    alignas(8) uint64_t bar[2];
+    uint32_t phase[2];
+    int timeout;
 };
 
 __device__ __forceinline__ int lev_size(const LevelGeom& lg, int lev) { return lg.size(lev); }
@@ -231,112 +235,104 @@ __device__ void column_dot(const MixedArgs& g, const double* Res, const float* y
     }
 }
 
-// Forward + backward solve L L^T D = Y in FP32 for all columns, in place in y
-// (column-major, nunk per column).  Warp w handles columns w, w + 8, ...; lanes
-// hold the rows of the current level; the level blocks are read from the factor.
-__device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const float* F, const int* loff,
-                             const int* u0, float* y, const MCtx& c) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int col = warp; col < g.R; col += kWarpsM) {
-        if (c.col_done[col]) continue;
-        float* yc = y + (size_t)col * g.nunk;
-        float prev[kMaxRowsPerLane];
-        int bprev = 0;
-        // forward: y_lev = L_lev^{-1} (y_lev - L_{lev,lev-1} y_{lev-1})
-        for (int lev = 0; lev < g.nlev; ++lev) {
-            const int b = lg.size(lev);
-            const float* Ld = F + loff[lev];
-            float t[kMaxRowsPerLane];
+// Forward + backward solve of L L^T D = Y in FP32 for every column still
+// refining, in place in y (column-major, nunk per column).  Level by level,
+//   forward   y_lev = Fw_lev [y_lev; y_{lev-1}],  Fw_lev = [L_lev^{-1} | -L_lev^{-1} L_{lev,lev-1}]
+//   backward  x_lev = Bw_lev [y_lev; x_{lev+1}],  Bw_lev = [L_lev^{-T} | -L_lev^{-T} L_{lev+1,lev}^T]
+// so each step is one small dense product over all columns.  The operators are
+// stored column-major ((b + b') x b) and streamed into two shared-memory buffers
+// by bulk asynchronous copies: the copy for step s+1 runs while step s computes.
+constexpr int kColGroup = 4;     // columns per work item
+constexpr int kItemsPerThread = 2;
+
+__device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const float* F, const int* opoff,
+                             const int* u0, float* y, float* opbuf, MCtx& c) {
+    const int R = g.R;
+    const int nsteps = 2 * g.nlev;
+    const int ngroups = (R + kColGroup - 1) / kColGroup;
+    uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
+    auto step_lev = [&](int st, int* dir) { *dir = st >= g.nlev; return *dir ? nsteps - 1 - st : st; };
+    auto issue = [&](int st) {
+        int dir;
+        const int lev = step_lev(st, &dir);
+        const int b = lg.size(lev);
+        const int lo = dir == 0 ? lev - 1 : lev + 1;
+        const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
+        const uint32_t bytes = (uint32_t)(((b * (b + bo) + 3) & ~3) * sizeof(float));
+        float* dst = opbuf + (size_t)(st & 1) * g.opmax;
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
+        bulk_copy_g2s(dst, F + opoff[2 * lev + dir], bytes, &c.bar[st & 1]);
+    };
+    if (threadIdx.x == 0) issue(0);
+    for (int st = 0; st < nsteps; ++st) {
+        int dir;
+        const int lev = step_lev(st, &dir);
+        const int b = lg.size(lev);
+        const int lo = dir == 0 ? lev - 1 : lev + 1;
+        const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
+        if (threadIdx.x == 0 && st + 1 < nsteps) issue(st + 1);
+        const uint32_t par = (st & 1) ? ph1 : ph0;
+        if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
+        if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        const float* op = opbuf + (size_t)(st & 1) * g.opmax;
+        const int work = b * ngroups;
+        const int ulev = u0[lev], ulo = bo > 0 ? u0[lo] : 0;
+        float acc[kItemsPerThread][kColGroup];
 #pragma unroll
-            for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                const int i = lane + 32 * s;
-                t[s] = i < b ? yc[u0[lev] + i] : 0.0f;
-            }
-            if (lev > 0) {
-                const float* C = F + loff[lev - 1] + bprev * (bprev + 1) / 2;  // L_{lev,lev-1}: b x bprev
-                for (int k = 0; k < bprev; ++k) {
-                    const float yk = __shfl_sync(0xffffffffu, prev[k >> 5], k & 31);
+        for (int it = 0; it < kItemsPerThread; ++it) {
+            const int item = threadIdx.x + it * kThreadsM;
 #pragma unroll
-                    for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                        const int i = lane + 32 * s;
-                        if (i < b) t[s] = fmaf(-C[i * bprev + k], yk, t[s]);
-                    }
+            for (int q = 0; q < kColGroup; ++q) acc[it][q] = 0.0f;
+            if (item < work) {
+                const int cg = item / b, i = item - cg * b;
+                const float* ycol[kColGroup];
+#pragma unroll
+                for (int q = 0; q < kColGroup; ++q) {
+                    const int col = min(cg * kColGroup + q, R - 1);
+                    ycol[q] = y + (size_t)col * g.nunk;
+                }
+                for (int k = 0; k < b; ++k) {
+                    const float a = op[k * b + i];
+#pragma unroll
+                    for (int q = 0; q < kColGroup; ++q) acc[it][q] = fmaf(a, ycol[q][ulev + k], acc[it][q]);
+                }
+                for (int k = 0; k < bo; ++k) {
+                    const float a = op[(b + k) * b + i];
+#pragma unroll
+                    for (int q = 0; q < kColGroup; ++q) acc[it][q] = fmaf(a, ycol[q][ulo + k], acc[it][q]);
                 }
             }
-            for (int k = 0; k < b; ++k) {
-                const int so = k >> 5, lo = k & 31;
-                float yk = 0.0f;
-#pragma unroll
-                for (int s = 0; s < kMaxRowsPerLane; ++s)
-                    if (s == so && lane == lo) { t[s] = t[s] / Ld[k * (k + 1) / 2 + k]; yk = t[s]; }
-                yk = __shfl_sync(0xffffffffu, yk, lo);
-#pragma unroll
-                for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                    const int i = lane + 32 * s;
-                    if (i > k && i < b) t[s] = fmaf(-Ld[i * (i + 1) / 2 + k], yk, t[s]);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                const int i = lane + 32 * s;
-                if (i < b) yc[u0[lev] + i] = t[s];
-                prev[s] = t[s];
-            }
-            bprev = b;
         }
-        // backward: x_lev = L_lev^{-T} (y_lev - L_{lev+1,lev}^T x_{lev+1})
-        int bnext = 0;
-        float nxt[kMaxRowsPerLane];
-        for (int lev = g.nlev - 1; lev >= 0; --lev) {
-            const int b = lg.size(lev);
-            const float* Ld = F + loff[lev];
-            float t[kMaxRowsPerLane];
+        __syncthreads();
 #pragma unroll
-            for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                const int i = lane + 32 * s;
-                t[s] = i < b ? yc[u0[lev] + i] : 0.0f;
-            }
-            if (bnext > 0) {
-                const float* C = Ld + b * (b + 1) / 2;   // L_{lev+1,lev}: bnext x b
-                for (int i = 0; i < bnext; ++i) {
-                    const float xi = __shfl_sync(0xffffffffu, nxt[i >> 5], i & 31);
+        for (int it = 0; it < kItemsPerThread; ++it) {
+            const int item = threadIdx.x + it * kThreadsM;
+            if (item < work) {
+                const int cg = item / b, i = item - cg * b;
 #pragma unroll
-                    for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                        const int k = lane + 32 * s;
-                        if (k < b) t[s] = fmaf(-C[i * b + k], xi, t[s]);
-                    }
+                for (int q = 0; q < kColGroup; ++q) {
+                    const int col = cg * kColGroup + q;
+                    if (col < R && !c.col_done[col]) y[(size_t)col * g.nunk + ulev + i] = acc[it][q];
                 }
             }
-            for (int k = b - 1; k >= 0; --k) {
-                const int so = k >> 5, lo = k & 31;
-                float xk = 0.0f;
-#pragma unroll
-                for (int s = 0; s < kMaxRowsPerLane; ++s)
-                    if (s == so && lane == lo) { t[s] = t[s] / Ld[k * (k + 1) / 2 + k]; xk = t[s]; }
-                xk = __shfl_sync(0xffffffffu, xk, lo);
-#pragma unroll
-                for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                    const int i = lane + 32 * s;
-                    if (i < k) t[s] = fmaf(-Ld[k * (k + 1) / 2 + i], xk, t[s]);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < kMaxRowsPerLane; ++s) {
-                const int i = lane + 32 * s;
-                if (i < b) yc[u0[lev] + i] = t[s];
-                nxt[s] = t[s];
-            }
-            bnext = b;
         }
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        c.phase[0] = ph0;
+        c.phase[1] = ph1;
+    }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
+__global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g) {
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
     float* y = W + (size_t)g.wfloats;                                    // nunk x R
-    int* loff = reinterpret_cast<int*>(y + (size_t)g.yfloats);         // nlev + 1 factor offsets
-    int* u0 = loff + (g.nlev + 1);                                      // nlev + 1 level starts
+    int* loff = reinterpret_cast<int*>(y + (size_t)g.yfloats);         // 2 nlev operator offsets (Fw, Bw)
+    int* u0 = loff + 2 * g.nlev;                                        // nlev + 1 level starts
+    float* opbuf = W;                                                   // 2 x opmax staging (solves only)
     __shared__ MCtx c;
     const LevelGeom lg{g.P, g.N, g.PN};
     const int R = g.R;
@@ -351,13 +347,19 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
         int o = 0, u = 0;
         for (int lev = 0; lev < g.nlev; ++lev) {
             const int b = lg.size(lev), bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
-            loff[lev] = o;
+            const int bp = lev > 0 ? lg.size(lev - 1) : 0;
+            loff[2 * lev] = o;                       // 16-byte aligned operator starts
+            o += (b * (b + bp) + 3) & ~3;
+            loff[2 * lev + 1] = o;
+            o += (b * (b + bn) + 3) & ~3;
             u0[lev] = u;
-            o += b * (b + 1) / 2 + bn * b;
             u += b;
         }
-        loff[g.nlev] = o;
         u0[g.nlev] = u;
+        mbar_init(&c.bar[0], 1);
+        mbar_init(&c.bar[1], 1);
+        c.phase[0] = 0;
+        c.phase[1] = 0;
     }
     __syncthreads();
 
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
             element_stiffness(g.P, Xd, c.Sdn);
             c.bad = 0;
             c.col_fail = 0;
+            c.timeout = 0;
             c.passes = 0;
             c.FK = 0.0;
         }
@@ -462,7 +465,12 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
 
         // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
         const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
+        float* Rhs = y;                               // level right-hand sides (y is free while factoring)
         for (int t = threadIdx.x; t < (b0 + b1) * g.wld; t += blockDim.x) W[t] = 0.0f;
+        for (int t = threadIdx.x; t < b0 * b0; t += blockDim.x) {
+            const int i = t / b0, k = t - i * b0;
+            Rhs[i * g.ldr + k] = k == i ? 1.0f : 0.0f;
+        }
         __syncthreads();   // (also publishes scale[] to the block)
         for (int lev = 0; lev < g.nlev; ++lev) {
             const int b = lg.size(lev);
@@ -498,56 +506,37 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
                     __syncthreads();
                 }
             }
-            if (threadIdx.x == 0) {
-                const float d = W[0];
-                if (!(d > 0.0f) && c.bad == 0) c.bad = 1;
-                c.inv_piv = rsqrtf(d);
-            }
-            __syncthreads();
-            for (int k = 0; k < b; ++k) {
-                const int m = nr - k - 1;
-                {
-                    const float inv = c.inv_piv;
-                    for (int t = threadIdx.x; t < m; t += blockDim.x) W[(k + 1 + t) * g.wld + k] *= inv;
-                    if (threadIdx.x == 0) W[k * g.wld + k] = 1.0f / inv;   // L_kk
-                }
-                __syncthreads();
-                if (m <= 0) break;
-                const int H = (m + 1) / 2, Wd = m + 1;
-                const int total = H * Wd;
-                const bool next_pivot = k + 1 < b;
-                int p = threadIdx.x / Wd, cc = threadIdx.x - (threadIdx.x / Wd) * Wd;
-                for (int e = threadIdx.x; e < total; e += blockDim.x) {
-                    const int ia = k + 1 + (m - 1 - p), ib = k + 1 + p;
-                    const bool second = cc >= m - p;
-                    const int i = second ? ib : ia;
-                    const int jcol = second ? k + 1 + (cc - (m - p)) : k + 1 + cc;
-                    if (!(second && ia == ib)) {
-                        const float v = fmaf(-W[i * g.wld + k], W[jcol * g.wld + k], W[i * g.wld + jcol]);
-                        W[i * g.wld + jcol] = v;
-                        if (next_pivot && i == k + 1 && jcol == k + 1) {
-                            if (!(v > 0.0f) && c.bad == 0) c.bad = k + 2;
-                            c.inv_piv = rsqrtf(v);
-                        }
-                    }
-                    cc += blockDim.x;
-                    while (cc >= Wd) { cc -= Wd; ++p; }
-                }
-                __syncthreads();
-            }
-            // store L_lev (packed lower) and L_{lev+1,lev} (bn x b) of this level
+            // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
+            // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
+            const int bp = lev > 0 ? lg.size(lev - 1) : 0;
+            blocked_cholesky_level<float, 8>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
             {
-                float* Fl = F + loff[lev];
-                const int nl = b * (b + 1) / 2;
-                for (int t = threadIdx.x; t < nl + bn * b; t += blockDim.x) {
-                    if (t < nl) {
-                        int i = 0, rem = t;
-                        while (rem > i) { rem -= i + 1; ++i; }
-                        Fl[t] = W[i * g.wld + rem];
-                    } else {
-                        const int q = t - nl, i = q / b, k = q - i * b;
-                        Fl[t] = W[(b + i) * g.wld + k];
+                // Fw (column-major (b + bp) x b) and Bw = [Linv^T | -Linv^T L_{lev+1,lev}^T]
+                // (column-major (b + bn) x b) to this block's scratch slot
+                float* Fw = F + loff[2 * lev];
+                float* Bw = F + loff[2 * lev + 1];
+                for (int t = threadIdx.x; t < b * (b + bp); t += blockDim.x) {
+                    const int k = t / b, i = t - k * b;
+                    Fw[t] = Rhs[i * g.ldr + k];
+                }
+                for (int t = threadIdx.x; t < b * (b + bn); t += blockDim.x) {
+                    const int k = t / b, i = t - k * b;
+                    float v;
+                    if (k < b) v = Rhs[k * g.ldr + i];
+                    else {
+                        const float* cn = W + (size_t)(b + (k - b)) * g.wld;
+                        float a = 0.0f;
+                        for (int mm = i; mm < b; ++mm) a = fmaf(Rhs[mm * g.ldr + i], cn[mm], a);
+                        v = -a;
                     }
+                    Bw[t] = v;
+                }
+                fence_proxy_async_global();   // the operators are read back by bulk copies
+                __syncthreads();
+                // right-hand sides of the next level: [I_bn | -L_{lev+1,lev}]
+                for (int t = threadIdx.x; t < bn * (bn + b); t += blockDim.x) {
+                    const int i = t / (bn + b), k = t - i * (bn + b);
+                    Rhs[i * g.ldr + k] = k < bn ? (k == i ? 1.0f : 0.0f) : -W[(size_t)(b + i) * g.wld + (k - bn)];
                 }
             }
             __syncthreads();
@@ -576,7 +565,7 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
             Z[t] = 0.0;
         }
         __syncthreads();
-        solve_factor(g, lg, F, loff, u0, y, c);
+        solve_factor(g, lg, F, loff, u0, y, opbuf, c);
         __syncthreads();
         column_dot(g, Res, y, scale, c.gamma, c);      // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
         __syncthreads();
@@ -600,7 +589,7 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
                 if (!c.col_done[col]) y[t] = (float)(Res[t] * scale[t - col * g.nunk]);
             }
             __syncthreads();
-            solve_factor(g, lg, F, loff, u0, y, c);
+            solve_factor(g, lg, F, loff, u0, y, opbuf, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.eps, c);
             __syncthreads();
@@ -685,7 +674,7 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
         }
         if (threadIdx.x == 0) {
             g.FK[K] = c.FK;
-            g.status[K] = c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+            g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
             if (g.iters) g.iters[K] = pass;
         }
         __syncthreads();
@@ -693,7 +682,7 @@ __global__ void __launch_bounds__(kThreadsM) k_local_mixed(const MixedArgs g) {
 }
 
 struct MixedLayout {
-    int nlev, nunk, wrows, wld, wfloats, yfloats;
+    int nlev, nunk, wrows, wld, wfloats, yfloats, bmax, opmax, ldr;
     size_t factor_floats, slot_bytes, off_G, off_Z, off_mass, off_scale, off_D, smem;
 };
 
@@ -708,13 +697,21 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.nlev = N + 1;
     L.nunk = (int)mesh->nloc - 1;
     size_t f = 0;
+    int bmax = 0, opmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) {
         const int b = size(lev), bn = lev + 1 < L.nlev ? size(lev + 1) : 0;
-        f += (size_t)b * (b + 1) / 2 + (size_t)bn * b;
+        const int bp = lev > 0 ? size(lev - 1) : 0;
+        const int fw = (b * (b + bp) + 3) & ~3, bw = (b * (b + bn) + 3) & ~3;
+        f += (size_t)fw + bw;
+        if (b > bmax) bmax = b;
+        if (fw > opmax) opmax = fw;
+        if (bw > opmax) opmax = bw;
     }
+    L.bmax = bmax;
+    L.opmax = opmax;
     L.factor_floats = f;
     L.wrows = size(0) + (N >= 1 ? size(1) : 0);
-    L.wld = L.wrows | 1;
+    L.wld = (L.wrows + 4) & ~3;   // rows 16-byte aligned for the vector panel loads
     const int R = (int)mesh->NI + 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     L.off_G = al(f * sizeof(float));
@@ -725,12 +722,15 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.slot_bytes = L.off_D + al((size_t)L.nunk * R * sizeof(double));
     size_t win = (size_t)L.wrows * L.wld;
     if (win < (size_t)R * R * 2) win = (size_t)R * R * 2;
+    if (win < (size_t)2 * L.opmax) win = (size_t)2 * L.opmax;
     win = (win + 3) & ~(size_t)3;
     L.wfloats = (int)win;
     size_t yf = (size_t)L.nunk * R;
     if (yf < (size_t)2 * R * 64) yf = (size_t)2 * R * 64;   // also holds two R x 64 staging chunks
+    L.ldr = (2 * bmax + 3) & ~3;
+    if (yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
-    L.smem = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + 2 * (size_t)(L.nlev + 1) * sizeof(int);
+    L.smem = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
     L.smem = (L.smem + 15) & ~(size_t)15;
     return L;
 }
@@ -765,9 +765,9 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     const MixedLayout L = mixed_layout(mesh);
     if (L.smem > 220 * 1024)
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED buffers exceed shared memory (r too large)");
-    const int maxlev = (mesh->desc.degree == 1 ? mesh->N : 4 * mesh->N);
-    if (maxlev > 32 * kMaxRowsPerLane)
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED level size above 128");
+    // the level solves map (row, group of 8 columns) to threads: one pass per block
+    if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED level x columns too large for one block");
     const int slots = mixed_slots(mesh, L);
     if (ws_bytes < (size_t)slots * L.slot_bytes)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
@@ -786,6 +786,9 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     g.wld = L.wld;
     g.wfloats = L.wfloats;
     g.yfloats = L.yfloats;
+    g.bmax = L.bmax;
+    g.opmax = L.opmax;
+    g.ldr = L.ldr;
     g.src_kind = f.kind;
     g.src_value = f.value;
     g.src_freq = f.freq;

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mhm.h"
+#include "mhm.h"
 
 namespace mhm {
 
