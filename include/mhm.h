@@ -164,6 +164,26 @@ mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, 
                                  int32_t* iters_dev, void* workspace_dev, size_t workspace_bytes,
                                  void* stream);
 
+/* Allocation-free variant of mhm_local_solve_batch with precision MHM_MIXED (the
+ * paper has no counterpart: it is an interface for callers that cannot allocate
+ * device memory while they run, e.g. a framework whose pool owns all device
+ * memory, or a latency-critical loop that must not call cudaMalloc).  Same
+ * arguments and outputs as mhm_local_solve_batch with MHM_MIXED, but the scratch
+ * memory comes from a fixed 32 MiB array inside the library's device image,
+ * which every GPU that loads the library holds until the process exits; the call
+ * allocates nothing.  Coarse elements whose per-element scratch exceeds 32 MiB
+ * are rejected with MHM_ERR_INVALID_ARG; a large batch runs with as many
+ * concurrent blocks as fit in the array.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls share the array,
+ * and each call overwrites what the previous one left there: calls that can
+ * overlap on the GPU (different streams without ordering) race and must not be
+ * issued. */
+mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
+                                         const mhm_solve_opts* opts, double* AK_dev, double* EK_dev,
+                                         double* BK_dev, double* FK_dev, int32_t* status_dev,
+                                         int32_t* iters_dev, void* stream);
+
 /* -------------------------------------------------------------- skeleton --- */
 
 /* reduceLocalProblems' gather (Eq. "mat_global"): sums the per-K blocks into

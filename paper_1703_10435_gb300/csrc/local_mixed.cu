@@ -18,6 +18,9 @@
 //     N~_j^T z = N_j^T z - c_j m^T z (N_j lives on one face only).
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <string>
+
 #include "local_common.cuh"
 
 namespace mhm {
@@ -810,6 +813,119 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     if (nK <= 0) return MHM_OK;
     const int grid = (int)(nK < slots ? nK : slots);
     k_local_mixed<<<grid, kThreadsM, L.smem, stream>>>(g);
+    MHM_CUDA_TRY(cudaGetLastError());
+    return MHM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the mixed-precision local solve.
+//
+// Some callers cannot allocate device memory while they run: a host framework
+// whose memory pool owns the whole device (allocating behind its back breaks
+// its accounting), or a latency-critical loop that must not call cudaMalloc or
+// cope with it failing.  For them this entry point takes its scratch from a
+// fixed array that lives in the library's own device image (kStaticScratch
+// bytes, held on every GPU that loads the library until the process exits)
+// instead of a caller-supplied workspace.  The caller still passes inputs and
+// outputs.
+namespace {
+
+constexpr size_t kStaticScratch = size_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratch];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mutex;
+static void* g_static_ptr[kMaxDevices];   // device address of g_static_scratch, per device
+
+}  // namespace
+
+extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kappa,
+                                                    const mhm_source* f, const mhm_solve_opts* opts,
+                                                    double* AK, double* EK, double* BK, double* FK,
+                                                    int32_t* status, int32_t* iters, void* stream) {
+    if (!mesh) return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: NULL mesh");
+    if (mesh->device < 0 || mesh->device >= kMaxDevices)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: mesh has no usable device");
+    if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: NULL pointer argument");
+    if (f->kind != MHM_SRC_CONST && f->kind != MHM_SRC_SINSIN)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: unknown source kind");
+    MHM_CUDA_TRY(cudaSetDevice(mesh->device));
+    mhm_solve_opts o{};
+    o.it_max = 8;
+    o.tol = 1e-12;
+    if (opts) o = *opts;
+    const int64_t K0 = o.K_begin, K1 = o.K_end > 0 ? o.K_end : mesh->nK;
+    if (K0 < 0 || K1 > mesh->nK || K0 > K1)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: K range out of bounds");
+    if (o.it_max < 1 || !(o.tol > 0.0))
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: it_max >= 1 and tol > 0 required");
+    const MixedLayout L = mixed_layout(mesh);
+    if (L.smem > 220 * 1024)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
+    if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: level x columns too large for one block");
+    if (L.slot_bytes > kStaticScratch)
+        return fail(MHM_ERR_INVALID_ARG,
+                    "mhm_local_solve_batch_noalloc: one coarse element needs " + std::to_string(L.slot_bytes) +
+                        " bytes of scratch, above the fixed " + std::to_string(kStaticScratch) + " bytes");
+    // Set-up, once per device with that device current: the device address of the
+    // fixed array (its name in host code is only a stand-in for the symbol).
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[mesh->device]) {
+            cudaError_t e = cudaGetSymbolAddress(&g_static_ptr[mesh->device], g_static_scratch);
+            if (e != cudaSuccess) {
+                g_static_ptr[mesh->device] = nullptr;
+                return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+            }
+        }
+        scratch = g_static_ptr[mesh->device];
+    }
+    const int64_t nK = K1 - K0;
+    if (nK <= 0) return MHM_OK;
+    const int64_t fit = (int64_t)(kStaticScratch / L.slot_bytes);
+    int64_t grid = mixed_slots(mesh, L);
+    if (grid > fit) grid = fit;
+    if (grid > nK) grid = nK;
+    MixedArgs g;
+    g.dm = mesh->dev();
+    g.kappa = kappa;
+    g.P = mesh->desc.degree;
+    g.N = mesh->N;
+    g.PN = mesh->PN;
+    g.dpf = mesh->dpf;
+    g.NI = (int)mesh->NI;
+    g.R = g.NI + 1;
+    g.nlev = L.nlev;
+    g.nunk = L.nunk;
+    g.wrows = L.wrows;
+    g.wld = L.wld;
+    g.wfloats = L.wfloats;
+    g.yfloats = L.yfloats;
+    g.bmax = L.bmax;
+    g.opmax = L.opmax;
+    g.ldr = L.ldr;
+    g.src_kind = f->kind;
+    g.src_value = f->value;
+    g.src_freq = f->freq;
+    g.K0 = K0;
+    g.K1 = K1;
+    g.it_max = o.it_max;
+    g.tol = o.tol;
+    g.ws = (char*)scratch;
+    g.slot_bytes = L.slot_bytes;
+    g.off_G = L.off_G;
+    g.off_Z = L.off_Z;
+    g.off_mass = L.off_mass;
+    g.off_scale = L.off_scale;
+    g.off_D = L.off_D;
+    g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
+    g.status = status;
+    g.iters = iters;
+    k_local_mixed<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }

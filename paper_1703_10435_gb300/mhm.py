@@ -35,6 +35,7 @@ Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
+    "mhm_local_solve_batch_noalloc",
 ]
 
 
@@ -81,10 +82,12 @@ def lib():
         L.mhm_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source), i32, ctypes.POINTER(SolveOpts),
                                             vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.mhm_assemble_skeleton.argtypes = [vp, vp, vp, ctypes.POINTER(Dirichlet), vp, vp, vp]
+        L.mhm_local_solve_batch_noalloc.argtypes = [vp, vp, ctypes.POINTER(Source), ctypes.POINTER(SolveOpts),
+                                                    vp, vp, vp, vp, vp, vp, vp]
         L.mhm_last_error.restype = ctypes.c_char_p
         L.mhm_measure_pipes.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
-                     "mhm_assemble_skeleton", "mhm_measure_pipes"):
+                     "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -153,6 +156,15 @@ def mhm_local_solve_batch(mesh: Mesh, kappa, source: Source, precision, opts: So
                                        None if opts is None else ctypes.byref(opts),
                                        _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters),
                                        _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def mhm_local_solve_batch_noalloc(mesh: Mesh, kappa, source: Source, opts: SolveOpts | None,
+                                  AK, EK, BK, FK, status, iters=None, stream=None):
+    """Mixed-precision local solves with the library's fixed scratch array (no allocation)."""
+    _check(lib().mhm_local_solve_batch_noalloc(mesh.handle, _ptr(kappa), ctypes.byref(source),
+                                               None if opts is None else ctypes.byref(opts),
+                                               _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status),
+                                               _ptr(iters), _stream(stream)))
 
 
 def mhm_assemble_skeleton(mesh: Mesh, AK, EK, dirichlet: Dirichlet | None, A_vals, E, stream=None):
