@@ -226,33 +226,91 @@ template <int NB> __device__ __forceinline__ void load_panel(const double* row, 
 // Schur complement; Rhs rows [0, b) hold L^{-1} Rhs and rows [b, rhs_rows) are
 // reduced by -L_{next,cur} (L^{-1} Rhs).  Panels of NB pivots are factored by
 // warp 0 (warp-synchronous), then all threads apply the rank-NB update.
-// ld and ldr must keep every row 16-byte aligned; *bad gets the first
-// non-positive pivot (+1).  Ends with a block barrier.
-template <typename T, int NB>
+// ld and ldr must keep every row 16-byte aligned; nr <= 32 RPL and
+// ncols <= 32 CPL; *bad gets the first non-positive pivot (+1).  Ends with a
+// block barrier.
+template <typename T, int NB, int RPL, int CPL>
 __device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int ldr, int rhs_rows, int ncols,
                                        int* bad) {
+    using T_ = T;
     for (int p0 = 0; p0 < b; p0 += NB) {
         const int pe = min(p0 + NB, b);
         if (threadIdx.x < 32) {
+            // Panel in registers: lane owns rows i = lane + 32 s of the panel columns and
+            // columns c = lane + 32 s of the panel's right-hand-side rows.
             const int lane = threadIdx.x;
-            for (int k = p0; k < pe; ++k) {
-                const T d = M[k * ld + k];
-                const T inv = rsqrt_t<T>(d);
-                if (lane == 0 && !(d > T(0)) && *bad == 0) *bad = k + 1;
-                for (int i = k + 1 + lane; i < nr; i += 32) M[i * ld + k] *= inv;
-                for (int c = lane; c < ncols; c += 32) Rhs[k * ldr + c] *= inv;
-                __syncwarp();
-                if (lane == 0) M[k * ld + k] = d * inv;
-                for (int j = k + 1; j < pe; ++j) {
-                    const T ljk = M[j * ld + k];
-                    for (int i = j + lane; i < nr; i += 32) M[i * ld + j] -= M[i * ld + k] * ljk;
-                }
-                for (int i = k + 1; i < pe; ++i) {
-                    const T lik = M[i * ld + k];
-                    for (int c = lane; c < ncols; c += 32) Rhs[i * ldr + c] -= lik * Rhs[k * ldr + c];
-                }
-                __syncwarp();
+            const int nbk = pe - p0;
+            T pr[RPL][NB];   // pr[s][q] = M[lane + 32 s][p0 + q]
+            T rh[NB][CPL];   // rh[q][s] = Rhs[p0 + q][lane + 32 s]
+#pragma unroll
+            for (int s2 = 0; s2 < RPL; ++s2) {
+                const int i = lane + 32 * s2;
+#pragma unroll
+                for (int q = 0; q < NB; ++q) pr[s2][q] = (i < nr && q < nbk && i >= p0 + q) ? M[i * ld + p0 + q] : T(0);
             }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+#pragma unroll
+                for (int s2 = 0; s2 < CPL; ++s2) {
+                    const int cidx = lane + 32 * s2;
+                    rh[q][s2] = (q < nbk && cidx < ncols) ? Rhs[(p0 + q) * ldr + cidx] : T(0);
+                }
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (q < nbk) {
+                    const int k = p0 + q;
+                    // pivot value from the lane owning row k
+                    T srcv = pr[0][q];
+#pragma unroll
+                    for (int s2 = 1; s2 < RPL; ++s2)
+                        if (s2 == (k >> 5)) srcv = pr[s2][q];
+                    const T d = __shfl_sync(0xffffffffu, srcv, k & 31);
+                    const T inv = rsqrt_t<T>(d);
+                    if (lane == 0 && !(d > T(0)) && *bad == 0) *bad = k + 1;
+                    // scale column q below the pivot; the diagonal becomes sqrt(d)
+#pragma unroll
+                    for (int s2 = 0; s2 < RPL; ++s2) {
+                        const int i = lane + 32 * s2;
+                        if (i > k) pr[s2][q] *= inv;
+                        else if (i == k) pr[s2][q] = d * inv;
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < CPL; ++s2) rh[q][s2] *= inv;
+                    // rank-1 update of the remaining panel columns and panel right-hand-side rows
+#pragma unroll
+                    for (int q2 = 0; q2 < NB; ++q2) {
+                        if (q2 > q && q2 < nbk) {
+                            const int j = p0 + q2;
+                            T srcl = pr[0][q];
+#pragma unroll
+                            for (int s2 = 1; s2 < RPL; ++s2)
+                                if (s2 == (j >> 5)) srcl = pr[s2][q];
+                            const T ljk = __shfl_sync(0xffffffffu, srcl, j & 31);
+#pragma unroll
+                            for (int s2 = 0; s2 < RPL; ++s2) {
+                                const int i = lane + 32 * s2;
+                                if (i >= j) pr[s2][q2] -= pr[s2][q] * ljk;
+                            }
+#pragma unroll
+                            for (int s2 = 0; s2 < CPL; ++s2) rh[q2][s2] -= ljk * rh[q][s2];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < RPL; ++s2) {
+                const int i = lane + 32 * s2;
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+                    if (i < nr && q < nbk && i >= p0 + q) M[i * ld + p0 + q] = pr[s2][q];
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+#pragma unroll
+                for (int s2 = 0; s2 < CPL; ++s2) {
+                    const int cidx = lane + 32 * s2;
+                    if (q < nbk && cidx < ncols) Rhs[(p0 + q) * ldr + cidx] = rh[q][s2];
+                }
         }
         __syncthreads();
         const int nbk = pe - p0;

@@ -187,7 +187,7 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_local_fp64(const Fp64Args g) {
+__global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
     extern __shared__ double smem[];
     __shared__ KCtx c;
     __shared__ double red[32];
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_local_fp64(const Fp64Args g) {
         }
         // Blocked right-looking Cholesky of the level's b pivots on the augmented window
         // rows; the right-hand-side columns (all window rows) are forward-substituted.
-        blocked_cholesky_level<double, 8>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
+        blocked_cholesky_level<double, 8, 4, 2>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
         // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
         for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
             int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row

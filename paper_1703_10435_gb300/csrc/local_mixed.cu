@@ -47,6 +47,8 @@ struct MixedArgs {
     double tol;
     char* ws;
     size_t slot_bytes, off_G, off_Z, off_mass, off_scale, off_D;
+    size_t off_kap_smem, off_scale_smem;
+    int kap_in_smem;
     double *AK, *EK, *BK, *FK;
     int32_t *status, *iters;
 };
@@ -163,32 +165,33 @@ __device__ __forceinline__ void lattice_of_unk(int PN, int u, int* X, int* Y) {
     *Y = y;
 }
 
-// Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64: the sum over
+// Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
+// FP32 right-hand side y(u, :) = s_u Res(u, :): the sum over
 // the fine triangles T containing u of kappa_T S_T[a_u][b] D(b).  P1 uses the
 // assembled 7-point row of the lattice (6 triangles, 7 coefficients); P2 sums
 // element by element.
 __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* kap, int u, const double* D,
-                               double* Res) {
+                               double* Res, float* y, const double s_u) {
     int X, Y;
     lattice_of_unk(g.PN, u, &X, &Y);
     const size_t ld = (size_t)g.nunk;
     if (g.P == 1) {
-        const int N = g.N, x = X, y = Y;
+        const int N = g.N, x = X, yl = Y;
         auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
         auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
-        const double k1 = kup(x, y), k2 = kup(x - 1, y), k3 = kup(x, y - 1);
-        const double k4 = kdn(x - 1, y - 1), k5 = kdn(x - 1, y), k6 = kdn(x, y - 1);
+        const double k1 = kup(x, yl), k2 = kup(x - 1, yl), k3 = kup(x, yl - 1);
+        const double k4 = kdn(x - 1, yl - 1), k5 = kdn(x - 1, yl), k6 = kdn(x, yl - 1);
         const double* Su = c.Sup;
         const double* Sd = c.Sdn;
         double w[7];
         int v[7];
         w[0] = k1 * Su[0] + k2 * Su[4] + k3 * Su[8] + k4 * Sd[4] + k5 * Sd[0] + k6 * Sd[8];  v[0] = u;
-        w[1] = k1 * Su[1] + k6 * Sd[7];  v[1] = unk(g.PN, x + 1, y);        // east
-        w[2] = k2 * Su[3] + k4 * Sd[5];  v[2] = unk(g.PN, x - 1, y);        // west
-        w[3] = k1 * Su[2] + k5 * Sd[1];  v[3] = unk(g.PN, x, y + 1);        // north
-        w[4] = k3 * Su[6] + k4 * Sd[3];  v[4] = unk(g.PN, x, y - 1);        // south
-        w[5] = k3 * Su[7] + k6 * Sd[6];  v[5] = unk(g.PN, x + 1, y - 1);    // south-east
-        w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(g.PN, x - 1, y + 1);    // north-west
+        w[1] = k1 * Su[1] + k6 * Sd[7];  v[1] = unk(g.PN, x + 1, yl);        // east
+        w[2] = k2 * Su[3] + k4 * Sd[5];  v[2] = unk(g.PN, x - 1, yl);        // west
+        w[3] = k1 * Su[2] + k5 * Sd[1];  v[3] = unk(g.PN, x, yl + 1);        // north
+        w[4] = k3 * Su[6] + k4 * Sd[3];  v[4] = unk(g.PN, x, yl - 1);        // south
+        w[5] = k3 * Su[7] + k6 * Sd[6];  v[5] = unk(g.PN, x + 1, yl - 1);    // south-east
+        w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(g.PN, x - 1, yl + 1);    // north-west
         for (int k = 1; k < 7; ++k)
             if (w[k] == 0.0 || v[k] < 0 || v[k] >= g.nunk) { w[k] = 0.0; v[k] = u; }
         for (int col = 0; col < g.R; ++col) {
@@ -197,7 +200,9 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
             double a = 0.0;
 #pragma unroll
             for (int k = 0; k < 7; ++k) a = fma(w[k], Dc[v[k]], a);
-            Res[col * ld + u] -= a;
+            const double rn = Res[col * ld + u] - a;
+            Res[col * ld + u] = rn;
+            y[col * ld + u] = (float)(rn * s_u);
         }
         return;
     }
@@ -218,7 +223,9 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
                 if (ub >= 0) a = fma(kt * S[ta[t] * 6 + b], Dc[ub], a);
             }
         }
-        Res[col * ld + u] -= a;
+        const double rn = Res[col * ld + u] - a;
+        Res[col * ld + u] = rn;
+        y[col * ld + u] = (float)(rn * s_u);
     }
 }
 
@@ -231,10 +238,10 @@ __device__ void column_dot(const MixedArgs& g, const double* Res, const float* y
         if (c.col_done[col]) continue;
         const double* rc = Res + (size_t)col * g.nunk;
         const float* yc = y + (size_t)col * g.nunk;
-        double a = 0.0;
-        for (int u = lane; u < g.nunk; u += 32) a = fma(rc[u] * s[u], (double)yc[u], a);
+        float a = 0.0f;   // an error estimate: FP32 is ample
+        for (int u = lane; u < g.nunk; u += 32) a = fmaf((float)rc[u] * (float)s[u], yc[u], a);
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) out[col] = a;
+        if (lane == 0) out[col] = (double)a;
     }
 }
 
@@ -267,14 +274,16 @@ __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const floa
         mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
         bulk_copy_g2s(dst, F + opoff[2 * lev + dir], bytes, &c.bar[st & 1]);
     };
-    if (threadIdx.x == 0) issue(0);
+    // copies are issued by the last thread, whose work item is empty in most steps
+    const bool issuer = threadIdx.x == blockDim.x - 1;
+    if (issuer) issue(0);
     for (int st = 0; st < nsteps; ++st) {
         int dir;
         const int lev = step_lev(st, &dir);
         const int b = lg.size(lev);
         const int lo = dir == 0 ? lev - 1 : lev + 1;
         const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
-        if (threadIdx.x == 0 && st + 1 < nsteps) issue(st + 1);
+        if (issuer && st + 1 < nsteps) issue(st + 1);
         const uint32_t par = (st & 1) ? ph1 : ph0;
         if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
         if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
@@ -329,12 +338,15 @@ __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const floa
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g) {
+template <int RPL, int CPL>
+__global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g) {
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
     float* y = W + (size_t)g.wfloats;                                    // nunk x R
     int* loff = reinterpret_cast<int*>(y + (size_t)g.yfloats);         // 2 nlev operator offsets (Fw, Bw)
     int* u0 = loff + 2 * g.nlev;                                        // nlev + 1 level starts
+    double* kap_s = reinterpret_cast<double*>(smem_raw + g.off_kap_smem);   // kappa of the current K (if staged)
+    double* scale = reinterpret_cast<double*>(g.ws + (size_t)blockIdx.x * g.slot_bytes + g.off_scale);   // 1/sqrt(diag A_p)
     float* opbuf = W;                                                   // 2 x opmax staging (solves only)
     __shared__ MCtx c;
     const LevelGeom lg{g.P, g.N, g.PN};
@@ -344,7 +356,6 @@ __global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g)
     double* G = reinterpret_cast<double*>(slot + g.off_G);
     double* Z = reinterpret_cast<double*>(slot + g.off_Z);
     double* mass = reinterpret_cast<double*>(slot + g.off_mass);
-    double* scale = reinterpret_cast<double*>(slot + g.off_scale);   // 1/sqrt(diag A_p)
 
     if (threadIdx.x == 0) {
         int o = 0, u = 0;
@@ -368,6 +379,12 @@ __global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g)
 
     for (int64_t K = g.K0 + blockIdx.x; K < g.K1; K += gridDim.x) {
         const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+        if (g.kap_in_smem) {
+            // stage this K's kappa in shared memory (read by assembly, scaling and residuals)
+            const int nf = g.N * g.N;
+            for (int t = threadIdx.x; t < nf; t += blockDim.x) kap_s[t] = kap[t];
+            kap = kap_s;   // published by the barrier after the per-K setup
+        }
         // ---- per-K setup
         if (threadIdx.x == 0) {
             for (int v = 0; v < 3; ++v) {
@@ -512,7 +529,7 @@ __global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g)
             // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
             // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
             const int bp = lev > 0 ? lg.size(lev - 1) : 0;
-            blocked_cholesky_level<float, 8>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
+            blocked_cholesky_level<float, 8, RPL, CPL>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
             {
                 // Fw (column-major (b + bp) x b) and Bw = [Linv^T | -Linv^T L_{lev+1,lev}^T]
                 // (column-major (b + bn) x b) to this block's scratch slot
@@ -584,13 +601,8 @@ __global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g)
             }
             __syncthreads();
             // Res -= A_p D (FP64, from kappa and the element matrices)
-            for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) apply_residual(g, c, kap, u, D64, Res);
+            for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) apply_residual(g, c, kap, u, D64, Res, y, scale[u]);
             ++pass;
-            __syncthreads();
-            for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int col = t / g.nunk;
-                if (!c.col_done[col]) y[t] = (float)(Res[t] * scale[t - col * g.nunk]);
-            }
             __syncthreads();
             solve_factor(g, lg, F, loff, u0, y, opbuf, c);
             __syncthreads();
@@ -687,6 +699,8 @@ __global__ void __launch_bounds__(kThreadsM, 2) k_local_mixed(const MixedArgs g)
 struct MixedLayout {
     int nlev, nunk, wrows, wld, wfloats, yfloats, bmax, opmax, ldr;
     size_t factor_floats, slot_bytes, off_G, off_Z, off_mass, off_scale, off_D, smem;
+    size_t off_kap_smem, off_scale_smem;
+    int kap_in_smem, rpl, cpl;
 };
 
 MixedLayout mixed_layout(const mhm_mesh* mesh) {
@@ -733,16 +747,41 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.ldr = (2 * bmax + 3) & ~3;
     if (yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
-    L.smem = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
-    L.smem = (L.smem + 15) & ~(size_t)15;
+    size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
+    off = (off + 15) & ~(size_t)15;
+    const size_t nf = (size_t)N * N;
+    L.kap_in_smem = nf <= 1024;
+    L.off_kap_smem = off;
+    off += L.kap_in_smem ? nf * sizeof(double) : 0;
+    L.off_scale_smem = 0;
+    L.smem = (off + 15) & ~(size_t)15;
+    // register shape of the warp panel: rows (window) and right-hand-side columns per lane
+    int ncols = 0;
+    for (int lev = 0; lev < L.nlev; ++lev) {
+        const int c = size(lev) + (lev > 0 ? size(lev - 1) : 0);
+        if (c > ncols) ncols = c;
+    }
+    if (L.wrows <= 64 && ncols <= 96) { L.rpl = 2; L.cpl = 3; }
+    else if (L.wrows <= 128 && ncols <= 128) { L.rpl = 4; L.cpl = 4; }
+    else { L.rpl = 0; L.cpl = 0; }
     return L;
+}
+
+using MixedKernel = void (*)(const MixedArgs);
+
+MixedKernel mixed_kernel(const MixedLayout& L) {
+    if (L.rpl == 2) return k_local_mixed<2, 3>;
+    if (L.rpl == 4) return k_local_mixed<4, 4>;
+    return nullptr;
 }
 
 int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
     int dev = mesh->device, sms = 0, per = 0;
+    MixedKernel k = mixed_kernel(L);
+    if (!k) return 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_local_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_local_mixed, kThreadsM, L.smem) != cudaSuccess || per < 1)
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsM, L.smem) != cudaSuccess || per < 1)
         per = 1;
     return sms * per;
 }
@@ -752,7 +791,7 @@ int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
 size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     if (mesh->device < 0) return 0;
     const MixedLayout L = mixed_layout(mesh);
-    if (L.smem > 220 * 1024) return 0;
+    if (L.smem > 220 * 1024 || !mixed_kernel(L)) return 0;
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(mesh->device);
@@ -766,7 +805,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
                               double* BK, double* FK, int32_t* status, int32_t* iters, void* workspace,
                               size_t ws_bytes, cudaStream_t stream) {
     const MixedLayout L = mixed_layout(mesh);
-    if (L.smem > 220 * 1024)
+    if (L.smem > 220 * 1024 || !mixed_kernel(L))
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED buffers exceed shared memory (r too large)");
     // the level solves map (row, group of 8 columns) to threads: one pass per block
     if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
@@ -806,13 +845,16 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     g.off_mass = L.off_mass;
     g.off_scale = L.off_scale;
     g.off_D = L.off_D;
+    g.off_kap_smem = L.off_kap_smem;
+    g.off_scale_smem = L.off_scale_smem;
+    g.kap_in_smem = L.kap_in_smem;
     g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
     g.status = status;
     g.iters = iters;
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
     const int grid = (int)(nK < slots ? nK : slots);
-    k_local_mixed<<<grid, kThreadsM, L.smem, stream>>>(g);
+    mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }
@@ -862,7 +904,7 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
     if (o.it_max < 1 || !(o.tol > 0.0))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: it_max >= 1 and tol > 0 required");
     const MixedLayout L = mixed_layout(mesh);
-    if (L.smem > 220 * 1024)
+    if (L.smem > 220 * 1024 || !mixed_kernel(L))
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
     if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: level x columns too large for one block");
@@ -922,10 +964,13 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
     g.off_mass = L.off_mass;
     g.off_scale = L.off_scale;
     g.off_D = L.off_D;
+    g.off_kap_smem = L.off_kap_smem;
+    g.off_scale_smem = L.off_scale_smem;
+    g.kap_in_smem = L.kap_in_smem;
     g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
     g.status = status;
     g.iters = iters;
-    k_local_mixed<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
+    mixed_kernel(L)<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }
