@@ -98,6 +98,14 @@ typedef struct {
     double c[6];
 } mhm_dirichlet;
 
+/* Exact solution for error norms (optional). */
+#define MHM_EXACT_SINSIN 1  /* u = c[1] sin(c[0] pi x) sin(c[0] pi y) */
+#define MHM_EXACT_POLY 2    /* u = c[0] + c[1] x + c[2] y + c[3] x^2 + c[4] x y + c[5] y^2 */
+typedef struct {
+    int32_t kind;
+    double c[6];
+} mhm_exact;
+
 /* Options of the local solves. */
 typedef struct {
     int32_t it_max;   /* MIXED: maximum refinement passes (>= 1) */
@@ -195,6 +203,35 @@ mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kap
 mhm_status mhm_assemble_skeleton(const mhm_mesh* mesh, const double* AK_dev, const double* EK_dev,
                                  const mhm_dirichlet* g, double* A_vals_dev, double* E_dev,
                                  void* stream);
+
+/* ---------------------------------------------------------- global solve --- */
+
+/* reduceLocalProblems' solve (Alg. 1; Sec. 3, Eq. "mat_global"): solves the
+ * saddle-point system [A B^T; B 0] [lambda; u0] = [E; F] in FP64 on the device,
+ * with A_vals_dev / E_dev from mhm_assemble_skeleton, B from BK_dev
+ * (B[K, K's local multiplier j] = BK_dev[K*N_I + j]) and F = FK_dev (n_K).
+ * Writes lambda_dev (n_lambda) and u0_dev (n_K).  The matrix is assembled in CSR
+ * and factored by cuSOLVER's sparse QR (a library direct solver; this stage is
+ * outside the local-problem hot path).  Allocates temporary device memory.
+ * Errors: INVALID_ARG (NULL, singular matrix), UNSUPPORTED, CUDA. */
+mhm_status mhm_solve_global(const mhm_mesh* mesh, const double* A_vals_dev, const double* E_dev,
+                            const double* BK_dev, const double* FK_dev, double* lambda_dev, double* u0_dev,
+                            void* stream);
+
+/* ------------------------------------------------------------ reconstruct --- */
+
+/* computeSolution (Alg. 1; Sec. 2, Eq. "u_Hh"; Sec. 3): u_{H,h} = u0_K +
+ * sum_i k_i eta_i + eta_f on every K, computed in FP64 as one zero-mean Neumann
+ * solve per K with the combined load sum_i k_i N~_i + f~ (the k_i are the global
+ * multipliers of K's local basis).  Writes u_nodal_dev[K*n_local + w] for every
+ * local DOF w of K (lattice order).  If err_sq_dev is not NULL (it needs
+ * `exact`), also writes err_sq_dev[2K] = ||u_{H,h} - u||^2_{L2(K)} and
+ * err_sq_dev[2K+1] = |u_{H,h} - u|^2_{H1(K)}, by the collapsed 4 x 4 Gauss rule
+ * on every fine triangle.  Allocates temporary device memory.
+ * Errors: INVALID_ARG, UNSUPPORTED (window beyond shared memory), CUDA. */
+mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
+                           const double* lambda_dev, const double* u0_dev, const mhm_exact* exact,
+                           double* u_nodal_dev, double* err_sq_dev, void* stream);
 
 /* ------------------------------------------------------------------ misc --- */
 

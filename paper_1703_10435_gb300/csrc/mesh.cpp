@@ -80,7 +80,7 @@ mhm_status upload(const std::vector<T>& h, T** d) {
 void free_mesh_device(mhm_mesh* m) {
     void* ptrs[] = {m->d_geom, m->d_sign, m->d_rev, m->d_btab, m->d_btab_sum, m->d_gauss_x,
                     m->d_gauss_w, m->d_face_v, m->d_face_K, m->d_tri_f, m->d_vxy, m->d_lam_off,
-                    m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs};
+                    m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs, m->d_aug_rowptr, m->d_aug_cols, m->d_aug_src, m->d_k_lambda};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -244,6 +244,41 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     }
     m->nnz = (int64_t)m->csr_cols.size();
 
+    // saddle-point pattern: rows of A followed by the columns L + K of the (one or two)
+    // K holding the row's face (B^T); then one row per K with its multipliers (B),
+    // columns sorted ascending
+    {
+        const int64_t L = m->nlam;
+        m->aug_rowptr.assign(L + m->nK + 1, 0);
+        for (int64_t j = 0; j < L; ++j) {
+            const int64_t e = j / m->dpf, u = j - e * m->dpf;
+            for (int32_t t = m->csr_rowptr[j]; t < m->csr_rowptr[j + 1]; ++t) {
+                m->aug_cols.push_back(m->csr_cols[t]);
+                m->aug_src.push_back(t);
+            }
+            for (int side = 0; side < 2; ++side) {
+                const int32_t K = m->face_K[2 * e + side];
+                if (K < 0) continue;
+                int a = 0;
+                while (m->tri_f[3 * K + a] != e) ++a;
+                m->aug_cols.push_back((int32_t)(L + K));
+                m->aug_src.push_back(-((int64_t)K * m->NI + a * m->dpf + u) - 1);
+            }
+            m->aug_rowptr[j + 1] = (int32_t)m->aug_cols.size();
+        }
+        for (int64_t K = 0; K < m->nK; ++K) {
+            std::vector<std::pair<int32_t, int64_t>> row;
+            for (int64_t i = 0; i < m->NI; ++i) row.emplace_back(m->k_lambda[K * m->NI + i], -(K * m->NI + i) - 1);
+            std::sort(row.begin(), row.end());
+            for (auto& pr : row) {
+                m->aug_cols.push_back(pr.first);
+                m->aug_src.push_back(pr.second);
+            }
+            m->aug_rowptr[L + K + 1] = (int32_t)m->aug_cols.size();
+        }
+        m->aug_nnz = (int64_t)m->aug_cols.size();
+    }
+
     // Gauss-Legendre tables, n = 1..kMaxGauss
     m->gauss_x.assign(mhm::kMaxGauss * mhm::kMaxGauss, 0.0);
     m->gauss_w.assign(mhm::kMaxGauss * mhm::kMaxGauss, 0.0);
@@ -312,6 +347,10 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     if (!st) st = upload(m->csr_rowptr, &m->d_csr_rowptr);
     if (!st) st = upload(m->nbr_ptr, &m->d_nbr_ptr);
     if (!st) st = upload(m->nbrs, &m->d_nbrs);
+    if (!st) st = upload(m->aug_rowptr, &m->d_aug_rowptr);
+    if (!st) st = upload(m->aug_cols, &m->d_aug_cols);
+    if (!st) st = upload(m->aug_src, &m->d_aug_src);
+    if (!st) st = upload(m->k_lambda, &m->d_k_lambda);
     if (st) {
         free_mesh_device(m);
         delete m;

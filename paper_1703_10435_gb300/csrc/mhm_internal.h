@@ -72,6 +72,11 @@ struct mhm_mesh {
     std::vector<int32_t> nbr_ptr;     // ne+1
     std::vector<mhm::FaceNbr> nbrs;   // per face neighbour blocks
     std::vector<double> btab, btab_sum, gauss_x, gauss_w;
+    // saddle-point system [A B^T; B 0] in CSR: pattern and, per entry, the source of its
+    // value (>= 0: index into the skeleton CSR values; < 0: -(index into BK) - 1)
+    int64_t aug_nnz = 0;
+    std::vector<int32_t> aug_rowptr, aug_cols;
+    std::vector<int64_t> aug_src;
 
     // device copies (owned)
     double* d_geom = nullptr;
@@ -89,6 +94,10 @@ struct mhm_mesh {
     int32_t* d_csr_rowptr = nullptr;
     int32_t* d_nbr_ptr = nullptr;
     mhm::FaceNbr* d_nbrs = nullptr;
+    int32_t* d_aug_rowptr = nullptr;
+    int32_t* d_aug_cols = nullptr;
+    int64_t* d_aug_src = nullptr;
+    int32_t* d_k_lambda = nullptr;
 
     mhm::DeviceMesh dev() const {
         return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w};

@@ -35,8 +35,10 @@ Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
-    "mhm_local_solve_batch_noalloc",
+    "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct",
 ]
+MHM_EXACT_SINSIN = 1
+MHM_EXACT_POLY = 2
 
 
 class MeshDesc(ctypes.Structure):
@@ -50,6 +52,10 @@ class Source(ctypes.Structure):
 
 class Dirichlet(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double * 6)]
+
+
+class Exact(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("c", ctypes.c_double * 6)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -84,10 +90,13 @@ def lib():
         L.mhm_assemble_skeleton.argtypes = [vp, vp, vp, ctypes.POINTER(Dirichlet), vp, vp, vp]
         L.mhm_local_solve_batch_noalloc.argtypes = [vp, vp, ctypes.POINTER(Source), ctypes.POINTER(SolveOpts),
                                                     vp, vp, vp, vp, vp, vp, vp]
+        L.mhm_solve_global.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.mhm_reconstruct.argtypes = [vp, vp, ctypes.POINTER(Source), vp, vp, ctypes.POINTER(Exact), vp, vp, vp]
         L.mhm_last_error.restype = ctypes.c_char_p
         L.mhm_measure_pipes.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
-                     "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc"):
+                     "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc",
+                     "mhm_solve_global", "mhm_reconstruct"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -171,6 +180,18 @@ def mhm_assemble_skeleton(mesh: Mesh, AK, EK, dirichlet: Dirichlet | None, A_val
     _check(lib().mhm_assemble_skeleton(mesh.handle, _ptr(AK), _ptr(EK),
                                        None if dirichlet is None else ctypes.byref(dirichlet),
                                        _ptr(A_vals), _ptr(E), _stream(stream)))
+
+
+def mhm_solve_global(mesh: Mesh, A_vals, E, BK, FK, lam, u0, stream=None):
+    _check(lib().mhm_solve_global(mesh.handle, _ptr(A_vals), _ptr(E), _ptr(BK), _ptr(FK), _ptr(lam), _ptr(u0),
+                                  _stream(stream)))
+
+
+def mhm_reconstruct(mesh: Mesh, kappa, source: Source, lam, u0, exact: Exact | None, u_nodal, err_sq=None,
+                    stream=None):
+    _check(lib().mhm_reconstruct(mesh.handle, _ptr(kappa), ctypes.byref(source), _ptr(lam), _ptr(u0),
+                                 None if exact is None else ctypes.byref(exact), _ptr(u_nodal), _ptr(err_sq),
+                                 _stream(stream)))
 
 
 def mhm_measure_pipes(device: int = 0):

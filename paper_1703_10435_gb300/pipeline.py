@@ -64,6 +64,22 @@ class Pipeline:
         self.local(kappa, source, opts, stream)
         self.skeleton(dirichlet, stream)
 
+    def solve_global(self, stream=None):
+        """lambda, u0 of Eq. "mat_global" from the current skeleton and per-K blocks."""
+        M = self.mesh
+        self.lam = torch.zeros(M.n_lambda, dtype=torch.float64, device=self.device)
+        self.u0 = torch.zeros(M.n_K, dtype=torch.float64, device=self.device)
+        mhm.mhm_solve_global(M, self.A_vals, self.E, self.BK, self.FK, self.lam, self.u0, stream)
+        return self.lam, self.u0
+
+    def reconstruct(self, kappa, source, exact=None, stream=None):
+        """Nodal u_{H,h} per K (n_K x n_local) and, with `exact`, per-K squared L2/H1 errors."""
+        M = self.mesh
+        u = torch.empty(M.n_K * M.n_local, dtype=torch.float64, device=self.device)
+        err = torch.empty(2 * M.n_K, dtype=torch.float64, device=self.device) if exact is not None else None
+        mhm.mhm_reconstruct(M, kappa, source, self.lam, self.u0, exact, u, err, stream)
+        return u.view(M.n_K, M.n_local), (None if err is None else err.view(M.n_K, 2))
+
     # host-side views for tests and reports
     def blocks(self):
         M = self.mesh
