@@ -66,6 +66,9 @@ struct MCtx {
     double eps[kMaxNI + 1];       // Res_c^T M Res_c per column
     int passes;
     int all_done;
+    int converged;
+    int col_frozen[kMaxNI + 1];   // no further solves for this column
+    double eps_prev[kMaxNI + 1];
     int col_fail;
     double red[kWarpsM];
     double mz[kMaxNI + 1];
@@ -235,7 +238,7 @@ __device__ void column_dot(const MixedArgs& g, const double* Res, const float* y
                            const MCtx& c) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int col = warp; col < g.R; col += kWarpsM) {
-        if (c.col_done[col]) continue;
+        if (c.col_frozen[col]) continue;
         const double* rc = Res + (size_t)col * g.nunk;
         const float* yc = y + (size_t)col * g.nunk;
         float a = 0.0f;   // an error estimate: FP32 is ample
@@ -325,7 +328,7 @@ __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const floa
 #pragma unroll
                 for (int q = 0; q < kColGroup; ++q) {
                     const int col = cg * kColGroup + q;
-                    if (col < R && !c.col_done[col]) y[(size_t)col * g.nunk + ulev + i] = acc[it][q];
+                    if (col < R && !c.col_frozen[col]) y[(size_t)col * g.nunk + ulev + i] = acc[it][q];
                 }
             }
         }
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             c.passes = 0;
             c.FK = 0.0;
         }
-        for (int col = threadIdx.x; col < R; col += blockDim.x) c.col_done[col] = 0;
+        for (int col = threadIdx.x; col < R; col += blockDim.x) c.col_done[col] = c.col_frozen[col] = 0;
         __syncthreads();
         if (g.src_kind == MHM_SRC_CONST) {
             if (threadIdx.x == 0) c.FK = g.src_value * c.area;
@@ -589,8 +592,24 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         __syncthreads();
         column_dot(g, Res, y, scale, c.gamma, c);      // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
         __syncthreads();
+        // Columns with a zero right-hand side are done at once (Z = 0, Res = G = 0).
+        // Otherwise, after each correction the next one D' = M Res gives
+        // eps = Res^T M Res ~ ||e||^2 (energy norm of the error of Z): a column stops
+        // when eps <= tol * gamma; and when linear convergence predicts that one more
+        // correction will get there (eps^2 / eps_prev, with a safety factor 4), that
+        // correction is applied without a further confirming solve.
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int col = 0; col < R; ++col) {
+                c.col_frozen[col] = c.col_done[col] = !(c.gamma[col] > 0.0);
+                c.eps_prev[col] = c.gamma[col];
+                all &= c.col_done[col];
+            }
+            c.all_done = all;
+        }
+        __syncthreads();
         int pass = 0;
-        for (;;) {
+        while (!c.all_done) {
             // D = s . y (FP64), Z += D
             for (int t = threadIdx.x; t < total; t += blockDim.x) {
                 const int col = t / g.nunk;
@@ -600,10 +619,21 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 Z[t] += d;
             }
             __syncthreads();
-            // Res -= A_p D (FP64, from kappa and the element matrices)
+            // Res -= A_p D (FP64, from kappa and the element matrices); y = s . Res
             for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) apply_residual(g, c, kap, u, D64, Res, y, scale[u]);
             ++pass;
             __syncthreads();
+            if (threadIdx.x == 0) {
+                int all = 1;
+                for (int col = 0; col < R; ++col) {
+                    if (c.col_frozen[col]) c.col_done[col] = 1;   // its last correction is in
+                    all &= c.col_done[col];
+                }
+                c.all_done = all || pass >= g.it_max;
+                c.converged = all;
+            }
+            __syncthreads();
+            if (c.all_done) break;
             solve_factor(g, lg, F, loff, u0, y, opbuf, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.eps, c);
@@ -611,15 +641,20 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             if (threadIdx.x == 0) {
                 int all = 1;
                 for (int col = 0; col < R; ++col) {
-                    if (!c.col_done[col] && c.eps[col] <= g.tol * c.gamma[col]) c.col_done[col] = 1;
+                    if (!c.col_frozen[col]) {
+                        const double eps = c.eps[col], lim = g.tol * c.gamma[col];
+                        if (eps <= lim) c.col_frozen[col] = c.col_done[col] = 1;
+                        else if (4.0 * eps * eps <= lim * c.eps_prev[col]) c.col_frozen[col] = 1;
+                        c.eps_prev[col] = eps;
+                    }
                     all &= c.col_done[col];
                 }
                 c.all_done = all;
+                c.converged = all;
             }
             __syncthreads();
-            if (c.all_done || pass >= g.it_max) break;
         }
-        const int converged = c.all_done;
+        const int converged = c.converged;
 
         // ---- local contributions X[j][i] = N~_j^T z_i + z_j^T Res_i; A_K = -(X + X^T)/2, E_K = X[:, f]
         {
