@@ -5,9 +5,12 @@ multipliers = 18 lambda right-hand sides + 1 source, log-uniform kappa with
 log10 kappa ~ U[-2, 2] per fine triangle, f = 1).
 
 One step = mhm_local_solve_batch + mhm_assemble_skeleton over all coarse
-triangles.  Prints one JSON line (see the design doc for every key).
+triangles.  Both arithmetic paths are timed: the headline `value` is the
+mixed-precision path (FP32 factorisation and solves, FP64 residuals), the
+all-FP64 path is reported beside it, with the L2 difference of the
+reconstructed u between the two.  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 """
 from __future__ import annotations
@@ -168,6 +171,56 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def residual_fmas_per_pass(w):
+    """FP64 multiply-adds of one refinement pass of the mixed path for one K: the
+    assembled 7-point (P1) rows of A_p applied to the R right-hand sides."""
+    N = w.N
+    if w.degree != 1:
+        return None
+    # On the right-isosceles coarse triangles of this mesh the lattice edge opposite
+    # each fine triangle's right angle carries a zero weight: the lower triangles
+    # couple E, W, SE, NW, the upper ones N, S, SE, NW (a 5-point row, the kernel
+    # skips the zero weights).
+    tot = 0
+    for dirs in (((1, 0), (-1, 0), (1, -1), (-1, 1)), ((0, 1), (0, -1), (1, -1), (-1, 1))):
+        nnz = 0
+        for y in range(N + 1):
+            for x in range(N + 1 - y):
+                if x == 0 and y == 0:
+                    continue
+                cnt = 1
+                for dx, dy in dirs:
+                    X, Y = x + dx, y + dy
+                    if X >= 0 and Y >= 0 and X + Y <= N and not (X == 0 and Y == 0):
+                        cnt += 1
+                nnz += cnt
+        tot += nnz
+    return tot / 2 * (w.n_I + 1)
+
+
+def time_path(p, kap, src, gd, steps, warmup, flush, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        p.step(kap, src, gd)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()                                  # evict the inputs from L2 between steps
+        ev[s][0].record(stream)
+        p.local(kap, src)
+        ev[s][1].record(stream)
+        p.skeleton(gd)
+        ev[s][2].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
+    local_ms = np.array([a.elapsed_time(b) for a, b, c in ev])
+    return step_ms, local_ms
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -178,8 +231,6 @@ def run_ours(args, w, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    precision = mhm.MHM_MIXED if args.precision == "mixed" else mhm.MHM_FP64
-    p = Pipeline.for_workload(w, local_rank, precision)
     kap_host = W.kappa_for(w)
     kap = torch.as_tensor(kap_host, device=dev).contiguous()
     src, gd = source_of(w), dirichlet_of(w)
@@ -190,41 +241,28 @@ def run_ours(args, w, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        p.step(kap, src, gd)
-    torch.cuda.synchronize()
-    assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
-
+    p64 = Pipeline.for_workload(w, local_rank, mhm.MHM_FP64)
+    pmx = Pipeline.for_workload(w, local_rank, mhm.MHM_MIXED)
     sampler = ClockSampler(local_rank)
     sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        flush.zero_()                                  # evict the inputs from L2 between steps
-        ev[s][0].record(stream)
-        p.local(kap, src)
-        ev[s][1].record(stream)
-        p.skeleton(gd)
-        ev[s][2].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    local_ms = [a.elapsed_time(b) for a, b, c in ev]
-    t_step = float(np.sum(step_ms))
+    step64, local64 = time_path(p64, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
+    stepmx, localmx = time_path(pmx, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
     clocks = sampler.stop()
+    for p in (p64, pmx):
+        assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
+    passes = pmx.iters.double().mean().item()
 
-    # end to end through the C ABI with host buffers: kappa H2D in, skeleton (A, E, B, F) D2H out
+    # end to end through the C ABI with host buffers (mixed path): kappa H2D in,
+    # skeleton system (A, E, B, F) D2H out
     kap_pin = torch.as_tensor(kap_host).pin_memory()
-    outs = [p.A_vals, p.E, p.BK, p.FK]
+    outs = [pmx.A_vals, pmx.E, pmx.BK, pmx.FK]
     outs_pin = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
     kap_dev2 = torch.empty_like(kap)
     h2d = kap_pin.numel() * 8
     d2h = sum(o.numel() * o.element_size() for o in outs)
     for _ in range(2):
         kap_dev2.copy_(kap_pin, non_blocking=True)
-        p.step(kap_dev2, src, gd)
+        pmx.step(kap_dev2, src, gd)
         for o, h in zip(outs, outs_pin):
             h.copy_(o, non_blocking=True)
     torch.cuda.synchronize()
@@ -233,41 +271,58 @@ def run_ours(args, w, rank, world, local_rank):
     e0.record(stream)
     for _ in range(args.steps):
         kap_dev2.copy_(kap_pin, non_blocking=True)
-        p.step(kap_dev2, src, gd)
+        pmx.step(kap_dev2, src, gd)
         for o, h in zip(outs, outs_pin):
             h.copy_(o, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     t_e2e = e0.elapsed_time(e1)
 
+    t_mx, t_64 = float(stepmx.sum()), float(step64.sum())
     if world > 1:
-        tt = torch.tensor([t_step, t_e2e], device=dev)
+        tt = torch.tensor([t_mx, t_64, t_e2e], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(tt[0]), float(tt[1])
+        t_mx, t_64, t_e2e = [float(v) for v in tt]
+
+    # L2 difference of the reconstructed u (and of the multipliers) between the two paths
+    err = None
+    if not args.no_solution_check:
+        g0 = time.perf_counter()
+        lam64, _ = p64.solve_global()
+        lammx, _ = pmx.solve_global()
+        u64, _ = p64.reconstruct(kap, src)
+        umx, _ = pmx.reconstruct(kap, src)
+        torch.cuda.synchronize()
+        g1 = time.perf_counter()
+        err = {"u_rel_l2_mixed_vs_fp64": float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)),
+               "lambda_rel_l2_mixed_vs_fp64": float(torch.linalg.norm(lammx - lam64) / torch.linalg.norm(lam64)),
+               "global_solve_and_reconstruct_s_both_paths": g1 - g0}
     if rank != 0:
         return
 
-    value = world * w.n_K * args.steps / (t_step * 1e-3)
-    e2e = world * w.n_K * args.steps / (t_e2e * 1e-3)
-    # roofline of the dominant kernel (the fused local solve): FP64 pipe
-    fl = 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K
-    local_s = float(np.mean(local_ms)) * 1e-3
+    units = world * w.n_K * args.steps
+    value, v64, e2e = units / (t_mx * 1e-3), units / (t_64 * 1e-3), units / (t_e2e * 1e-3)
     pipes = mhm.mhm_measure_pipes(local_rank)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    peak_clock = clocks["sm_max_mhz"] if clocks else 2070.0
-    if precision == mhm.MHM_FP64:
-        # 2 FP64 FMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2.07 GHz over 152 SMs)
-        peak = 2 * 2 * sms * peak_clock * 1e6 / 1e12
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": fl / local_s / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": fl / local_s / 1e12 / peak, "traffic": None,
-                "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
-                "kernel": "k_local_fp64", "flops_per_launch": fl}
-    else:
-        peak = 2 * 128 * sms * peak_clock * 1e6 / 1e12
-        roof = {"bound": "alu", "pipe": "fp32", "achieved": fl / local_s / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": fl / local_s / 1e12 / peak, "traffic": None,
-                "peak_measured_microbench": pipes["fp32_gflops"] / 1e3,
-                "kernel": "k_local_mixed", "flops_per_launch": fl}
+    clk = clocks["sm_max_mhz"] if clocks else 2070.0
+    # GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal over 152 SMs at 2.07 GHz);
+    # 128 FP32 FMA per clock per SM
+    peak64 = 2 * 2 * sms * clk * 1e6 / 1e12
+    peak32 = 2 * 128 * sms * clk * 1e6 / 1e12
+    fl64 = 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K
+    t_local64 = float(local64.mean()) * 1e-3
+    t_localmx = float(localmx.mean()) * 1e-3
+    res = residual_fmas_per_pass(w)
+    fl_res = None if res is None else 2.0 * res * passes * w.n_K
+    roof_mx = {"kernel": "k_local_mixed", "bound": "alu", "pipe": "fp64 (refinement residuals)",
+               "achieved": (fl_res / t_localmx / 1e12) if fl_res else None, "peak": peak64, "unit": "TFLOP/s",
+               "frac": (fl_res / t_localmx / 1e12 / peak64) if fl_res else None, "traffic": None,
+               "flops_per_launch": fl_res, "refinement_passes_mean": passes,
+               "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
+               "fp64_equivalent_local_solve_tflops": fl64 / t_localmx / 1e12}
+    roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64", "achieved": fl64 / t_local64 / 1e12,
+               "peak": peak64, "unit": "TFLOP/s", "frac": fl64 / t_local64 / 1e12 / peak64, "traffic": None,
+               "flops_per_launch": fl64, "peak_measured_microbench": pipes["fp64_gflops"] / 1e3}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -283,17 +338,19 @@ def run_ours(args, w, rank, world, local_rank):
     line = {
         "metric": "coarse elements/s (local solves + skeleton assembly)",
         "value": value, "unit": "coarse elements/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == mhm.MHM_FP64 else "f32+f64",
-        "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": t_mx / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "n_K": w.n_K, "r": w.r, "degree": w.degree, "n_local": w.n_local,
                    "m": w.m, "l": w.l, "rhs": w.n_I + 1, "field": w.field, "seed": w.seed,
-                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
-        "local_solve_ms": float(np.mean(local_ms)),
-        "skeleton_ms": float(np.mean(np.array(step_ms) - np.array(local_ms))),
-        "roofline": roof,
+                   "precision": "mixed (FP32 factor and solves, FP64 residuals)",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "K-range shard per GPU" if world > 1 else "single GPU"},
+        "fp64_path": {"value": v64, "ms_per_step": t_64 / args.steps, "dtype": "f64", "roofline": roof_64},
+        "mixed_over_fp64": value / v64,
+        "error": err,
+        "local_solve_ms": float(localmx.mean()),
+        "skeleton_ms": float((stepmx - localmx).mean()),
+        "roofline": roof_mx,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "coarse elements/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 3 * args.steps,
@@ -309,10 +366,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solution-check", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

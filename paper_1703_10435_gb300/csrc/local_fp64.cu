@@ -187,6 +187,7 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
     }
 }
 
+template <int RPL>
 __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
     extern __shared__ double smem[];
     __shared__ KCtx c;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
         }
         // Blocked right-looking Cholesky of the level's b pivots on the augmented window
         // rows; the right-hand-side columns (all window rows) are forward-substituted.
-        blocked_cholesky_level<double, 8, 4, 2>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
+        blocked_cholesky_level<double, 8, RPL, 2>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
         // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
         for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
             int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
@@ -357,10 +358,14 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mh
     const size_t smem = ((size_t)rows * g.ld + (size_t)g.R * g.R) * sizeof(double);
     if (smem > 220 * 1024)
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window exceeds shared memory (r too large)");
-    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (rows > 128 || g.R > 64)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window rows > 128 or more than 64 right-hand sides");
+    // register shape of the warp panel: window rows per lane
+    void (*kern)(const Fp64Args) = rows <= 64 ? k_local_fp64<2> : k_local_fp64<4>;
+    MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t nblk = K1 - K0;
     if (nblk <= 0) return MHM_OK;
-    k_local_fp64<<<(unsigned)nblk, kThreads, smem, stream>>>(g);
+    kern<<<(unsigned)nblk, kThreads, smem, stream>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }

@@ -202,7 +202,8 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
             const double* Dc = D + col * ld;
             double a = 0.0;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) a = fma(w[k], Dc[v[k]], a);
+            for (int k = 0; k < 7; ++k)
+                if (w[k] != 0.0) a = fma(w[k], Dc[v[k]], a);   // zero weights: edges at right angles
             const double rn = Res[col * ld + u] - a;
             Res[col * ld + u] = rn;
             y[col * ld + u] = (float)(rn * s_u);
