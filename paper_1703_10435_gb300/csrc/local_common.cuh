@@ -318,6 +318,7 @@ __device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int 
         const int m = nr - pe;
         if (m > 0) {
             const int H = (m + 1) / 2, Wd = m + 1, total = H * Wd;
+#pragma unroll 2
             for (int e = threadIdx.x; e < total; e += blockDim.x) {
                 const int p = e / Wd, cc = e - p * Wd;
                 const bool second = cc >= m - p;
@@ -340,6 +341,7 @@ __device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int 
         // right-hand sides: rows [pe, rhs_rows)
         const int rr = rhs_rows - pe;
         if (rr > 0) {
+#pragma unroll 2
             for (int e = threadIdx.x; e < rr * ncols; e += blockDim.x) {
                 const int i = pe + e / ncols, c = e - (e / ncols) * ncols;
                 T acc = Rhs[i * ldr + c];

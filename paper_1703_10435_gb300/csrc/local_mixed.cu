@@ -260,8 +260,11 @@ constexpr int kColGroup = 4;     // columns per work item
 constexpr int kItemsPerThread = 2;
 
 __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const float* F, const int* opoff,
-                             const int* u0, float* y, float* opbuf, MCtx& c) {
-    const int R = g.R;
+                             const int* u0, float* y, float* opbuf, float* tbuf, MCtx& c) {
+    // One block barrier per level step: each step writes its result into one of two
+    // small buffers T (column-major, ld bmax) and, meanwhile, copies the previous
+    // step's result from the other buffer into y.
+    const int R = g.R, ldt = g.bmax;
     const int nsteps = 2 * g.nlev;
     const int ngroups = (R + kColGroup - 1) / kColGroup;
     uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
@@ -281,6 +284,7 @@ __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const floa
     // copies are issued by the last thread, whose work item is empty in most steps
     const bool issuer = threadIdx.x == blockDim.x - 1;
     if (issuer) issue(0);
+    int prev_lev = -1, prev_b = 0;
     for (int st = 0; st < nsteps; ++st) {
         int dir;
         const int lev = step_lev(st, &dir);
@@ -288,52 +292,68 @@ __device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const floa
         const int lo = dir == 0 ? lev - 1 : lev + 1;
         const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
         if (issuer && st + 1 < nsteps) issue(st + 1);
+        const float* tprev = tbuf + (size_t)((st + 1) & 1) * ldt * R;
+        float* tcur = tbuf + (size_t)(st & 1) * ldt * R;
+        // the previous step's result goes to y (nobody reads those entries of y now)
+        if (prev_lev >= 0) {
+            for (int t = threadIdx.x; t < prev_b * R; t += blockDim.x) {
+                const int col = t / prev_b, i = t - col * prev_b;
+                if (!c.col_frozen[col]) y[(size_t)col * g.nunk + u0[prev_lev] + i] = tprev[col * ldt + i];
+            }
+        }
         const uint32_t par = (st & 1) ? ph1 : ph0;
         if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
         if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
         const float* op = opbuf + (size_t)(st & 1) * g.opmax;
         const int work = b * ngroups;
-        const int ulev = u0[lev], ulo = bo > 0 ? u0[lo] : 0;
-        float acc[kItemsPerThread][kColGroup];
+        const int ulev = u0[lev];
+        // the level's own input: the right-hand side (forward) or the forward result
+        // (backward; for the last level it is still in the previous buffer)
+        const bool own_in_t = (st == g.nlev);
 #pragma unroll
         for (int it = 0; it < kItemsPerThread; ++it) {
             const int item = threadIdx.x + it * kThreadsM;
-#pragma unroll
-            for (int q = 0; q < kColGroup; ++q) acc[it][q] = 0.0f;
             if (item < work) {
                 const int cg = item / b, i = item - cg * b;
-                const float* ycol[kColGroup];
+                float acc[kColGroup];
+                const float* yo[kColGroup];
+                const float* yt[kColGroup];
 #pragma unroll
                 for (int q = 0; q < kColGroup; ++q) {
+                    acc[q] = 0.0f;
                     const int col = min(cg * kColGroup + q, R - 1);
-                    ycol[q] = y + (size_t)col * g.nunk;
+                    yo[q] = own_in_t ? tprev + col * ldt : y + (size_t)col * g.nunk + ulev;
+                    yt[q] = tprev + col * ldt;
                 }
+#pragma unroll 4
                 for (int k = 0; k < b; ++k) {
                     const float a = op[k * b + i];
 #pragma unroll
-                    for (int q = 0; q < kColGroup; ++q) acc[it][q] = fmaf(a, ycol[q][ulev + k], acc[it][q]);
+                    for (int q = 0; q < kColGroup; ++q) acc[q] = fmaf(a, yo[q][k], acc[q]);
                 }
+#pragma unroll 4
                 for (int k = 0; k < bo; ++k) {
                     const float a = op[(b + k) * b + i];
 #pragma unroll
-                    for (int q = 0; q < kColGroup; ++q) acc[it][q] = fmaf(a, ycol[q][ulo + k], acc[it][q]);
+                    for (int q = 0; q < kColGroup; ++q) acc[q] = fmaf(a, yt[q][k], acc[q]);
                 }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < kItemsPerThread; ++it) {
-            const int item = threadIdx.x + it * kThreadsM;
-            if (item < work) {
-                const int cg = item / b, i = item - cg * b;
 #pragma unroll
                 for (int q = 0; q < kColGroup; ++q) {
                     const int col = cg * kColGroup + q;
-                    if (col < R && !c.col_frozen[col]) y[(size_t)col * g.nunk + ulev + i] = acc[it][q];
+                    if (col < R) tcur[col * ldt + i] = acc[q];
                 }
             }
         }
+        prev_lev = lev;
+        prev_b = b;
         __syncthreads();
+    }
+    {
+        const float* tlast = tbuf + (size_t)((nsteps - 1) & 1) * ldt * R;
+        for (int t = threadIdx.x; t < prev_b * R; t += blockDim.x) {
+            const int col = t / prev_b, i = t - col * prev_b;
+            if (!c.col_frozen[col]) y[(size_t)col * g.nunk + u0[prev_lev] + i] = tlast[col * ldt + i];
+        }
     }
     if (threadIdx.x == 0) {
         c.phase[0] = ph0;
@@ -352,6 +372,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
     double* kap_s = reinterpret_cast<double*>(smem_raw + g.off_kap_smem);   // kappa of the current K (if staged)
     double* scale = reinterpret_cast<double*>(g.ws + (size_t)blockIdx.x * g.slot_bytes + g.off_scale);   // 1/sqrt(diag A_p)
     float* opbuf = W;                                                   // 2 x opmax staging (solves only)
+    float* tbuf = W + 2 * (size_t)g.opmax;                              // 2 x bmax x R level results (solves only)
     __shared__ MCtx c;
     const LevelGeom lg{g.P, g.N, g.PN};
     const int R = g.R;
@@ -589,7 +610,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             Z[t] = 0.0;
         }
         __syncthreads();
-        solve_factor(g, lg, F, loff, u0, y, opbuf, c);
+        solve_factor(g, lg, F, loff, u0, y, opbuf, tbuf, c);
         __syncthreads();
         column_dot(g, Res, y, scale, c.gamma, c);      // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
         __syncthreads();
@@ -635,7 +656,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
             __syncthreads();
             if (c.all_done) break;
-            solve_factor(g, lg, F, loff, u0, y, opbuf, c);
+            solve_factor(g, lg, F, loff, u0, y, opbuf, tbuf, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.eps, c);
             __syncthreads();
@@ -775,7 +796,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.slot_bytes = L.off_D + al((size_t)L.nunk * R * sizeof(double));
     size_t win = (size_t)L.wrows * L.wld;
     if (win < (size_t)R * R * 2) win = (size_t)R * R * 2;
-    if (win < (size_t)2 * L.opmax) win = (size_t)2 * L.opmax;
+    if (win < (size_t)2 * L.opmax + (size_t)2 * bmax * R) win = (size_t)2 * L.opmax + (size_t)2 * bmax * R;
     win = (win + 3) & ~(size_t)3;
     L.wfloats = (int)win;
     size_t yf = (size_t)L.nunk * R;
@@ -786,7 +807,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
     off = (off + 15) & ~(size_t)15;
     const size_t nf = (size_t)N * N;
-    L.kap_in_smem = nf <= 1024;
+    L.kap_in_smem = 0;   // kappa is read from global memory (L2-resident after first touch)
     L.off_kap_smem = off;
     off += L.kap_in_smem ? nf * sizeof(double) : 0;
     L.off_scale_smem = 0;
