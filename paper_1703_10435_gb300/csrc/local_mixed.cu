@@ -18,6 +18,7 @@
 //     N~_j^T z = N_j^T z - c_j m^T z (N_j lives on one face only).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -33,12 +34,13 @@ constexpr int kWarpsM = kThreadsM / 32;
 struct MixedArgs {
     DeviceMesh dm;
     const double* kappa;
-    int P, N, PN, dpf, NI, R, nlev, nunk;
+    int P, N, PN, dpf, NI, R, Rp, nlev, nunk;   // Rp: row length of y (= R)
     int wrows, wld;               // FP32 window rows and leading dimension
     int wfloats;                  // floats reserved for the window (also holds R x R doubles)
-    int yfloats;                  // floats reserved for the right-hand-side block (>= nunk R)
+    int yfloats;                  // floats reserved for the right-hand-side block (>= nunk Rp)
     int bmax;                     // largest level size
-    int opmax;                    // floats of the largest level operator (multiple of 4)
+    int opmax;                    // floats of the largest level operator (fragment order, multiple of 128)
+    int stage_floats;             // floats of one staged solve operand (fragment order)
     int ldr;                      // leading dimension of the level right-hand sides (multiple of 4)
     int src_kind;
     double src_value, src_freq;
@@ -47,10 +49,16 @@ struct MixedArgs {
     double tol;
     char* ws;
     size_t slot_bytes, off_G, off_Z, off_mass, off_scale, off_D;
-    size_t off_kap_smem, off_scale_smem;
+    size_t off_kap_smem, off_scale_smem, off_sinfo, off_cw;
     int kap_in_smem;
     double *AK, *EK, *BK, *FK;
     int32_t *status, *iters;
+    // level-Schur operators computed by the factor kernel for the chunk [Kc0, K1)
+    float* Tall;                  // t_stride floats per K
+    float* cwall;                 // 4 nunk floats per K
+    int* fbad;                    // pivot flag per K
+    int64_t Kc0;
+    size_t t_stride;
 };
 
 struct MCtx {
@@ -76,8 +84,6 @@ struct MCtx {
     uint32_t phase[2];
     int timeout;
 };
-
-__device__ __forceinline__ int lev_size(const LevelGeom& lg, int lev) { return lg.size(lev); }
 
 // Fine-triangle vertices in physical coordinates.
 __device__ __forceinline__ void fine_xy(const MCtx& c, int N, bool up, int i, int j, double X[3][2]) {
@@ -168,6 +174,28 @@ __device__ __forceinline__ void lattice_of_unk(int PN, int u, int* X, int* Y) {
     *Y = y;
 }
 
+// The assembled P1 row of unknown u at lattice point (x, yl): the weights of u and
+// of its six lattice neighbours (east, west, north, south, south-east, north-west:
+// the edges of the six fine triangles around it) and their unknown indices.  A
+// neighbour outside K, the pinned DOF, or an edge of zero weight (a right angle)
+// gets weight 0 and index u.
+__device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su, const double* Sd, const double* kap,
+                                       int x, int yl, int u, double w[7], int v[7]) {
+    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
+    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
+    const double k1 = kup(x, yl), k2 = kup(x - 1, yl), k3 = kup(x, yl - 1);
+    const double k4 = kdn(x - 1, yl - 1), k5 = kdn(x - 1, yl), k6 = kdn(x, yl - 1);
+    w[0] = k1 * Su[0] + k2 * Su[4] + k3 * Su[8] + k4 * Sd[4] + k5 * Sd[0] + k6 * Sd[8];  v[0] = u;
+    w[1] = k1 * Su[1] + k6 * Sd[7];  v[1] = unk(PN, x + 1, yl);        // east
+    w[2] = k2 * Su[3] + k4 * Sd[5];  v[2] = unk(PN, x - 1, yl);        // west
+    w[3] = k1 * Su[2] + k5 * Sd[1];  v[3] = unk(PN, x, yl + 1);        // north
+    w[4] = k3 * Su[6] + k4 * Sd[3];  v[4] = unk(PN, x, yl - 1);        // south
+    w[5] = k3 * Su[7] + k6 * Sd[6];  v[5] = unk(PN, x + 1, yl - 1);    // south-east
+    w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(PN, x - 1, yl + 1);    // north-west
+    for (int k = 1; k < 7; ++k)
+        if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
+}
+
 // Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
 // FP32 right-hand side y(u, :) = s_u Res(u, :): the sum over
 // the fine triangles T containing u of kappa_T S_T[a_u][b] D(b).  P1 uses the
@@ -179,24 +207,9 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
     lattice_of_unk(g.PN, u, &X, &Y);
     const size_t ld = (size_t)g.nunk;
     if (g.P == 1) {
-        const int N = g.N, x = X, yl = Y;
-        auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
-        auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
-        const double k1 = kup(x, yl), k2 = kup(x - 1, yl), k3 = kup(x, yl - 1);
-        const double k4 = kdn(x - 1, yl - 1), k5 = kdn(x - 1, yl), k6 = kdn(x, yl - 1);
-        const double* Su = c.Sup;
-        const double* Sd = c.Sdn;
         double w[7];
         int v[7];
-        w[0] = k1 * Su[0] + k2 * Su[4] + k3 * Su[8] + k4 * Sd[4] + k5 * Sd[0] + k6 * Sd[8];  v[0] = u;
-        w[1] = k1 * Su[1] + k6 * Sd[7];  v[1] = unk(g.PN, x + 1, yl);        // east
-        w[2] = k2 * Su[3] + k4 * Sd[5];  v[2] = unk(g.PN, x - 1, yl);        // west
-        w[3] = k1 * Su[2] + k5 * Sd[1];  v[3] = unk(g.PN, x, yl + 1);        // north
-        w[4] = k3 * Su[6] + k4 * Sd[3];  v[4] = unk(g.PN, x, yl - 1);        // south
-        w[5] = k3 * Su[7] + k6 * Sd[6];  v[5] = unk(g.PN, x + 1, yl - 1);    // south-east
-        w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(g.PN, x - 1, yl + 1);    // north-west
-        for (int k = 1; k < 7; ++k)
-            if (w[k] == 0.0 || v[k] < 0 || v[k] >= g.nunk) { w[k] = 0.0; v[k] = u; }
+        p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
         for (int col = 0; col < g.R; ++col) {
             if (c.col_done[col]) continue;
             const double* Dc = D + col * ld;
@@ -206,7 +219,7 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
                 if (w[k] != 0.0) a = fma(w[k], Dc[v[k]], a);   // zero weights: edges at right angles
             const double rn = Res[col * ld + u] - a;
             Res[col * ld + u] = rn;
-            y[col * ld + u] = (float)(rn * s_u);
+            y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
         }
         return;
     }
@@ -229,155 +242,488 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
         }
         const double rn = Res[col * ld + u] - a;
         Res[col * ld + u] = rn;
-        y[col * ld + u] = (float)(rn * s_u);
+        y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
     }
 }
 
 // out[c] = sum_u Res(u, c) s(u) y(u, c) for the columns still refining (warp per
 // column, fixed summation order).
-__device__ void column_dot(const MixedArgs& g, const double* Res, const float* y, const double* s, double* out,
+__device__ __noinline__ void column_dot(const MixedArgs& g, const double* Res, const float* y, const double* s, double* out,
                            const MCtx& c) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int col = warp; col < g.R; col += kWarpsM) {
         if (c.col_frozen[col]) continue;
         const double* rc = Res + (size_t)col * g.nunk;
-        const float* yc = y + (size_t)col * g.nunk;
         float a = 0.0f;   // an error estimate: FP32 is ample
-        for (int u = lane; u < g.nunk; u += 32) a = fmaf((float)rc[u] * (float)s[u], yc[u], a);
+        for (int u = lane; u < g.nunk; u += 32) a = fmaf((float)rc[u] * (float)s[u], y[(size_t)u * g.Rp + col], a);
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) out[col] = (double)a;
     }
 }
 
 // Forward + backward solve of L L^T D = Y in FP32 for every column still
-// refining, in place in y (column-major, nunk per column).  Level by level,
-//   forward   y_lev = Fw_lev [y_lev; y_{lev-1}],  Fw_lev = [L_lev^{-1} | -L_lev^{-1} L_{lev,lev-1}]
-//   backward  x_lev = Bw_lev [y_lev; x_{lev+1}],  Bw_lev = [L_lev^{-T} | -L_lev^{-T} L_{lev+1,lev}^T]
-// so each step is one small dense product over all columns.  The operators are
-// stored column-major ((b + b') x b) and streamed into two shared-memory buffers
-// by bulk asynchronous copies: the copy for step s+1 runs while step s computes.
-constexpr int kColGroup = 4;     // columns per work item
-constexpr int kItemsPerThread = 2;
+// refining, in place in y (node-major: y[u * R + col]).  Level by level,
+//   forward   y_lev = Fw_lev [y_{lev-1}; y_lev],  Fw_lev = [-L_lev^{-1} L_{lev,lev-1} | L_lev^{-1}]
+//   backward  x_lev = Bw_lev [x_{lev+1}; y_lev],  Bw_lev = [-L_lev^{-T} L_{lev+1,lev}^T | L_lev^{-T}]
+// so each step is one small dense product T = Op B (b x K times K x R,
+// K = b' + b, the neighbouring level's rows first).  It runs on the tensor
+// cores as warp-level m16n8k8 TF32 products with a three-term split of both
+// operands (x = hi + lo, both TF32; hi*hi + hi*lo + lo*hi in FP32
+// accumulators), which keeps FP32 accuracy (hi keeps the 10 leading mantissa
+// bits that the tensor core reads, lo = x - hi is exact in FP32, and the
+// product drops lo*lo and the bits of lo below TF32: about 2^-20 relative):
+// one warp per 16 x 8 output tile,
+// its operands read as one 16-byte and one 8-byte shared load per 8 x 8 block.
+// Op is stored by the factorisation in fragment order; B is staged in fragment
+// order by the step before (its result tiles, which become the next level's
+// neighbouring rows, and the next level's own rows copied from y), double
+// buffered, so a step needs one block barrier.  The operators stream into two
+// shared-memory buffers by bulk asynchronous copies, the copy for step s+1
+// running while step s computes.
+// Split by masking (the rounding conversion is a slow multi-cycle instruction here).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds1(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts1(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
 
-__device__ void solve_factor(const MixedArgs& g, const LevelGeom& lg, const float* F, const int* opoff,
-                             const int* u0, float* y, float* opbuf, float* tbuf, MCtx& c) {
-    // One block barrier per level step: each step writes its result into one of two
-    // small buffers T (column-major, ld bmax) and, meanwhile, copies the previous
-    // step's result from the other buffer into y.
-    const int R = g.R, ldt = g.bmax;
+// Fragment positions (floats).  A operand (row-major 16 x 8 tiles, tile (mt, kt)
+// of KT k-tiles, 128 floats each): lane = 4 g + t holds A[g][t], A[g+8][t],
+// A[g][t+4], A[g+8][t+4] at 4 lane + 0..3 (the factorisation writes this order).
+// B operand (8 x 8 tiles, tile (kt, nt) of NT n-tiles): lane = 4 g + t holds B[t][g], B[t+4][g].
+__device__ __forceinline__ int frag_b_pos(int k, int n, int NT) {
+    const int lane = (n & 7) * 4 + (k & 3);
+    return (((k >> 3) * NT + (n >> 3)) * 32 + lane) * 2 + ((k >> 2) & 1);
+}
+// Floats of an operator of b rows and K columns in fragment order.
+__host__ __device__ __forceinline__ int frag_op_floats(int b, int K) {
+    return ((b + 15) / 16) * ((K + 7) / 8) * 128;
+}
+
+// One warp's 16 x 8 output tile: C = sum over the KT k-tiles of A(mt, kt) B(kt, nt)
+// with the three-term split, in three independent accumulator chains (hi*hi,
+// hi*lo, lo*hi) summed at the end.  KT > 0 is a compile-time trip count (the
+// loop is fully unrolled and scheduled); KT = 0 takes the run-time count kt_n.
+template <int KT>
+__device__ __forceinline__ void tile_product(uint32_t aa, uint32_t ba, uint32_t bstep, int kt_n, float (&c)[4]) {
+    float chh[4] = {0.f, 0.f, 0.f, 0.f}, chl[4] = {0.f, 0.f, 0.f, 0.f}, clh[4] = {0.f, 0.f, 0.f, 0.f};
+    const int n = KT > 0 ? KT : kt_n;
+    float4 av = lds4(aa);
+    float2 bv = lds2(ba);
+#pragma unroll
+    for (int kt = 0; kt < n; ++kt) {
+        float4 an = av;
+        float2 bn = bv;
+        if (kt + 1 < n) {
+            aa += 512u;
+            ba += bstep;
+            an = lds4(aa);
+            bn = lds2(ba);
+        }
+        uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+        split_tf32(av.x, ah[0], al[0]);
+        split_tf32(av.y, ah[1], al[1]);
+        split_tf32(av.z, ah[2], al[2]);
+        split_tf32(av.w, ah[3], al[3]);
+        split_tf32(bv.x, bh0, bl0);
+        split_tf32(bv.y, bh1, bl1);
+        mma_tf32(chh, ah, bh0, bh1);
+        mma_tf32(chl, ah, bl0, bl1);
+        mma_tf32(clh, al, bh0, bh1);
+        av = an;
+        bv = bn;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c[e] = chh[e] + (chl[e] + clh[e]);
+}
+
+// Per solve step, built once per block: (b | bo << 8, ulev | uo << 16, unused,
+// operator offset in floats).
+__device__ __forceinline__ int4 solve_step_info(const LevelGeom& lg, int nlev, const int* opoff, const int* u0,
+                                                int st) {
+    const int dir = st >= nlev, lev = dir ? 2 * nlev - 1 - st : st;
+    const int b = lg.size(lev);
+    const int lo = dir == 0 ? lev - 1 : lev + 1;
+    const int bo = (lo >= 0 && lo < nlev) ? lg.size(lo) : 0;
+    return make_int4(b | (bo << 8), u0[lev] | ((bo > 0 ? u0[lo] : 0) << 16), 0, opoff[2 * lev + dir]);
+}
+
+// Copies the own rows (b rows from y row u) of a step into B-fragment order at
+// k = bo + i.  Element t = threadIdx.x + j * blockDim.x of the b x R block is
+// (i0 + j rq + carry, c0 + j rr - carry R): (i0, c0, rq, rr) precomputed per solve.
+__device__ __forceinline__ void stage_own(uint32_t y_s, uint32_t stg, int R, int NT, int b, int bo, int u, int i0,
+                                          int c0, int rq, int rr) {
+    int i = i0, col = c0;
+    for (int t = threadIdx.x; t < b * R; t += kThreadsM) {
+        sts1(stg + 4u * frag_b_pos(bo + i, col, NT), lds1(y_s + 4u * (uint32_t)((u + i) * R + col)));
+        i += rq;
+        col += rr;
+        if (col >= R) { col -= R; ++i; }
+    }
+}
+
+__device__ __noinline__ void solve_factor(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
+                                          float* opbuf, float* stage, MCtx& c) {
+    const int R = g.R, NT = (R + 7) >> 3;
     const int nsteps = 2 * g.nlev;
-    const int ngroups = (R + kColGroup - 1) / kColGroup;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const uint32_t y_s = smem_u32(y), op_s = smem_u32(opbuf), st_s = smem_u32(stage);
     uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
-    auto step_lev = [&](int st, int* dir) { *dir = st >= g.nlev; return *dir ? nsteps - 1 - st : st; };
+    const int si0 = threadIdx.x / R, sc0 = threadIdx.x - si0 * R, srq = kThreadsM / R, srr = kThreadsM - srq * R;
+    uint64_t frozen = 0;
+    for (int col = 0; col < R; ++col)
+        if (c.col_frozen[col]) frozen |= 1ull << col;
     auto issue = [&](int st) {
-        int dir;
-        const int lev = step_lev(st, &dir);
-        const int b = lg.size(lev);
-        const int lo = dir == 0 ? lev - 1 : lev + 1;
-        const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
-        const uint32_t bytes = (uint32_t)(((b * (b + bo) + 3) & ~3) * sizeof(float));
-        float* dst = opbuf + (size_t)(st & 1) * g.opmax;
+        const int4 si = sinfo[st];
+        const int b = si.x & 0xff, bo = si.x >> 8;
+        const uint32_t bytes = (uint32_t)frag_op_floats(b, b + bo) * 4u;
         fence_proxy_async_shared();
         mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
-        bulk_copy_g2s(dst, F + opoff[2 * lev + dir], bytes, &c.bar[st & 1]);
+        bulk_copy_g2s(opbuf + (size_t)(st & 1) * g.opmax, F + si.w, bytes, &c.bar[st & 1]);
     };
-    // copies are issued by the last thread, whose work item is empty in most steps
-    const bool issuer = threadIdx.x == blockDim.x - 1;
+    // copies are issued by lane 0 of the last warp, which holds no output tile while
+    // a level has at most 7 (16 x 8) tiles
+    const bool issuer = threadIdx.x == kThreadsM - 32;
     if (issuer) issue(0);
-    int prev_lev = -1, prev_b = 0;
+    // both staging buffers start at zero (padding columns stay zero); step 0's rows
+    for (int t = threadIdx.x; t < 2 * g.stage_floats; t += kThreadsM) stage[t] = 0.0f;
+    __syncthreads();
+    {
+        const int4 si = sinfo[0];
+        stage_own(y_s, st_s, R, NT, si.x & 0xff, si.x >> 8, si.y & 0xffff, si0, sc0, srq, srr);
+    }
+    __syncthreads();
     for (int st = 0; st < nsteps; ++st) {
-        int dir;
-        const int lev = step_lev(st, &dir);
-        const int b = lg.size(lev);
-        const int lo = dir == 0 ? lev - 1 : lev + 1;
-        const int bo = (lo >= 0 && lo < g.nlev) ? lg.size(lo) : 0;
+        const int4 si = sinfo[st];
+        const int b = si.x & 0xff, bo = si.x >> 8;
+        const int ulev = si.y & 0xffff;
+        const int K = b + bo, KT = (K + 7) >> 3, MT = (b + 15) >> 4;
+        // the other operator buffer was last read in step st-1, which ended with a barrier
         if (issuer && st + 1 < nsteps) issue(st + 1);
-        const float* tprev = tbuf + (size_t)((st + 1) & 1) * ldt * R;
-        float* tcur = tbuf + (size_t)(st & 1) * ldt * R;
-        // the previous step's result goes to y (nobody reads those entries of y now)
-        if (prev_lev >= 0) {
-            for (int t = threadIdx.x; t < prev_b * R; t += blockDim.x) {
-                const int col = t / prev_b, i = t - col * prev_b;
-                if (!c.col_frozen[col]) y[(size_t)col * g.nunk + u0[prev_lev] + i] = tprev[col * ldt + i];
-            }
-        }
         const uint32_t par = (st & 1) ? ph1 : ph0;
         if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
         if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
-        const float* op = opbuf + (size_t)(st & 1) * g.opmax;
-        const int work = b * ngroups;
-        const int ulev = u0[lev];
-        // the level's own input: the right-hand side (forward) or the forward result
-        // (backward; for the last level it is still in the previous buffer)
-        const bool own_in_t = (st == g.nlev);
+        const uint32_t op0 = op_s + (uint32_t)((st & 1) * g.opmax) * 4u;
+        const uint32_t sb0 = st_s + (uint32_t)((st & 1) * g.stage_floats) * 4u;
+        const uint32_t sb1 = st_s + (uint32_t)(((st + 1) & 1) * g.stage_floats) * 4u;
+        for (int q = warp; q < MT * NT; q += kWarpsM) {
+            const int mt = q / NT, nt = q - mt * NT;
+            const uint32_t aa = op0 + (uint32_t)(((mt * KT) * 32 + lane) * 16);
+            const uint32_t ba = sb0 + (uint32_t)((nt * 32 + lane) * 8);
+            const uint32_t bstep = (uint32_t)(NT * 32 * 8);
+            float cv[4];
+            switch (KT) {
+                case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
+                case 2: tile_product<2>(aa, ba, bstep, KT, cv); break;
+                case 3: tile_product<3>(aa, ba, bstep, KT, cv); break;
+                case 4: tile_product<4>(aa, ba, bstep, KT, cv); break;
+                case 5: tile_product<5>(aa, ba, bstep, KT, cv); break;
+                case 6: tile_product<6>(aa, ba, bstep, KT, cv); break;
+                case 7: tile_product<7>(aa, ba, bstep, KT, cv); break;
+                case 8: tile_product<8>(aa, ba, bstep, KT, cv); break;
+                default: tile_product<0>(aa, ba, bstep, KT, cv); break;
+            }
+            // C tile: rows mt*16 + gq (+8), columns nt*8 + 2 tq (+1).  Result rows go to y
+            // (columns still refining) and, as k = i, to the next step's operand.
 #pragma unroll
-        for (int it = 0; it < kItemsPerThread; ++it) {
-            const int item = threadIdx.x + it * kThreadsM;
-            if (item < work) {
-                const int cg = item / b, i = item - cg * b;
-                float acc[kColGroup];
-                const float* yo[kColGroup];
-                const float* yt[kColGroup];
-#pragma unroll
-                for (int q = 0; q < kColGroup; ++q) {
-                    acc[q] = 0.0f;
-                    const int col = min(cg * kColGroup + q, R - 1);
-                    yo[q] = own_in_t ? tprev + col * ldt : y + (size_t)col * g.nunk + ulev;
-                    yt[q] = tprev + col * ldt;
-                }
-#pragma unroll 4
-                for (int k = 0; k < b; ++k) {
-                    const float a = op[k * b + i];
-#pragma unroll
-                    for (int q = 0; q < kColGroup; ++q) acc[q] = fmaf(a, yo[q][k], acc[q]);
-                }
-#pragma unroll 4
-                for (int k = 0; k < bo; ++k) {
-                    const float a = op[(b + k) * b + i];
-#pragma unroll
-                    for (int q = 0; q < kColGroup; ++q) acc[q] = fmaf(a, yt[q][k], acc[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < kColGroup; ++q) {
-                    const int col = cg * kColGroup + q;
-                    if (col < R) tcur[col * ldt + i] = acc[q];
+            for (int e = 0; e < 4; ++e) {
+                const int i = mt * 16 + gq + 8 * (e >> 1), col = nt * 8 + 2 * tq + (e & 1);
+                if (i < b && col < R) {
+                    const float v = cv[e];
+                    if (!(frozen >> col & 1)) sts1(y_s + 4u * (uint32_t)((ulev + i) * R + col), v);
+                    if (st + 1 < nsteps) sts1(sb1 + 4u * frag_b_pos(i, col, NT), v);
                 }
             }
         }
-        prev_lev = lev;
-        prev_b = b;
-        __syncthreads();
-    }
-    {
-        const float* tlast = tbuf + (size_t)((nsteps - 1) & 1) * ldt * R;
-        for (int t = threadIdx.x; t < prev_b * R; t += blockDim.x) {
-            const int col = t / prev_b, i = t - col * prev_b;
-            if (!c.col_frozen[col]) y[(size_t)col * g.nunk + u0[prev_lev] + i] = tlast[col * ldt + i];
+        // the next step's own rows (at the turn from forward to backward they are this
+        // step's result, already staged above)
+        if (st + 1 < nsteps && st + 1 != g.nlev) {
+            const int4 sn = sinfo[st + 1];
+            stage_own(y_s, sb1, R, NT, sn.x & 0xff, sn.x >> 8, sn.y & 0xffff, si0, sc0, srq, srr);
         }
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         c.phase[0] = ph0;
         c.phase[1] = ph1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// P1 levels of at most 32 unknowns: block LDL^T by level Schur complements.
+//
+// With s = D^-1/2 (unit diagonal after scaling), level lev couples to the level
+// below only through each point's south and south-east edges: C_lev (b_lev x
+// b_{lev-1}) has two entries per row.  The scaled matrix factors as
+// A = L diag(S_lev) L^T, L_{lev,lev-1} = C_lev T_{lev-1}, T = S^-1, with
+//   S_0 = A_00,   S_lev = A_{lev,lev} - C_lev T_{lev-1} C_lev^T,
+// so each level needs one sparse update (four entries of T_{lev-1} per entry of
+// S_lev) and one dense inverse T_lev, computed by Gauss-Jordan elimination in a
+// warp's registers (row p in lane p; SPD: no pivoting).  A solve is then
+//   forward   v_lev = T_lev (r_lev - C_lev v_{lev-1})
+//   backward  x_lev = v_lev - T_lev (C_{lev+1}^T x_{lev+1})
+// one b x b tensor-core product per level step, with T_lev stored once for both
+// directions.  Couplings cw (scaled, FP32): [east | west | south | south-east] x nunk.
+constexpr int kSchurMax = 32;     // largest level handled by this path
+constexpr int kSLd = kSchurMax + 1;
+
+// Row k travels through shared memory (rowbuf: 2 x 32 floats per warp, row k
+// published unscaled by lane k); every lane applies a[j] -= g_k r[j] with
+// g_k = a_ik / a_kk, or 1 - 1/a_kk in lane k (which turns its row into r / a_kk).
+__device__ __noinline__ void gauss_jordan_warp(const float* Sb, float* Tb, float* rowbuf, int b, int lev, int* bad) {
+    const int lane = threadIdx.x & 31;
+    float a[kSchurMax];
+#pragma unroll
+    for (int j = 0; j < kSchurMax; ++j) a[j] = (lane < b && j < b) ? Sb[lane * kSLd + j] : (lane == j ? 1.0f : 0.0f);
+#pragma unroll
+    for (int k = 0; k < kSchurMax; ++k) {
+        if (k < b) {
+            float* rb = rowbuf + (k & 1) * kSchurMax;
+            if (lane == k) {
+#pragma unroll
+                for (int j = 0; j < kSchurMax; j += 4)
+                    *reinterpret_cast<float4*>(rb + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+            }
+            __syncwarp();
+            float r[kSchurMax];
+#pragma unroll
+            for (int j = 0; j < kSchurMax; j += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(rb + j);
+                r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
+            }
+            const float piv = r[k];
+            if (lane == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
+            const float d = __frcp_rn(piv);
+            const float gk = lane == k ? 1.0f - d : a[k] * d;
+#pragma unroll
+            for (int j = 0; j < kSchurMax; ++j)
+                if (j < b) a[j] = fmaf(-gk, r[j], a[j]);
+            a[k] = lane == k ? d : -gk;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kSchurMax; ++j) Tb[lane * kSLd + j] = a[j];
+}
+
+// T (b x b, row-major ld kSLd in shared memory) to global memory in fragment order,
+// zero beyond b; tiles are distributed over the warps [w0, w0 + nw) of the caller.
+__device__ __forceinline__ void write_frag_op(const float* Tb, int b, float* dst, int w0, int nw) {
+    const int KT = (b + 7) >> 3, MT = (b + 15) >> 4, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int tile = warp - w0; tile < MT * KT; tile += nw) {
+        const int mt = tile / KT, kt = tile - mt * KT;
+        const int i0 = mt * 16 + g, i1 = i0 + 8, k0 = kt * 8 + t, k1 = k0 + 4;
+        float4 v;
+        v.x = (i0 < b && k0 < b) ? Tb[i0 * kSLd + k0] : 0.0f;
+        v.y = (i1 < b && k0 < b) ? Tb[i1 * kSLd + k0] : 0.0f;
+        v.z = (i0 < b && k1 < b) ? Tb[i0 * kSLd + k1] : 0.0f;
+        v.w = (i1 < b && k1 < b) ? Tb[i1 * kSLd + k1] : 0.0f;
+        reinterpret_cast<float4*>(dst)[tile * 32 + lane] = v;
+    }
+}
+
+// S_lev = A_{lev,lev} - C_lev T_{lev-1} C_lev^T (row-major, ld kSLd): this thread's row
+// p (if p < b), columns q0, q0 + qstride, ...
+__device__ __forceinline__ void schur_update(const float* cwE, const float* cwW, const float* cwS, const float* cwSE,
+                                             const float* Tb, float* Sb, int lev, int b, int ul, int p, int q0,
+                                             int qstride) {
+    const int off = lev == 1 ? 1 : 0;   // level 0 starts at x = 1 (the pinned point)
+    if (p < b) {
+        const float cps = lev > 0 ? cwS[ul + p] : 0.0f, cpse = lev > 0 ? cwSE[ul + p] : 0.0f;
+        const int ps = p - off, pse = p + 1 - off;
+        for (int q = q0; q < b; q += qstride) {
+            float sv = p == q ? 1.0f : (q == p + 1 ? cwE[ul + p] : (q == p - 1 ? cwW[ul + p] : 0.0f));
+            if (lev > 0) {
+                const int qs = q - off, qse = q + 1 - off;
+                const float cqs = cwS[ul + q], cqse = cwSE[ul + q];
+                float acc = cpse * Tb[pse * kSLd + qse] * cqse;
+                if (qs >= 0) acc = fmaf(cpse * Tb[pse * kSLd + qs], cqs, acc);
+                if (ps >= 0) {
+                    acc = fmaf(cps * Tb[ps * kSLd + qse], cqse, acc);
+                    if (qs >= 0) acc = fmaf(cps * Tb[ps * kSLd + qs], cqs, acc);
+                }
+                sv -= acc;
+            }
+            Sb[p * kSLd + q] = sv;
+        }
+    }
+}
+
+// Factor pass: T_lev for every level, written to the scratch slot (F + loff[lev]) in
+// tensor-core fragment order.  Sb, Tb: kSchurMax x kSLd floats of shared memory.
+__device__ __noinline__ void schur_factor(const MixedArgs& g, const int* loff, const int* u0, const float* cw,
+                                          float* Sb, float* Tb, float* rowbuf, float* F, MCtx& c) {
+    const LevelGeom lg{g.P, g.N, g.PN};
+    const int nu = g.nunk;
+    for (int lev = 0; lev < g.nlev; ++lev) {
+        const int b = lg.size(lev);
+        schur_update(cw, cw + nu, cw + 2 * nu, cw + 3 * nu, Tb, Sb, lev, b, u0[lev], threadIdx.x & 31, threadIdx.x >> 5,
+                     kWarpsM);
+        __syncthreads();
+        if (threadIdx.x < 32) gauss_jordan_warp(Sb, Tb, rowbuf, b, lev, &c.bad);
+        __syncthreads();
+        write_frag_op(Tb, b, F + loff[lev], 0, kWarpsM);   // Tb stays for the next level's update
+    }
+    fence_proxy_async_global();   // T is read back by bulk copies
     __syncthreads();
 }
 
+// Per solve step of this path: (b | dir << 8, ulev | uo << 16, b_other | lev << 16, T offset).
+__device__ __forceinline__ int4 schur_step_info(const LevelGeom& lg, int nlev, const int* loff, const int* u0,
+                                                int st) {
+    const int dir = st >= nlev, lev = dir ? 2 * nlev - 2 - st : st;
+    const int lo = dir ? lev + 1 : lev - 1;
+    const int bo = (lo >= 0 && lo < nlev) ? lg.size(lo) : 0;
+    return make_int4(lg.size(lev) | (dir << 8), u0[lev] | ((bo > 0 ? u0[lo] : 0) << 16), bo | (lev << 16), loff[lev]);
+}
+
+__device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
+                                         const float* cw, float* opbuf, float* stage, MCtx& c) {
+    const int R = g.R, NT = (R + 7) >> 3, nu = g.nunk;
+    const int nsteps = 2 * g.nlev - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const uint32_t y_s = smem_u32(y), op_s = smem_u32(opbuf), st_s = smem_u32(stage);
+    const float* cwS = cw + 2 * nu;
+    const float* cwSE = cw + 3 * nu;
+    uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
+    uint64_t frozen = 0;
+    for (int col = 0; col < R; ++col)
+        if (c.col_frozen[col]) frozen |= 1ull << col;
+    const int si0 = threadIdx.x / R, sc0 = threadIdx.x - si0 * R, srq = kThreadsM / R, srr = kThreadsM - srq * R;
+    auto issue = [&](int st) {
+        const int4 si = sinfo[st];
+        const uint32_t bytes = (uint32_t)frag_op_floats(si.x & 0xff, si.x & 0xff) * 4u;
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
+        bulk_copy_g2s(opbuf + (size_t)(st & 1) * g.opmax, F + si.w, bytes, &c.bar[st & 1]);
+    };
+    // lane 0 of the last warp issues the copies (it holds no output tile while a level has <= 7 tiles)
+    const bool issuer = threadIdx.x == kThreadsM - 32;
+    if (issuer) issue(0);
+    for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
+    __syncthreads();
+    for (int st = 0; st < nsteps; ++st) {
+        const int4 si = sinfo[st];
+        const int b = si.x & 0xff, dir = si.x >> 8;
+        const int ulev = si.y & 0xffff, uo = si.y >> 16;
+        const int bo = si.z & 0xffff, lev = si.z >> 16;
+        if (issuer && st + 1 < nsteps) issue(st + 1);
+        // B (b x R) in fragment order: forward r_lev - C_lev v_{lev-1}; backward C_{lev+1}^T x_{lev+1}
+        {
+            const int xo = lev == 0 ? 1 : 0;       // lattice x of position 0
+            const int off = lev == 1 ? 1 : 0;      // level below starts at x = 1
+            int i = si0, col = sc0;
+            for (int t = threadIdx.x; t < b * R; t += kThreadsM) {
+                const int x = i + xo;
+                float v;
+                if (dir == 0) {
+                    v = lds1(y_s + 4u * (uint32_t)((ulev + i) * R + col));
+                    if (lev > 0) {
+                        const int ps = x - off, pse = x + 1 - off;
+                        float a = cwSE[ulev + i] * lds1(y_s + 4u * (uint32_t)((uo + pse) * R + col));
+                        if (ps >= 0) a = fmaf(cwS[ulev + i], lds1(y_s + 4u * (uint32_t)((uo + ps) * R + col)), a);
+                        v -= a;
+                    }
+                } else {
+                    v = 0.0f;
+                    if (x < bo) v = cwS[uo + x] * lds1(y_s + 4u * (uint32_t)((uo + x) * R + col));
+                    if (x >= 1) v = fmaf(cwSE[uo + x - 1], lds1(y_s + 4u * (uint32_t)((uo + x - 1) * R + col)), v);
+                }
+                sts1(st_s + 4u * frag_b_pos(i, col, NT), v);
+                i += srq;
+                col += srr;
+                if (col >= R) { col -= R; ++i; }
+            }
+        }
+        const uint32_t par = (st & 1) ? ph1 : ph0;
+        if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
+        if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        __syncthreads();
+        const int KT = (b + 7) >> 3, MT = (b + 15) >> 4;
+        const uint32_t op0 = op_s + (uint32_t)((st & 1) * g.opmax) * 4u;
+        for (int q = warp; q < MT * NT; q += kWarpsM) {
+            const int mt = q / NT, nt = q - mt * NT;
+            const uint32_t aa = op0 + (uint32_t)(((mt * KT) * 32 + lane) * 16);
+            const uint32_t ba = st_s + (uint32_t)((nt * 32 + lane) * 8);
+            const uint32_t bstep = (uint32_t)(NT * 32 * 8);
+            float cv[4];
+            switch (KT) {
+                case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
+                case 2: tile_product<2>(aa, ba, bstep, KT, cv); break;
+                case 3: tile_product<3>(aa, ba, bstep, KT, cv); break;
+                default: tile_product<4>(aa, ba, bstep, KT, cv); break;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = mt * 16 + gq + 8 * (e >> 1), col = nt * 8 + 2 * tq + (e & 1);
+                if (i < b && col < R && !(frozen >> col & 1)) {
+                    const uint32_t ya = y_s + 4u * (uint32_t)((ulev + i) * R + col);
+                    sts1(ya, dir == 0 ? cv[e] : lds1(ya) - cv[e]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        c.phase[0] = ph0;
+        c.phase[1] = ph1;
+    }
+}
+
+// The level factorisation, the solves and the column dots run out of line: each
+// then keeps its working set (register panel, accumulator tiles) in registers
+// instead of sharing the kernel's register budget with the per-K state live
+// around it.
 template <int RPL, int CPL>
+__device__ __noinline__ void cholesky_level_f32(float* M, int ld, int b, int nr, float* Rhs, int ldr, int rhs_rows,
+                                                int ncols, int* bad) {
+    blocked_cholesky_level<float, 8, RPL, CPL>(M, ld, b, nr, Rhs, ldr, rhs_rows, ncols, bad);
+}
+
+// MODE 0: generic level operators (Cholesky); 1: level Schur complements factored in
+// this kernel; 2: level Schur operators precomputed by k_schur_factor.
+template <int RPL, int CPL, int MODE>
 __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g) {
+    constexpr bool SCHUR = MODE >= 1;
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
     float* y = W + (size_t)g.wfloats;                                    // nunk x R
     int* loff = reinterpret_cast<int*>(y + (size_t)g.yfloats);         // 2 nlev operator offsets (Fw, Bw)
     int* u0 = loff + 2 * g.nlev;                                        // nlev + 1 level starts
+    int4* sinfo = reinterpret_cast<int4*>(smem_raw + g.off_sinfo);      // 2 nlev solve steps
     double* kap_s = reinterpret_cast<double*>(smem_raw + g.off_kap_smem);   // kappa of the current K (if staged)
     double* scale = reinterpret_cast<double*>(g.ws + (size_t)blockIdx.x * g.slot_bytes + g.off_scale);   // 1/sqrt(diag A_p)
     float* opbuf = W;                                                   // 2 x opmax staging (solves only)
-    float* tbuf = W + 2 * (size_t)g.opmax;                              // 2 x bmax x R level results (solves only)
+    float* stage = W + 2 * (size_t)g.opmax;                             // staged solve operand(s) (solves only)
+    float* cw = reinterpret_cast<float*>(smem_raw + g.off_cw);          // level-Schur path: 4 x nunk couplings
     __shared__ MCtx c;
     const LevelGeom lg{g.P, g.N, g.PN};
     const int R = g.R;
     char* slot = g.ws + (size_t)blockIdx.x * g.slot_bytes;
-    float* F = reinterpret_cast<float*>(slot);
+    float* F = reinterpret_cast<float*>(slot);   // level operators (MODE 2: per K, set below)
     double* G = reinterpret_cast<double*>(slot + g.off_G);
     double* Z = reinterpret_cast<double*>(slot + g.off_Z);
     double* mass = reinterpret_cast<double*>(slot + g.off_mass);
@@ -387,14 +733,23 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         for (int lev = 0; lev < g.nlev; ++lev) {
             const int b = lg.size(lev), bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
             const int bp = lev > 0 ? lg.size(lev - 1) : 0;
-            loff[2 * lev] = o;                       // 16-byte aligned operator starts
-            o += (b * (b + bp) + 3) & ~3;
-            loff[2 * lev + 1] = o;
-            o += (b * (b + bn) + 3) & ~3;
+            if (SCHUR) {
+                loff[lev] = o;                       // T_lev in fragment order
+                o += frag_op_floats(b, b);
+            } else {
+                loff[2 * lev] = o;                   // operators in fragment order (16-byte aligned)
+                o += frag_op_floats(b, b + bp);
+                loff[2 * lev + 1] = o;
+                o += frag_op_floats(b, b + bn);
+            }
             u0[lev] = u;
             u += b;
         }
         u0[g.nlev] = u;
+        if (SCHUR)
+            for (int st = 0; st < 2 * g.nlev - 1; ++st) sinfo[st] = schur_step_info(lg, g.nlev, loff, u0, st);
+        else
+            for (int st = 0; st < 2 * g.nlev; ++st) sinfo[st] = solve_step_info(lg, g.nlev, loff, u0, st);
         mbar_init(&c.bar[0], 1);
         mbar_init(&c.bar[1], 1);
         c.phase[0] = 0;
@@ -508,92 +863,135 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
         }
 
-        // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
-        const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
-        float* Rhs = y;                               // level right-hand sides (y is free while factoring)
-        for (int t = threadIdx.x; t < (b0 + b1) * g.wld; t += blockDim.x) W[t] = 0.0f;
-        for (int t = threadIdx.x; t < b0 * b0; t += blockDim.x) {
-            const int i = t / b0, k = t - i * b0;
-            Rhs[i * g.ldr + k] = k == i ? 1.0f : 0.0f;
-        }
-        __syncthreads();   // (also publishes scale[] to the block)
-        for (int lev = 0; lev < g.nlev; ++lev) {
-            const int b = lg.size(lev);
-            const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
-            const int nr = b + bn;
-            if (bn > 0) {
-                // element matrices of fine row lev in four colour classes
-                const int P = g.P, N = g.N, nb = P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
-                for (int cls = 0; cls < 4; ++cls) {
-                    const bool up = cls < 2;
-                    const int parity = cls & 1;
-                    const int ntri = up ? N - lev : N - 1 - lev;
-                    const int ncls = (ntri - parity + 1) / 2;
-                    for (int t = threadIdx.x; t < ncls * npair; t += blockDim.x) {
-                        const int ti = t / npair, item = t - ti * npair;
-                        const int i = parity + 2 * ti;
-                        int nx[6], ny[6];
-                        element_nodes(P, up, i, lev, nx, ny);
-                        const double kt = kap[kap_index(N, up, i, lev)];
-                        const double* S = up ? c.Sup : c.Sdn;
-                        int a = 0, rem = item;
-                        while (rem >= nb - a) { rem -= nb - a; ++a; }
-                        const int bb = a + rem;
-                        const int pa = lg.pos(nx[a], ny[a]), pb = lg.pos(nx[bb], ny[bb]);
-                        if (pa < 0 || pb < 0) continue;
-                        const int ra = pa + (lg.level_of_row(ny[a]) == lev ? 0 : b);
-                        const int rb = pb + (lg.level_of_row(ny[bb]) == lev ? 0 : b);
-                        const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-                        // symmetric diagonal scaling: the FP32 factor is of D^-1/2 A_p D^-1/2
-                        const double sab = scale[unk(g.PN, nx[a], ny[a])] * scale[unk(g.PN, nx[bb], ny[bb])];
-                        W[hi * g.wld + lo] += (float)(kt * S[a * nb + bb] * sab);
-                    }
-                    __syncthreads();
-                }
-            }
-            // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
-            // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
-            const int bp = lev > 0 ? lg.size(lev - 1) : 0;
-            blocked_cholesky_level<float, 8, RPL, CPL>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
-            {
-                // Fw (column-major (b + bp) x b) and Bw = [Linv^T | -Linv^T L_{lev+1,lev}^T]
-                // (column-major (b + bn) x b) to this block's scratch slot
-                float* Fw = F + loff[2 * lev];
-                float* Bw = F + loff[2 * lev + 1];
-                for (int t = threadIdx.x; t < b * (b + bp); t += blockDim.x) {
-                    const int k = t / b, i = t - k * b;
-                    Fw[t] = Rhs[i * g.ldr + k];
-                }
-                for (int t = threadIdx.x; t < b * (b + bn); t += blockDim.x) {
-                    const int k = t / b, i = t - k * b;
-                    float v;
-                    if (k < b) v = Rhs[k * g.ldr + i];
-                    else {
-                        const float* cn = W + (size_t)(b + (k - b)) * g.wld;
-                        float a = 0.0f;
-                        for (int mm = i; mm < b; ++mm) a = fmaf(Rhs[mm * g.ldr + i], cn[mm], a);
-                        v = -a;
-                    }
-                    Bw[t] = v;
-                }
-                fence_proxy_async_global();   // the operators are read back by bulk copies
-                __syncthreads();
-                // right-hand sides of the next level: [I_bn | -L_{lev+1,lev}]
-                for (int t = threadIdx.x; t < bn * (bn + b); t += blockDim.x) {
-                    const int i = t / (bn + b), k = t - i * (bn + b);
-                    Rhs[i * g.ldr + k] = k < bn ? (k == i ? 1.0f : 0.0f) : -W[(size_t)(b + i) * g.wld + (k - bn)];
-                }
+        if constexpr (MODE == 2) {
+            // ---- precomputed level-Schur operators of this K: couplings to shared memory
+            __syncthreads();
+            const int64_t kk = K - g.Kc0;
+            F = g.Tall + kk * (int64_t)g.t_stride;
+            const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
+            for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
+            if (threadIdx.x == 0) c.bad = g.fbad[kk];
+            __syncthreads();
+        } else if constexpr (MODE == 1) {
+            // ---- FP32 factorisation by level Schur complements: scaled couplings first
+            __syncthreads();   // (publishes scale[] to the block)
+            for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) {
+                int X, Y;
+                lattice_of_unk(g.PN, u, &X, &Y);
+                double w[7];
+                int v[7];
+                p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
+                const double su = scale[u];
+                cw[u] = (float)(w[1] * su * scale[v[1]]);
+                cw[g.nunk + u] = (float)(w[2] * su * scale[v[2]]);
+                cw[2 * g.nunk + u] = (float)(w[4] * su * scale[v[4]]);
+                cw[3 * g.nunk + u] = (float)(w[5] * su * scale[v[5]]);
             }
             __syncthreads();
-            if (bn > 0) {
-                for (int t = threadIdx.x; t < bn * bn; t += blockDim.x) {
-                    const int i = t / bn, jj = t - i * bn;
-                    if (jj <= i) W[i * g.wld + jj] = W[(b + i) * g.wld + b + jj];
+            schur_factor(g, loff, u0, cw, W, W + kSchurMax * kSLd, W + 2 * kSchurMax * kSLd, F, c);
+        } else {
+            // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
+            const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
+            float* Rhs = y;                               // level right-hand sides (y is free while factoring)
+            for (int t = threadIdx.x; t < (b0 + b1) * g.wld; t += blockDim.x) W[t] = 0.0f;
+            for (int t = threadIdx.x; t < b0 * b0; t += blockDim.x) {
+                const int i = t / b0, k = t - i * b0;
+                Rhs[i * g.ldr + k] = k == i ? 1.0f : 0.0f;
+            }
+            __syncthreads();   // (also publishes scale[] to the block)
+            for (int lev = 0; lev < g.nlev; ++lev) {
+                const int b = lg.size(lev);
+                const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
+                const int nr = b + bn;
+                if (bn > 0) {
+                    // element matrices of fine row lev in four colour classes
+                    const int P = g.P, N = g.N, nb = P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
+                    for (int cls = 0; cls < 4; ++cls) {
+                        const bool up = cls < 2;
+                        const int parity = cls & 1;
+                        const int ntri = up ? N - lev : N - 1 - lev;
+                        const int ncls = (ntri - parity + 1) / 2;
+                        for (int t = threadIdx.x; t < ncls * npair; t += blockDim.x) {
+                            const int ti = t / npair, item = t - ti * npair;
+                            const int i = parity + 2 * ti;
+                            int nx[6], ny[6];
+                            element_nodes(P, up, i, lev, nx, ny);
+                            const double kt = kap[kap_index(N, up, i, lev)];
+                            const double* S = up ? c.Sup : c.Sdn;
+                            int a = 0, rem = item;
+                            while (rem >= nb - a) { rem -= nb - a; ++a; }
+                            const int bb = a + rem;
+                            const int pa = lg.pos(nx[a], ny[a]), pb = lg.pos(nx[bb], ny[bb]);
+                            if (pa < 0 || pb < 0) continue;
+                            const int ra = pa + (lg.level_of_row(ny[a]) == lev ? 0 : b);
+                            const int rb = pb + (lg.level_of_row(ny[bb]) == lev ? 0 : b);
+                            const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+                            // symmetric diagonal scaling: the FP32 factor is of D^-1/2 A_p D^-1/2
+                            const double sab = scale[unk(g.PN, nx[a], ny[a])] * scale[unk(g.PN, nx[bb], ny[bb])];
+                            W[hi * g.wld + lo] += (float)(kt * S[a * nb + bb] * sab);
+                        }
+                        __syncthreads();
+                    }
+                }
+                // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
+                // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
+                const int bp = lev > 0 ? lg.size(lev - 1) : 0;
+                cholesky_level_f32<RPL, CPL>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
+                {
+                    // Fw = [-Linv L_{lev,lev-1} | Linv] (b x (bp + b)) and
+                    // Bw = [-Linv^T L_{lev+1,lev}^T | Linv^T] (b x (bn + b)) to this block's scratch
+                    // slot in tensor-core fragment order, zero beyond the operator
+                    float* Fw = F + loff[2 * lev];
+                    float* Bw = F + loff[2 * lev + 1];
+                    {
+                        const int K = bp + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
+                        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                            const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
+                            const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
+                            const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
+                            float v = 0.0f;
+                            if (i < b && k < K) v = k < bp ? Rhs[i * g.ldr + b + k] : Rhs[i * g.ldr + (k - bp)];
+                            Fw[t] = v;
+                        }
+                    }
+                    {
+                        const int K = bn + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
+                        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                            const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
+                            const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
+                            const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
+                            float v = 0.0f;
+                            if (i < b && k < K) {
+                                if (k >= bn) v = Rhs[(k - bn) * g.ldr + i];
+                                else {
+                                    const float* cn = W + (size_t)(b + k) * g.wld;
+                                    float a = 0.0f;
+                                    for (int mm = i; mm < b; ++mm) a = fmaf(Rhs[mm * g.ldr + i], cn[mm], a);
+                                    v = -a;
+                                }
+                            }
+                            Bw[t] = v;
+                        }
+                    }
+                    fence_proxy_async_global();   // the operators are read back by bulk copies
+                    __syncthreads();
+                    // right-hand sides of the next level: [I_bn | -L_{lev+1,lev}]
+                    for (int t = threadIdx.x; t < bn * (bn + b); t += blockDim.x) {
+                        const int i = t / (bn + b), k = t - i * (bn + b);
+                        Rhs[i * g.ldr + k] = k < bn ? (k == i ? 1.0f : 0.0f) : -W[(size_t)(b + i) * g.wld + (k - bn)];
+                    }
                 }
                 __syncthreads();
-                const int bnn = lev + 2 < g.nlev ? lg.size(lev + 2) : 0;
-                for (int t = threadIdx.x; t < bnn * g.wld; t += blockDim.x) W[bn * g.wld + t] = 0.0f;
-                __syncthreads();
+                if (bn > 0) {
+                    for (int t = threadIdx.x; t < bn * bn; t += blockDim.x) {
+                        const int i = t / bn, jj = t - i * bn;
+                        if (jj <= i) W[i * g.wld + jj] = W[(b + i) * g.wld + b + jj];
+                    }
+                    __syncthreads();
+                    const int bnn = lev + 2 < g.nlev ? lg.size(lev + 2) : 0;
+                    for (int t = threadIdx.x; t < bnn * g.wld; t += blockDim.x) W[bn * g.wld + t] = 0.0f;
+                    __syncthreads();
+                }
             }
         }
 
@@ -605,12 +1003,14 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         double* Res = G;
         double* D64 = reinterpret_cast<double*>(slot + g.off_D);
         const int total = g.nunk * R;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            y[t] = (float)(Res[t] * scale[t % g.nunk]);
-            Z[t] = 0.0;
+        for (int t = threadIdx.x; t < g.nunk * g.Rp; t += blockDim.x) {
+            const int u = t / g.Rp, col = t - u * g.Rp;
+            y[t] = col < R ? (float)(Res[(size_t)col * g.nunk + u] * scale[u]) : 0.0f;
         }
+        for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
         __syncthreads();
-        solve_factor(g, lg, F, loff, u0, y, opbuf, tbuf, c);
+        if constexpr (SCHUR) solve_schur(g, F, sinfo, y, cw, opbuf, stage, c);
+        else solve_factor(g, F, sinfo, y, opbuf, stage, c);
         __syncthreads();
         column_dot(g, Res, y, scale, c.gamma, c);      // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
         __syncthreads();
@@ -634,9 +1034,9 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         while (!c.all_done) {
             // D = s . y (FP64), Z += D
             for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int col = t / g.nunk;
+                const int col = t / g.nunk, u = t - col * g.nunk;
                 if (c.col_done[col]) continue;
-                const double d = (double)y[t] * scale[t - col * g.nunk];
+                const double d = (double)y[(size_t)u * g.Rp + col] * scale[u];
                 D64[t] = d;
                 Z[t] += d;
             }
@@ -656,7 +1056,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
             __syncthreads();
             if (c.all_done) break;
-            solve_factor(g, lg, F, loff, u0, y, opbuf, tbuf, c);
+            if constexpr (SCHUR) solve_schur(g, F, sinfo, y, cw, opbuf, stage, c);
+            else solve_factor(g, F, sinfo, y, opbuf, stage, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.eps, c);
             __syncthreads();
@@ -753,14 +1154,111 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
     }
 }
 
-struct MixedLayout {
-    int nlev, nunk, wrows, wld, wfloats, yfloats, bmax, opmax, ldr;
-    size_t factor_floats, slot_bytes, off_G, off_Z, off_mass, off_scale, off_D, smem;
-    size_t off_kap_smem, off_scale_smem;
-    int kap_in_smem, rpl, cpl;
+// ---------------------------------------------------------------------------
+// The level-Schur factorisation as its own kernel: one warp per coarse triangle
+// (four per 128-thread block).  Each factorisation is a long chain of small
+// dependent steps (a Gauss-Jordan inverse per level); run one per warp, many of
+// them share an SM instead of each holding a whole block of the solve kernel.
+// Per K of the chunk [Kc0, K1) it writes T_lev of every level (fragment order,
+// t_stride floats), the scaled couplings (4 x nunk floats) and the pivot flag.
+constexpr int kFactorWarps = 4;
+
+struct FactorSmem {   // per warp
+    float Sb[kSchurMax * kSLd];
+    float Tb[kSchurMax * kSLd];
+    alignas(16) float rowbuf[2 * kSchurMax];
+    double Su[9], Sd[9];
+    int bad;
 };
 
-MixedLayout mixed_layout(const mhm_mesh* mesh) {
+__global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedArgs g) {
+    extern __shared__ unsigned char fs_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t K = g.Kc0 + (int64_t)blockIdx.x * kFactorWarps + warp;
+    if (K >= g.K1) return;
+    FactorSmem& fs = reinterpret_cast<FactorSmem*>(fs_raw)[warp];
+    const int nu = g.nunk;
+    double* scale = reinterpret_cast<double*>(fs_raw + kFactorWarps * sizeof(FactorSmem)) + (size_t)warp * nu;
+    const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+    const int64_t kk = K - g.Kc0;
+    float* cw = g.cwall + kk * 4 * (int64_t)nu;
+    float* T = g.Tall + kk * (int64_t)g.t_stride;
+    if (lane == 0) {
+        // the two fine-triangle shapes (up and down) of the uniform refinement
+        double V[3][2];
+        for (int v = 0; v < 3; ++v) {
+            V[v][0] = g.dm.geom[6 * K + 2 * v];
+            V[v][1] = g.dm.geom[6 * K + 2 * v + 1];
+        }
+        const double e1x = (V[1][0] - V[0][0]) / g.N, e1y = (V[1][1] - V[0][1]) / g.N;
+        const double e2x = (V[2][0] - V[0][0]) / g.N, e2y = (V[2][1] - V[0][1]) / g.N;
+        const double Xu[3][2] = {{V[0][0], V[0][1]}, {V[0][0] + e1x, V[0][1] + e1y}, {V[0][0] + e2x, V[0][1] + e2y}};
+        const double Xd[3][2] = {{V[0][0] + e1x, V[0][1] + e1y},
+                                 {V[0][0] + e1x + e2x, V[0][1] + e1y + e2y},
+                                 {V[0][0] + e2x, V[0][1] + e2y}};
+        element_stiffness(1, Xu, fs.Su);
+        element_stiffness(1, Xd, fs.Sd);
+        fs.bad = 0;
+    }
+    __syncwarp();
+    for (int u = lane; u < nu; u += 32) {
+        int X, Y;
+        lattice_of_unk(g.PN, u, &X, &Y);
+        double w[7];
+        int v[7];
+        p1_row(g.N, g.PN, nu, fs.Su, fs.Sd, kap, X, Y, u, w, v);
+        scale[u] = 1.0 / sqrt(w[0]);
+    }
+    __syncwarp();
+    for (int u = lane; u < nu; u += 32) {
+        int X, Y;
+        lattice_of_unk(g.PN, u, &X, &Y);
+        double w[7];
+        int v[7];
+        p1_row(g.N, g.PN, nu, fs.Su, fs.Sd, kap, X, Y, u, w, v);
+        const double su = scale[u];
+        cw[u] = (float)(w[1] * su * scale[v[1]]);
+        cw[nu + u] = (float)(w[2] * su * scale[v[2]]);
+        cw[2 * nu + u] = (float)(w[4] * su * scale[v[4]]);
+        cw[3 * nu + u] = (float)(w[5] * su * scale[v[5]]);
+    }
+    __syncwarp();
+    const LevelGeom lg{1, g.N, g.PN};
+    int ul = 0, o = 0;
+    for (int lev = 0; lev < g.nlev; ++lev) {
+        const int b = lg.size(lev);
+        schur_update(cw, cw + nu, cw + 2 * nu, cw + 3 * nu, fs.Tb, fs.Sb, lev, b, ul, lane, 0, 1);
+        __syncwarp();
+        gauss_jordan_warp(fs.Sb, fs.Tb, fs.rowbuf, b, lev, &fs.bad);
+        __syncwarp();
+        write_frag_op(fs.Tb, b, T + o, warp, 1);
+        __syncwarp();
+        o += frag_op_floats(b, b);
+        ul += b;
+    }
+    if (lane == 0) g.fbad[kk] = fs.bad;
+}
+
+size_t factor_smem_bytes(int nunk) {
+    return kFactorWarps * (sizeof(FactorSmem) + (size_t)nunk * sizeof(double));
+}
+
+struct MixedLayout {
+    int nlev, nunk, wrows, wld, wfloats, yfloats, bmax, opmax, ldr, Rp, stage_floats;
+    size_t factor_floats, slot_bytes, off_G, off_Z, off_mass, off_scale, off_D, smem;
+    size_t off_kap_smem, off_scale_smem, off_sinfo, off_cw;
+    int kap_in_smem, rpl, cpl;
+    bool schur;   // P1 with levels of at most kSchurMax unknowns: level-Schur factorisation
+    int mode;     // kernel MODE (0 generic, 1 Schur in the kernel, 2 Schur by k_schur_factor)
+    size_t chunk_k_bytes;   // MODE 2: scratch per K of a chunk (T, couplings, pivot flag)
+};
+
+constexpr int64_t kChunkMax = 8192;   // MODE 2: coarse triangles per factor + solve launch pair
+
+// split: the level-Schur path factors in k_schur_factor (MODE 2) instead of in the
+// solve kernel (MODE 1; the allocation-free entry, whose scratch cannot hold the
+// per-K operators of a whole chunk).
+MixedLayout mixed_layout(const mhm_mesh* mesh, bool split = true) {
     MixedLayout L{};
     const int P = mesh->desc.degree, N = mesh->N;
     auto size = [&](int lev) {
@@ -770,16 +1268,24 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     };
     L.nlev = N + 1;
     L.nunk = (int)mesh->nloc - 1;
+    int bmax = 0;
+    for (int lev = 0; lev < L.nlev; ++lev) bmax = std::max(bmax, size(lev));
+    L.schur = P == 1 && bmax <= kSchurMax && mesh->NI + 1 <= 64;
+    L.mode = L.schur ? (split ? 2 : 1) : 0;
     size_t f = 0;
-    int bmax = 0, opmax = 0;
+    int opmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) {
         const int b = size(lev), bn = lev + 1 < L.nlev ? size(lev + 1) : 0;
         const int bp = lev > 0 ? size(lev - 1) : 0;
-        const int fw = (b * (b + bp) + 3) & ~3, bw = (b * (b + bn) + 3) & ~3;
-        f += (size_t)fw + bw;
-        if (b > bmax) bmax = b;
-        if (fw > opmax) opmax = fw;
-        if (bw > opmax) opmax = bw;
+        if (L.schur) {
+            const int t = frag_op_floats(b, b);
+            f += (size_t)t;
+            opmax = std::max(opmax, t);
+        } else {
+            const int fw = frag_op_floats(b, b + bp), bw = frag_op_floats(b, b + bn);
+            f += (size_t)fw + bw;
+            opmax = std::max(opmax, std::max(fw, bw));
+        }
     }
     L.bmax = bmax;
     L.opmax = opmax;
@@ -788,7 +1294,8 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.wld = (L.wrows + 4) & ~3;   // rows 16-byte aligned for the vector panel loads
     const int R = (int)mesh->NI + 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    L.off_G = al(f * sizeof(float));
+    L.off_G = L.mode == 2 ? 0 : al(f * sizeof(float));   // MODE 2 keeps the operators outside the slots
+    L.chunk_k_bytes = al(f * sizeof(float)) + al((size_t)4 * L.nunk * sizeof(float)) + 256;
     L.off_Z = L.off_G + al((size_t)L.nunk * R * sizeof(double));
     L.off_mass = L.off_Z + al((size_t)L.nunk * R * sizeof(double));
     L.off_scale = L.off_mass + al((size_t)L.nunk * sizeof(double));
@@ -796,13 +1303,28 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.slot_bytes = L.off_D + al((size_t)L.nunk * R * sizeof(double));
     size_t win = (size_t)L.wrows * L.wld;
     if (win < (size_t)R * R * 2) win = (size_t)R * R * 2;
-    if (win < (size_t)2 * L.opmax + (size_t)2 * bmax * R) win = (size_t)2 * L.opmax + (size_t)2 * bmax * R;
+    // staged solve operand: K-tiles x n-tiles x 64 floats, K = b + b' of the largest step
+    L.Rp = R;
+    int ktmax = 0;
+    for (int lev = 0; lev < L.nlev; ++lev) {
+        const int b = size(lev), bn = lev + 1 < L.nlev ? size(lev + 1) : 0, bp = lev > 0 ? size(lev - 1) : 0;
+        ktmax = std::max(ktmax, (b + std::max(bn, bp) + 7) / 8);
+    }
+    if (L.schur) {
+        // one staged operand of K = b; the factorisation's S and T (kSchurMax x kSLd each)
+        L.stage_floats = ((bmax + 7) / 8) * ((R + 7) / 8) * 64;
+        win = std::max((size_t)2 * L.opmax + (size_t)L.stage_floats, (size_t)R * R * 2);
+        if (L.mode == 1) win = std::max(win, (size_t)2 * kSchurMax * kSLd + 2 * kSchurMax);   // S, T, pivot rows
+    } else {
+        L.stage_floats = ktmax * ((R + 7) / 8) * 64;
+        if (win < (size_t)2 * L.opmax + (size_t)2 * L.stage_floats) win = (size_t)2 * L.opmax + (size_t)2 * L.stage_floats;
+    }
     win = (win + 3) & ~(size_t)3;
     L.wfloats = (int)win;
-    size_t yf = (size_t)L.nunk * R;
+    size_t yf = (size_t)L.nunk * L.Rp;
     if (yf < (size_t)2 * R * 64) yf = (size_t)2 * R * 64;   // also holds two R x 64 staging chunks
     L.ldr = (2 * bmax + 3) & ~3;
-    if (yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
+    if (!L.schur && yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
     size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
     off = (off + 15) & ~(size_t)15;
@@ -811,6 +1333,11 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
     L.off_kap_smem = off;
     off += L.kap_in_smem ? nf * sizeof(double) : 0;
     L.off_scale_smem = 0;
+    off = (off + 15) & ~(size_t)15;
+    L.off_sinfo = off;
+    off += (size_t)2 * L.nlev * 16;
+    L.off_cw = off;
+    if (L.schur) off += (size_t)4 * L.nunk * sizeof(float);
     L.smem = (off + 15) & ~(size_t)15;
     // register shape of the warp panel: rows (window) and right-hand-side columns per lane
     int ncols = 0;
@@ -818,7 +1345,8 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
         const int c = size(lev) + (lev > 0 ? size(lev - 1) : 0);
         if (c > ncols) ncols = c;
     }
-    if (L.wrows <= 64 && ncols <= 96) { L.rpl = 2; L.cpl = 3; }
+    if (L.schur) { L.rpl = 2; L.cpl = 3; }
+    else if (L.wrows <= 64 && ncols <= 96) { L.rpl = 2; L.cpl = 3; }
     else if (L.wrows <= 128 && ncols <= 128) { L.rpl = 4; L.cpl = 4; }
     else { L.rpl = 0; L.cpl = 0; }
     return L;
@@ -827,8 +1355,10 @@ MixedLayout mixed_layout(const mhm_mesh* mesh) {
 using MixedKernel = void (*)(const MixedArgs);
 
 MixedKernel mixed_kernel(const MixedLayout& L) {
-    if (L.rpl == 2) return k_local_mixed<2, 3>;
-    if (L.rpl == 4) return k_local_mixed<4, 4>;
+    if (L.mode == 2) return k_local_mixed<2, 3, 2>;
+    if (L.mode == 1) return k_local_mixed<2, 3, 1>;
+    if (L.rpl == 2) return k_local_mixed<2, 3, 0>;
+    if (L.rpl == 4) return k_local_mixed<4, 4, 0>;
     return nullptr;
 }
 
@@ -845,6 +1375,61 @@ int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
 
 }  // namespace
 
+namespace {
+
+int64_t chunk_of(const mhm_mesh* mesh, const MixedLayout& L) {
+    return L.mode == 2 ? std::min<int64_t>(mesh->nK, kChunkMax) : 0;
+}
+
+MixedArgs mixed_args(const mhm_mesh* mesh, const MixedLayout& L, const double* kappa, const mhm_source& f,
+                     const mhm_solve_opts& o, double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                     int32_t* iters, char* ws) {
+    MixedArgs g{};
+    g.dm = mesh->dev();
+    g.kappa = kappa;
+    g.P = mesh->desc.degree;
+    g.N = mesh->N;
+    g.PN = mesh->PN;
+    g.dpf = mesh->dpf;
+    g.NI = (int)mesh->NI;
+    g.R = g.NI + 1;
+    g.Rp = L.Rp;
+    g.nlev = L.nlev;
+    g.nunk = L.nunk;
+    g.wrows = L.wrows;
+    g.wld = L.wld;
+    g.wfloats = L.wfloats;
+    g.yfloats = L.yfloats;
+    g.bmax = L.bmax;
+    g.opmax = L.opmax;
+    g.stage_floats = L.stage_floats;
+    g.ldr = L.ldr;
+    g.src_kind = f.kind;
+    g.src_value = f.value;
+    g.src_freq = f.freq;
+    g.it_max = o.it_max;
+    g.tol = o.tol;
+    g.ws = ws;
+    g.slot_bytes = L.slot_bytes;
+    g.off_G = L.off_G;
+    g.off_Z = L.off_Z;
+    g.off_mass = L.off_mass;
+    g.off_scale = L.off_scale;
+    g.off_D = L.off_D;
+    g.off_kap_smem = L.off_kap_smem;
+    g.off_scale_smem = L.off_scale_smem;
+    g.off_sinfo = L.off_sinfo;
+    g.off_cw = L.off_cw;
+    g.kap_in_smem = L.kap_in_smem;
+    g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
+    g.status = status;
+    g.iters = iters;
+    g.t_stride = L.factor_floats;
+    return g;
+}
+
+}  // namespace
+
 size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     if (mesh->device < 0) return 0;
     const MixedLayout L = mixed_layout(mesh);
@@ -852,7 +1437,7 @@ size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(mesh->device);
-    const size_t bytes = (size_t)mixed_slots(mesh, L) * L.slot_bytes;
+    const size_t bytes = (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(mesh, L) * L.chunk_k_bytes;
     cudaSetDevice(cur);
     return bytes;
 }
@@ -864,58 +1449,44 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     const MixedLayout L = mixed_layout(mesh);
     if (L.smem > 220 * 1024 || !mixed_kernel(L))
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED buffers exceed shared memory (r too large)");
-    // the level solves map (row, group of 8 columns) to threads: one pass per block
-    if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED level x columns too large for one block");
     const int slots = mixed_slots(mesh, L);
-    if (ws_bytes < (size_t)slots * L.slot_bytes)
+    const int64_t chunk = chunk_of(mesh, L);
+    const size_t slots_bytes = (size_t)slots * L.slot_bytes;
+    if (ws_bytes < slots_bytes + (size_t)chunk * L.chunk_k_bytes)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
-    MixedArgs g;
-    g.dm = mesh->dev();
-    g.kappa = kappa;
-    g.P = mesh->desc.degree;
-    g.N = mesh->N;
-    g.PN = mesh->PN;
-    g.dpf = mesh->dpf;
-    g.NI = (int)mesh->NI;
-    g.R = g.NI + 1;
-    g.nlev = L.nlev;
-    g.nunk = L.nunk;
-    g.wrows = L.wrows;
-    g.wld = L.wld;
-    g.wfloats = L.wfloats;
-    g.yfloats = L.yfloats;
-    g.bmax = L.bmax;
-    g.opmax = L.opmax;
-    g.ldr = L.ldr;
-    g.src_kind = f.kind;
-    g.src_value = f.value;
-    g.src_freq = f.freq;
-    g.K0 = K0;
-    g.K1 = K1;
-    g.it_max = opts.it_max;
-    g.tol = opts.tol;
-    g.ws = (char*)workspace;
-    g.slot_bytes = L.slot_bytes;
-    g.off_G = L.off_G;
-    g.off_Z = L.off_Z;
-    g.off_mass = L.off_mass;
-    g.off_scale = L.off_scale;
-    g.off_D = L.off_D;
-    g.off_kap_smem = L.off_kap_smem;
-    g.off_scale_smem = L.off_scale_smem;
-    g.kap_in_smem = L.kap_in_smem;
-    g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
-    g.status = status;
-    g.iters = iters;
+    MixedArgs g = mixed_args(mesh, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
-    const int grid = (int)(nK < slots ? nK : slots);
-    mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
-    MHM_CUDA_TRY(cudaGetLastError());
+    if (L.mode != 2) {
+        g.K0 = K0;
+        g.K1 = K1;
+        const int grid = (int)(nK < slots ? nK : slots);
+        mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
+        MHM_CUDA_TRY(cudaGetLastError());
+        return MHM_OK;
+    }
+    // MODE 2: per chunk, the factor kernel writes T, couplings and pivot flags behind the
+    // slots; the solve kernel reads them (stream order separates the two)
+    char* cbase = (char*)workspace + slots_bytes;
+    const size_t tb = (size_t)chunk * ((L.factor_floats * sizeof(float) + 255) & ~(size_t)255);
+    g.Tall = reinterpret_cast<float*>(cbase);
+    g.cwall = reinterpret_cast<float*>(cbase + tb);
+    g.fbad = reinterpret_cast<int*>(cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float));
+    const size_t fsmem = factor_smem_bytes(L.nunk);
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    for (int64_t c0 = K0; c0 < K1; c0 += chunk) {
+        const int64_t c1 = std::min(K1, c0 + chunk);
+        g.Kc0 = c0;
+        g.K0 = c0;
+        g.K1 = c1;
+        k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, stream>>>(g);
+        MHM_CUDA_TRY(cudaGetLastError());
+        const int grid = (int)(c1 - c0 < slots ? c1 - c0 : slots);
+        mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
+        MHM_CUDA_TRY(cudaGetLastError());
+    }
     return MHM_OK;
 }
-
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the mixed-precision local solve.
@@ -960,11 +1531,9 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: K range out of bounds");
     if (o.it_max < 1 || !(o.tol > 0.0))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: it_max >= 1 and tol > 0 required");
-    const MixedLayout L = mixed_layout(mesh);
+    const MixedLayout L = mixed_layout(mesh, false);   // factor inside the solve kernel
     if (L.smem > 220 * 1024 || !mixed_kernel(L))
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
-    if (L.bmax * (((int)mesh->NI + 1 + kColGroup - 1) / kColGroup) > kItemsPerThread * kThreadsM)
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: level x columns too large for one block");
     if (L.slot_bytes > kStaticScratch)
         return fail(MHM_ERR_INVALID_ARG,
                     "mhm_local_solve_batch_noalloc: one coarse element needs " + std::to_string(L.slot_bytes) +
@@ -989,44 +1558,9 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
     int64_t grid = mixed_slots(mesh, L);
     if (grid > fit) grid = fit;
     if (grid > nK) grid = nK;
-    MixedArgs g;
-    g.dm = mesh->dev();
-    g.kappa = kappa;
-    g.P = mesh->desc.degree;
-    g.N = mesh->N;
-    g.PN = mesh->PN;
-    g.dpf = mesh->dpf;
-    g.NI = (int)mesh->NI;
-    g.R = g.NI + 1;
-    g.nlev = L.nlev;
-    g.nunk = L.nunk;
-    g.wrows = L.wrows;
-    g.wld = L.wld;
-    g.wfloats = L.wfloats;
-    g.yfloats = L.yfloats;
-    g.bmax = L.bmax;
-    g.opmax = L.opmax;
-    g.ldr = L.ldr;
-    g.src_kind = f->kind;
-    g.src_value = f->value;
-    g.src_freq = f->freq;
+    MixedArgs g = mixed_args(mesh, L, kappa, *f, o, AK, EK, BK, FK, status, iters, (char*)scratch);
     g.K0 = K0;
     g.K1 = K1;
-    g.it_max = o.it_max;
-    g.tol = o.tol;
-    g.ws = (char*)scratch;
-    g.slot_bytes = L.slot_bytes;
-    g.off_G = L.off_G;
-    g.off_Z = L.off_Z;
-    g.off_mass = L.off_mass;
-    g.off_scale = L.off_scale;
-    g.off_D = L.off_D;
-    g.off_kap_smem = L.off_kap_smem;
-    g.off_scale_smem = L.off_scale_smem;
-    g.kap_in_smem = L.kap_in_smem;
-    g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
-    g.status = status;
-    g.iters = iters;
     mixed_kernel(L)<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
