@@ -59,6 +59,7 @@ struct MixedArgs {
     int* fbad;                    // pivot flag per K
     int64_t Kc0;
     size_t t_stride;
+    int* kcounter;                // dynamic K assignment (zeroed before the launch); NULL: static
 };
 
 struct MCtx {
@@ -79,6 +80,8 @@ struct MCtx {
     double eps_prev[kMaxNI + 1];
     int col_fail;
     double red[kWarpsM];
+    float epsred[2][32];          // level-Schur solve: per row-tile partial sums of g^T T g per column
+    int64_t nextK;
     double mz[kMaxNI + 1];
     alignas(8) uint64_t bar[2];
     uint32_t phase[2];
@@ -600,8 +603,12 @@ __device__ __forceinline__ int4 schur_step_info(const LevelGeom& lg, int nlev, c
     return make_int4(lg.size(lev) | (dir << 8), u0[lev] | ((bo > 0 ? u0[lo] : 0) << 16), bo | (lev << 16), loff[lev]);
 }
 
+// Also returns eps[col] = r^T (L D L^T)^{-1} r = sum over levels of g_lev^T T_lev g_lev,
+// accumulated from the forward steps (g_lev is a forward step's staged operand,
+// T_lev g_lev its result) in a fixed order.  Needs R <= 32: one output tile per warp,
+// warp w at (row tile w / NT, column tile w % NT) at every level.
 __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
-                                         const float* cw, float* opbuf, float* stage, MCtx& c) {
+                                         const float* cw, float* opbuf, float* stage, double* eps, MCtx& c) {
     const int R = g.R, NT = (R + 7) >> 3, nu = g.nunk;
     const int nsteps = 2 * g.nlev - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
@@ -625,6 +632,7 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     if (issuer) issue(0);
     for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
     __syncthreads();
+    float eacc0 = 0.0f, eacc1 = 0.0f;   // this lane's two columns (2 tq, 2 tq + 1 of its column tile)
     for (int st = 0; st < nsteps; ++st) {
         const int4 si = sinfo[st];
         const int b = si.x & 0xff, dir = si.x >> 8;
@@ -679,14 +687,32 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int i = mt * 16 + gq + 8 * (e >> 1), col = nt * 8 + 2 * tq + (e & 1);
-                if (i < b && col < R && !(frozen >> col & 1)) {
-                    const uint32_t ya = y_s + 4u * (uint32_t)((ulev + i) * R + col);
-                    sts1(ya, dir == 0 ? cv[e] : lds1(ya) - cv[e]);
+                if (i < b && col < R) {
+                    if (dir == 0) {
+                        const float gv = lds1(st_s + 4u * frag_b_pos(i, col, NT)) * cv[e];
+                        if (e & 1) eacc1 += gv; else eacc0 += gv;
+                    }
+                    if (!(frozen >> col & 1)) {
+                        const uint32_t ya = y_s + 4u * (uint32_t)((ulev + i) * R + col);
+                        sts1(ya, dir == 0 ? cv[e] : lds1(ya) - cv[e]);
+                    }
                 }
             }
         }
         __syncthreads();
     }
+    // eps: sum over the 8 row lanes of each column (lanes with equal tq), then the two row tiles
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        eacc0 += __shfl_xor_sync(0xffffffffu, eacc0, o);
+        eacc1 += __shfl_xor_sync(0xffffffffu, eacc1, o);
+    }
+    if (warp < 2 * NT && gq == 0) {
+        c.epsred[warp / NT][(warp % NT) * 8 + 2 * tq] = eacc0;
+        c.epsred[warp / NT][(warp % NT) * 8 + 2 * tq + 1] = eacc1;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) eps[threadIdx.x] = (double)c.epsred[0][threadIdx.x] + (double)c.epsred[1][threadIdx.x];
     if (threadIdx.x == 0) {
         c.phase[0] = ph0;
         c.phase[1] = ph1;
@@ -757,7 +783,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
     }
     __syncthreads();
 
-    for (int64_t K = g.K0 + blockIdx.x; K < g.K1; K += gridDim.x) {
+    // coarse triangles: K0 + blockIdx.x, then (dynamic) the next index from the counter
+    // or (static) every gridDim.x-th
+    if (threadIdx.x == 0) c.nextK = g.kcounter ? g.K0 + gridDim.x + atomicAdd(g.kcounter, 1) : 0;
+    for (int64_t K = g.K0 + blockIdx.x; K < g.K1;) {
         const double* kap = g.kappa + K * (int64_t)g.N * g.N;
         if (g.kap_in_smem) {
             // stage this K's kappa in shared memory (read by assembly, scaling and residuals)
@@ -1009,11 +1038,16 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         }
         for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
         __syncthreads();
-        if constexpr (SCHUR) solve_schur(g, F, sinfo, y, cw, opbuf, stage, c);
-        else solve_factor(g, F, sinfo, y, opbuf, stage, c);
-        __syncthreads();
-        column_dot(g, Res, y, scale, c.gamma, c);      // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
-        __syncthreads();
+        // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
+        if constexpr (SCHUR) {
+            solve_schur(g, F, sinfo, y, cw, opbuf, stage, c.gamma, c);
+            __syncthreads();
+        } else {
+            solve_factor(g, F, sinfo, y, opbuf, stage, c);
+            __syncthreads();
+            column_dot(g, Res, y, scale, c.gamma, c);
+            __syncthreads();
+        }
         // Columns with a zero right-hand side are done at once (Z = 0, Res = G = 0).
         // Otherwise, after each correction the next one D' = M Res gives
         // eps = Res^T M Res ~ ||e||^2 (energy norm of the error of Z): a column stops
@@ -1056,11 +1090,15 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
             __syncthreads();
             if (c.all_done) break;
-            if constexpr (SCHUR) solve_schur(g, F, sinfo, y, cw, opbuf, stage, c);
-            else solve_factor(g, F, sinfo, y, opbuf, stage, c);
-            __syncthreads();
-            column_dot(g, Res, y, scale, c.eps, c);
-            __syncthreads();
+            if constexpr (SCHUR) {
+                solve_schur(g, F, sinfo, y, cw, opbuf, stage, c.eps, c);
+                __syncthreads();
+            } else {
+                solve_factor(g, F, sinfo, y, opbuf, stage, c);
+                __syncthreads();
+                column_dot(g, Res, y, scale, c.eps, c);
+                __syncthreads();
+            }
             if (threadIdx.x == 0) {
                 int all = 1;
                 for (int col = 0; col < R; ++col) {
@@ -1151,6 +1189,13 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             if (g.iters) g.iters[K] = pass;
         }
         __syncthreads();
+        if (g.kcounter) {
+            K = c.nextK;
+            __syncthreads();
+            if (threadIdx.x == 0) c.nextK = g.K0 + gridDim.x + atomicAdd(g.kcounter, 1);
+        } else {
+            K += gridDim.x;
+        }
     }
 }
 
@@ -1270,7 +1315,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, bool split = true) {
     L.nunk = (int)mesh->nloc - 1;
     int bmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) bmax = std::max(bmax, size(lev));
-    L.schur = P == 1 && bmax <= kSchurMax && mesh->NI + 1 <= 64;
+    L.schur = P == 1 && bmax <= kSchurMax && mesh->NI + 1 <= 32;
     L.mode = L.schur ? (split ? 2 : 1) : 0;
     size_t f = 0;
     int opmax = 0;
@@ -1437,7 +1482,7 @@ size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(mesh->device);
-    const size_t bytes = (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(mesh, L) * L.chunk_k_bytes;
+    const size_t bytes = (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(mesh, L) * L.chunk_k_bytes + 256;
     cudaSetDevice(cur);
     return bytes;
 }
@@ -1452,14 +1497,19 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     const int slots = mixed_slots(mesh, L);
     const int64_t chunk = chunk_of(mesh, L);
     const size_t slots_bytes = (size_t)slots * L.slot_bytes;
-    if (ws_bytes < slots_bytes + (size_t)chunk * L.chunk_k_bytes)
+    if (ws_bytes < slots_bytes + (size_t)chunk * L.chunk_k_bytes + 256)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
+    // dynamic assignment of coarse triangles to blocks: a counter behind the scratch,
+    // zeroed in stream order before every solve launch
+    int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)chunk * L.chunk_k_bytes);
     MixedArgs g = mixed_args(mesh, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
+    g.kcounter = counter;
     if (L.mode != 2) {
         g.K0 = K0;
         g.K1 = K1;
+        MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(nK < slots ? nK : slots);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
         MHM_CUDA_TRY(cudaGetLastError());
@@ -1481,6 +1531,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
         g.K1 = c1;
         k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, stream>>>(g);
         MHM_CUDA_TRY(cudaGetLastError());
+        MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(c1 - c0 < slots ? c1 - c0 : slots);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
         MHM_CUDA_TRY(cudaGetLastError());
