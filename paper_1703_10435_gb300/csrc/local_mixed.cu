@@ -57,6 +57,8 @@ struct MixedArgs {
     float* Tall;                  // t_stride floats per K
     float* cwall;                 // 4 nunk floats per K
     int* fbad;                    // pivot flag per K
+    double* scall;                // s_u = A_uu^-1/2, nunk per K
+    double* ahall;                // scaled stencil S A S: 7 x nunk per K (self, E, W, N, S, SE, NW)
     int64_t Kc0;
     size_t t_stride;
     int* kcounter;                // dynamic K assignment (zeroed before the launch); NULL: static
@@ -197,6 +199,26 @@ __device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su
     w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(PN, x - 1, yl + 1);    // north-west
     for (int k = 1; k < 7; ++k)
         if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
+}
+
+// Conversions between FP32 and FP64 by rearranging the IEEE-754 fields on the
+// integer pipe (a hardware conversion occupies the FP64 pipe here, at the rate of
+// an FP64 multiply-add).  f2d_bits is exact for zero and normal numbers (FP32
+// subnormals flush to zero); d2f_bits truncates the significand (round toward
+// zero) and flushes magnitudes below the FP32 normal range to zero.  Only finite
+// values of FP32 range pass through them.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint32_t hi = e ? (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu) : (b & 0x80000000u);
+    const uint32_t lo = e ? (b << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (e <= 0) return __uint_as_float(hi & 0x80000000u);
+    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
 // Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
@@ -608,7 +630,8 @@ __device__ __forceinline__ int4 schur_step_info(const LevelGeom& lg, int nlev, c
 // T_lev g_lev its result) in a fixed order.  Needs R <= 32: one output tile per warp,
 // warp w at (row tile w / NT, column tile w % NT) at every level.
 __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
-                                         const float* cw, float* opbuf, float* stage, double* eps, MCtx& c) {
+                                         const float* cw, const double* Rh, float* opbuf, float* stage, double* eps,
+                                         MCtx& c) {
     const int R = g.R, NT = (R + 7) >> 3, nu = g.nunk;
     const int nsteps = 2 * g.nlev - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
@@ -639,7 +662,8 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
         const int ulev = si.y & 0xffff, uo = si.y >> 16;
         const int bo = si.z & 0xffff, lev = si.z >> 16;
         if (issuer && st + 1 < nsteps) issue(st + 1);
-        // B (b x R) in fragment order: forward r_lev - C_lev v_{lev-1}; backward C_{lev+1}^T x_{lev+1}
+        // B (b x R) in fragment order: forward r_lev - C_lev v_{lev-1} (r = the FP32 rounding of
+        // the scaled residual Rh); backward C_{lev+1}^T x_{lev+1}
         {
             const int xo = lev == 0 ? 1 : 0;       // lattice x of position 0
             const int off = lev == 1 ? 1 : 0;      // level below starts at x = 1
@@ -648,7 +672,7 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
                 const int x = i + xo;
                 float v;
                 if (dir == 0) {
-                    v = lds1(y_s + 4u * (uint32_t)((ulev + i) * R + col));
+                    v = d2f_bits(Rh[(size_t)(ulev + i) * R + col]);   // right-hand side: the scaled residual
                     if (lev > 0) {
                         const int ps = x - off, pse = x + 1 - off;
                         float a = cwSE[ulev + i] * lds1(y_s + 4u * (uint32_t)((uo + pse) * R + col));
@@ -855,340 +879,568 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
         }
         __syncthreads();
 
-        // ---- right-hand sides G (FP64, column-major) and the mass vector
-        for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) {
-            int X, Y;
-            lattice_of_unk(g.PN, u, &X, &Y);
-            int ti[6], tj[6], ta[6];
-            bool tup[6];
-            const int n = incident(g.P, g.N, X, Y, ti, tj, tup, ta);
-            double m = 0.0, fh = 0.0, diag = 0.0;
-            const int nb = g.P == 1 ? 3 : 6;
-            for (int t = 0; t < n; ++t) {
-                const double mt = c.area_fine * element_mass_frac(g.P, ta[t]);
-                m += mt;
-                diag += kap[kap_index(g.N, tup[t], ti[t], tj[t])] * (tup[t] ? c.Sup : c.Sdn)[ta[t] * nb + ta[t]];
-                if (g.src_kind == MHM_SRC_CONST) fh += g.src_value * mt;
-                else {
-                    double Xv[3][2];
-                    fine_xy(c, g.N, tup[t], ti[t], tj[t], Xv);
-                    fh += cell_src(g, Xv, g.P, ta[t]);
+        if constexpr (SCHUR) {
+            // ---- Level-Schur path in scaled variables (node-major, index u R + col):
+            //   Zh = S^-1 Z, Rh = S (G - A Z), Ah = S A S, S = diag(A_uu^-1/2).
+            // A correction is Zh += y (the FP32 solve output, exactly), the residual update
+            // Rh -= Ah y reads y at the stencil points, and z_j^T Res_i = Zh_j^T Rh_i.
+            double* Rh = G;
+            double* Zh = Z;
+            double* smass = mass;   // s_u m_u
+            const double* sc;
+            const double* ah;       // 7 x nunk: self, E, W, N, S, SE, NW
+            const int nu = g.nunk;
+            if constexpr (MODE == 2) {
+                __syncthreads();
+                const int64_t kk = K - g.Kc0;
+                F = g.Tall + kk * (int64_t)g.t_stride;
+                sc = g.scall + kk * (int64_t)nu;
+                ah = g.ahall + kk * 7 * (int64_t)nu;
+                const float* src = g.cwall + kk * 4 * (int64_t)nu;
+                for (int t = threadIdx.x; t < 4 * nu; t += blockDim.x) cw[t] = src[t];
+                if (threadIdx.x == 0) c.bad = g.fbad[kk];
+            } else {
+                double* ahw = reinterpret_cast<double*>(slot + g.off_D);
+                for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+                    int X, Y;
+                    lattice_of_unk(g.PN, u, &X, &Y);
+                    double w[7];
+                    int v[7];
+                    p1_row(g.N, g.PN, nu, c.Sup, c.Sdn, kap, X, Y, u, w, v);
+                    scale[u] = 1.0 / sqrt(w[0]);
                 }
+                __syncthreads();
+                for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+                    int X, Y;
+                    lattice_of_unk(g.PN, u, &X, &Y);
+                    double w[7];
+                    int v[7];
+                    p1_row(g.N, g.PN, nu, c.Sup, c.Sdn, kap, X, Y, u, w, v);
+                    const double su = scale[u];
+                    double a7[7];
+                    for (int d = 0; d < 7; ++d) a7[d] = w[d] * su * scale[v[d]];
+                    cw[u] = (float)a7[1];
+                    cw[nu + u] = (float)a7[2];
+                    cw[2 * nu + u] = (float)a7[4];
+                    cw[3 * nu + u] = (float)a7[5];
+                    for (int d = 0; d < 7; ++d) ahw[(size_t)d * nu + u] = a7[d];
+                }
+                __syncthreads();
+                schur_factor(g, loff, u0, cw, W, W + kSchurMax * kSLd, W + 2 * kSchurMax * kSLd, F, c);
+                sc = scale;
+                ah = ahw;
             }
-            mass[u] = m;
-            scale[u] = 1.0 / sqrt(diag);
-            for (int col = 0; col < R; ++col) {
-                double v = -c.cproj[col] * m;
-                if (col == g.NI) v += fh;
-                else {
-                    const int a = col / g.dpf, jf = col - a * g.dpf;
-                    const int kl = face_position(g.PN, X, Y, a);
-                    if (kl >= 0) {
-                        const int kk = c.rev[a] ? g.PN - kl : kl;
-                        v += -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk];
+            // ---- right-hand sides Rh = S G (compatible loads, pinned DOF left out), S m, Zh = 0
+            for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+                int X, Y;
+                lattice_of_unk(g.PN, u, &X, &Y);
+                int ti[6], tj[6], ta[6];
+                bool tup[6];
+                const int n = incident(1, g.N, X, Y, ti, tj, tup, ta);
+                double m = 0.0, fh = 0.0;
+                for (int t = 0; t < n; ++t) {
+                    const double mt = c.area_fine * element_mass_frac(1, ta[t]);
+                    m += mt;
+                    if (g.src_kind == MHM_SRC_CONST) fh += g.src_value * mt;
+                    else {
+                        double Xv[3][2];
+                        fine_xy(c, g.N, tup[t], ti[t], tj[t], Xv);
+                        fh += cell_src(g, Xv, 1, ta[t]);
                     }
                 }
-                G[(size_t)col * g.nunk + u] = v;
+                const double su = sc[u];
+                smass[u] = su * m;
+                for (int col = 0; col < R; ++col) {
+                    double v = -c.cproj[col] * m;
+                    if (col == g.NI) v += fh;
+                    else {
+                        const int a = col / g.dpf, jf = col - a * g.dpf;
+                        const int kl = face_position(g.PN, X, Y, a);
+                        if (kl >= 0) {
+                            const int kk2 = c.rev[a] ? g.PN - kl : kl;
+                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk2];
+                        }
+                    }
+                    Rh[(size_t)u * R + col] = su * v;
+                    Zh[(size_t)u * R + col] = 0.0;
+                }
             }
-        }
-
-        if constexpr (MODE == 2) {
-            // ---- precomputed level-Schur operators of this K: couplings to shared memory
             __syncthreads();
-            const int64_t kk = K - g.Kc0;
-            F = g.Tall + kk * (int64_t)g.t_stride;
-            const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
-            for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
-            if (threadIdx.x == 0) c.bad = g.fbad[kk];
+            // ---- refinement (as in the generic path, in scaled variables)
+            solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.gamma, c);
             __syncthreads();
-        } else if constexpr (MODE == 1) {
-            // ---- FP32 factorisation by level Schur complements: scaled couplings first
-            __syncthreads();   // (publishes scale[] to the block)
+            if (threadIdx.x == 0) {
+                int all = 1;
+                for (int col = 0; col < R; ++col) {
+                    c.col_frozen[col] = c.col_done[col] = !(c.gamma[col] > 0.0);
+                    c.eps_prev[col] = c.gamma[col];
+                    all &= c.col_done[col];
+                }
+                c.all_done = all;
+            }
+            __syncthreads();
+            int pass = 0;
+            while (!c.all_done) {
+                // Zh += y and Rh -= Ah y in one pass (y read at the node and its stencil points)
+                for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+                    int X, Y;
+                    lattice_of_unk(g.PN, u, &X, &Y);
+                    int v[7];
+                    v[0] = u;
+                    v[1] = unk(g.PN, X + 1, Y);
+                    v[2] = unk(g.PN, X - 1, Y);
+                    v[3] = unk(g.PN, X, Y + 1);
+                    v[4] = unk(g.PN, X, Y - 1);
+                    v[5] = unk(g.PN, X + 1, Y - 1);
+                    v[6] = unk(g.PN, X - 1, Y + 1);
+                    double a[7];
+#pragma unroll
+                    for (int d = 0; d < 7; ++d) {
+                        a[d] = ah[(size_t)d * nu + u];
+                        if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
+                    }
+                    for (int col = 0; col < R; ++col) {
+                        if (c.col_done[col]) continue;
+                        const size_t o = (size_t)u * R + col;
+                        const double d0 = f2d_bits(y[o]);
+                        Zh[o] += d0;
+                        double r = fma(-a[0], d0, Rh[o]);
+#pragma unroll
+                        for (int d = 1; d < 7; ++d)
+                            if (a[d] != 0.0) r = fma(-a[d], f2d_bits(y[(size_t)v[d] * R + col]), r);
+                        Rh[o] = r;
+                    }
+                }
+                ++pass;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int all = 1;
+                    for (int col = 0; col < R; ++col) {
+                        if (c.col_frozen[col]) c.col_done[col] = 1;   // its last correction is in
+                        all &= c.col_done[col];
+                    }
+                    c.all_done = all || pass >= g.it_max;
+                    c.converged = all;
+                }
+                __syncthreads();
+                if (c.all_done) break;
+                solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.eps, c);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int all = 1;
+                    for (int col = 0; col < R; ++col) {
+                        if (!c.col_frozen[col]) {
+                            const double eps = c.eps[col], lim = g.tol * c.gamma[col];
+                            if (eps <= lim) c.col_frozen[col] = c.col_done[col] = 1;
+                            else if (4.0 * eps * eps <= lim * c.eps_prev[col]) c.col_frozen[col] = 1;
+                            c.eps_prev[col] = eps;
+                        }
+                        all &= c.col_done[col];
+                    }
+                    c.all_done = all;
+                    c.converged = all;
+                }
+                __syncthreads();
+            }
+            const int converged = c.converged;
+            // ---- outputs X[j][i] = N~_j^T z_i + z_j^T Res_i = (S N~_j)^T Zh_i + Zh_j^T Rh_i
+            {
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                for (int col = warp; col < R; col += kWarpsM) {          // (S m)^T Zh per column
+                    double mz = 0.0;
+                    for (int u = lane; u < nu; u += 32) mz = fma(smass[u], Zh[(size_t)u * R + col], mz);
+                    for (int o = 16; o > 0; o >>= 1) mz += __shfl_down_sync(0xffffffffu, mz, o);
+                    if (lane == 0) c.mz[col] = mz;
+                }
+            }
+            // correction Gram Zh^T Rh in FP32 (it is of the size of the error of Z), by node chunks
+            float corr[(kMaxNI + 1) * (kMaxNI + 1) / kThreadsM + 1];
+            const int npair = R * R;
+            for (int q = 0; q * kThreadsM < npair; ++q) corr[q] = 0.0f;
+            constexpr int kChunk = 64;
+            float* zs = y;                       // R x kChunk
+            float* rs = y + R * kChunk;          // R x kChunk
+            for (int base = 0; base < nu; base += kChunk) {
+                const int cnt = min(kChunk, nu - base);
+                __syncthreads();
+                for (int t = threadIdx.x; t < R * kChunk; t += blockDim.x) {
+                    const int uu = t / R, col = t - uu * R;
+                    const size_t o = (size_t)(base + uu) * R + col;
+                    zs[col * kChunk + uu] = uu < cnt ? d2f_bits(Zh[o]) : 0.0f;
+                    rs[col * kChunk + uu] = uu < cnt ? d2f_bits(Rh[o]) : 0.0f;
+                }
+                __syncthreads();
+                for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) {
+                    const int t = q * kThreadsM + threadIdx.x, j = t / R, i = t - j * R;
+                    float a = 0.0f;
+                    for (int uu = 0; uu < kChunk; ++uu) a = fmaf(zs[j * kChunk + uu], rs[i * kChunk + uu], a);
+                    corr[q] += a;
+                }
+            }
+            __syncthreads();
+            double* xbuf = reinterpret_cast<double*>(W);   // R x R doubles
+            for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) xbuf[q * kThreadsM + threadIdx.x] = corr[q];
+            __syncthreads();
+            for (int t = threadIdx.x; t < g.NI * R; t += blockDim.x) {
+                const int j = t / R, col = t - j * R;
+                const int a = j / g.dpf, jf = j - a * g.dpf;
+                double sacc = 0.0;
+                for (int kl = 0; kl <= g.PN; ++kl) {
+                    int X, Y;
+                    if (a == 2) { X = kl; Y = 0; }
+                    else if (a == 0) { X = g.PN - kl; Y = kl; }
+                    else { X = 0; Y = g.PN - kl; }
+                    const int u = unk(g.PN, X, Y);
+                    if (u < 0) continue;
+                    const int kk2 = c.rev[a] ? g.PN - kl : kl;
+                    sacc = fma((-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk2]) * sc[u], Zh[(size_t)u * R + col],
+                               sacc);
+                }
+                xbuf[j * R + col] += sacc - c.cproj[j] * c.mz[col];
+            }
+            __syncthreads();
+            const int NI = g.NI;
+            for (int t = threadIdx.x; t < NI * NI; t += blockDim.x) {
+                const int j = t / NI, i = t - j * NI;
+                g.AK[K * NI * NI + t] = -0.5 * (xbuf[j * R + i] + xbuf[i * R + j]);
+            }
+            for (int j = threadIdx.x; j < NI; j += blockDim.x) {
+                g.EK[K * NI + j] = xbuf[j * R + NI];
+                const int a = j / g.dpf, jf = j - a * g.dpf;
+                g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
+            }
+            if (threadIdx.x == 0) {
+                g.FK[K] = c.FK;
+                g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                if (g.iters) g.iters[K] = pass;
+            }
+            __syncthreads();
+        } else {
+            // ---- right-hand sides G (FP64, column-major) and the mass vector
             for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) {
                 int X, Y;
                 lattice_of_unk(g.PN, u, &X, &Y);
-                double w[7];
-                int v[7];
-                p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
-                const double su = scale[u];
-                cw[u] = (float)(w[1] * su * scale[v[1]]);
-                cw[g.nunk + u] = (float)(w[2] * su * scale[v[2]]);
-                cw[2 * g.nunk + u] = (float)(w[4] * su * scale[v[4]]);
-                cw[3 * g.nunk + u] = (float)(w[5] * su * scale[v[5]]);
-            }
-            __syncthreads();
-            schur_factor(g, loff, u0, cw, W, W + kSchurMax * kSLd, W + 2 * kSchurMax * kSLd, F, c);
-        } else {
-            // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
-            const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
-            float* Rhs = y;                               // level right-hand sides (y is free while factoring)
-            for (int t = threadIdx.x; t < (b0 + b1) * g.wld; t += blockDim.x) W[t] = 0.0f;
-            for (int t = threadIdx.x; t < b0 * b0; t += blockDim.x) {
-                const int i = t / b0, k = t - i * b0;
-                Rhs[i * g.ldr + k] = k == i ? 1.0f : 0.0f;
-            }
-            __syncthreads();   // (also publishes scale[] to the block)
-            for (int lev = 0; lev < g.nlev; ++lev) {
-                const int b = lg.size(lev);
-                const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
-                const int nr = b + bn;
-                if (bn > 0) {
-                    // element matrices of fine row lev in four colour classes
-                    const int P = g.P, N = g.N, nb = P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
-                    for (int cls = 0; cls < 4; ++cls) {
-                        const bool up = cls < 2;
-                        const int parity = cls & 1;
-                        const int ntri = up ? N - lev : N - 1 - lev;
-                        const int ncls = (ntri - parity + 1) / 2;
-                        for (int t = threadIdx.x; t < ncls * npair; t += blockDim.x) {
-                            const int ti = t / npair, item = t - ti * npair;
-                            const int i = parity + 2 * ti;
-                            int nx[6], ny[6];
-                            element_nodes(P, up, i, lev, nx, ny);
-                            const double kt = kap[kap_index(N, up, i, lev)];
-                            const double* S = up ? c.Sup : c.Sdn;
-                            int a = 0, rem = item;
-                            while (rem >= nb - a) { rem -= nb - a; ++a; }
-                            const int bb = a + rem;
-                            const int pa = lg.pos(nx[a], ny[a]), pb = lg.pos(nx[bb], ny[bb]);
-                            if (pa < 0 || pb < 0) continue;
-                            const int ra = pa + (lg.level_of_row(ny[a]) == lev ? 0 : b);
-                            const int rb = pb + (lg.level_of_row(ny[bb]) == lev ? 0 : b);
-                            const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-                            // symmetric diagonal scaling: the FP32 factor is of D^-1/2 A_p D^-1/2
-                            const double sab = scale[unk(g.PN, nx[a], ny[a])] * scale[unk(g.PN, nx[bb], ny[bb])];
-                            W[hi * g.wld + lo] += (float)(kt * S[a * nb + bb] * sab);
+                int ti[6], tj[6], ta[6];
+                bool tup[6];
+                const int n = incident(g.P, g.N, X, Y, ti, tj, tup, ta);
+                double m = 0.0, fh = 0.0, diag = 0.0;
+                const int nb = g.P == 1 ? 3 : 6;
+                for (int t = 0; t < n; ++t) {
+                    const double mt = c.area_fine * element_mass_frac(g.P, ta[t]);
+                    m += mt;
+                    diag += kap[kap_index(g.N, tup[t], ti[t], tj[t])] * (tup[t] ? c.Sup : c.Sdn)[ta[t] * nb + ta[t]];
+                    if (g.src_kind == MHM_SRC_CONST) fh += g.src_value * mt;
+                    else {
+                        double Xv[3][2];
+                        fine_xy(c, g.N, tup[t], ti[t], tj[t], Xv);
+                        fh += cell_src(g, Xv, g.P, ta[t]);
+                    }
+                }
+                mass[u] = m;
+                scale[u] = 1.0 / sqrt(diag);
+                for (int col = 0; col < R; ++col) {
+                    double v = -c.cproj[col] * m;
+                    if (col == g.NI) v += fh;
+                    else {
+                        const int a = col / g.dpf, jf = col - a * g.dpf;
+                        const int kl = face_position(g.PN, X, Y, a);
+                        if (kl >= 0) {
+                            const int kk = c.rev[a] ? g.PN - kl : kl;
+                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk];
                         }
+                    }
+                    G[(size_t)col * g.nunk + u] = v;
+                }
+            }
+
+            if constexpr (MODE == 2) {
+                // ---- precomputed level-Schur operators of this K: couplings to shared memory
+                __syncthreads();
+                const int64_t kk = K - g.Kc0;
+                F = g.Tall + kk * (int64_t)g.t_stride;
+                const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
+                for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
+                if (threadIdx.x == 0) c.bad = g.fbad[kk];
+                __syncthreads();
+            } else if constexpr (MODE == 1) {
+                // ---- FP32 factorisation by level Schur complements: scaled couplings first
+                __syncthreads();   // (publishes scale[] to the block)
+                for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) {
+                    int X, Y;
+                    lattice_of_unk(g.PN, u, &X, &Y);
+                    double w[7];
+                    int v[7];
+                    p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
+                    const double su = scale[u];
+                    cw[u] = (float)(w[1] * su * scale[v[1]]);
+                    cw[g.nunk + u] = (float)(w[2] * su * scale[v[2]]);
+                    cw[2 * g.nunk + u] = (float)(w[4] * su * scale[v[4]]);
+                    cw[3 * g.nunk + u] = (float)(w[5] * su * scale[v[5]]);
+                }
+                __syncthreads();
+                schur_factor(g, loff, u0, cw, W, W + kSchurMax * kSLd, W + 2 * kSchurMax * kSLd, F, c);
+            } else {
+                // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
+                const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
+                float* Rhs = y;                               // level right-hand sides (y is free while factoring)
+                for (int t = threadIdx.x; t < (b0 + b1) * g.wld; t += blockDim.x) W[t] = 0.0f;
+                for (int t = threadIdx.x; t < b0 * b0; t += blockDim.x) {
+                    const int i = t / b0, k = t - i * b0;
+                    Rhs[i * g.ldr + k] = k == i ? 1.0f : 0.0f;
+                }
+                __syncthreads();   // (also publishes scale[] to the block)
+                for (int lev = 0; lev < g.nlev; ++lev) {
+                    const int b = lg.size(lev);
+                    const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
+                    const int nr = b + bn;
+                    if (bn > 0) {
+                        // element matrices of fine row lev in four colour classes
+                        const int P = g.P, N = g.N, nb = P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
+                        for (int cls = 0; cls < 4; ++cls) {
+                            const bool up = cls < 2;
+                            const int parity = cls & 1;
+                            const int ntri = up ? N - lev : N - 1 - lev;
+                            const int ncls = (ntri - parity + 1) / 2;
+                            for (int t = threadIdx.x; t < ncls * npair; t += blockDim.x) {
+                                const int ti = t / npair, item = t - ti * npair;
+                                const int i = parity + 2 * ti;
+                                int nx[6], ny[6];
+                                element_nodes(P, up, i, lev, nx, ny);
+                                const double kt = kap[kap_index(N, up, i, lev)];
+                                const double* S = up ? c.Sup : c.Sdn;
+                                int a = 0, rem = item;
+                                while (rem >= nb - a) { rem -= nb - a; ++a; }
+                                const int bb = a + rem;
+                                const int pa = lg.pos(nx[a], ny[a]), pb = lg.pos(nx[bb], ny[bb]);
+                                if (pa < 0 || pb < 0) continue;
+                                const int ra = pa + (lg.level_of_row(ny[a]) == lev ? 0 : b);
+                                const int rb = pb + (lg.level_of_row(ny[bb]) == lev ? 0 : b);
+                                const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+                                // symmetric diagonal scaling: the FP32 factor is of D^-1/2 A_p D^-1/2
+                                const double sab = scale[unk(g.PN, nx[a], ny[a])] * scale[unk(g.PN, nx[bb], ny[bb])];
+                                W[hi * g.wld + lo] += (float)(kt * S[a * nb + bb] * sab);
+                            }
+                            __syncthreads();
+                        }
+                    }
+                    // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
+                    // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
+                    const int bp = lev > 0 ? lg.size(lev - 1) : 0;
+                    cholesky_level_f32<RPL, CPL>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
+                    {
+                        // Fw = [-Linv L_{lev,lev-1} | Linv] (b x (bp + b)) and
+                        // Bw = [-Linv^T L_{lev+1,lev}^T | Linv^T] (b x (bn + b)) to this block's scratch
+                        // slot in tensor-core fragment order, zero beyond the operator
+                        float* Fw = F + loff[2 * lev];
+                        float* Bw = F + loff[2 * lev + 1];
+                        {
+                            const int K = bp + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
+                            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                                const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
+                                const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
+                                const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
+                                float v = 0.0f;
+                                if (i < b && k < K) v = k < bp ? Rhs[i * g.ldr + b + k] : Rhs[i * g.ldr + (k - bp)];
+                                Fw[t] = v;
+                            }
+                        }
+                        {
+                            const int K = bn + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
+                            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                                const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
+                                const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
+                                const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
+                                float v = 0.0f;
+                                if (i < b && k < K) {
+                                    if (k >= bn) v = Rhs[(k - bn) * g.ldr + i];
+                                    else {
+                                        const float* cn = W + (size_t)(b + k) * g.wld;
+                                        float a = 0.0f;
+                                        for (int mm = i; mm < b; ++mm) a = fmaf(Rhs[mm * g.ldr + i], cn[mm], a);
+                                        v = -a;
+                                    }
+                                }
+                                Bw[t] = v;
+                            }
+                        }
+                        fence_proxy_async_global();   // the operators are read back by bulk copies
+                        __syncthreads();
+                        // right-hand sides of the next level: [I_bn | -L_{lev+1,lev}]
+                        for (int t = threadIdx.x; t < bn * (bn + b); t += blockDim.x) {
+                            const int i = t / (bn + b), k = t - i * (bn + b);
+                            Rhs[i * g.ldr + k] = k < bn ? (k == i ? 1.0f : 0.0f) : -W[(size_t)(b + i) * g.wld + (k - bn)];
+                        }
+                    }
+                    __syncthreads();
+                    if (bn > 0) {
+                        for (int t = threadIdx.x; t < bn * bn; t += blockDim.x) {
+                            const int i = t / bn, jj = t - i * bn;
+                            if (jj <= i) W[i * g.wld + jj] = W[(b + i) * g.wld + b + jj];
+                        }
+                        __syncthreads();
+                        const int bnn = lev + 2 < g.nlev ? lg.size(lev + 2) : 0;
+                        for (int t = threadIdx.x; t < bnn * g.wld; t += blockDim.x) W[bn * g.wld + t] = 0.0f;
                         __syncthreads();
                     }
                 }
-                // Blocked Cholesky of this level; its right-hand sides Rhs = [I | -L_{lev,lev-1}]
-                // come out as the forward operator Fw_lev = [L^{-1} | -L^{-1} L_{lev,lev-1}].
-                const int bp = lev > 0 ? lg.size(lev - 1) : 0;
-                cholesky_level_f32<RPL, CPL>(W, g.wld, b, nr, Rhs, g.ldr, b, b + bp, &c.bad);
-                {
-                    // Fw = [-Linv L_{lev,lev-1} | Linv] (b x (bp + b)) and
-                    // Bw = [-Linv^T L_{lev+1,lev}^T | Linv^T] (b x (bn + b)) to this block's scratch
-                    // slot in tensor-core fragment order, zero beyond the operator
-                    float* Fw = F + loff[2 * lev];
-                    float* Bw = F + loff[2 * lev + 1];
-                    {
-                        const int K = bp + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
-                        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                            const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
-                            const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
-                            const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
-                            float v = 0.0f;
-                            if (i < b && k < K) v = k < bp ? Rhs[i * g.ldr + b + k] : Rhs[i * g.ldr + (k - bp)];
-                            Fw[t] = v;
-                        }
-                    }
-                    {
-                        const int K = bn + b, KT = (K + 7) >> 3, n = frag_op_floats(b, K);
-                        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                            const int tile = t >> 7, r = t & 127, ln = r >> 2, e = r & 3;
-                            const int i = (tile / KT) * 16 + (ln >> 2) + 8 * (e & 1);
-                            const int k = (tile % KT) * 8 + (ln & 3) + 4 * (e >> 1);
-                            float v = 0.0f;
-                            if (i < b && k < K) {
-                                if (k >= bn) v = Rhs[(k - bn) * g.ldr + i];
-                                else {
-                                    const float* cn = W + (size_t)(b + k) * g.wld;
-                                    float a = 0.0f;
-                                    for (int mm = i; mm < b; ++mm) a = fmaf(Rhs[mm * g.ldr + i], cn[mm], a);
-                                    v = -a;
-                                }
-                            }
-                            Bw[t] = v;
-                        }
-                    }
-                    fence_proxy_async_global();   // the operators are read back by bulk copies
-                    __syncthreads();
-                    // right-hand sides of the next level: [I_bn | -L_{lev+1,lev}]
-                    for (int t = threadIdx.x; t < bn * (bn + b); t += blockDim.x) {
-                        const int i = t / (bn + b), k = t - i * (bn + b);
-                        Rhs[i * g.ldr + k] = k < bn ? (k == i ? 1.0f : 0.0f) : -W[(size_t)(b + i) * g.wld + (k - bn)];
-                    }
-                }
-                __syncthreads();
-                if (bn > 0) {
-                    for (int t = threadIdx.x; t < bn * bn; t += blockDim.x) {
-                        const int i = t / bn, jj = t - i * bn;
-                        if (jj <= i) W[i * g.wld + jj] = W[(b + i) * g.wld + b + jj];
-                    }
-                    __syncthreads();
-                    const int bnn = lev + 2 < g.nlev ? lg.size(lev + 2) : 0;
-                    for (int t = threadIdx.x; t < bnn * g.wld; t += blockDim.x) W[bn * g.wld + t] = 0.0f;
-                    __syncthreads();
-                }
             }
-        }
 
-        // ---- refinement.  M = (L L^T)^{-1} (scaled) approximates A_p^{-1}.  The buffer G
-        // becomes the residual Res = G - A_p Z, kept exact in FP64 by Res -= A_p D for
-        // every correction D = M Res added to Z.  The outputs use the corrected
-        // bilinear form N~^T Z + Z^T Res, whose error e^T A_p e is quadratic in the
-        // error e of Z; eps_c = Res_c^T M Res_c estimates ||e_c||^2_{A_p}.
-        double* Res = G;
-        double* D64 = reinterpret_cast<double*>(slot + g.off_D);
-        const int total = g.nunk * R;
-        for (int t = threadIdx.x; t < g.nunk * g.Rp; t += blockDim.x) {
-            const int u = t / g.Rp, col = t - u * g.Rp;
-            y[t] = col < R ? (float)(Res[(size_t)col * g.nunk + u] * scale[u]) : 0.0f;
-        }
-        for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
-        __syncthreads();
-        // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
-        if constexpr (SCHUR) {
-            solve_schur(g, F, sinfo, y, cw, opbuf, stage, c.gamma, c);
+            // ---- refinement.  M = (L L^T)^{-1} (scaled) approximates A_p^{-1}.  The buffer G
+            // becomes the residual Res = G - A_p Z, kept exact in FP64 by Res -= A_p D for
+            // every correction D = M Res added to Z.  The outputs use the corrected
+            // bilinear form N~^T Z + Z^T Res, whose error e^T A_p e is quadratic in the
+            // error e of Z; eps_c = Res_c^T M Res_c estimates ||e_c||^2_{A_p}.
+            double* Res = G;
+            double* D64 = reinterpret_cast<double*>(slot + g.off_D);
+            const int total = g.nunk * R;
+            for (int t = threadIdx.x; t < g.nunk * g.Rp; t += blockDim.x) {
+                const int u = t / g.Rp, col = t - u * g.Rp;
+                y[t] = col < R ? (float)(Res[(size_t)col * g.nunk + u] * scale[u]) : 0.0f;
+            }
+            for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
             __syncthreads();
-        } else {
+            // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
             solve_factor(g, F, sinfo, y, opbuf, stage, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.gamma, c);
             __syncthreads();
-        }
-        // Columns with a zero right-hand side are done at once (Z = 0, Res = G = 0).
-        // Otherwise, after each correction the next one D' = M Res gives
-        // eps = Res^T M Res ~ ||e||^2 (energy norm of the error of Z): a column stops
-        // when eps <= tol * gamma; and when linear convergence predicts that one more
-        // correction will get there (eps^2 / eps_prev, with a safety factor 4), that
-        // correction is applied without a further confirming solve.
-        if (threadIdx.x == 0) {
-            int all = 1;
-            for (int col = 0; col < R; ++col) {
-                c.col_frozen[col] = c.col_done[col] = !(c.gamma[col] > 0.0);
-                c.eps_prev[col] = c.gamma[col];
-                all &= c.col_done[col];
-            }
-            c.all_done = all;
-        }
-        __syncthreads();
-        int pass = 0;
-        while (!c.all_done) {
-            // D = s . y (FP64), Z += D
-            for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int col = t / g.nunk, u = t - col * g.nunk;
-                if (c.col_done[col]) continue;
-                const double d = (double)y[(size_t)u * g.Rp + col] * scale[u];
-                D64[t] = d;
-                Z[t] += d;
-            }
-            __syncthreads();
-            // Res -= A_p D (FP64, from kappa and the element matrices); y = s . Res
-            for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) apply_residual(g, c, kap, u, D64, Res, y, scale[u]);
-            ++pass;
-            __syncthreads();
+            // Columns with a zero right-hand side are done at once (Z = 0, Res = G = 0).
+            // Otherwise, after each correction the next one D' = M Res gives
+            // eps = Res^T M Res ~ ||e||^2 (energy norm of the error of Z): a column stops
+            // when eps <= tol * gamma; and when linear convergence predicts that one more
+            // correction will get there (eps^2 / eps_prev, with a safety factor 4), that
+            // correction is applied without a further confirming solve.
             if (threadIdx.x == 0) {
                 int all = 1;
                 for (int col = 0; col < R; ++col) {
-                    if (c.col_frozen[col]) c.col_done[col] = 1;   // its last correction is in
+                    c.col_frozen[col] = c.col_done[col] = !(c.gamma[col] > 0.0);
+                    c.eps_prev[col] = c.gamma[col];
                     all &= c.col_done[col];
                 }
-                c.all_done = all || pass >= g.it_max;
-                c.converged = all;
+                c.all_done = all;
             }
             __syncthreads();
-            if (c.all_done) break;
-            if constexpr (SCHUR) {
-                solve_schur(g, F, sinfo, y, cw, opbuf, stage, c.eps, c);
+            int pass = 0;
+            while (!c.all_done) {
+                // D = s . y (FP64), Z += D
+                for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                    const int col = t / g.nunk, u = t - col * g.nunk;
+                    if (c.col_done[col]) continue;
+                    const double d = (double)y[(size_t)u * g.Rp + col] * scale[u];
+                    D64[t] = d;
+                    Z[t] += d;
+                }
                 __syncthreads();
-            } else {
+                // Res -= A_p D (FP64, from kappa and the element matrices); y = s . Res
+                for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) apply_residual(g, c, kap, u, D64, Res, y, scale[u]);
+                ++pass;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int all = 1;
+                    for (int col = 0; col < R; ++col) {
+                        if (c.col_frozen[col]) c.col_done[col] = 1;   // its last correction is in
+                        all &= c.col_done[col];
+                    }
+                    c.all_done = all || pass >= g.it_max;
+                    c.converged = all;
+                }
+                __syncthreads();
+                if (c.all_done) break;
                 solve_factor(g, F, sinfo, y, opbuf, stage, c);
                 __syncthreads();
                 column_dot(g, Res, y, scale, c.eps, c);
                 __syncthreads();
+                if (threadIdx.x == 0) {
+                    int all = 1;
+                    for (int col = 0; col < R; ++col) {
+                        if (!c.col_frozen[col]) {
+                            const double eps = c.eps[col], lim = g.tol * c.gamma[col];
+                            if (eps <= lim) c.col_frozen[col] = c.col_done[col] = 1;
+                            else if (4.0 * eps * eps <= lim * c.eps_prev[col]) c.col_frozen[col] = 1;
+                            c.eps_prev[col] = eps;
+                        }
+                        all &= c.col_done[col];
+                    }
+                    c.all_done = all;
+                    c.converged = all;
+                }
+                __syncthreads();
+            }
+            const int converged = c.converged;
+
+            // ---- local contributions X[j][i] = N~_j^T z_i + z_j^T Res_i; A_K = -(X + X^T)/2, E_K = X[:, f]
+            {
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                for (int col = warp; col < R; col += kWarpsM) {          // m^T z per column
+                    const double* zc = Z + (size_t)col * g.nunk;
+                    double mz = 0.0;
+                    for (int u = lane; u < g.nunk; u += 32) mz = fma(mass[u], zc[u], mz);
+                    for (int o = 16; o > 0; o >>= 1) mz += __shfl_down_sync(0xffffffffu, mz, o);
+                    if (lane == 0) c.mz[col] = mz;
+                }
+            }
+            // correction Gram Z^T Res in FP32 (it is of the size of the error of Z), by node chunks
+            float corr[(kMaxNI + 1) * (kMaxNI + 1) / kThreadsM + 1];
+            const int npair = R * R;
+            for (int q = 0; q * kThreadsM < npair; ++q) corr[q] = 0.0f;
+            constexpr int kChunk = 64;
+            float* zs = y;                       // R x kChunk
+            float* rs = y + R * kChunk;          // R x kChunk
+            for (int base = 0; base < g.nunk; base += kChunk) {
+                const int cnt = min(kChunk, g.nunk - base);
+                __syncthreads();
+                for (int t = threadIdx.x; t < R * kChunk; t += blockDim.x) {
+                    const int col = t / kChunk, uu = t - col * kChunk;
+                    zs[t] = uu < cnt ? (float)Z[(size_t)col * g.nunk + base + uu] : 0.0f;
+                    rs[t] = uu < cnt ? (float)Res[(size_t)col * g.nunk + base + uu] : 0.0f;
+                }
+                __syncthreads();
+                for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) {
+                    const int t = q * kThreadsM + threadIdx.x, j = t / R, i = t - j * R;
+                    float a = 0.0f;
+                    for (int uu = 0; uu < kChunk; ++uu) a = fmaf(zs[j * kChunk + uu], rs[i * kChunk + uu], a);
+                    corr[q] += a;
+                }
+            }
+            __syncthreads();
+            double* xbuf = reinterpret_cast<double*>(W);   // reuse the window: R x R doubles
+            for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) xbuf[q * kThreadsM + threadIdx.x] = corr[q];
+            __syncthreads();
+            for (int t = threadIdx.x; t < g.NI * R; t += blockDim.x) {
+                const int j = t / R, col = t - j * R;
+                const int a = j / g.dpf, jf = j - a * g.dpf;
+                const double* zc = Z + (size_t)col * g.nunk;
+                double s = 0.0;
+                for (int kl = 0; kl <= g.PN; ++kl) {
+                    int X, Y;
+                    if (a == 2) { X = kl; Y = 0; }
+                    else if (a == 0) { X = g.PN - kl; Y = kl; }
+                    else { X = 0; Y = g.PN - kl; }
+                    const int u = unk(g.PN, X, Y);
+                    if (u < 0) continue;
+                    const int kk = c.rev[a] ? g.PN - kl : kl;
+                    s += (-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk]) * zc[u];
+                }
+                xbuf[j * R + col] += s - c.cproj[j] * c.mz[col];
+            }
+            __syncthreads();
+            const int NI = g.NI;
+            for (int t = threadIdx.x; t < NI * NI; t += blockDim.x) {
+                const int j = t / NI, i = t - j * NI;
+                g.AK[K * NI * NI + t] = -0.5 * (xbuf[j * R + i] + xbuf[i * R + j]);
+            }
+            for (int j = threadIdx.x; j < NI; j += blockDim.x) {
+                g.EK[K * NI + j] = xbuf[j * R + NI];
+                const int a = j / g.dpf, jf = j - a * g.dpf;
+                g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
             }
             if (threadIdx.x == 0) {
-                int all = 1;
-                for (int col = 0; col < R; ++col) {
-                    if (!c.col_frozen[col]) {
-                        const double eps = c.eps[col], lim = g.tol * c.gamma[col];
-                        if (eps <= lim) c.col_frozen[col] = c.col_done[col] = 1;
-                        else if (4.0 * eps * eps <= lim * c.eps_prev[col]) c.col_frozen[col] = 1;
-                        c.eps_prev[col] = eps;
-                    }
-                    all &= c.col_done[col];
-                }
-                c.all_done = all;
-                c.converged = all;
+                g.FK[K] = c.FK;
+                g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                if (g.iters) g.iters[K] = pass;
             }
             __syncthreads();
         }
-        const int converged = c.converged;
-
-        // ---- local contributions X[j][i] = N~_j^T z_i + z_j^T Res_i; A_K = -(X + X^T)/2, E_K = X[:, f]
-        {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int col = warp; col < R; col += kWarpsM) {          // m^T z per column
-                const double* zc = Z + (size_t)col * g.nunk;
-                double mz = 0.0;
-                for (int u = lane; u < g.nunk; u += 32) mz = fma(mass[u], zc[u], mz);
-                for (int o = 16; o > 0; o >>= 1) mz += __shfl_down_sync(0xffffffffu, mz, o);
-                if (lane == 0) c.mz[col] = mz;
-            }
-        }
-        // correction Gram Z^T Res in FP32 (it is of the size of the error of Z), by node chunks
-        float corr[(kMaxNI + 1) * (kMaxNI + 1) / kThreadsM + 1];
-        const int npair = R * R;
-        for (int q = 0; q * kThreadsM < npair; ++q) corr[q] = 0.0f;
-        constexpr int kChunk = 64;
-        float* zs = y;                       // R x kChunk
-        float* rs = y + R * kChunk;          // R x kChunk
-        for (int base = 0; base < g.nunk; base += kChunk) {
-            const int cnt = min(kChunk, g.nunk - base);
-            __syncthreads();
-            for (int t = threadIdx.x; t < R * kChunk; t += blockDim.x) {
-                const int col = t / kChunk, uu = t - col * kChunk;
-                zs[t] = uu < cnt ? (float)Z[(size_t)col * g.nunk + base + uu] : 0.0f;
-                rs[t] = uu < cnt ? (float)Res[(size_t)col * g.nunk + base + uu] : 0.0f;
-            }
-            __syncthreads();
-            for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) {
-                const int t = q * kThreadsM + threadIdx.x, j = t / R, i = t - j * R;
-                float a = 0.0f;
-                for (int uu = 0; uu < kChunk; ++uu) a = fmaf(zs[j * kChunk + uu], rs[i * kChunk + uu], a);
-                corr[q] += a;
-            }
-        }
-        __syncthreads();
-        double* xbuf = reinterpret_cast<double*>(W);   // reuse the window: R x R doubles
-        for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) xbuf[q * kThreadsM + threadIdx.x] = corr[q];
-        __syncthreads();
-        for (int t = threadIdx.x; t < g.NI * R; t += blockDim.x) {
-            const int j = t / R, col = t - j * R;
-            const int a = j / g.dpf, jf = j - a * g.dpf;
-            const double* zc = Z + (size_t)col * g.nunk;
-            double s = 0.0;
-            for (int kl = 0; kl <= g.PN; ++kl) {
-                int X, Y;
-                if (a == 2) { X = kl; Y = 0; }
-                else if (a == 0) { X = g.PN - kl; Y = kl; }
-                else { X = 0; Y = g.PN - kl; }
-                const int u = unk(g.PN, X, Y);
-                if (u < 0) continue;
-                const int kk = c.rev[a] ? g.PN - kl : kl;
-                s += (-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk]) * zc[u];
-            }
-            xbuf[j * R + col] += s - c.cproj[j] * c.mz[col];
-        }
-        __syncthreads();
-        const int NI = g.NI;
-        for (int t = threadIdx.x; t < NI * NI; t += blockDim.x) {
-            const int j = t / NI, i = t - j * NI;
-            g.AK[K * NI * NI + t] = -0.5 * (xbuf[j * R + i] + xbuf[i * R + j]);
-        }
-        for (int j = threadIdx.x; j < NI; j += blockDim.x) {
-            g.EK[K * NI + j] = xbuf[j * R + NI];
-            const int a = j / g.dpf, jf = j - a * g.dpf;
-            g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
-        }
-        if (threadIdx.x == 0) {
-            g.FK[K] = c.FK;
-            g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
-            if (g.iters) g.iters[K] = pass;
-        }
-        __syncthreads();
         if (g.kcounter) {
             K = c.nextK;
             __syncthreads();
@@ -1262,10 +1514,15 @@ __global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedA
         int v[7];
         p1_row(g.N, g.PN, nu, fs.Su, fs.Sd, kap, X, Y, u, w, v);
         const double su = scale[u];
-        cw[u] = (float)(w[1] * su * scale[v[1]]);
-        cw[nu + u] = (float)(w[2] * su * scale[v[2]]);
-        cw[2 * nu + u] = (float)(w[4] * su * scale[v[4]]);
-        cw[3 * nu + u] = (float)(w[5] * su * scale[v[5]]);
+        double ah[7];
+        for (int d = 0; d < 7; ++d) ah[d] = w[d] * su * scale[v[d]];
+        cw[u] = (float)ah[1];
+        cw[nu + u] = (float)ah[2];
+        cw[2 * nu + u] = (float)ah[4];
+        cw[3 * nu + u] = (float)ah[5];
+        double* ahK = g.ahall + kk * 7 * (int64_t)nu;
+        for (int d = 0; d < 7; ++d) ahK[(size_t)d * nu + u] = ah[d];
+        g.scall[kk * (int64_t)nu + u] = su;
     }
     __syncwarp();
     const LevelGeom lg{1, g.N, g.PN};
@@ -1340,7 +1597,8 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, bool split = true) {
     const int R = (int)mesh->NI + 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     L.off_G = L.mode == 2 ? 0 : al(f * sizeof(float));   // MODE 2 keeps the operators outside the slots
-    L.chunk_k_bytes = al(f * sizeof(float)) + al((size_t)4 * L.nunk * sizeof(float)) + 256;
+    L.chunk_k_bytes = al(f * sizeof(float)) + al((size_t)4 * L.nunk * sizeof(float)) + 256 +
+                      al((size_t)L.nunk * sizeof(double)) + al((size_t)7 * L.nunk * sizeof(double));
     L.off_Z = L.off_G + al((size_t)L.nunk * R * sizeof(double));
     L.off_mass = L.off_Z + al((size_t)L.nunk * R * sizeof(double));
     L.off_scale = L.off_mass + al((size_t)L.nunk * sizeof(double));
@@ -1522,6 +1780,11 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
     g.Tall = reinterpret_cast<float*>(cbase);
     g.cwall = reinterpret_cast<float*>(cbase + tb);
     g.fbad = reinterpret_cast<int*>(cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float));
+    {
+        char* p = cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float) + (((size_t)chunk * sizeof(int) + 255) & ~(size_t)255);
+        g.scall = reinterpret_cast<double*>(p);
+        g.ahall = reinterpret_cast<double*>(p + (((size_t)chunk * L.nunk * sizeof(double) + 255) & ~(size_t)255));
+    }
     const size_t fsmem = factor_smem_bytes(L.nunk);
     MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int64_t c0 = K0; c0 < K1; c0 += chunk) {
