@@ -171,6 +171,16 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def measured_peaks():
+    """The measured peaks of this GPU pool (HBM copy GB/s, bf16 TFLOP/s), if present."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 def residual_fmas_per_pass(w):
     """FP64 multiply-adds of one refinement pass of the mixed path for one K: the
     assembled 7-point (P1) rows of A_p applied to the R right-hand sides."""
@@ -199,10 +209,15 @@ def residual_fmas_per_pass(w):
 
 
 def time_path(p, kap, src, gd, steps, warmup, flush, stream, barrier):
+    """Times `steps` steps (local solves + skeleton), with the library's CUDA events
+    around each of its local-solve kernel launches on the same stream; returns the
+    step and local-solve times (ms) and {kernel: (launches, total ms)}."""
     import torch
+    from paper_1703_10435_gb300 import mhm
     for _ in range(warmup):
         p.step(kap, src, gd)
     torch.cuda.synchronize()
+    mhm.mhm_set_timing(p.mesh, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
@@ -216,9 +231,11 @@ def time_path(p, kap, src, gd, steps, warmup, flush, stream, barrier):
         ev[s][2].record(stream)
     torch.cuda.synchronize()
     barrier()
+    kern = mhm.mhm_kernel_times(p.mesh)
+    mhm.mhm_set_timing(p.mesh, False)
     step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
     local_ms = np.array([a.elapsed_time(b) for a, b, c in ev])
-    return step_ms, local_ms
+    return step_ms, local_ms, kern
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -245,8 +262,8 @@ def run_ours(args, w, rank, world, local_rank):
     pmx = Pipeline.for_workload(w, local_rank, mhm.MHM_MIXED)
     sampler = ClockSampler(local_rank)
     sampler.start()
-    step64, local64 = time_path(p64, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
-    stepmx, localmx = time_path(pmx, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
+    step64, local64, kern64 = time_path(p64, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
+    stepmx, localmx, kernmx = time_path(pmx, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
     clocks = sampler.stop()
     for p in (p64, pmx):
         assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
@@ -309,20 +326,48 @@ def run_ours(args, w, rank, world, local_rank):
     # 128 FP32 FMA per clock per SM
     peak64 = 2 * 2 * sms * clk * 1e6 / 1e12
     peak32 = 2 * 128 * sms * clk * 1e6 / 1e12
-    fl64 = 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K
-    t_local64 = float(local64.mean()) * 1e-3
-    t_localmx = float(localmx.mean()) * 1e-3
+    # Per-kernel average launch durations over the timed region: the library's CUDA
+    # events around each local-solve launch, on the launching stream.
+    def per_launch(kern, name):
+        n, ms = kern.get(name, (0, 0.0))
+        return (n, ms / n * 1e-3) if n else (0, None)
+    n64, t_k64 = per_launch(kern64, "k_local_fp64")
+    nmx, t_kmx = per_launch(kernmx, "k_local_mixed")
+    nfac, t_kfac = per_launch(kernmx, "k_schur_factor")
+    fl64 = 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K * args.steps / max(n64, 1)
+    K_per_launch = w.n_K * args.steps / max(nmx, 1)
     res = residual_fmas_per_pass(w)
-    fl_res = None if res is None else 2.0 * res * passes * w.n_K
+    fl_res = None if res is None else 2.0 * res * passes * K_per_launch
+    # tensor-core level products of the mixed solves: 2 b^2 R useful flops per level step
+    # (forward every level, backward all but the last), about `passes` solves per K
+    tc = None
+    if w.degree == 1 and t_kmx:
+        sizes = [w.N + 1 - lev - (lev == 0) for lev in range(w.N + 1)]
+        per_solve = 2.0 * (w.n_I + 1) * (2 * sum(b * b for b in sizes) - sizes[-1] ** 2)
+        fl_tc = per_solve * passes * K_per_launch
+        # dense TF32 tensor peak: the measured bf16 burst figure times the nominal tf32/bf16 ratio
+        peak_bf16 = measured_peaks().get("bf16_tflops")
+        peak_tf32 = peak_bf16 * (1.1 / 2.25) if peak_bf16 else None
+        tc = {"pipe": "tensor (TF32, three-term split: 3 MMA per product)", "algorithmic_flops_per_launch": fl_tc,
+              "achieved": fl_tc / t_kmx / 1e12, "peak": peak_tf32, "unit": "TFLOP/s",
+              "frac": (fl_tc / t_kmx / 1e12 / peak_tf32) if peak_tf32 else None,
+              "peak_source": "MEASURED_PEAKS.json bf16 burst x 1.1/2.25 (nominal tf32/bf16)"}
     roof_mx = {"kernel": "k_local_mixed", "bound": "alu", "pipe": "fp64 (refinement residuals)",
-               "achieved": (fl_res / t_localmx / 1e12) if fl_res else None, "peak": peak64, "unit": "TFLOP/s",
-               "frac": (fl_res / t_localmx / 1e12 / peak64) if fl_res else None, "traffic": None,
-               "flops_per_launch": fl_res, "refinement_passes_mean": passes,
-               "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
-               "fp64_equivalent_local_solve_tflops": fl64 / t_localmx / 1e12}
-    roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64", "achieved": fl64 / t_local64 / 1e12,
-               "peak": peak64, "unit": "TFLOP/s", "frac": fl64 / t_local64 / 1e12 / peak64, "traffic": None,
-               "flops_per_launch": fl64, "peak_measured_microbench": pipes["fp64_gflops"] / 1e3}
+               "achieved": (fl_res / t_kmx / 1e12) if (fl_res and t_kmx) else None, "peak": peak64, "unit": "TFLOP/s",
+               "frac": (fl_res / t_kmx / 1e12 / peak64) if (fl_res and t_kmx) else None, "traffic": None,
+               "flops_per_launch": fl_res, "launch_ms": t_kmx * 1e3 if t_kmx else None, "launches": nmx,
+               "refinement_passes_mean": passes,
+               "peak_source": "2 FP64 FMA/clk/SM x SMs x max SM clock", "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
+               "tensor": tc,
+               "factor_kernel": {"kernel": "k_schur_factor", "launch_ms": t_kfac * 1e3 if t_kfac else None,
+                                 "launches": nfac},
+               "fp64_equivalent_local_solve_tflops": 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K
+               / (float(localmx.mean()) * 1e-3) / 1e12}
+    roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64",
+               "achieved": fl64 / t_k64 / 1e12 if t_k64 else None, "peak": peak64, "unit": "TFLOP/s",
+               "frac": fl64 / t_k64 / 1e12 / peak64 if t_k64 else None, "traffic": None,
+               "flops_per_launch": fl64, "launch_ms": t_k64 * 1e3 if t_k64 else None, "launches": n64,
+               "peak_measured_microbench": pipes["fp64_gflops"] / 1e3}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -353,7 +398,9 @@ def run_ours(args, w, rank, world, local_rank):
         "roofline": roof_mx,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "coarse elements/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        # our kernels in the timed region of the headline (mixed) path: the local-solve
+        # launches recorded by the library plus the two skeleton kernels per step
+        "gpu_launches": sum(n for n, _ in kernmx.values()) + 2 * args.steps,
         "clocks": clocks,
         "pipes_gflops": pipes,
     }

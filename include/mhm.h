@@ -243,6 +243,22 @@ const char* mhm_last_error(void);
  * over the whole GPU, 2 flops per FMA.  Synchronous. */
 mhm_status mhm_measure_pipes(int32_t device, double* out_host);
 
+/* Per-kernel timing of the local solves, a measurement aid with no counterpart in
+ * the paper.  After mhm_set_timing(mesh, 1), every mhm_local_solve_batch call on
+ * `mesh` records a CUDA event on its stream before and after each of its kernel
+ * launches (library-owned events, created on first need and reused).
+ * mhm_kernel_times waits for the events recorded since timing was enabled or last
+ * read and writes, for each kernel id below (MHM_N_KERNELS entries each, host
+ * arrays), the number of launches and their total duration in milliseconds; it then
+ * starts a new reading.  Not thread-safe for calls on the same mesh.
+ * Errors: INVALID_ARG (NULL argument, host-only mesh), CUDA. */
+#define MHM_KERNEL_LOCAL_FP64 0   /* FP64 local solve */
+#define MHM_KERNEL_LOCAL_MIXED 1  /* mixed-precision local solve and refinement */
+#define MHM_KERNEL_SCHUR_FACTOR 2 /* mixed path, P1: level Schur complement inverses */
+#define MHM_N_KERNELS 3
+mhm_status mhm_set_timing(mhm_mesh* mesh, int32_t enable);
+mhm_status mhm_kernel_times(const mhm_mesh* mesh, int32_t* launches_host, double* ms_host);
+
 #ifdef __cplusplus
 }
 #endif

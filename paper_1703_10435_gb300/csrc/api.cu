@@ -23,6 +23,25 @@ mhm_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? MHM_ERR_OOM : MHM_ERR_CUDA;
 }
 
+void timing_begin(const mhm_mesh* m) {
+    m->tev_used = 0;
+    m->tev_kernel.clear();
+}
+
+void timing_mark(const mhm_mesh* m, int kernel, cudaStream_t s, bool start) {
+    if (!m->timing) return;
+    if (m->tev_used == m->tev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            m->timing = false;   // no timing rather than a failed solve
+            return;
+        }
+        m->tev.push_back(e);
+    }
+    cudaEventRecord(m->tev[m->tev_used++], s);
+    if (start) m->tev_kernel.push_back(kernel);
+}
+
 bool device_supported(int device) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return false;
@@ -155,5 +174,35 @@ extern "C" mhm_status mhm_measure_pipes(int32_t device, double* out) {
     out[1] = time_fma<float, 16>(sms, 1 << 16);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mhm_measure_pipes");
+    return MHM_OK;
+}
+
+extern "C" mhm_status mhm_set_timing(mhm_mesh* mesh, int32_t enable) {
+    if (!mesh || mesh->device < 0) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_set_timing: no device mesh");
+    mesh->timing = enable != 0;
+    mhm::timing_begin(mesh);
+    return MHM_OK;
+}
+
+extern "C" mhm_status mhm_kernel_times(const mhm_mesh* mesh, int32_t* launches, double* ms) {
+    if (!mesh || mesh->device < 0 || !launches || !ms)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_kernel_times: NULL argument or host-only mesh");
+    for (int k = 0; k < MHM_N_KERNELS; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+    }
+    for (size_t i = 0; i < mesh->tev_kernel.size() && 2 * i + 1 < mesh->tev_used; ++i) {
+        cudaEvent_t a = mesh->tev[2 * i], b = mesh->tev[2 * i + 1];
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess) return mhm::cuda_fail(e, "mhm_kernel_times");
+        const int k = mesh->tev_kernel[i];
+        if (k >= 0 && k < MHM_N_KERNELS) {
+            launches[k] += 1;
+            ms[k] += t;
+        }
+    }
+    mhm::timing_begin(mesh);   // the next reading covers the calls from here on
     return MHM_OK;
 }

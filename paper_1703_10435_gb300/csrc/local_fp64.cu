@@ -365,7 +365,9 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mh
     MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t nblk = K1 - K0;
     if (nblk <= 0) return MHM_OK;
+    timing_mark(mesh, MHM_KERNEL_LOCAL_FP64, stream, true);
     kern<<<(unsigned)nblk, kThreads, smem, stream>>>(g);
+    timing_mark(mesh, MHM_KERNEL_LOCAL_FP64, stream, false);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }

@@ -172,10 +172,15 @@ __device__ __forceinline__ int unk(int PN, int X, int Y) {
     return Y * (PN + 1) - Y * (Y - 1) / 2 + X - 1;
 }
 
+// Row y of lattice DOF d = u + 1 solves S(y) <= d < S(y + 1), S(y) = y (2 PN + 3 - y) / 2
+// (the first DOF of row y): the root of the quadratic in FP32, then an exact fix-up.
 __device__ __forceinline__ void lattice_of_unk(int PN, int u, int* X, int* Y) {
-    int d = u + 1, y = 0;
-    while (d >= PN + 1 - y) { d -= PN + 1 - y; ++y; }
-    *X = d;
+    const int d = u + 1, b = 2 * PN + 3;
+    int y = (int)(0.5f * ((float)b - sqrtf((float)(b * b - 8 * d))));
+    y = max(0, min(y, PN));
+    while (y < PN && (y + 1) * (b - y - 1) / 2 <= d) ++y;
+    while (y > 0 && y * (b - y) / 2 > d) --y;
+    *X = d - y * (b - y) / 2;
     *Y = y;
 }
 
@@ -654,6 +659,12 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     const bool issuer = threadIdx.x == kThreadsM - 32;
     if (issuer) issue(0);
     for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
+    // the right-hand side r = FP32 rounding of Rh, in y (frozen columns keep their pending correction);
+    // node-major on both sides, so the reads are coalesced and all in flight together
+    for (int t = threadIdx.x; t < nu * R; t += kThreadsM) {
+        const int col = t % R;
+        if (!(frozen >> col & 1)) y[t] = d2f_bits(Rh[t]);
+    }
     __syncthreads();
     float eacc0 = 0.0f, eacc1 = 0.0f;   // this lane's two columns (2 tq, 2 tq + 1 of its column tile)
     for (int st = 0; st < nsteps; ++st) {
@@ -672,7 +683,7 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
                 const int x = i + xo;
                 float v;
                 if (dir == 0) {
-                    v = d2f_bits(Rh[(size_t)(ulev + i) * R + col]);   // right-hand side: the scaled residual
+                    v = lds1(y_s + 4u * (uint32_t)((ulev + i) * R + col));   // right-hand side
                     if (lev > 0) {
                         const int ps = x - off, pse = x + 1 - off;
                         float a = cwSE[ulev + i] * lds1(y_s + 4u * (uint32_t)((uo + pse) * R + col));
@@ -740,6 +751,57 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     if (threadIdx.x == 0) {
         c.phase[0] = ph0;
         c.phase[1] = ph1;
+    }
+}
+
+// One refinement pass of the level-Schur path, in scaled variables, for the columns
+// not done: Zh_u += y_u and Rh_u -= sum_v Ah_uv y_v over the stencil points v of u,
+// accumulated in FP64 (y widened on the integer pipe).  A node's entries are read 8
+// columns at a time before they are used, so that their loads are in flight
+// together.  Thread per node; `done` has bit col set for the columns to skip.
+__device__ __noinline__ void fused_residual(int PN, int nu, int R, const double* __restrict__ ah, const float* y,
+                                            double* __restrict__ Zh, double* __restrict__ Rh, uint64_t done) {
+    const uint32_t y_s = smem_u32(y);
+    for (int u = threadIdx.x; u < nu; u += kThreadsM) {
+        int X, Y;
+        lattice_of_unk(PN, u, &X, &Y);
+        int v[7];
+        v[0] = u;
+        v[1] = unk(PN, X + 1, Y);
+        v[2] = unk(PN, X - 1, Y);
+        v[3] = unk(PN, X, Y + 1);
+        v[4] = unk(PN, X, Y - 1);
+        v[5] = unk(PN, X + 1, Y - 1);
+        v[6] = unk(PN, X - 1, Y + 1);
+        double a[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+            a[d] = ah[(size_t)d * nu + u];
+            if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
+        }
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            double zr[8], rr[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = c0 + j;
+                const bool on = col < R && !(done >> col & 1);
+                zr[j] = on ? Zh[(size_t)u * R + col] : 0.0;
+                rr[j] = on ? Rh[(size_t)u * R + col] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = c0 + j;
+                if (col < R && !(done >> col & 1)) {
+                    const double d0 = f2d_bits(lds1(y_s + 4u * (uint32_t)(u * R + col)));
+                    Zh[(size_t)u * R + col] = zr[j] + d0;
+                    double r = fma(-a[0], d0, rr[j]);
+#pragma unroll
+                    for (int d = 1; d < 7; ++d)
+                        if (a[d] != 0.0) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
+                    Rh[(size_t)u * R + col] = r;
+                }
+            }
+        }
     }
 }
 
@@ -982,34 +1044,11 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             int pass = 0;
             while (!c.all_done) {
                 // Zh += y and Rh -= Ah y in one pass (y read at the node and its stencil points)
-                for (int u = threadIdx.x; u < nu; u += blockDim.x) {
-                    int X, Y;
-                    lattice_of_unk(g.PN, u, &X, &Y);
-                    int v[7];
-                    v[0] = u;
-                    v[1] = unk(g.PN, X + 1, Y);
-                    v[2] = unk(g.PN, X - 1, Y);
-                    v[3] = unk(g.PN, X, Y + 1);
-                    v[4] = unk(g.PN, X, Y - 1);
-                    v[5] = unk(g.PN, X + 1, Y - 1);
-                    v[6] = unk(g.PN, X - 1, Y + 1);
-                    double a[7];
-#pragma unroll
-                    for (int d = 0; d < 7; ++d) {
-                        a[d] = ah[(size_t)d * nu + u];
-                        if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
-                    }
-                    for (int col = 0; col < R; ++col) {
-                        if (c.col_done[col]) continue;
-                        const size_t o = (size_t)u * R + col;
-                        const double d0 = f2d_bits(y[o]);
-                        Zh[o] += d0;
-                        double r = fma(-a[0], d0, Rh[o]);
-#pragma unroll
-                        for (int d = 1; d < 7; ++d)
-                            if (a[d] != 0.0) r = fma(-a[d], f2d_bits(y[(size_t)v[d] * R + col]), r);
-                        Rh[o] = r;
-                    }
+                {
+                    uint64_t done = 0;
+                    for (int col = 0; col < R; ++col)
+                        if (c.col_done[col]) done |= 1ull << col;
+                    fused_residual(g.PN, nu, R, ah, y, Zh, Rh, done);
                 }
                 ++pass;
                 __syncthreads();
@@ -1043,62 +1082,76 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 __syncthreads();
             }
             const int converged = c.converged;
-            // ---- outputs X[j][i] = N~_j^T z_i + z_j^T Res_i = (S N~_j)^T Zh_i + Zh_j^T Rh_i
+            // ---- outputs X[j][i] = N~_j^T z_i + z_j^T Res_i = (S N~_j)^T Zh_i + Zh_j^T Rh_i.
+            // Lane = column, warps take node rows in turn: every row read is one coalesced
+            // load of R doubles.  The Gram Zh^T Rh (the correction, of the size of the error
+            // of Z) accumulates in FP32, one R x R partial per warp in shared memory; the mass
+            // term (S m)^T Zh in FP64; partials are summed in a fixed warp order.
             {
                 const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                for (int col = warp; col < R; col += kWarpsM) {          // (S m)^T Zh per column
+                const bool lc = lane < R;
+                // in y (free now): 8 R x R float partials, 8 x R double mass partials, R x R result
+                const int gfl = (kWarpsM * R * R + 1) & ~1;
+                float* gpart = y;
+                double* mpart = reinterpret_cast<double*>(y + gfl);
+                double* xbuf = reinterpret_cast<double*>(y + gfl + 2 * kWarpsM * R);
+                float acc[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+                double mzp = 0.0;
+                for (int u = warp; u < nu; u += kWarpsM) {
+                    const double zh = lc ? Zh[(size_t)u * R + lane] : 0.0;
+                    const double rh = lc ? Rh[(size_t)u * R + lane] : 0.0;
+                    mzp = fma(smass[u], zh, mzp);
+                    const float zf = d2f_bits(zh), rf = d2f_bits(rh);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float ri = __shfl_sync(0xffffffffu, rf, i);
+                        if (i < R) acc[i] = fmaf(zf, ri, acc[i]);
+                    }
+                }
+                if (lc) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < R) gpart[(warp * R + lane) * R + i] = acc[i];
+                    mpart[warp * R + lane] = mzp;
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+                    float sg = 0.0f;
+                    for (int w2 = 0; w2 < kWarpsM; ++w2) sg += gpart[w2 * R * R + t];
+                    xbuf[t] = sg;
+                }
+                if (threadIdx.x < R) {
                     double mz = 0.0;
-                    for (int u = lane; u < nu; u += 32) mz = fma(smass[u], Zh[(size_t)u * R + col], mz);
-                    for (int o = 16; o > 0; o >>= 1) mz += __shfl_down_sync(0xffffffffu, mz, o);
-                    if (lane == 0) c.mz[col] = mz;
-                }
-            }
-            // correction Gram Zh^T Rh in FP32 (it is of the size of the error of Z), by node chunks
-            float corr[(kMaxNI + 1) * (kMaxNI + 1) / kThreadsM + 1];
-            const int npair = R * R;
-            for (int q = 0; q * kThreadsM < npair; ++q) corr[q] = 0.0f;
-            constexpr int kChunk = 64;
-            float* zs = y;                       // R x kChunk
-            float* rs = y + R * kChunk;          // R x kChunk
-            for (int base = 0; base < nu; base += kChunk) {
-                const int cnt = min(kChunk, nu - base);
-                __syncthreads();
-                for (int t = threadIdx.x; t < R * kChunk; t += blockDim.x) {
-                    const int uu = t / R, col = t - uu * R;
-                    const size_t o = (size_t)(base + uu) * R + col;
-                    zs[col * kChunk + uu] = uu < cnt ? d2f_bits(Zh[o]) : 0.0f;
-                    rs[col * kChunk + uu] = uu < cnt ? d2f_bits(Rh[o]) : 0.0f;
+                    for (int w2 = 0; w2 < kWarpsM; ++w2) mz += mpart[w2 * R + threadIdx.x];
+                    c.mz[threadIdx.x] = mz;
                 }
                 __syncthreads();
-                for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) {
-                    const int t = q * kThreadsM + threadIdx.x, j = t / R, i = t - j * R;
-                    float a = 0.0f;
-                    for (int uu = 0; uu < kChunk; ++uu) a = fmaf(zs[j * kChunk + uu], rs[i * kChunk + uu], a);
-                    corr[q] += a;
+                // boundary terms (S N_j)^T Zh: warp per face, lane = column, FP64
+                if (warp < 3 && lc) {
+                    const int a = warp;
+                    double sb[kMaxFaceDofs];
+                    for (int jf = 0; jf < g.dpf; ++jf) sb[jf] = 0.0;
+                    for (int kl = 0; kl <= g.PN; ++kl) {
+                        int X, Y;
+                        if (a == 2) { X = kl; Y = 0; }
+                        else if (a == 0) { X = g.PN - kl; Y = kl; }
+                        else { X = 0; Y = g.PN - kl; }
+                        const int u = unk(g.PN, X, Y);
+                        if (u < 0) continue;
+                        const int kk2 = c.rev[a] ? g.PN - kl : kl;
+                        const double zs = sc[u] * Zh[(size_t)u * R + lane] * (-c.sgn[a] * c.flen[a]);
+                        for (int jf = 0; jf < g.dpf; ++jf) sb[jf] = fma(g.dm.btab[jf * (g.PN + 1) + kk2], zs, sb[jf]);
+                    }
+                    for (int jf = 0; jf < g.dpf; ++jf) {
+                        const int j = a * g.dpf + jf;
+                        xbuf[j * R + lane] += sb[jf] - c.cproj[j] * c.mz[lane];
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
-            double* xbuf = reinterpret_cast<double*>(W);   // R x R doubles
-            for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) xbuf[q * kThreadsM + threadIdx.x] = corr[q];
-            __syncthreads();
-            for (int t = threadIdx.x; t < g.NI * R; t += blockDim.x) {
-                const int j = t / R, col = t - j * R;
-                const int a = j / g.dpf, jf = j - a * g.dpf;
-                double sacc = 0.0;
-                for (int kl = 0; kl <= g.PN; ++kl) {
-                    int X, Y;
-                    if (a == 2) { X = kl; Y = 0; }
-                    else if (a == 0) { X = g.PN - kl; Y = kl; }
-                    else { X = 0; Y = g.PN - kl; }
-                    const int u = unk(g.PN, X, Y);
-                    if (u < 0) continue;
-                    const int kk2 = c.rev[a] ? g.PN - kl : kl;
-                    sacc = fma((-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk2]) * sc[u], Zh[(size_t)u * R + col],
-                               sacc);
-                }
-                xbuf[j * R + col] += sacc - c.cproj[j] * c.mz[col];
-            }
-            __syncthreads();
+            const double* xbuf = reinterpret_cast<const double*>(y + ((kWarpsM * R * R + 1) & ~1) + 2 * kWarpsM * R);
             const int NI = g.NI;
             for (int t = threadIdx.x; t < NI * NI; t += blockDim.x) {
                 const int j = t / NI, i = t - j * NI;
@@ -1628,6 +1681,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, bool split = true) {
     if (yf < (size_t)2 * R * 64) yf = (size_t)2 * R * 64;   // also holds two R x 64 staging chunks
     L.ldr = (2 * bmax + 3) & ~3;
     if (!L.schur && yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
+    if (L.schur) yf = std::max(yf, (size_t)(10 * R * R + 16 * R + 8));      // and the output partials
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
     size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
     off = (off + 15) & ~(size_t)15;
@@ -1769,7 +1823,9 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
         g.K1 = K1;
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(nK < slots ? nK : slots);
+        timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
+        timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
         return MHM_OK;
     }
@@ -1792,11 +1848,15 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
         g.Kc0 = c0;
         g.K0 = c0;
         g.K1 = c1;
+        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, true);
         k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, stream>>>(g);
+        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(c1 - c0 < slots ? c1 - c0 : slots);
+        timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
+        timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
     }
     return MHM_OK;

@@ -370,6 +370,7 @@ extern "C" void mhm_destroy_mesh(mhm_mesh* m) {
     cudaGetDevice(&cur);
     cudaSetDevice(m->device);
     free_mesh_device(m);
+    for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
     cudaSetDevice(cur);
     delete m;
 }

@@ -14,6 +14,10 @@ namespace mhm {
 // Thread-local error text behind mhm_last_error().
 void set_error(const std::string& msg);
 mhm_status fail(mhm_status code, const std::string& msg);
+// Local-solve timing marks (no-ops unless timing is enabled on the mesh): begin starts a
+// new reading; start/stop go around each kernel launch on stream s.
+void timing_begin(const mhm_mesh* m);
+void timing_mark(const mhm_mesh* m, int kernel, cudaStream_t s, bool start);
 mhm_status cuda_fail(cudaError_t e, const char* what);
 
 #define MHM_CUDA_TRY(expr)                                              \
@@ -52,6 +56,12 @@ struct DeviceMesh {
 
 struct mhm_mesh {
     int device = 0;
+    // per-kernel timing of the local solves (mhm_set_timing): events recorded on the
+    // caller's stream around each launch since the last reading, pairs (start, stop)
+    mutable bool timing = false;
+    mutable std::vector<cudaEvent_t> tev;      // event pool, reused
+    mutable std::vector<int32_t> tev_kernel;   // kernel id per recorded pair
+    mutable size_t tev_used = 0;
     mhm_mesh_desc desc{};
     int64_t nK = 0, ne = 0, nv = 0, nlam = 0, nfine = 0, nloc = 0, NI = 0, nnz = 0;
     int32_t N = 1, PN = 1, dpf = 1;  // 2^r, P*N, dofs per face m(l+1)

@@ -35,8 +35,11 @@ Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
-    "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct",
+    "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
 ]
+MHM_KERNEL_LOCAL_FP64, MHM_KERNEL_LOCAL_MIXED, MHM_KERNEL_SCHUR_FACTOR = range(3)
+MHM_N_KERNELS = 3
+KERNEL_NAMES = ("k_local_fp64", "k_local_mixed", "k_schur_factor")
 MHM_EXACT_SINSIN = 1
 MHM_EXACT_POLY = 2
 
@@ -94,9 +97,11 @@ def lib():
         L.mhm_reconstruct.argtypes = [vp, vp, ctypes.POINTER(Source), vp, vp, ctypes.POINTER(Exact), vp, vp, vp]
         L.mhm_last_error.restype = ctypes.c_char_p
         L.mhm_measure_pipes.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        L.mhm_set_timing.argtypes = [vp, i32]
+        L.mhm_kernel_times.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
                      "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc",
-                     "mhm_solve_global", "mhm_reconstruct"):
+                     "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -198,3 +203,16 @@ def mhm_measure_pipes(device: int = 0):
     out = (ctypes.c_double * 2)()
     _check(lib().mhm_measure_pipes(device, out))
     return {"fp64_gflops": out[0], "fp32_gflops": out[1]}
+
+
+def mhm_set_timing(mesh: Mesh, enable: bool = True):
+    """Record CUDA events around each kernel launch of the following local solves on `mesh`."""
+    _check(lib().mhm_set_timing(mesh.handle, 1 if enable else 0))
+
+
+def mhm_kernel_times(mesh: Mesh):
+    """{kernel name: (launches, total ms)} of the timed local solves on `mesh` since the last reading."""
+    n = (ctypes.c_int32 * MHM_N_KERNELS)()
+    ms = (ctypes.c_double * MHM_N_KERNELS)()
+    _check(lib().mhm_kernel_times(mesh.handle, n, ms))
+    return {KERNEL_NAMES[k]: (int(n[k]), float(ms[k])) for k in range(MHM_N_KERNELS) if n[k] > 0}
