@@ -181,6 +181,36 @@ def measured_peaks():
         return {}
 
 
+# Kernel sources whose hash a recorded ncu traffic figure belongs to.
+TRAFFIC_SOURCES = {
+    "k_local_mixed": ("k_local_mixed_c2.md", ["local_mixed.cu", "local_common.cuh", "mhm_internal.h"]),
+    "k_local_fp64": ("k_local_fp64_c2.md", ["local_fp64.cu", "local_common.cuh", "mhm_internal.h"]),
+}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` on
+    the 2048-element workload, from the ncu summary under profiles/, or None when the
+    kernel's sources changed since that capture (hash mismatch) or for other workloads."""
+    import hashlib
+    if workload != "c2_hetero_fp64" or kernel not in TRAFFIC_SOURCES:
+        return None
+    md, srcs = TRAFFIC_SOURCES[kernel]
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(root, "profiles", md)).read()
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(os.path.join(root, "paper_1703_10435_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith(("traffic_bytes", "sources_sha")))
+    if fields.get("sources_sha256", "").strip() != h.hexdigest():
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def residual_fmas_per_pass(w):
     """FP64 multiply-adds of one refinement pass of the mixed path for one K: the
     assembled 7-point (P1) rows of A_p applied to the R right-hand sides."""
@@ -354,7 +384,8 @@ def run_ours(args, w, rank, world, local_rank):
               "peak_source": "MEASURED_PEAKS.json bf16 burst x 1.1/2.25 (nominal tf32/bf16)"}
     roof_mx = {"kernel": "k_local_mixed", "bound": "alu", "pipe": "fp64 (refinement residuals)",
                "achieved": (fl_res / t_kmx / 1e12) if (fl_res and t_kmx) else None, "peak": peak64, "unit": "TFLOP/s",
-               "frac": (fl_res / t_kmx / 1e12 / peak64) if (fl_res and t_kmx) else None, "traffic": None,
+               "frac": (fl_res / t_kmx / 1e12 / peak64) if (fl_res and t_kmx) else None,
+               "traffic": recorded_traffic("k_local_mixed", w.name),
                "flops_per_launch": fl_res, "launch_ms": t_kmx * 1e3 if t_kmx else None, "launches": nmx,
                "refinement_passes_mean": passes,
                "peak_source": "2 FP64 FMA/clk/SM x SMs x max SM clock", "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
@@ -365,7 +396,8 @@ def run_ours(args, w, rank, world, local_rank):
                / (float(localmx.mean()) * 1e-3) / 1e12}
     roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64",
                "achieved": fl64 / t_k64 / 1e12 if t_k64 else None, "peak": peak64, "unit": "TFLOP/s",
-               "frac": fl64 / t_k64 / 1e12 / peak64 if t_k64 else None, "traffic": None,
+               "frac": fl64 / t_k64 / 1e12 / peak64 if t_k64 else None,
+               "traffic": recorded_traffic("k_local_fp64", w.name),
                "flops_per_launch": fl64, "launch_ms": t_k64 * 1e3 if t_k64 else None, "launches": n64,
                "peak_measured_microbench": pipes["fp64_gflops"] / 1e3}
 
