@@ -39,10 +39,12 @@ def assemble(mesh: CoarseMesh, locals_):
     return A, scipy.sparse.csr_matrix(B), E, F
 
 
-def dirichlet_term(mesh: CoarseMesh, g, N: int = 1) -> np.ndarray:
+def dirichlet_term(mesh: CoarseMesh, g, N=1) -> np.ndarray:
     """G_j = (g, psi_j)_F for boundary faces F (None = homogeneous), by Gauss
     quadrature on every piece between consecutive subface breakpoints and the
-    N fine nodes of the face (exact for g piecewise polynomial on the submesh)."""
+    N fine nodes of the face (exact for g piecewise polynomial on the submesh).
+    N: segments per face, one number or one per coarse element (a boundary face
+    takes the value of its element)."""
     G = np.zeros(mesh.n_lambda)
     if g is None:
         return G
@@ -53,7 +55,8 @@ def dirichlet_term(mesh: CoarseMesh, g, N: int = 1) -> np.ndarray:
         length = float(np.linalg.norm(x_hi - x_lo))
         m_e, l_e = int(mesh.m_e[e]), int(mesh.l_e[e])
         gx, gw = gauss_legendre_01(l_e + 4)
-        cuts = sorted(set([k / N for k in range(N + 1)] + [q / m_e for q in range(m_e + 1)]))
+        N_e = int(N) if np.ndim(N) == 0 else int(N[mesh.edge_tris[e][0]])
+        cuts = sorted(set([k / N_e for k in range(N_e + 1)] + [q / m_e for q in range(m_e + 1)]))
         for alpha, beta in zip(cuts[:-1], cuts[1:]):
             q = int(np.floor(0.5 * (alpha + beta) * m_e))
             for xk, wk in zip(gx, gw):

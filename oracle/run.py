@@ -37,16 +37,19 @@ class OracleRun:
 
 
 def run(nx, ny, r, P, m, l, kappa, f, g=None, K_subset=None, do_global=True) -> OracleRun:
-    """kappa: (N_K, 4^r) array in the fine-triangle order; f: constant or callable;
-    g: callable boundary data or None.  K_subset limits the local solves (then
-    no global solve is done)."""
+    """r: refinement level of every K, or one level per K (the local problems are
+    independent: each K's submesh is its own, the multipliers live on the coarse
+    faces).  kappa: per K (or per K of K_subset) the 4^r_K values in the
+    fine-triangle order; f: constant or callable; g: callable boundary data or
+    None.  K_subset limits the local solves (then no global solve is done)."""
     mesh = build_mesh(nx, ny, m, l)
+    r_of = (lambda K: int(r)) if np.ndim(r) == 0 else (lambda K: int(r[K]))
     Ks = range(mesh.n_K) if K_subset is None else K_subset
-    locals_ = [solve_local(mesh, K, r, P, kappa[i if K_subset is not None else K], f)
+    locals_ = [solve_local(mesh, K, r_of(K), P, kappa[i if K_subset is not None else K], f)
                for i, K in enumerate(Ks)]
     if K_subset is not None or not do_global:
         return OracleRun(mesh, locals_, None, None, None, None, None, None, None)
     A, B, E, F = globalsys.assemble(mesh, locals_)
-    G = globalsys.dirichlet_term(mesh, g, 1 << r)
+    G = globalsys.dirichlet_term(mesh, g, [1 << r_of(K) for K in range(mesh.n_K)])
     lam, u0 = globalsys.solve(mesh, A, B, E, F, G)
     return OracleRun(mesh, locals_, A, B, E, F, G, lam, u0)

@@ -328,3 +328,53 @@ def test_convergence_rates_sinsin():
     rates = np.log2(e[:-1] / e[1:])
     assert 1.8 < rates[-1, 0] < 2.3, rates
     assert 0.9 < rates[-1, 1] < 1.15, rates
+
+
+# ---- refinement level per coarse element (the multipliers live on the coarse faces;
+# every element's submesh is its own)
+
+def test_per_element_levels_equal_uniform():
+    """A per-element level list that is uniform gives the uniform run's system exactly."""
+    rng = np.random.default_rng(3)
+    kap = 10.0 ** rng.uniform(-1, 1, (8, 16))
+    a = run(2, 2, 2, 1, 1, 1, kap, 1.0)
+    b = run(2, 2, [2] * 8, 1, 1, 1, list(kap), 1.0)
+    assert np.array_equal(a.A.toarray(), b.A.toarray()) and np.array_equal(a.E, b.E)
+    assert np.array_equal(a.lam, b.lam)
+
+
+def test_per_element_levels_exact_linear():
+    """kappa = 1, u linear: exact on every submesh, whatever each element's level."""
+    g = lambda x, y: 1 + 2 * x - 3 * y
+    rng = np.random.default_rng(4)
+    rs = rng.integers(1, 4, 18)
+    o = run(3, 3, rs, 1, 1, 1, [np.ones(4 ** int(r)) for r in rs], 0.0, g=g)
+    assert _max_nodal_error(o, g) < 1e-12
+    assert sorted(set(len(loc.eta) for loc in o.locals)) == sorted(set((2 ** int(r) + 1) * (2 ** int(r) + 2) // 2 for r in rs))
+
+
+@pytest.mark.parametrize("P", [1, 2])
+def test_per_element_levels_exact_layered(P):
+    """Layered kappa on strips of height H / 2^r_min with f = 0 and u(y) = int 1/kappa:
+    every fine triangle of every element lies in one strip, so the method is exact
+    with elements of different levels side by side."""
+    from paper_1703_10435_gb300 import workloads as W
+    nx = ny = 2
+    rng = np.random.default_rng(5)
+    rs = rng.integers(1, 4, 2 * nx * ny)
+    rmin = int(rs.min())
+    hs = 1.0 / (ny * (1 << rmin))
+    ks = 10.0 ** (-2 + 4 * W.uniform01(6, np.arange(ny * (1 << rmin), dtype=np.uint64), 0, 0))
+    kap = []
+    for K, r in enumerate(rs):
+        cen = W.fine_centroids(W.coarse_vertices(nx, ny), 1 << int(r))[K]
+        kap.append(ks[np.floor(cen[..., 1] / hs).astype(int)])
+    cum = np.concatenate([[0.0], np.cumsum(hs / ks)])
+
+    def u(x, y):
+        y = np.asarray(y, dtype=float)
+        s = np.clip(np.floor(y / hs).astype(int), 0, len(ks) - 1)
+        return cum[s] + (y - s * hs) / ks[s]
+
+    o = run(nx, ny, rs, P, 1, 1, kap, 0.0, g=u)
+    assert _max_nodal_error(o, u) < 1e-11 * cum[-1]
