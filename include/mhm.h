@@ -34,6 +34,8 @@
  *    point (i,j), i+j <= PN, is local DOF sum_{j'<j}(PN+1-j') + i.  kappa is
  *    given per fine triangle, per K in ascending order, and inside K row by
  *    row: the N-j "up" triangles then the N-1-j "down" triangles of row j.
+ *    With a level per K (mhm_mesh_desc.r_per_K) K has its own N = 2^r_K and
+ *    its kappa starts at MHM_Q_KAPPA_OFFSET[K].
  *
  * Memory: every pointer named *_dev is device memory owned by the caller; the
  * library keeps no reference to it after the call returns.  Host pointers
@@ -83,6 +85,10 @@ typedef struct {
     int32_t r;        /* refinement level of every K (2^r segments per face), 0..7 */
     int32_t degree;   /* local Lagrange degree P: 1 or 2 */
     int32_t m, l;     /* subfaces per face (>= 1) and multiplier degree (>= 0) */
+    const int8_t* r_per_K;  /* optional, host, n_K entries in 0..7: the refinement level
+                             * of each K (each local problem is on its own submesh; the
+                             * multipliers live on the coarse faces); NULL: every K at r.
+                             * Read during mhm_create_mesh only. */
 } mhm_mesh_desc;
 
 typedef struct {
@@ -109,9 +115,15 @@ typedef struct {
 /* Options of the local solves. */
 typedef struct {
     int32_t it_max;   /* MIXED: maximum refinement passes (>= 1) */
-    double tol;       /* MIXED: stop when max_c |dz_c| <= tol * max_c |z_c| */
+    double tol;       /* MIXED: a column stops when its energy-norm error estimate
+                       * r^T M r <= tol * g^T M g (M the FP32 preconditioner) */
     int64_t K_begin;  /* process K in [K_begin, K_end); K_end <= 0 means n_K */
     int64_t K_end;
+    int32_t no_fallback;  /* MIXED: 0 (default): elements whose refinement fails (not
+                           * converged in it_max passes, FP32 pivot breakdown) are solved
+                           * again by the FP64 path, their iters entry set to -1;
+                           * 1: they keep their failure status.  MIXED runs P1
+                           * levels wider than 32 points (r >= 6) on the FP64 path. */
 } mhm_solve_opts;
 
 /* ------------------------------------------------------------------ mesh --- */
@@ -126,7 +138,8 @@ void mhm_destroy_mesh(mhm_mesh* mesh);
 
 /* Queries for sizes and for the integer structure (bit-exact parity). */
 #define MHM_Q_SIZES 0          /* int64[8]: n_K, n_faces, n_vertices, n_lambda, n_fine per K,
-                                  n_local per K, N_I per K, skeleton nnz */
+                                  n_local per K (with per-K levels: of the finest K),
+                                  N_I per K, skeleton nnz */
 #define MHM_Q_TRI_VERTS 1      /* int32[n_K*3] vertex ids, CCW */
 #define MHM_Q_TRI_FACES 2      /* int32[n_K*3] face id of local face a */
 #define MHM_Q_TRI_SIGNS 3      /* int8[n_K*3]  s = n . n_F^K */
@@ -137,6 +150,9 @@ void mhm_destroy_mesh(mhm_mesh* mesh);
 #define MHM_Q_CSR_COLS 8       /* int32[nnz] skeleton CSR column ids */
 #define MHM_Q_VERTEX_XY 9      /* double[n_vertices*2] */
 #define MHM_Q_FACE_NORMALS 10  /* double[n_faces*2] */
+#define MHM_Q_R_OF_K 11        /* int8[n_K] refinement level of each K */
+#define MHM_Q_KAPPA_OFFSET 12  /* int64[n_K+1] first kappa value of each K (4^r_K values per K) */
+#define MHM_Q_NODAL_OFFSET 13  /* int64[n_K+1] first value of each K in mhm_reconstruct's u_nodal */
 /* Copies the queried table into host_out (bytes must be >= its size).
  * Errors: INVALID_ARG (unknown query, short buffer). */
 mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, size_t bytes);
@@ -186,7 +202,8 @@ mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, 
  * make that first call before any stream capture.  All calls share the array,
  * and each call overwrites what the previous one left there: calls that can
  * overlap on the GPU (different streams without ordering) race and must not be
- * issued. */
+ * issued.  Elements whose refinement fails keep their failure status (there is
+ * no FP64 re-solve here: opts->no_fallback is treated as 1). */
 mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
                                          const mhm_solve_opts* opts, double* AK_dev, double* EK_dev,
                                          double* BK_dev, double* FK_dev, int32_t* status_dev,
@@ -224,7 +241,7 @@ mhm_status mhm_solve_global(const mhm_mesh* mesh, const double* A_vals_dev, cons
  * sum_i k_i eta_i + eta_f on every K, computed in FP64 as one zero-mean Neumann
  * solve per K with the combined load sum_i k_i N~_i + f~ (the k_i are the global
  * multipliers of K's local basis).  Writes u_nodal_dev[K*n_local + w] for every
- * local DOF w of K (lattice order).  If err_sq_dev is not NULL (it needs
+ * local DOF w of K (lattice order); with a level per K, u_nodal_dev[MHM_Q_NODAL_OFFSET[K] + w].  If err_sq_dev is not NULL (it needs
  * `exact`), also writes err_sq_dev[2K] = ||u_{H,h} - u||^2_{L2(K)} and
  * err_sq_dev[2K+1] = |u_{H,h} - u|^2_{H1(K)}, by the collapsed 4 x 4 Gauss rule
  * on every fine triangle.  Allocates temporary device memory.

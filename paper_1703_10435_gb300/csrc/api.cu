@@ -2,6 +2,8 @@
 // kernels.  No entry point falls back to the CPU.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <string>
 
@@ -49,6 +51,20 @@ bool device_supported(int device) {
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
     return major == 10 && minor == 3;
+}
+
+void level_range(const Level& lv, int64_t K0, int64_t K1, int64_t* i0, int64_t* i1) {
+    if (lv.K.empty()) {   // uniform mesh: the launch index is K
+        *i0 = K0;
+        *i1 = K1;
+        return;
+    }
+    *i0 = std::lower_bound(lv.K.begin(), lv.K.end(), (int32_t)K0) - lv.K.begin();
+    *i1 = std::lower_bound(lv.K.begin(), lv.K.end(), (int32_t)std::min<int64_t>(K1, INT32_MAX)) - lv.K.begin();
+}
+
+bool fp64_level(const mhm_mesh* mesh, const Level& lv) {
+    return mesh->desc.degree == 1 && lv.N > 32;
 }
 
 // Makes the mesh's device current; fails for host-only meshes.
@@ -100,17 +116,28 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
     if (K0 < 0 || K1 > mesh->nK || K0 > K1)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: K range out of bounds");
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == MHM_FP64)
-        return launch_local_fp64(mesh, kappa, *f, K0, K1, AK, EK, BK, FK, status, iters, s);
+    if (precision != MHM_FP64 && precision != MHM_MIXED)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown precision");
     if (precision == MHM_MIXED) {
         if (o.it_max < 1 || !(o.tol > 0.0))
             return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: it_max >= 1 and tol > 0 required");
         const size_t need = mixed_workspace_bytes(mesh);
         if (ws_bytes < need || (need > 0 && !workspace))
             return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
-        return launch_local_mixed(mesh, kappa, *f, o, K0, K1, AK, EK, BK, FK, status, iters, workspace, ws_bytes, s);
     }
-    return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown precision");
+    // one launch sequence per refinement level, in stream order (the mixed path reuses
+    // the workspace from level to level)
+    for (const Level& lv : mesh->levels) {
+        int64_t i0 = 0, i1 = 0;
+        level_range(lv, K0, K1, &i0, &i1);
+        if (i1 <= i0) continue;
+        st = precision == MHM_FP64 || fp64_level(mesh, lv)
+                 ? launch_local_fp64(mesh, lv, kappa, *f, i0, i1, AK, EK, BK, FK, status, iters, s)
+                 : launch_local_mixed(mesh, lv, kappa, *f, o, i0, i1, AK, EK, BK, FK, status, iters, workspace,
+                                      ws_bytes, s);
+        if (st) return st;
+    }
+    return MHM_OK;
 }
 
 extern "C" mhm_status mhm_assemble_skeleton(const mhm_mesh* mesh, const double* AK, const double* EK,

@@ -43,6 +43,8 @@ struct Fp64Args {
     int64_t K0;
     double *AK, *EK, *BK, *FK;
     int32_t *status, *iters;
+    const int32_t* kcount;   // launch indices >= *kcount do nothing (NULL: no bound)
+    int fallback;            // 1: re-solving elements of a failed mixed refinement (iters = -1)
 };
 
 struct KCtx {
@@ -192,12 +194,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
     extern __shared__ double smem[];
     __shared__ KCtx c;
     __shared__ double red[32];
-    const int64_t K = g.K0 + blockIdx.x;
+    const int64_t ki = g.K0 + blockIdx.x;                          // launch index within the level
+    if (g.kcount && ki >= *g.kcount) return;                       // (whole block: no barrier passed)
+    const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;  // coarse element
     const LevelGeom lg{g.P, g.N, g.PN};
     const int R = g.R;
     double* W = smem;                                 // window: rows x ld
     double* gram = smem + (size_t)g.rows * g.ld;      // R x R, upper triangle used
-    const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+    const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
 
     // ---- per-K setup
     if (threadIdx.x == 0) {
@@ -312,15 +316,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
     if (threadIdx.x == 0) {
         g.FK[K] = FK;
         g.status[K] = c.bad ? MHM_ERR_INVALID_ARG : 0;
-        if (g.iters) g.iters[K] = 1;
+        if (g.iters) g.iters[K] = g.fallback ? -1 : 1;
     }
 }
 
 }  // namespace
 
-int fp64_window_rows(const mhm_mesh* mesh) {
+int fp64_window_rows(const mhm_mesh* mesh, const Level& lv) {
     // largest b + b' over consecutive levels: levels 0 and 1
-    const int P = mesh->desc.degree, N = mesh->N;
+    const int P = mesh->desc.degree, N = lv.N;
     auto size = [&](int lev) {
         if (P == 1) return N + 1 - lev - (lev == 0);
         if (lev == N) return 1;
@@ -329,21 +333,25 @@ int fp64_window_rows(const mhm_mesh* mesh) {
     return size(0) + (N >= 1 ? size(1) : 0);
 }
 
-mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mhm_source& f, int64_t K0,
-                             int64_t K1, double* AK, double* EK, double* BK, double* FK, int32_t* status,
-                             int32_t* iters, cudaStream_t stream) {
+static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
+                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
+                              int32_t* status, int32_t* iters, const int32_t* list, const int32_t* count,
+                              cudaStream_t stream) {
     Fp64Args g;
-    g.dm = mesh->dev();
+    g.dm = mesh->dev(lv);
+    g.kcount = count;
+    g.fallback = list != nullptr;
+    if (list) g.dm.klist = list;
     g.kappa = kappa;
     g.P = mesh->desc.degree;
-    g.N = mesh->N;
-    g.PN = mesh->PN;
+    g.N = lv.N;
+    g.PN = lv.PN;
     g.M = mesh->desc.m;
     g.L = mesh->desc.l;
     g.dpf = mesh->dpf;
     g.NI = (int)mesh->NI;
     g.R = g.NI + 1;
-    const int rows = fp64_window_rows(mesh);
+    const int rows = fp64_window_rows(mesh, lv);
     g.rows = rows;
     g.rhs0 = rows;
     g.ld = rows + g.R;
@@ -370,6 +378,19 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mh
     timing_mark(mesh, MHM_KERNEL_LOCAL_FP64, stream, false);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
+}
+
+mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
+                             int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                             int32_t* iters, cudaStream_t stream) {
+    // K0, K1: launch indices within the level (its K list, or K itself on a uniform mesh)
+    return launch_fp64(mesh, lv, kappa, f, K0, K1, AK, EK, BK, FK, status, iters, nullptr, nullptr, stream);
+}
+
+mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
+                                  const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
+                                  double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream) {
+    return launch_fp64(mesh, lv, kappa, f, 0, max_n, AK, EK, BK, FK, status, iters, list, count, stream);
 }
 
 }  // namespace mhm

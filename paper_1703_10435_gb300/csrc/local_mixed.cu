@@ -872,8 +872,9 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
     // coarse triangles: K0 + blockIdx.x, then (dynamic) the next index from the counter
     // or (static) every gridDim.x-th
     if (threadIdx.x == 0) c.nextK = g.kcounter ? g.K0 + gridDim.x + atomicAdd(g.kcounter, 1) : 0;
-    for (int64_t K = g.K0 + blockIdx.x; K < g.K1;) {
-        const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+    for (int64_t ki = g.K0 + blockIdx.x; ki < g.K1;) {                  // launch index within the level
+        const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;      // coarse element
+        const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
         if (g.kap_in_smem) {
             // stage this K's kappa in shared memory (read by assembly, scaling and residuals)
             const int nf = g.N * g.N;
@@ -954,7 +955,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             const int nu = g.nunk;
             if constexpr (MODE == 2) {
                 __syncthreads();
-                const int64_t kk = K - g.Kc0;
+                const int64_t kk = ki - g.Kc0;
                 F = g.Tall + kk * (int64_t)g.t_stride;
                 sc = g.scall + kk * (int64_t)nu;
                 ah = g.ahall + kk * 7 * (int64_t)nu;
@@ -1209,7 +1210,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             if constexpr (MODE == 2) {
                 // ---- precomputed level-Schur operators of this K: couplings to shared memory
                 __syncthreads();
-                const int64_t kk = K - g.Kc0;
+                const int64_t kk = ki - g.Kc0;
                 F = g.Tall + kk * (int64_t)g.t_stride;
                 const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
                 for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
@@ -1495,11 +1496,11 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             __syncthreads();
         }
         if (g.kcounter) {
-            K = c.nextK;
+            ki = c.nextK;
             __syncthreads();
             if (threadIdx.x == 0) c.nextK = g.K0 + gridDim.x + atomicAdd(g.kcounter, 1);
         } else {
-            K += gridDim.x;
+            ki += gridDim.x;
         }
     }
 }
@@ -1524,13 +1525,14 @@ struct FactorSmem {   // per warp
 __global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedArgs g) {
     extern __shared__ unsigned char fs_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t K = g.Kc0 + (int64_t)blockIdx.x * kFactorWarps + warp;
-    if (K >= g.K1) return;
+    const int64_t ki = g.Kc0 + (int64_t)blockIdx.x * kFactorWarps + warp;   // launch index within the level
+    if (ki >= g.K1) return;
+    const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;
     FactorSmem& fs = reinterpret_cast<FactorSmem*>(fs_raw)[warp];
     const int nu = g.nunk;
     double* scale = reinterpret_cast<double*>(fs_raw + kFactorWarps * sizeof(FactorSmem)) + (size_t)warp * nu;
-    const double* kap = g.kappa + K * (int64_t)g.N * g.N;
-    const int64_t kk = K - g.Kc0;
+    const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
+    const int64_t kk = ki - g.Kc0;
     float* cw = g.cwall + kk * 4 * (int64_t)nu;
     float* T = g.Tall + kk * (int64_t)g.t_stride;
     if (lane == 0) {
@@ -1613,16 +1615,16 @@ constexpr int64_t kChunkMax = 8192;   // MODE 2: coarse triangles per factor + s
 // split: the level-Schur path factors in k_schur_factor (MODE 2) instead of in the
 // solve kernel (MODE 1; the allocation-free entry, whose scratch cannot hold the
 // per-K operators of a whole chunk).
-MixedLayout mixed_layout(const mhm_mesh* mesh, bool split = true) {
+MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = true) {
     MixedLayout L{};
-    const int P = mesh->desc.degree, N = mesh->N;
+    const int P = mesh->desc.degree, N = lv.N;
     auto size = [&](int lev) {
         if (P == 1) return N + 1 - lev - (lev == 0);
         if (lev == N) return 1;
         return (2 * N - 2 * lev + 1) + (2 * N - 2 * lev) - (lev == 0);
     };
     L.nlev = N + 1;
-    L.nunk = (int)mesh->nloc - 1;
+    L.nunk = (int)lv.nloc - 1;
     int bmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) bmax = std::max(bmax, size(lev));
     L.schur = P == 1 && bmax <= kSchurMax && mesh->NI + 1 <= 32;
@@ -1734,19 +1736,19 @@ int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
 
 namespace {
 
-int64_t chunk_of(const mhm_mesh* mesh, const MixedLayout& L) {
-    return L.mode == 2 ? std::min<int64_t>(mesh->nK, kChunkMax) : 0;
+int64_t chunk_of(const Level& lv, const MixedLayout& L) {
+    return L.mode == 2 ? std::min<int64_t>(lv.nK, kChunkMax) : 0;
 }
 
-MixedArgs mixed_args(const mhm_mesh* mesh, const MixedLayout& L, const double* kappa, const mhm_source& f,
-                     const mhm_solve_opts& o, double* AK, double* EK, double* BK, double* FK, int32_t* status,
-                     int32_t* iters, char* ws) {
+MixedArgs mixed_args(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L, const double* kappa,
+                     const mhm_source& f, const mhm_solve_opts& o, double* AK, double* EK, double* BK, double* FK,
+                     int32_t* status, int32_t* iters, char* ws) {
     MixedArgs g{};
-    g.dm = mesh->dev();
+    g.dm = mesh->dev(lv);
     g.kappa = kappa;
     g.P = mesh->desc.degree;
-    g.N = mesh->N;
-    g.PN = mesh->PN;
+    g.N = lv.N;
+    g.PN = lv.PN;
     g.dpf = mesh->dpf;
     g.NI = (int)mesh->NI;
     g.R = g.NI + 1;
@@ -1787,37 +1789,70 @@ MixedArgs mixed_args(const mhm_mesh* mesh, const MixedLayout& L, const double* k
 
 }  // namespace
 
+// The K of launch indices [i0, i1) whose status is not OK, appended to list (order of
+// arrival; each K's result does not depend on it).
+__global__ void k_collect_failed(const int32_t* klist, int64_t i0, int64_t i1, const int32_t* status, int32_t* list,
+                                 int32_t* count) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t K = klist ? (int64_t)klist[i] : i;
+        if (status[K] != MHM_OK) list[atomicAdd(count, 1)] = (int32_t)K;
+    }
+}
+
+// Workspace of one level: the slots, the chunk arrays, the assignment counter, and the
+// list of failed elements (count + one entry per element of the level).
+static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L) {
+    return (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(lv, L) * L.chunk_k_bytes + 256 + 256 +
+           (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
+}
+
 size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     if (mesh->device < 0) return 0;
-    const MixedLayout L = mixed_layout(mesh);
-    if (L.smem > 220 * 1024 || !mixed_kernel(L)) return 0;
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(mesh->device);
-    const size_t bytes = (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(mesh, L) * L.chunk_k_bytes + 256;
+    size_t bytes = 0;   // the levels run one after the other on the stream: the largest need
+    for (const Level& lv : mesh->levels) {
+        if (fp64_level(mesh, lv)) continue;   // runs on the FP64 path: no workspace
+        const MixedLayout L = mixed_layout(mesh, lv);
+        if (L.smem > 220 * 1024 || !mixed_kernel(L)) continue;
+        bytes = std::max(bytes, level_workspace(mesh, lv, L));
+    }
     cudaSetDevice(cur);
     return bytes;
 }
 
-mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                               const mhm_solve_opts& opts, int64_t K0, int64_t K1, double* AK, double* EK,
                               double* BK, double* FK, int32_t* status, int32_t* iters, void* workspace,
                               size_t ws_bytes, cudaStream_t stream) {
-    const MixedLayout L = mixed_layout(mesh);
+    // K0, K1: launch indices within the level (its K list, or K itself on a uniform mesh)
+    const MixedLayout L = mixed_layout(mesh, lv);
     if (L.smem > 220 * 1024 || !mixed_kernel(L))
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: MIXED buffers exceed shared memory (r too large)");
     const int slots = mixed_slots(mesh, L);
-    const int64_t chunk = chunk_of(mesh, L);
+    const int64_t chunk = chunk_of(lv, L);
     const size_t slots_bytes = (size_t)slots * L.slot_bytes;
-    if (ws_bytes < slots_bytes + (size_t)chunk * L.chunk_k_bytes + 256)
+    if (ws_bytes < level_workspace(mesh, lv, L))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
     // dynamic assignment of coarse triangles to blocks: a counter behind the scratch,
     // zeroed in stream order before every solve launch
     int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)chunk * L.chunk_k_bytes);
-    MixedArgs g = mixed_args(mesh, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
+    MixedArgs g = mixed_args(mesh, lv, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
     g.kcounter = counter;
+    // elements whose refinement failed are solved again by the FP64 path (list behind the counter)
+    auto fallback = [&]() -> mhm_status {
+        if (opts.no_fallback) return MHM_OK;
+        int32_t* fcount = reinterpret_cast<int32_t*>((char*)counter + 256);
+        int32_t* flist = reinterpret_cast<int32_t*>((char*)counter + 512);
+        MHM_CUDA_TRY(cudaMemsetAsync(fcount, 0, sizeof(int32_t), stream));
+        const int64_t nb = std::min<int64_t>((nK + 255) / 256, 1024);
+        k_collect_failed<<<(unsigned)nb, 256, 0, stream>>>(g.dm.klist, K0, K1, status, flist, fcount);
+        MHM_CUDA_TRY(cudaGetLastError());
+        return launch_local_fp64_list(mesh, lv, kappa, f, flist, fcount, nK, AK, EK, BK, FK, status, iters, stream);
+    };
     if (L.mode != 2) {
         g.K0 = K0;
         g.K1 = K1;
@@ -1827,7 +1862,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
-        return MHM_OK;
+        return fallback();
     }
     // MODE 2: per chunk, the factor kernel writes T, couplings and pivot flags behind the
     // slots; the solve kernel reads them (stream order separates the two)
@@ -1859,7 +1894,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const m
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
     }
-    return MHM_OK;
+    return fallback();
 }
 
 // ---------------------------------------------------------------------------
@@ -1905,13 +1940,16 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: K range out of bounds");
     if (o.it_max < 1 || !(o.tol > 0.0))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: it_max >= 1 and tol > 0 required");
-    const MixedLayout L = mixed_layout(mesh, false);   // factor inside the solve kernel
-    if (L.smem > 220 * 1024 || !mixed_kernel(L))
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
-    if (L.slot_bytes > kStaticScratch)
-        return fail(MHM_ERR_INVALID_ARG,
-                    "mhm_local_solve_batch_noalloc: one coarse element needs " + std::to_string(L.slot_bytes) +
-                        " bytes of scratch, above the fixed " + std::to_string(kStaticScratch) + " bytes");
+    for (const Level& lv : mesh->levels) {
+        if (fp64_level(mesh, lv)) continue;
+        const MixedLayout L = mixed_layout(mesh, lv, false);   // factor inside the solve kernel
+        if (L.smem > 220 * 1024 || !mixed_kernel(L))
+            return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
+        if (L.slot_bytes > kStaticScratch)
+            return fail(MHM_ERR_INVALID_ARG,
+                        "mhm_local_solve_batch_noalloc: one coarse element needs " + std::to_string(L.slot_bytes) +
+                            " bytes of scratch, above the fixed " + std::to_string(kStaticScratch) + " bytes");
+    }
     // Set-up, once per device with that device current: the device address of the
     // fixed array (its name in host code is only a stand-in for the symbol).
     void* scratch = nullptr;
@@ -1926,17 +1964,29 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         }
         scratch = g_static_ptr[mesh->device];
     }
-    const int64_t nK = K1 - K0;
-    if (nK <= 0) return MHM_OK;
-    const int64_t fit = (int64_t)(kStaticScratch / L.slot_bytes);
-    int64_t grid = mixed_slots(mesh, L);
-    if (grid > fit) grid = fit;
-    if (grid > nK) grid = nK;
-    MixedArgs g = mixed_args(mesh, L, kappa, *f, o, AK, EK, BK, FK, status, iters, (char*)scratch);
-    g.K0 = K0;
-    g.K1 = K1;
-    mixed_kernel(L)<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
-    MHM_CUDA_TRY(cudaGetLastError());
+    // one launch per refinement level, in stream order (each reuses the fixed array)
+    for (const Level& lv : mesh->levels) {
+        int64_t i0 = 0, i1 = 0;
+        level_range(lv, K0, K1, &i0, &i1);
+        const int64_t nK = i1 - i0;
+        if (nK <= 0) continue;
+        if (fp64_level(mesh, lv)) {   // the FP64 path needs no scratch
+            const mhm_status st = launch_local_fp64(mesh, lv, kappa, *f, i0, i1, AK, EK, BK, FK, status, iters,
+                                                    (cudaStream_t)stream);
+            if (st) return st;
+            continue;
+        }
+        const MixedLayout L = mixed_layout(mesh, lv, false);
+        const int64_t fit = (int64_t)(kStaticScratch / L.slot_bytes);
+        int64_t grid = mixed_slots(mesh, L);
+        if (grid > fit) grid = fit;
+        if (grid > nK) grid = nK;
+        MixedArgs g = mixed_args(mesh, lv, L, kappa, *f, o, AK, EK, BK, FK, status, iters, (char*)scratch);
+        g.K0 = i0;
+        g.K1 = i1;
+        mixed_kernel(L)<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);
+        MHM_CUDA_TRY(cudaGetLastError());
+    }
     return MHM_OK;
 }
 

@@ -83,6 +83,51 @@ void free_mesh_device(mhm_mesh* m) {
                     m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs, m->d_aug_rowptr, m->d_aug_cols, m->d_aug_src, m->d_k_lambda};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (m->d_kap_off) cudaFree(m->d_kap_off);
+    if (m->d_nod_off) cudaFree(m->d_nod_off);
+    for (mhm::Level& lv : m->levels) {
+        if (lv.d_K) cudaFree(lv.d_K);
+        if (lv.d_btab) cudaFree(lv.d_btab);
+        lv.d_K = nullptr;
+        lv.d_btab = nullptr;
+    }
+}
+
+// Face-load table of one level: btab[jf][k] = int_0^1 psi_jf(tau) phi_k(tau) dtau, phi_k
+// the 1-D Lagrange basis of degree P on N segments; Gauss pieces split at fine nodes and
+// subfaces; btab_sum[jf] = int_0^1 psi_jf.
+static void face_load_table(int P, int N, int M, int L, const std::vector<double>& gauss_x,
+                            const std::vector<double>& gauss_w, std::vector<double>& btab,
+                            std::vector<double>& btab_sum) {
+    const int PN = P * N, dpf = M * (L + 1);
+    btab.assign((size_t)dpf * (PN + 1), 0.0);
+    btab_sum.assign(dpf, 0.0);
+    std::vector<double> cuts;
+    for (int k = 0; k <= N; ++k) cuts.push_back((double)k / N);
+    for (int q = 1; q < M; ++q) cuts.push_back((double)q / M);
+    std::sort(cuts.begin(), cuts.end());
+    const int ng = (P + L + 2) / 2 + 1;
+    const double* gx = &gauss_x[(ng - 1) * mhm::kMaxGauss];
+    const double* gw = &gauss_w[(ng - 1) * mhm::kMaxGauss];
+    for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+        double al = cuts[c], be = cuts[c + 1];
+        if (be - al < 1e-15) continue;
+        double mid = 0.5 * (al + be);
+        int seg = std::min(N - 1, (int)std::floor(mid * N));
+        int q = std::min(M - 1, (int)std::floor(mid * M));
+        for (int g = 0; g < ng; ++g) {
+            double tau = al + (be - al) * gx[g], w = (be - al) * gw[g];
+            double v[3];
+            lagrange1d(P, tau * N - seg, v);
+            double xi = 2.0 * (tau * M - q) - 1.0;
+            for (int p = 0; p <= L; ++p) {
+                double psi = legendre_p(p, xi);
+                int jf = q * (L + 1) + p;
+                for (int b = 0; b <= P; ++b) btab[(size_t)jf * (PN + 1) + P * seg + b] += w * psi * v[b];
+                btab_sum[jf] += w * psi;
+            }
+        }
+    }
 }
 
 extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device, mhm_mesh** out) {
@@ -92,6 +137,15 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     if (d.nx < 1 || d.ny < 1 || (int64_t)d.nx * d.ny > (1 << 26))
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: nx, ny out of range");
     if (d.r < 0 || d.r > 7) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: r must be in 0..7");
+    int r_top = d.r;   // the finest level (sizes reported per K are of this level)
+    if (d.r_per_K) {
+        r_top = 0;
+        for (int64_t K = 0; K < 2LL * d.nx * d.ny; ++K) {
+            if (d.r_per_K[K] < 0 || d.r_per_K[K] > 7)
+                return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: every r_per_K must be in 0..7");
+            r_top = std::max(r_top, (int)d.r_per_K[K]);
+        }
+    }
     if (d.degree != 1 && d.degree != 2) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: degree must be 1 or 2");
     if (d.m < 1 || d.l < 0 || d.m * (d.l + 1) > mhm::kMaxFaceDofs)
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: m >= 1, l >= 0 and m(l+1) <= 16 required");
@@ -106,8 +160,9 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     mhm_mesh* m = new mhm_mesh();
     m->device = device;
     m->desc = d;
+    m->desc.r_per_K = nullptr;   // the caller's array is read here only
     const int nx = d.nx, ny = d.ny;
-    m->N = 1 << d.r;
+    m->N = 1 << r_top;
     m->PN = d.degree * m->N;
     m->dpf = d.m * (d.l + 1);
     m->nv = (int64_t)(nx + 1) * (ny + 1);
@@ -285,37 +340,41 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     for (int n = 1; n <= mhm::kMaxGauss; ++n)
         gauss_legendre01(n, &m->gauss_x[(n - 1) * mhm::kMaxGauss], &m->gauss_w[(n - 1) * mhm::kMaxGauss]);
 
-    // face-load table: btab[jf][k] = int_0^1 psi_jf(tau) phi_k(tau) dtau, phi_k the 1-D
-    // Lagrange basis of degree P on N segments; pieces split at fine nodes and subfaces.
-    {
-        const int P = d.degree, N = m->N, PN = m->PN, M = d.m, L = d.l;
-        m->btab.assign((size_t)m->dpf * (PN + 1), 0.0);
-        m->btab_sum.assign(m->dpf, 0.0);
-        std::vector<double> cuts;
-        for (int k = 0; k <= N; ++k) cuts.push_back((double)k / N);
-        for (int q = 1; q < M; ++q) cuts.push_back((double)q / M);
-        std::sort(cuts.begin(), cuts.end());
-        const int ng = (P + L + 2) / 2 + 1;
-        const double* gx = &m->gauss_x[(ng - 1) * mhm::kMaxGauss];
-        const double* gw = &m->gauss_w[(ng - 1) * mhm::kMaxGauss];
-        for (size_t c = 0; c + 1 < cuts.size(); ++c) {
-            double al = cuts[c], be = cuts[c + 1];
-            if (be - al < 1e-15) continue;
-            double mid = 0.5 * (al + be);
-            int seg = std::min(N - 1, (int)std::floor(mid * N));
-            int q = std::min(M - 1, (int)std::floor(mid * M));
-            for (int g = 0; g < ng; ++g) {
-                double tau = al + (be - al) * gx[g], w = (be - al) * gw[g];
-                double v[3];
-                lagrange1d(P, tau * N - seg, v);
-                double xi = 2.0 * (tau * M - q) - 1.0;
-                for (int p = 0; p <= L; ++p) {
-                    double psi = legendre_p(p, xi);
-                    int jf = q * (L + 1) + p;
-                    for (int b = 0; b <= P; ++b) m->btab[(size_t)jf * (PN + 1) + P * seg + b] += w * psi * v[b];
-                    m->btab_sum[jf] += w * psi;
-                }
-            }
+    // face-load table of the mesh's (finest) level, and the levels
+    face_load_table(d.degree, m->N, d.m, d.l, m->gauss_x, m->gauss_w, m->btab, m->btab_sum);
+    if (!d.r_per_K) {
+        mhm::Level lv;
+        lv.r = d.r;
+        lv.N = m->N;
+        lv.PN = m->PN;
+        lv.nK = m->nK;
+        lv.nfine = m->nfine;
+        lv.nloc = m->nloc;
+        m->levels.push_back(lv);
+    } else {
+        m->per_k_levels = true;
+        m->r_of_K.assign(d.r_per_K, d.r_per_K + m->nK);
+        m->kap_off.assign(m->nK + 1, 0);
+        m->nod_off.assign(m->nK + 1, 0);
+        for (int64_t K = 0; K < m->nK; ++K) {
+            const int64_t N = 1LL << m->r_of_K[K], PN = d.degree * N;
+            m->kap_off[K + 1] = m->kap_off[K] + N * N;
+            m->nod_off[K + 1] = m->nod_off[K] + (PN + 1) * (PN + 2) / 2;
+        }
+        for (int r = 0; r <= 7; ++r) {
+            mhm::Level lv;
+            lv.r = r;
+            lv.N = 1 << r;
+            lv.PN = d.degree * lv.N;
+            lv.nfine = (int64_t)lv.N * lv.N;
+            lv.nloc = (int64_t)(lv.PN + 1) * (lv.PN + 2) / 2;
+            for (int64_t K = 0; K < m->nK; ++K)
+                if (m->r_of_K[K] == r) lv.K.push_back((int32_t)K);
+            lv.nK = (int64_t)lv.K.size();
+            if (lv.nK == 0) continue;
+            std::vector<double> bsum;
+            face_load_table(d.degree, lv.N, d.m, d.l, m->gauss_x, m->gauss_w, lv.btab, bsum);
+            m->levels.push_back(std::move(lv));
         }
     }
 
@@ -351,6 +410,14 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     if (!st) st = upload(m->aug_cols, &m->d_aug_cols);
     if (!st) st = upload(m->aug_src, &m->d_aug_src);
     if (!st) st = upload(m->k_lambda, &m->d_k_lambda);
+    if (m->per_k_levels) {
+        if (!st) st = upload(m->kap_off, &m->d_kap_off);
+        if (!st) st = upload(m->nod_off, &m->d_nod_off);
+        for (mhm::Level& lv : m->levels) {
+            if (!st) st = upload(lv.K, &lv.d_K);
+            if (!st) st = upload(lv.btab, &lv.d_btab);
+        }
+    }
     if (st) {
         free_mesh_device(m);
         delete m;
@@ -399,6 +466,18 @@ extern "C" mhm_status mhm_mesh_query(const mhm_mesh* m, int32_t what, void* out,
         case MHM_Q_CSR_COLS: return copy_out(m->csr_cols, out, bytes);
         case MHM_Q_VERTEX_XY: return copy_out(m->vxy, out, bytes);
         case MHM_Q_FACE_NORMALS: return copy_out(m->normals, out, bytes);
+        case MHM_Q_R_OF_K: {
+            if (m->per_k_levels) return copy_out(m->r_of_K, out, bytes);
+            return copy_out(std::vector<int8_t>(m->nK, (int8_t)m->desc.r), out, bytes);
+        }
+        case MHM_Q_KAPPA_OFFSET:
+        case MHM_Q_NODAL_OFFSET: {
+            if (m->per_k_levels) return copy_out(what == MHM_Q_KAPPA_OFFSET ? m->kap_off : m->nod_off, out, bytes);
+            std::vector<int64_t> o(m->nK + 1);
+            const int64_t per = what == MHM_Q_KAPPA_OFFSET ? m->nfine : m->nloc;
+            for (int64_t K = 0; K <= m->nK; ++K) o[K] = K * per;
+            return copy_out(o, out, bytes);
+        }
         default: return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_mesh_query: unknown query");
     }
 }

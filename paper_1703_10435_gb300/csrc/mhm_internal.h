@@ -50,6 +50,19 @@ struct DeviceMesh {
     const double* btab_sum;  // dofs_per_face: int psi_{q,p} over [0,1]
     const double* gauss_x;   // kMaxGauss * kMaxGauss: n-point Gauss-Legendre nodes on [0,1], row n-1
     const double* gauss_w;
+    const int32_t* klist;    // coarse element of each launch index (NULL: the index itself)
+    const int64_t* kap_off;  // first kappa value of each K (NULL: K * 4^r)
+};
+
+// The coarse elements of one refinement level: the local-solve and reconstruction
+// kernels run one launch per level (uniform meshes have a single level).
+struct Level {
+    int r = 0, N = 1, PN = 1;
+    int64_t nK = 0, nfine = 0, nloc = 0;
+    std::vector<int32_t> K;        // ascending; empty on a uniform mesh (K = launch index)
+    std::vector<double> btab;      // face-load table of this level (dofs_per_face x (PN + 1))
+    int32_t* d_K = nullptr;
+    double* d_btab = nullptr;      // NULL: the mesh's table (uniform mesh)
 };
 
 }  // namespace mhm
@@ -109,21 +122,45 @@ struct mhm_mesh {
     int64_t* d_aug_src = nullptr;
     int32_t* d_k_lambda = nullptr;
 
+    // refinement level per K (meshes built with r_per_K; uniform meshes leave these empty)
+    bool per_k_levels = false;
+    std::vector<int8_t> r_of_K;           // n_K
+    std::vector<int64_t> kap_off;         // n_K + 1: first kappa value of K (4^r_K values each)
+    std::vector<int64_t> nod_off;         // n_K + 1: first nodal value of K in mhm_reconstruct's output
+    int64_t* d_kap_off = nullptr;
+    int64_t* d_nod_off = nullptr;
+    std::vector<mhm::Level> levels;       // one per level present, ascending r
+
     mhm::DeviceMesh dev() const {
-        return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w};
+        return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w, nullptr, nullptr};
+    }
+    mhm::DeviceMesh dev(const mhm::Level& lv) const {
+        return mhm::DeviceMesh{d_geom, d_sign, d_rev, lv.d_btab ? lv.d_btab : d_btab, d_btab_sum, d_gauss_x,
+                               d_gauss_w, lv.d_K, d_kap_off};
     }
 };
 
 namespace mhm {
 // Launchers (defined in the .cu files).
-mhm_status launch_local_fp64(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
                              int32_t* status, int32_t* iters, cudaStream_t stream);
-mhm_status launch_local_mixed(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                               const mhm_solve_opts& opts, int64_t K0, int64_t K1, double* AK,
                               double* EK, double* BK, double* FK, int32_t* status, int32_t* iters,
                               void* workspace, size_t ws_bytes, cudaStream_t stream);
-size_t mixed_workspace_bytes(const mhm_mesh* mesh);
+// FP64 local solves of the K in list[0 .. *count) (device count, at most max_n) of level lv:
+// the re-solve of elements whose mixed refinement failed (their iters entry becomes -1).
+mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
+                                  const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
+                                  double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream);
+size_t mixed_workspace_bytes(const mhm_mesh* mesh);   // largest over the levels
+// A level the MIXED precision runs on the FP64 path: P1 levels wider than 32 points.  Their
+// FP32 factor (levels of 64 points, jumps of 1e4 in kappa) is too inaccurate to drive the
+// FP64 refinement to the tolerance in a few passes, and its error estimate is not reliable.
+bool fp64_level(const mhm_mesh* mesh, const Level& lv);
+// [i0, i1): the launch indices of level lv whose K lies in [K0, K1)
+void level_range(const Level& lv, int64_t K0, int64_t K1, int64_t* i0, int64_t* i1);
 mhm_status launch_skeleton(const mhm_mesh* mesh, const double* AK, const double* EK,
                            const mhm_dirichlet* g, double* A_vals, double* E, cudaStream_t stream);
 bool device_supported(int device);

@@ -30,8 +30,9 @@ struct RecArgs {
     double ex[6];
     char* ws;
     size_t slot_bytes;
-    int64_t nK;
-    double* u_out;              // n_K * nloc
+    int64_t nK;                 // launch indices of this level
+    const int64_t* nod_off;     // first nodal value of each K in u_out (NULL: K * nloc)
+    double* u_out;              // n_K * nloc (per-K levels: at nod_off)
     double* err_out;            // n_K * 2 (squared L2, squared H1 seminorm) or NULL
 };
 
@@ -130,8 +131,9 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
     double* Fst = reinterpret_cast<double*>(slot);   // per level: L (b x b), C (bn x b), y (b)
     const int nb = g.P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
 
-    for (int64_t K = blockIdx.x; K < g.nK; K += gridDim.x) {
-        const double* kap = g.kappa + K * (int64_t)g.N * g.N;
+    for (int64_t ki = blockIdx.x; ki < g.nK; ki += gridDim.x) {
+        const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;      // coarse element
+        const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
         if (threadIdx.x == 0) {
             for (int v = 0; v < 3; ++v) {
                 c.X[v][0] = g.dm.geom[6 * K + 2 * v];
@@ -320,7 +322,8 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
             }
         }
         const double shift = g.u0[K] - block_sum(mzp, c) / c.area;
-        for (int w = threadIdx.x; w < g.nloc; w += blockDim.x) g.u_out[K * g.nloc + w] = zs[w] + shift;
+        double* uK = g.u_out + (g.nod_off ? g.nod_off[K] : K * (int64_t)g.nloc);
+        for (int w = threadIdx.x; w < g.nloc; w += blockDim.x) uK[w] = zs[w] + shift;
         if (g.err_out) {
             const double* gx = g.dm.gauss_x + 3 * kMaxGauss;
             const double* gw = g.dm.gauss_w + 3 * kMaxGauss;
@@ -389,56 +392,60 @@ extern "C" mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa,
         return fail(MHM_ERR_INVALID_ARG, "mhm_reconstruct: unknown exact-solution kind");
     MHM_CUDA_TRY(cudaSetDevice(mesh->device));
     cudaStream_t s = (cudaStream_t)stream;
-    RecArgs g;
-    g.dm = mesh->dev();
-    g.kappa = kappa;
-    g.lambda = lambda;
-    g.u0 = u0;
-    g.k_lambda = mesh->d_k_lambda;
-    g.P = mesh->desc.degree;
-    g.N = mesh->N;
-    g.PN = mesh->PN;
-    g.dpf = mesh->dpf;
-    g.NI = (int)mesh->NI;
-    g.nlev = mesh->N + 1;
-    g.nloc = (int)mesh->nloc;
-    auto size = [&](int lev) {
-        if (g.P == 1) return g.N + 1 - lev - (lev == 0);
-        if (lev == g.N) return 1;
-        return (2 * g.N - 2 * lev + 1) + (2 * g.N - 2 * lev) - (lev == 0);
-    };
-    g.rows = size(0) + (g.N >= 1 ? size(1) : 0);
-    g.rhs = g.rows;                      // right-hand side right after the symmetric part
-    g.ld = (g.rows + 2) & ~1;            // even: 16-byte rows for the vector panel loads
-    g.src_kind = f->kind;
-    g.src_value = f->value;
-    g.src_freq = f->freq;
-    g.ex_kind = exact ? (exact->kind == MHM_EXACT_SINSIN ? 1 : 2) : 0;
-    for (int i = 0; i < 6; ++i) g.ex[i] = exact ? exact->c[i] : 0.0;
-    size_t per = 0;
-    for (int lev = 0; lev < g.nlev; ++lev) {
-        const int b = size(lev), bn = lev + 1 < g.nlev ? size(lev + 1) : 0;
-        per += (size_t)b * b + (size_t)bn * b + b;
+    // one launch per refinement level, in stream order
+    for (const Level& lv : mesh->levels) {
+        RecArgs g;
+        g.dm = mesh->dev(lv);
+        g.kappa = kappa;
+        g.lambda = lambda;
+        g.u0 = u0;
+        g.k_lambda = mesh->d_k_lambda;
+        g.P = mesh->desc.degree;
+        g.N = lv.N;
+        g.PN = lv.PN;
+        g.dpf = mesh->dpf;
+        g.NI = (int)mesh->NI;
+        g.nlev = lv.N + 1;
+        g.nloc = (int)lv.nloc;
+        auto size = [&](int lev) {
+            if (g.P == 1) return g.N + 1 - lev - (lev == 0);
+            if (lev == g.N) return 1;
+            return (2 * g.N - 2 * lev + 1) + (2 * g.N - 2 * lev) - (lev == 0);
+        };
+        g.rows = size(0) + (g.N >= 1 ? size(1) : 0);
+        g.rhs = g.rows;                      // right-hand side right after the symmetric part
+        g.ld = (g.rows + 2) & ~1;            // even: 16-byte rows for the vector panel loads
+        g.src_kind = f->kind;
+        g.src_value = f->value;
+        g.src_freq = f->freq;
+        g.ex_kind = exact ? (exact->kind == MHM_EXACT_SINSIN ? 1 : 2) : 0;
+        for (int i = 0; i < 6; ++i) g.ex[i] = exact ? exact->c[i] : 0.0;
+        size_t per = 0;
+        for (int lev = 0; lev < g.nlev; ++lev) {
+            const int b = size(lev), bn = lev + 1 < g.nlev ? size(lev + 1) : 0;
+            per += (size_t)b * b + (size_t)bn * b + b;
+        }
+        g.slot_bytes = ((per * sizeof(double)) + 255) & ~(size_t)255;
+        g.nK = lv.nK;
+        g.nod_off = mesh->d_nod_off;
+        g.u_out = u_nodal;
+        g.err_out = err_sq;
+        const size_t smem = ((size_t)g.rows * g.ld + (size_t)g.nloc) * sizeof(double);
+        if (smem > 220 * 1024) return fail(MHM_ERR_UNSUPPORTED, "mhm_reconstruct: window exceeds shared memory");
+        MHM_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_reconstruct, kThreadsR, smem);
+        int64_t grid = (int64_t)sms * (occ > 0 ? occ : 1);
+        if (grid > lv.nK) grid = lv.nK;
+        char* ws = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&ws, (size_t)grid * g.slot_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: cudaMallocAsync");
+        g.ws = ws;
+        k_reconstruct<<<(unsigned)grid, kThreadsR, smem, s>>>(g);
+        e = cudaGetLastError();
+        cudaFreeAsync(ws, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: launch");
     }
-    g.slot_bytes = ((per * sizeof(double)) + 255) & ~(size_t)255;
-    g.nK = mesh->nK;
-    g.u_out = u_nodal;
-    g.err_out = err_sq;
-    const size_t smem = ((size_t)g.rows * g.ld + (size_t)g.nloc) * sizeof(double);
-    if (smem > 220 * 1024) return fail(MHM_ERR_UNSUPPORTED, "mhm_reconstruct: window exceeds shared memory");
-    MHM_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int sms = 0, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_reconstruct, kThreadsR, smem);
-    int64_t grid = (int64_t)sms * (occ > 0 ? occ : 1);
-    if (grid > mesh->nK) grid = mesh->nK;
-    char* ws = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&ws, (size_t)grid * g.slot_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: cudaMallocAsync");
-    g.ws = ws;
-    k_reconstruct<<<(unsigned)grid, kThreadsR, smem, s>>>(g);
-    e = cudaGetLastError();
-    cudaFreeAsync(ws, s);
-    if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: launch");
     return MHM_OK;
 }

@@ -30,7 +30,7 @@ MHM_SRC_CONST = 0
 MHM_SRC_SINSIN = 1
 
 Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q_K_LAMBDA, \
-    Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS = range(11)
+    Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS, Q_R_OF_K, Q_KAPPA_OFFSET, Q_NODAL_OFFSET = range(14)
 
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
@@ -46,7 +46,8 @@ MHM_EXACT_POLY = 2
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("r", ctypes.c_int32),
-                ("degree", ctypes.c_int32), ("m", ctypes.c_int32), ("l", ctypes.c_int32)]
+                ("degree", ctypes.c_int32), ("m", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("r_per_K", ctypes.c_void_p)]
 
 
 class Source(ctypes.Structure):
@@ -63,7 +64,7 @@ class Exact(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("it_max", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("K_begin", ctypes.c_int64), ("K_end", ctypes.c_int64)]
+                ("K_begin", ctypes.c_int64), ("K_end", ctypes.c_int64), ("no_fallback", ctypes.c_int32)]
 
 
 class MHMError(RuntimeError):
@@ -126,8 +127,13 @@ def _stream(stream):
 class Mesh:
     """Owning handle of an mhm_mesh (splitProblem)."""
 
-    def __init__(self, nx, ny, r, degree, m, l, device: int = 0):
-        self.desc = MeshDesc(nx, ny, r, degree, m, l)
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, r_per_K=None):
+        """r_per_K: optional refinement level of every K (sequence of n_K ints); r is
+        then ignored."""
+        rk = None
+        if r_per_K is not None:
+            rk = np.ascontiguousarray(np.asarray(r_per_K, dtype=np.int8))
+        self.desc = MeshDesc(nx, ny, r, degree, m, l, None if rk is None else rk.ctypes.data)
         h = ctypes.c_void_p()
         _check(lib().mhm_create_mesh(ctypes.byref(self.desc), device, ctypes.byref(h)))
         self.handle = h
@@ -135,6 +141,9 @@ class Mesh:
         s = self.query(Q_SIZES, np.int64, 8)
         (self.n_K, self.n_faces, self.n_vertices, self.n_lambda, self.n_fine, self.n_local,
          self.n_I, self.nnz) = [int(v) for v in s]
+        self.r_of_K = self.query(Q_R_OF_K, np.int8, self.n_K)
+        self.kappa_offset = self.query(Q_KAPPA_OFFSET, np.int64, self.n_K + 1)   # 4^r_K values per K
+        self.nodal_offset = self.query(Q_NODAL_OFFSET, np.int64, self.n_K + 1)   # n_local(r_K) values per K
 
     def query(self, what, dtype, count):
         out = np.empty(count, dtype=dtype)
@@ -153,8 +162,8 @@ class Mesh:
             pass
 
 
-def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0) -> Mesh:
-    return Mesh(nx, ny, r, degree, m, l, device)
+def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0, r_per_K=None) -> Mesh:
+    return Mesh(nx, ny, r, degree, m, l, device, r_per_K)
 
 
 def mhm_local_workspace_size(mesh: Mesh, precision: int) -> int:

@@ -35,8 +35,8 @@ class _RawPtr:
 
 
 class Pipeline:
-    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64):
-        self.mesh = mhm.Mesh(nx, ny, r, degree, m, l, device)
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64, r_per_K=None):
+        self.mesh = mhm.Mesh(nx, ny, r, degree, m, l, device, r_per_K)
         self.device = torch.device("cuda", device)
         self.precision = precision
         M = self.mesh
@@ -55,7 +55,7 @@ class Pipeline:
 
     @classmethod
     def for_workload(cls, w: Workload, device: int = 0, precision: int = mhm.MHM_FP64):
-        return cls(w.nx, w.ny, w.r, w.degree, w.m, w.l, device, precision)
+        return cls(w.nx, w.ny, w.r, w.degree, w.m, w.l, device, precision, getattr(w, "r_per_K", None))
 
     def set_precision(self, precision: int):
         self.precision = precision
@@ -83,12 +83,14 @@ class Pipeline:
         return self.lam, self.u0
 
     def reconstruct(self, kappa, source, exact=None, stream=None):
-        """Nodal u_{H,h} per K (n_K x n_local) and, with `exact`, per-K squared L2/H1 errors."""
+        """Nodal u_{H,h} per K (n_K x n_local; with a level per K a flat array, K's values
+        at mesh.nodal_offset[K]) and, with `exact`, per-K squared L2/H1 errors."""
         M = self.mesh
-        u = torch.empty(M.n_K * M.n_local, dtype=torch.float64, device=self.device)
+        u = torch.empty(int(M.nodal_offset[-1]), dtype=torch.float64, device=self.device)
         err = torch.empty(2 * M.n_K, dtype=torch.float64, device=self.device) if exact is not None else None
         mhm.mhm_reconstruct(M, kappa, source, self.lam, self.u0, exact, u, err, stream)
-        return u.view(M.n_K, M.n_local), (None if err is None else err.view(M.n_K, 2))
+        uv = u if len(set(M.r_of_K.tolist())) > 1 else u.view(M.n_K, M.n_local)
+        return uv, (None if err is None else err.view(M.n_K, 2))
 
     def local_waves(self, kappa_host, source, budget_bytes: int, opts=None, stream=None):
         """Local solves in memory-admitted waves: kappa stays on the host (pinned) and is

@@ -208,6 +208,25 @@ class Workload:
     source_freq: float = 1.0
     dirichlet: tuple | None = None   # (a, b, c) for g = a + b x + c y, None = homogeneous
     seed: int = 0
+    levels: str | None = None        # None: every K at r; "channels": level per K from the channel field
+    r_cap: int = 6                   # largest level a K gets ("channels")
+
+    @property
+    def r_per_K(self):
+        """Refinement level of every K (None: uniform r).  "channels": r_K = 7, 6, 5, 4, 3
+        for a centroid within H/2, H, 2H, 4H of the nearest channel line, else (H the
+        coarse square size), capped at r_cap."""
+        if self.levels is None:
+            return None
+        if self.levels != "channels":
+            raise ValueError(self.levels)
+        cen = coarse_vertices(self.nx, self.ny).mean(axis=1)
+        d = ChannelField(self.seed).distance(cen)
+        H = 1.0 / self.nx
+        r = np.full(self.n_K, 3, dtype=np.int8)
+        for thr, lev in ((4 * H, 4), (2 * H, 5), (H, 6), (0.5 * H, 7)):
+            r[d < thr] = lev
+        return np.minimum(r, self.r_cap).astype(np.int8)
 
     @property
     def n_K(self) -> int:
@@ -242,11 +261,38 @@ WORKLOADS = {
     "c3_grf_mixed": Workload("c3_grf_mixed", 128, 128, 5, 1, 2, 2, "grf4", "const", 1.0),
     # 256x256 squares (131072 K), r=4 P2 (561 DOFs), m=3 l=1, GRF contrast 1e6, f = 1
     "c5_p2_large": Workload("c5_p2_large", 256, 256, 4, 2, 3, 1, "grf6", "const", 1.0),
+    # uneven levels: 64x64 squares, level per K from 16 channels of kappa = 1e4, P1, one
+    # subface with degree 2 multipliers on every face
+    "c4_channels": Workload("c4_channels", 64, 64, 3, 1, 1, 2, "channels", "const", 1.0, levels="channels"),
 }
 
 
+def kappa_levels(w: Workload, K_index=None):
+    """Per K (all, or those in K_index) the kappa values of its own level (4^r_K values,
+    fine-triangle order): a list of arrays.  For a workload with a level per K."""
+    rk = w.r_per_K
+    verts = coarse_vertices(w.nx, w.ny)
+    Ks = np.arange(w.n_K) if K_index is None else np.asarray(K_index)
+    out = [None] * len(Ks)
+    for r in sorted(set(int(rk[K]) for K in Ks)):
+        sel = [i for i, K in enumerate(Ks) if rk[K] == r]
+        cen = fine_centroids(verts[Ks[sel]], 1 << r)
+        if w.field == "channels":
+            vals = ChannelField(w.seed).kappa(cen)
+        elif w.field == "one":
+            vals = np.ones(cen.shape[:-1])
+        else:
+            raise ValueError(w.field)
+        for j, i in enumerate(sel):
+            out[i] = vals[j].reshape(-1)
+    return out
+
+
 def kappa_for(w: Workload, K_index: np.ndarray | None = None) -> np.ndarray:
-    """kappa array (n_K_selected, N*N) for workload `w` (all K, or the K in `K_index`)."""
+    """kappa array (n_K_selected, N*N) for workload `w` (all K, or the K in `K_index`);
+    for a workload with a level per K the concatenated per-K blocks (flat)."""
+    if w.r_per_K is not None:
+        return np.concatenate(kappa_levels(w, K_index))
     verts = coarse_vertices(w.nx, w.ny)
     Ks = np.arange(w.n_K) if K_index is None else np.asarray(K_index)
     if w.field == "one":

@@ -1,0 +1,137 @@
+"""A refinement level per coarse element (each local problem on its own submesh;
+the multipliers on the coarse faces): every K against the oracle on a small mesh
+with levels 1..6, exact recovery through the whole pipeline, and the uneven
+channel workload at full size sampled per level."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.local import solve_local
+from oracle.mesh import build_mesh
+from oracle.run import run
+from paper_1703_10435_gb300 import mhm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_10435_gb300 import build
+    build.build()
+
+
+def _levels_case():
+    nx = ny = 3
+    rng = np.random.default_rng(21)
+    rs = rng.integers(1, 6, 2 * nx * ny).astype(np.int8)
+    rs[[4, 11]] = 6                                   # two level-6 locals (64-wide levels)
+    kap = [10.0 ** rng.uniform(-2, 2, 4 ** int(r)) for r in rs]
+    return nx, ny, rs, kap
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("precision,tol", [(mhm.MHM_FP64, 1e-10), (mhm.MHM_MIXED, 1e-9)])
+def test_levels_every_element_vs_oracle(precision, tol):
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    m, l = 1, 2
+    p = Pipeline(nx, ny, 0, 1, m, l, 0, precision, r_per_K=rs)
+    kd = torch.as_tensor(np.concatenate(kap), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    p.local(kd, src)
+    torch.cuda.synchronize()
+    assert int(p.status.abs().sum()) == 0
+    NI = p.mesh.n_I
+    AK = p.AK.view(-1, NI, NI).cpu().numpy()
+    EK = p.EK.view(-1, NI).cpu().numpy()
+    mesh = build_mesh(nx, ny, m, l)
+    for K in range(len(rs)):
+        o = solve_local(mesh, K, int(rs[K]), 1, kap[K], 1.0)
+        assert _rel(AK[K], o.AK) < tol, (K, int(rs[K]))
+        scale = max(np.linalg.norm(o.EK), np.linalg.norm(o.AK) * abs(o.FK) / max(np.linalg.norm(o.BK), 1e-300), 1e-300)
+        assert np.linalg.norm(EK[K] - o.EK) / scale < tol, (K, int(rs[K]))
+    if precision == mhm.MHM_MIXED:   # the allocation-free entry runs the same levels
+        AK2 = torch.empty_like(p.AK)
+        EK2, BK2, FK2 = torch.empty_like(p.EK), torch.empty_like(p.BK), torch.empty_like(p.FK)
+        st2 = torch.empty_like(p.status)
+        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, None, AK2, EK2, BK2, FK2, st2)
+        torch.cuda.synchronize()
+        assert int(st2.abs().sum()) == 0
+        assert _rel(AK2.cpu().numpy(), p.AK.cpu().numpy()) < tol
+
+
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_levels_exact_linear_pipeline(precision):
+    """kappa = 1, u = 1 + 2x - 3y: recovered exactly at every node of every level."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, _ = _levels_case()
+    p = Pipeline(nx, ny, 0, 1, 1, 1, 0, precision, r_per_K=rs)
+    kd = torch.ones(int(p.mesh.kappa_offset[-1]), dtype=torch.float64, device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 0.0, 1.0)
+    gd = mhm.Dirichlet((mhm.ctypes.c_double * 6)(1.0, 2.0, -3.0, 0.0, 0.0, 0.0))
+    p.step(kd, src, gd)
+    p.solve_global()
+    ex = mhm.Exact(mhm.MHM_EXACT_POLY, (mhm.ctypes.c_double * 6)(1.0, 2.0, -3.0, 0.0, 0.0, 0.0))
+    u, err = p.reconstruct(kd, src, ex)
+    torch.cuda.synchronize()
+    assert int(p.status.abs().sum()) == 0
+    assert float(err.sum()) < 1e-18
+    # nodal values against g at the lattice points of each K's own level
+    o = run(nx, ny, rs, 1, 1, 1, [np.ones(4 ** int(r)) for r in rs], 0.0, g=lambda x, y: 1 + 2 * x - 3 * y)
+    uh = u.cpu().numpy()
+    for K, loc in enumerate(o.locals):
+        a, b = int(p.mesh.nodal_offset[K]), int(p.mesh.nodal_offset[K + 1])
+        xy = loc.sub.node_xy
+        assert np.abs(uh[a:b] - (1 + 2 * xy[:, 0] - 3 * xy[:, 1])).max() < 1e-10, K
+
+
+def test_channel_workload_full_size():
+    """The uneven channel workload (8192 K, levels 3..6): every level present, FP64 and
+    mixed agree, and sampled elements of each level match the oracle."""
+    from paper_1703_10435_gb300.pipeline import Pipeline, source_of
+    w = W.WORKLOADS["c4_channels"]
+    rk = w.r_per_K
+    assert set(np.unique(rk).tolist()) == {3, 4, 5, 6}
+    kd = torch.as_tensor(W.kappa_for(w), device="cuda")
+    out = {}
+    for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
+        p = Pipeline.for_workload(w, 0, prec)
+        p.local(kd, source_of(w))
+        torch.cuda.synchronize()
+        assert int(p.status.abs().sum()) == 0
+        out[prec] = p.AK.view(w.n_K, -1)
+        if prec == mhm.MHM_MIXED:
+            # levels 3..5 converge in FP32 + refinement; the 64-wide level-6 locals run
+            # on the FP64 path (one pass)
+            it = p.iters.cpu().numpy()
+            assert np.all(it[rk <= 5] >= 2) and np.all(it[rk == 6] == 1)
+    d = (torch.linalg.norm(out[mhm.MHM_MIXED] - out[mhm.MHM_FP64], dim=1) / torch.linalg.norm(out[mhm.MHM_FP64], dim=1)).max()
+    assert float(d) < 1e-9
+    # Per level: the median element and the first element crossing a channel (kappa 1 and
+    # 1e4 inside it), each path against the oracle.  The bound is 1e-10, or the FP64
+    # error bound 10 u cond(A_p) (u = 2^-53, cond on the mean-zero space) where that is
+    # larger: a crossing level-6 element has cond ~2e7, where two FP64 solvers (dense
+    # bordered LU here, pinned Cholesky on the GPU) can only agree to ~3e-9.
+    from oracle.local import assemble_stiffness
+    mesh = build_mesh(w.nx, w.ny, w.m, w.l)
+    NI = 3 * w.m * (w.l + 1)
+    for r in (3, 4, 5, 6):
+        idx = np.flatnonzero(rk == r)
+        picks = [int(idx[len(idx) // 2])]
+        for K in idx:
+            if W.kappa_levels(w, [int(K)])[0].max() > 1.0:
+                picks.append(int(K))
+                break
+        for K in picks:
+            kap = W.kappa_levels(w, [K])[0]
+            o = solve_local(mesh, K, r, 1, kap, 1.0)
+            ev = np.linalg.eigvalsh(assemble_stiffness(o.sub, kap).toarray())
+            tol = max(1e-10, 10 * 2.0 ** -53 * ev[-1] / ev[1])
+            for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
+                assert _rel(out[prec][K].view(NI, NI).cpu().numpy(), o.AK) < tol, (r, K, prec, tol)

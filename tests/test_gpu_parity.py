@@ -185,6 +185,21 @@ def test_mixed_reports_nonconvergence_with_one_pass():
     w = W.Workload("t", 1, 1, 4, 1, 1, 1, "log_uniform", "const", 1.0, seed=1)
     p = _pipeline(w, mhm.MHM_MIXED)
     from paper_1703_10435_gb300.pipeline import source_of
-    p.local(torch.as_tensor(W.kappa_for(w), device="cuda"), source_of(w), mhm.SolveOpts(1, 1e-13, 0, 0))
+    p.local(torch.as_tensor(W.kappa_for(w), device="cuda"), source_of(w), mhm.SolveOpts(1, 1e-13, 0, 0, 1))
     torch.cuda.synchronize()
     assert set(p.status.cpu().tolist()) == {mhm.MHM_ERR_NOT_CONVERGED}
+
+
+def test_mixed_failures_fall_back_to_fp64():
+    """By default the elements whose refinement fails are solved again in FP64: status
+    OK, iters -1, and blocks identical to the FP64 path's."""
+    w = W.Workload("t", 2, 2, 4, 1, 1, 1, "log_uniform", "const", 1.0, seed=1)
+    from paper_1703_10435_gb300.pipeline import source_of
+    kap = torch.as_tensor(W.kappa_for(w), device="cuda")
+    p = _pipeline(w, mhm.MHM_MIXED)
+    p.local(kap, source_of(w), mhm.SolveOpts(1, 1e-13, 0, 0))
+    p64 = _pipeline(w, mhm.MHM_FP64)
+    p64.local(kap, source_of(w))
+    torch.cuda.synchronize()
+    assert set(p.status.cpu().tolist()) == {0} and set(p.iters.cpu().tolist()) == {-1}
+    assert torch.equal(p.AK, p64.AK) and torch.equal(p.EK, p64.EK)

@@ -19,7 +19,9 @@ def built():
 
 @pytest.mark.parametrize("precision,expect", [
     (mhm.MHM_FP64, {"k_local_fp64": 1}),
-    (mhm.MHM_MIXED, {"k_schur_factor": 1, "k_local_mixed": 1}),
+    # mixed: factor, solve, and the FP64 re-solve of failed elements (launched with a
+    # device-side count, here zero)
+    (mhm.MHM_MIXED, {"k_schur_factor": 1, "k_local_mixed": 1, "k_local_fp64": 1}),
 ])
 def test_kernel_times(precision, expect):
     from paper_1703_10435_gb300.pipeline import Pipeline, source_of

@@ -82,3 +82,29 @@ def test_errors_are_reported(lib):
     code = lib.mhm_local_solve_batch(M.handle, None, None, 0, None, None, None, None, None, None, None,
                                      None, 0, None)
     assert code == mhm.MHM_ERR_UNSUPPORTED
+
+
+def test_per_element_levels_queries():
+    """A level per K: the queries give each K's level, its kappa block (4^r_K values)
+    and its block of nodal values (n_local of its level), in K order."""
+    from paper_1703_10435_gb300 import mhm
+    rng = np.random.default_rng(11)
+    rs = rng.integers(0, 5, 2 * 3 * 2)
+    for P in (1, 2):
+        m = mhm.Mesh(3, 2, 0, P, 1, 1, device=-1, r_per_K=rs)
+        assert np.array_equal(m.r_of_K, rs)
+        N = 2 ** rs.astype(np.int64)
+        assert np.array_equal(m.kappa_offset, np.concatenate([[0], np.cumsum(N * N)]))
+        nloc = (P * N + 1) * (P * N + 2) // 2
+        assert np.array_equal(m.nodal_offset, np.concatenate([[0], np.cumsum(nloc)]))
+        assert m.n_fine == int((N * N).max()) and m.n_local == int(nloc.max())
+        # the skeleton does not depend on the levels
+        u = mhm.Mesh(3, 2, 2, P, 1, 1, device=-1)
+        assert (m.n_lambda, m.n_I, m.nnz) == (u.n_lambda, u.n_I, u.nnz)
+        assert np.array_equal(u.kappa_offset, np.arange(13) * 16) and np.all(u.r_of_K == 2)
+
+
+def test_per_element_levels_reject_out_of_range():
+    from paper_1703_10435_gb300 import mhm
+    with pytest.raises(mhm.MHMError):
+        mhm.Mesh(1, 1, 0, 1, 1, 1, device=-1, r_per_K=[3, 8])
