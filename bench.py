@@ -111,8 +111,9 @@ def oracle_sample(w, Ks, kap):
     from oracle.run import source_fn
     mesh = build_mesh(w.nx, w.ny, w.m, w.l)
     f = float(w.source_value) if w.source == "const" else source_fn("sinsin", w.source_value, w.source_freq)
+    rk = w.r_per_K
     for i, K in enumerate(Ks):
-        solve_local(mesh, int(K), w.r, w.degree, kap[i], f)
+        solve_local(mesh, int(K), w.r if rk is None else int(rk[K]), w.degree, kap[i], f)
     return len(Ks)
 
 
@@ -125,13 +126,13 @@ def time_oracle(w, n_sample, cores, pool=None):
     """Seconds for the oracle's local solves of n_sample coarse triangles on `cores` processes."""
     from paper_1703_10435_gb300 import workloads as W
     Ks = np.arange(n_sample) % w.n_K
-    kap = W.kappa_for(w, Ks)
+    kap = W.kappa_for(w, Ks) if w.r_per_K is None else W.kappa_levels(w, Ks)
     chunks = np.array_split(np.arange(n_sample), cores)
     t0 = time.perf_counter()
     if pool is None:
         oracle_sample(w, Ks, kap)
     else:
-        futs = [pool.submit(oracle_sample, w, Ks[c], kap[c]) for c in chunks if len(c)]
+        futs = [pool.submit(oracle_sample, w, Ks[c], [kap[i] for i in c]) for c in chunks if len(c)]
         for fu in futs:
             fu.result()
     return time.perf_counter() - t0
@@ -211,10 +212,25 @@ def recorded_traffic(kernel, workload):
     return float(fields["traffic_bytes_per_launch"])
 
 
-def residual_fmas_per_pass(w):
-    """FP64 multiply-adds of one refinement pass of the mixed path for one K: the
-    assembled 7-point (P1) rows of A_p applied to the R right-hand sides."""
-    N = w.N
+def level_counts(w):
+    """{refinement level: number of K} of workload w."""
+    rk = w.r_per_K
+    if rk is None:
+        return {w.r: w.n_K}
+    return {int(r): int((rk == r).sum()) for r in np.unique(rk)}
+
+
+def mixed_level(w, r):
+    """True where the mixed path runs level r in mixed precision (P1 levels wider than
+    32 points run on the FP64 path)."""
+    return not (w.degree == 1 and (1 << r) > 32)
+
+
+def residual_fmas_per_pass(w, N=None):
+    """FP64 multiply-adds of one refinement pass of the mixed path for one K of N
+    segments per face (default: the workload's): the assembled 7-point (P1) rows of
+    A_p applied to the R right-hand sides."""
+    N = w.N if N is None else N
     if w.degree != 1:
         return None
     # On the right-isosceles coarse triangles of this mesh the lattice edge opposite
@@ -297,7 +313,8 @@ def run_ours(args, w, rank, world, local_rank):
     clocks = sampler.stop()
     for p in (p64, pmx):
         assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
-    passes = pmx.iters.double().mean().item()
+    itv = pmx.iters.cpu().numpy()
+    passes = float(itv[itv > 0].mean()) if np.any(itv > 0) else 0.0   # elements refined in mixed precision
 
     # end to end through the C ABI with host buffers (mixed path): kappa H2D in,
     # skeleton system (A, E, B, F) D2H out
@@ -356,29 +373,41 @@ def run_ours(args, w, rank, world, local_rank):
     # 128 FP32 FMA per clock per SM
     peak64 = 2 * 2 * sms * clk * 1e6 / 1e12
     peak32 = 2 * 128 * sms * clk * 1e6 / 1e12
-    # Per-kernel average launch durations over the timed region: the library's CUDA
-    # events around each local-solve launch, on the launching stream.
-    def per_launch(kern, name):
-        n, ms = kern.get(name, (0, 0.0))
-        return (n, ms / n * 1e-3) if n else (0, None)
-    n64, t_k64 = per_launch(kern64, "k_local_fp64")
-    nmx, t_kmx = per_launch(kernmx, "k_local_mixed")
-    nfac, t_kfac = per_launch(kernmx, "k_schur_factor")
-    fl64 = 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K * args.steps / max(n64, 1)
-    K_per_launch = w.n_K * args.steps / max(nmx, 1)
-    res = residual_fmas_per_pass(w)
-    fl_res = None if res is None else 2.0 * res * passes * K_per_launch
-    # tensor-core level products of the mixed solves: 2 b^2 R useful flops per level step
-    # (forward every level, backward all but the last), about `passes` solves per K
+    # Kernel durations over the timed region: the library's CUDA events around each
+    # local-solve launch, on the launching stream.
+    # Algorithmic work per step, summed over the refinement levels (one launch per level
+    # and step); achieved = work per step / kernel time per step (= per launch when a
+    # step is one launch).
+    lv = level_counts(w)
+    R = w.n_I + 1
+    it_all = pmx.iters.cpu().numpy()
+    rk = w.r_per_K if w.r_per_K is not None else np.full(w.n_K, w.r)
+    fl64 = 2.0 * sum(c * algorithmic_fmas(w.degree, 1 << r, R) for r, c in lv.items())
+    t_k64 = kern64["k_local_fp64"][1] * 1e-3 / args.steps if "k_local_fp64" in kern64 else None
+    t_kmx = kernmx["k_local_mixed"][1] * 1e-3 / args.steps if "k_local_mixed" in kernmx else None
+    t_kfac = kernmx["k_schur_factor"][1] * 1e-3 / args.steps if "k_schur_factor" in kernmx else None
+    n64, nmx, nfac = [kern.get(k, (0, 0.0))[0] for kern, k in ((kern64, "k_local_fp64"), (kernmx, "k_local_mixed"),
+                                                                (kernmx, "k_schur_factor"))]
+    fl_res, fl_tc = 0.0, 0.0
+    for r, c in lv.items():
+        if not mixed_level(w, r):
+            continue
+        it = it_all[rk == r]
+        p_r = float(it[it > 0].mean()) if np.any(it > 0) else 0.0
+        res = residual_fmas_per_pass(w, 1 << r)
+        if res is not None:
+            fl_res += 2.0 * res * p_r * c
+        if w.degree == 1:
+            N = 1 << r
+            sizes = [N + 1 - l_ - (l_ == 0) for l_ in range(N + 1)]
+            fl_tc += 2.0 * R * (2 * sum(b * b for b in sizes) - sizes[-1] ** 2) * p_r * c
+    fl_res = fl_res or None
     tc = None
-    if w.degree == 1 and t_kmx:
-        sizes = [w.N + 1 - lev - (lev == 0) for lev in range(w.N + 1)]
-        per_solve = 2.0 * (w.n_I + 1) * (2 * sum(b * b for b in sizes) - sizes[-1] ** 2)
-        fl_tc = per_solve * passes * K_per_launch
+    if fl_tc and t_kmx:
         # dense TF32 tensor peak: the measured bf16 burst figure times the nominal tf32/bf16 ratio
         peak_bf16 = measured_peaks().get("bf16_tflops")
         peak_tf32 = peak_bf16 * (1.1 / 2.25) if peak_bf16 else None
-        tc = {"pipe": "tensor (TF32, three-term split: 3 MMA per product)", "algorithmic_flops_per_launch": fl_tc,
+        tc = {"pipe": "tensor (TF32, three-term split: 3 MMA per product)", "algorithmic_flops_per_step": fl_tc,
               "achieved": fl_tc / t_kmx / 1e12, "peak": peak_tf32, "unit": "TFLOP/s",
               "frac": (fl_tc / t_kmx / 1e12 / peak_tf32) if peak_tf32 else None,
               "peak_source": "MEASURED_PEAKS.json bf16 burst x 1.1/2.25 (nominal tf32/bf16)"}
@@ -386,19 +415,19 @@ def run_ours(args, w, rank, world, local_rank):
                "achieved": (fl_res / t_kmx / 1e12) if (fl_res and t_kmx) else None, "peak": peak64, "unit": "TFLOP/s",
                "frac": (fl_res / t_kmx / 1e12 / peak64) if (fl_res and t_kmx) else None,
                "traffic": recorded_traffic("k_local_mixed", w.name),
-               "flops_per_launch": fl_res, "launch_ms": t_kmx * 1e3 if t_kmx else None, "launches": nmx,
+               "flops_per_step": fl_res, "kernel_ms_per_step": t_kmx * 1e3 if t_kmx else None, "launches": nmx,
                "refinement_passes_mean": passes,
                "peak_source": "2 FP64 FMA/clk/SM x SMs x max SM clock", "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
                "tensor": tc,
-               "factor_kernel": {"kernel": "k_schur_factor", "launch_ms": t_kfac * 1e3 if t_kfac else None,
+               "factor_kernel": {"kernel": "k_schur_factor", "kernel_ms_per_step": t_kfac * 1e3 if t_kfac else None,
                                  "launches": nfac},
-               "fp64_equivalent_local_solve_tflops": 2.0 * algorithmic_fmas(w.degree, w.N, w.n_I + 1) * w.n_K
-               / (float(localmx.mean()) * 1e-3) / 1e12}
+               "levels": {str(r): c for r, c in lv.items()},
+               "fp64_equivalent_local_solve_tflops": fl64 / (float(localmx.mean()) * 1e-3) / 1e12}
     roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64",
                "achieved": fl64 / t_k64 / 1e12 if t_k64 else None, "peak": peak64, "unit": "TFLOP/s",
                "frac": fl64 / t_k64 / 1e12 / peak64 if t_k64 else None,
                "traffic": recorded_traffic("k_local_fp64", w.name),
-               "flops_per_launch": fl64, "launch_ms": t_k64 * 1e3 if t_k64 else None, "launches": n64,
+               "flops_per_step": fl64, "kernel_ms_per_step": t_k64 * 1e3 if t_k64 else None, "launches": n64,
                "peak_measured_microbench": pipes["fp64_gflops"] / 1e3}
 
     cpu = None
