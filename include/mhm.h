@@ -175,11 +175,17 @@ mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, siz
  *   FK_dev[K]                     = (f, 1)_K
  *   status_dev[K]                 = 0, or MHM_ERR_NOT_CONVERGED (MIXED refinement
  *                                   hit it_max), or MHM_ERR_INVALID_ARG (non-positive pivot)
- *   iters_dev[K]                  = refinement passes taken (1 for FP64); may be NULL
+ *   iters_dev[K]                  = refinement passes taken (1 for FP64; -1: MIXED
+ *                                   refinement failed and K was solved again in FP64); may be NULL
  * Arrays are indexed by absolute K; entries outside the range are untouched.
- * kappa_dev: n_K * 4^r doubles, > 0.  workspace_dev: at least
- * mhm_local_workspace_size bytes (may be NULL when that size is 0).
- * stream: a cudaStream_t (NULL = legacy default stream).
+ * kappa_dev: n_K * 4^r doubles (with a level per K: 4^r_K from
+ * MHM_Q_KAPPA_OFFSET[K]), > 0.  workspace_dev: at least mhm_local_workspace_size
+ * bytes (may be NULL when that size is 0).
+ * stream: a cudaStream_t (NULL = legacy default stream).  On a mesh with several
+ * refinement levels the levels run concurrently: the first on `stream`, the others
+ * on library-owned side streams that wait for the work `stream` held when the call
+ * was made, and `stream` waits for them before its later work (stream-ordered as a
+ * whole; calls on the same mesh from several host threads must not interleave).
  * Errors: INVALID_ARG (NULL pointers, bad options, workspace too small),
  * UNSUPPORTED, CUDA (launch failure). */
 mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,

@@ -125,18 +125,51 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         if (ws_bytes < need || (need > 0 && !workspace))
             return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
     }
-    // one launch sequence per refinement level, in stream order (the mixed path reuses
-    // the workspace from level to level)
+    // One launch sequence per refinement level.  The levels are independent (disjoint
+    // elements and outputs), so with several of them the first runs on the caller's stream
+    // and the others on side streams forked from it (an event after the caller's earlier
+    // work) and joined back (the caller's stream waits for each); a mixed level uses its
+    // own region of the workspace.
+    std::vector<const Level*> run;
+    std::vector<int64_t> r0, r1;
     for (const Level& lv : mesh->levels) {
         int64_t i0 = 0, i1 = 0;
         level_range(lv, K0, K1, &i0, &i1);
         if (i1 <= i0) continue;
-        st = precision == MHM_FP64 || fp64_level(mesh, lv)
-                 ? launch_local_fp64(mesh, lv, kappa, *f, i0, i1, AK, EK, BK, FK, status, iters, s)
-                 : launch_local_mixed(mesh, lv, kappa, *f, o, i0, i1, AK, EK, BK, FK, status, iters, workspace,
-                                      ws_bytes, s);
-        if (st) return st;
+        run.push_back(&lv);
+        r0.push_back(i0);
+        r1.push_back(i1);
     }
+    const size_t nside = run.empty() ? 0 : run.size() - 1;
+    if (nside > 0) {
+        while (mesh->side.size() < nside) {
+            cudaStream_t ss;
+            cudaEvent_t ev;
+            MHM_CUDA_TRY(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
+            MHM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            mesh->side.push_back(ss);
+            mesh->side_done.push_back(ev);
+        }
+        if (!mesh->fork_ev) MHM_CUDA_TRY(cudaEventCreateWithFlags(&mesh->fork_ev, cudaEventDisableTiming));
+        MHM_CUDA_TRY(cudaEventRecord(mesh->fork_ev, s));
+    }
+    size_t offset = 0;
+    for (size_t i = 0; i < run.size(); ++i) {
+        const Level& lv = *run[i];
+        cudaStream_t si = i == 0 ? s : mesh->side[i - 1];
+        if (i > 0) MHM_CUDA_TRY(cudaStreamWaitEvent(si, mesh->fork_ev, 0));
+        if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
+            st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, si);
+        } else {
+            const size_t need = mixed_level_workspace(mesh, lv);
+            st = launch_local_mixed(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters,
+                                    (char*)workspace + offset, ws_bytes - offset, si);
+            offset += need;
+        }
+        if (st) return st;
+        if (i > 0) MHM_CUDA_TRY(cudaEventRecord(mesh->side_done[i - 1], si));
+    }
+    for (size_t i = 0; i < nside; ++i) MHM_CUDA_TRY(cudaStreamWaitEvent(s, mesh->side_done[i], 0));
     return MHM_OK;
 }
 

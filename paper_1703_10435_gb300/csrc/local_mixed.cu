@@ -1806,18 +1806,20 @@ static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const Mixed
            (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
 }
 
+size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv) {
+    if (mesh->device < 0 || fp64_level(mesh, lv)) return 0;   // FP64 levels need no workspace
+    const MixedLayout L = mixed_layout(mesh, lv);
+    if (L.smem > 220 * 1024 || !mixed_kernel(L)) return 0;
+    return (level_workspace(mesh, lv, L) + 255) & ~(size_t)255;
+}
+
 size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
     if (mesh->device < 0) return 0;
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(mesh->device);
-    size_t bytes = 0;   // the levels run one after the other on the stream: the largest need
-    for (const Level& lv : mesh->levels) {
-        if (fp64_level(mesh, lv)) continue;   // runs on the FP64 path: no workspace
-        const MixedLayout L = mixed_layout(mesh, lv);
-        if (L.smem > 220 * 1024 || !mixed_kernel(L)) continue;
-        bytes = std::max(bytes, level_workspace(mesh, lv, L));
-    }
+    size_t bytes = 0;   // the levels may run at the same time: a region each
+    for (const Level& lv : mesh->levels) bytes += mixed_level_workspace(mesh, lv);
     cudaSetDevice(cur);
     return bytes;
 }

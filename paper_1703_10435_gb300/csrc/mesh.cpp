@@ -438,6 +438,9 @@ extern "C" void mhm_destroy_mesh(mhm_mesh* m) {
     cudaSetDevice(m->device);
     free_mesh_device(m);
     for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
+    for (cudaStream_t ss : m->side) cudaStreamDestroy(ss);
+    for (cudaEvent_t e : m->side_done) cudaEventDestroy(e);
+    if (m->fork_ev) cudaEventDestroy(m->fork_ev);
     cudaSetDevice(cur);
     delete m;
 }

@@ -130,6 +130,10 @@ struct mhm_mesh {
     int64_t* d_kap_off = nullptr;
     int64_t* d_nod_off = nullptr;
     std::vector<mhm::Level> levels;       // one per level present, ascending r
+    // streams and events of the concurrent per-level launches (created on first use)
+    mutable std::vector<cudaStream_t> side;
+    mutable std::vector<cudaEvent_t> side_done;
+    mutable cudaEvent_t fork_ev = nullptr;
 
     mhm::DeviceMesh dev() const {
         return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w, nullptr, nullptr};
@@ -154,7 +158,8 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
 mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                                   const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
                                   double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream);
-size_t mixed_workspace_bytes(const mhm_mesh* mesh);   // largest over the levels
+size_t mixed_workspace_bytes(const mhm_mesh* mesh);   // the levels' regions, one after the other
+size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv);   // one level's region (0: FP64 level)
 // A level the MIXED precision runs on the FP64 path: P1 levels wider than 32 points.  Their
 // FP32 factor (levels of 64 points, jumps of 1e4 in kappa) is too inaccurate to drive the
 // FP64 refinement to the tolerance in a few passes, and its error estimate is not reliable.

@@ -135,3 +135,31 @@ def test_channel_workload_full_size():
             tol = max(1e-10, 10 * 2.0 ** -53 * ev[-1] / ev[1])
             for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
                 assert _rel(out[prec][K].view(NI, NI).cpu().numpy(), o.AK) < tol, (r, K, prec, tol)
+
+
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_levels_graph_replay(precision):
+    """The step on a mesh of several levels (levels forked to side streams and joined
+    back) captured once in a CUDA graph: every replay gives the eager result bit for bit.
+    The first, eager call creates the side streams before the capture."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    p = Pipeline(nx, ny, 0, 1, 1, 2, 0, precision, r_per_K=rs)
+    kd = torch.as_tensor(np.concatenate(kap), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    p.step(kd, src)
+    torch.cuda.synchronize()
+    ref_A, ref_AK = p.A_vals.clone(), p.AK.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            p.step(kd, src, stream=s)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        p.A_vals.zero_()
+        p.AK.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(p.A_vals, ref_A) and torch.equal(p.AK, ref_AK)
