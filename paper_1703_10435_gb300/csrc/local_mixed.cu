@@ -1801,8 +1801,15 @@ __global__ void k_collect_failed(const int32_t* klist, int64_t i0, int64_t i1, c
 
 // Workspace of one level: the slots, the chunk arrays, the assignment counter, and the
 // list of failed elements (count + one entry per element of the level).
+// chunk regions of a level: two (factor of chunk c+1 beside the solve of chunk c) when
+// the level spans several chunks
+static int chunk_buffers(const Level& lv, const MixedLayout& L) {
+    return (L.mode == 2 && lv.nK > kChunkMax) ? 2 : 1;
+}
+
 static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L) {
-    return (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_of(lv, L) * L.chunk_k_bytes + 256 + 256 +
+    return (size_t)mixed_slots(mesh, L) * L.slot_bytes +
+           (size_t)chunk_buffers(lv, L) * chunk_of(lv, L) * L.chunk_k_bytes + 256 + 256 +
            (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
 }
 
@@ -1839,7 +1846,8 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
     // dynamic assignment of coarse triangles to blocks: a counter behind the scratch,
     // zeroed in stream order before every solve launch
-    int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)chunk * L.chunk_k_bytes);
+    const int nbuf = chunk_buffers(lv, L);
+    int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)nbuf * chunk * L.chunk_k_bytes);
     MixedArgs g = mixed_args(mesh, lv, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
@@ -1866,35 +1874,60 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         MHM_CUDA_TRY(cudaGetLastError());
         return fallback();
     }
-    // MODE 2: per chunk, the factor kernel writes T, couplings and pivot flags behind the
-    // slots; the solve kernel reads them (stream order separates the two)
-    char* cbase = (char*)workspace + slots_bytes;
-    const size_t tb = (size_t)chunk * ((L.factor_floats * sizeof(float) + 255) & ~(size_t)255);
-    g.Tall = reinterpret_cast<float*>(cbase);
-    g.cwall = reinterpret_cast<float*>(cbase + tb);
-    g.fbad = reinterpret_cast<int*>(cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float));
-    {
-        char* p = cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float) + (((size_t)chunk * sizeof(int) + 255) & ~(size_t)255);
-        g.scall = reinterpret_cast<double*>(p);
-        g.ahall = reinterpret_cast<double*>(p + (((size_t)chunk * L.nunk * sizeof(double) + 255) & ~(size_t)255));
-    }
+    // MODE 2: per chunk, the factor kernel writes T, couplings, scaling, scaled stencil and
+    // pivot flags into a chunk region behind the slots; the solve kernel reads them.  With
+    // several chunks the factor launches run on the level's own stream, one chunk ahead:
+    // region c % 2 is refilled once the solve of chunk c - 2 is done with it.
     const size_t fsmem = factor_smem_bytes(L.nunk);
     MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-    for (int64_t c0 = K0; c0 < K1; c0 += chunk) {
+    const bool pipelined = K1 - K0 > chunk;   // then nbuf == 2 (the level has more than one chunk)
+    if (pipelined) {
+        if (!lv.fstream) {
+            MHM_CUDA_TRY(cudaStreamCreateWithFlags(&lv.fstream, cudaStreamNonBlocking));
+            MHM_CUDA_TRY(cudaEventCreateWithFlags(&lv.fstart, cudaEventDisableTiming));
+            for (int b = 0; b < 2; ++b) {
+                MHM_CUDA_TRY(cudaEventCreateWithFlags(&lv.fdone[b], cudaEventDisableTiming));
+                MHM_CUDA_TRY(cudaEventCreateWithFlags(&lv.mdone[b], cudaEventDisableTiming));
+            }
+        }
+        MHM_CUDA_TRY(cudaEventRecord(lv.fstart, stream));
+        MHM_CUDA_TRY(cudaStreamWaitEvent(lv.fstream, lv.fstart, 0));
+    }
+    cudaStream_t fs = pipelined ? lv.fstream : stream;
+    int c = 0;
+    for (int64_t c0 = K0; c0 < K1; c0 += chunk, ++c) {
         const int64_t c1 = std::min(K1, c0 + chunk);
+        const int b = pipelined ? (c & 1) : 0;
+        char* cbase = (char*)workspace + slots_bytes + (size_t)b * chunk * L.chunk_k_bytes;
+        const size_t tb = (size_t)chunk * ((L.factor_floats * sizeof(float) + 255) & ~(size_t)255);
+        g.Tall = reinterpret_cast<float*>(cbase);
+        g.cwall = reinterpret_cast<float*>(cbase + tb);
+        g.fbad = reinterpret_cast<int*>(cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float));
+        {
+            char* p = cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float) +
+                      (((size_t)chunk * sizeof(int) + 255) & ~(size_t)255);
+            g.scall = reinterpret_cast<double*>(p);
+            g.ahall = reinterpret_cast<double*>(p + (((size_t)chunk * L.nunk * sizeof(double) + 255) & ~(size_t)255));
+        }
         g.Kc0 = c0;
         g.K0 = c0;
         g.K1 = c1;
-        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, true);
-        k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, stream>>>(g);
-        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, false);
+        if (pipelined && c >= 2) MHM_CUDA_TRY(cudaStreamWaitEvent(fs, lv.mdone[b], 0));
+        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, true);
+        k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, fs>>>(g);
+        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, false);
         MHM_CUDA_TRY(cudaGetLastError());
+        if (pipelined) {
+            MHM_CUDA_TRY(cudaEventRecord(lv.fdone[b], fs));
+            MHM_CUDA_TRY(cudaStreamWaitEvent(stream, lv.fdone[b], 0));
+        }
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(c1 - c0 < slots ? c1 - c0 : slots);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
+        if (pipelined) MHM_CUDA_TRY(cudaEventRecord(lv.mdone[b], stream));
     }
     return fallback();
 }

@@ -90,6 +90,9 @@ void free_mesh_device(mhm_mesh* m) {
         if (lv.d_btab) cudaFree(lv.d_btab);
         lv.d_K = nullptr;
         lv.d_btab = nullptr;
+        if (lv.fstream) cudaStreamDestroy(lv.fstream);
+        for (cudaEvent_t e : {lv.fstart, lv.fdone[0], lv.fdone[1], lv.mdone[0], lv.mdone[1]})
+            if (e) cudaEventDestroy(e);
     }
 }
 

@@ -63,6 +63,10 @@ struct Level {
     std::vector<double> btab;      // face-load table of this level (dofs_per_face x (PN + 1))
     int32_t* d_K = nullptr;
     double* d_btab = nullptr;      // NULL: the mesh's table (uniform mesh)
+    // mixed path, several chunks: the factor launches run on their own stream, one chunk
+    // ahead of the solve launches (created on first use)
+    mutable cudaStream_t fstream = nullptr;
+    mutable cudaEvent_t fstart = nullptr, fdone[2] = {nullptr, nullptr}, mdone[2] = {nullptr, nullptr};
 };
 
 }  // namespace mhm
