@@ -222,8 +222,8 @@ def level_counts(w):
 
 def mixed_level(w, r):
     """True where the mixed path runs level r in mixed precision (P1 levels wider than
-    32 points run on the FP64 path)."""
-    return not (w.degree == 1 and (1 << r) > 32)
+    32 points, and P2 levels of r >= 5, run on the FP64 path)."""
+    return (1 << r) <= 32 if w.degree == 1 else r <= 4
 
 
 def residual_fmas_per_pass(w, N=None):

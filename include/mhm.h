@@ -123,7 +123,8 @@ typedef struct {
                            * converged in it_max passes, FP32 pivot breakdown) are solved
                            * again by the FP64 path, their iters entry set to -1;
                            * 1: they keep their failure status.  MIXED runs P1
-                           * levels wider than 32 points (r >= 6) on the FP64 path. */
+                           * levels wider than 32 points (r >= 6) and P2 levels of
+                           * r >= 5 on the FP64 path. */
 } mhm_solve_opts;
 
 /* ------------------------------------------------------------------ mesh --- */
@@ -159,8 +160,11 @@ mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, si
 
 /* ---------------------------------------------------------- local solves --- */
 
-/* Bytes of device scratch memory mhm_local_solve_batch needs for `precision`
- * (0 for MHM_FP64, whose factors live in shared memory only). */
+/* Bytes of device scratch memory mhm_local_solve_batch needs for `precision`: a
+ * region per refinement level of the mesh, one after the other.  MHM_FP64 levels
+ * whose level window fits in shared memory need none (0 for a mesh of those
+ * only); wider windows (P1 r = 7, P2 r = 5) live in one slot per SM of
+ * rows x (rows + N_I + 1) doubles.  MHM_MIXED adds its per-level buffers. */
 mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes);
 
 /* solveLocalProblem for K in [opts->K_begin, opts->K_end) (all K by default):
@@ -203,7 +207,8 @@ mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, 
  * which every GPU that loads the library holds until the process exits; the call
  * allocates nothing.  Coarse elements whose per-element scratch exceeds 32 MiB
  * are rejected with MHM_ERR_INVALID_ARG; a large batch runs with as many
- * concurrent blocks as fit in the array.  The first call on a device looks up
+ * concurrent blocks as fit in the array (the FP64 levels of the MIXED precision
+ * with windows wider than shared memory too).  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current:
  * make that first call before any stream capture.  All calls share the array,
  * and each call overwrites what the previous one left there: calls that can

@@ -64,7 +64,25 @@ void level_range(const Level& lv, int64_t K0, int64_t K1, int64_t* i0, int64_t* 
 }
 
 bool fp64_level(const mhm_mesh* mesh, const Level& lv) {
-    return mesh->desc.degree == 1 && lv.N > 32;
+    if (mesh->desc.degree == 1) return lv.N > 32;
+    return fp64_window_rows(mesh, lv) > 128;
+}
+
+size_t level_workspace_bytes(const mhm_mesh* mesh, const Level& lv, int32_t precision) {
+    const size_t b = (precision == MHM_FP64 || fp64_level(mesh, lv)) ? fp64_level_workspace(mesh, lv)
+                                                                       : mixed_level_workspace(mesh, lv);
+    return (b + 255) & ~(size_t)255;
+}
+
+size_t local_workspace_bytes(const mhm_mesh* mesh, int32_t precision) {
+    if (mesh->device < 0) return 0;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(mesh->device);
+    size_t bytes = 0;   // the levels may run at the same time: a region each
+    for (const Level& lv : mesh->levels) bytes += level_workspace_bytes(mesh, lv, precision);
+    cudaSetDevice(cur);
+    return bytes;
 }
 
 // Makes the mesh's device current; fails for host-only meshes.
@@ -85,12 +103,8 @@ extern "C" const char* mhm_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes) {
     if (!mesh || !bytes) return fail(MHM_ERR_INVALID_ARG, "mhm_local_workspace_size: NULL argument");
-    if (precision == MHM_FP64) {
-        *bytes = 0;
-        return MHM_OK;
-    }
-    if (precision == MHM_MIXED) {
-        *bytes = mixed_workspace_bytes(mesh);
+    if (precision == MHM_FP64 || precision == MHM_MIXED) {
+        *bytes = local_workspace_bytes(mesh, precision);
         return MHM_OK;
     }
     return fail(MHM_ERR_INVALID_ARG, "mhm_local_workspace_size: unknown precision");
@@ -118,10 +132,10 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
     cudaStream_t s = (cudaStream_t)stream;
     if (precision != MHM_FP64 && precision != MHM_MIXED)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown precision");
-    if (precision == MHM_MIXED) {
-        if (o.it_max < 1 || !(o.tol > 0.0))
-            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: it_max >= 1 and tol > 0 required");
-        const size_t need = mixed_workspace_bytes(mesh);
+    if (precision == MHM_MIXED && (o.it_max < 1 || !(o.tol > 0.0)))
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: it_max >= 1 and tol > 0 required");
+    {
+        const size_t need = local_workspace_bytes(mesh, precision);
         if (ws_bytes < need || (need > 0 && !workspace))
             return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
     }
@@ -129,7 +143,7 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
     // elements and outputs), so with several of them the first runs on the caller's stream
     // and the others on side streams forked from it (an event after the caller's earlier
     // work) and joined back (the caller's stream waits for each); a mixed level uses its
-    // own region of the workspace.
+    // own region of the workspace (levels without one get an empty region).
     std::vector<const Level*> run;
     std::vector<int64_t> r0, r1;
     for (const Level& lv : mesh->levels) {
@@ -158,14 +172,15 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         const Level& lv = *run[i];
         cudaStream_t si = i == 0 ? s : mesh->side[i - 1];
         if (i > 0) MHM_CUDA_TRY(cudaStreamWaitEvent(si, mesh->fork_ev, 0));
+        const size_t need = level_workspace_bytes(mesh, lv, precision);
+        void* region = need ? (char*)workspace + offset : nullptr;
         if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
-            st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, si);
+            st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, region, need, si);
         } else {
-            const size_t need = mixed_level_workspace(mesh, lv);
-            st = launch_local_mixed(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters,
-                                    (char*)workspace + offset, ws_bytes - offset, si);
-            offset += need;
+            st = launch_local_mixed(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters, region,
+                                    need, si);
         }
+        offset += need;
         if (st) return st;
         if (i > 0) MHM_CUDA_TRY(cudaEventRecord(mesh->side_done[i - 1], si));
     }

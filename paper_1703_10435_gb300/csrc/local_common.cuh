@@ -21,35 +21,40 @@ namespace mhm {
 
 struct LevelGeom {
     int P, N, PN;
+    int pin_x = 0, pin_y = 0;   // the pinned lattice point (in level 0 or 1; default DOF 0)
     __device__ __forceinline__ int n_levels() const { return N + 1; }
+    __device__ __forceinline__ int level_of_row(int y) const { return P == 1 ? y : (y >> 1); }
     // number of unknowns of level `lev` (pinned DOF excluded)
     __device__ __forceinline__ int size(int lev) const {
-        if (P == 1) return N + 1 - lev - (lev == 0);
-        if (lev == N) return 1;
-        return (2 * N - 2 * lev + 1) + (2 * N - 2 * lev) - (lev == 0);
+        const int pinned = lev == level_of_row(pin_y);
+        if (P == 1) return N + 1 - lev - pinned;
+        if (lev == N) return 1 - pinned;
+        return (2 * N - 2 * lev + 1) + (2 * N - 2 * lev) - pinned;
     }
-    __device__ __forceinline__ int level_of_row(int y) const { return P == 1 ? y : (y >> 1); }
     // position of lattice point (x, y) inside its level; -1 for the pinned DOF
     __device__ __forceinline__ int pos(int x, int y) const {
-        if (y == 0) return x - 1;
-        if (P == 1 || (y & 1) == 0) return x;
-        return (PN - y + 2) - (y == 1) + x;  // row y-1 has PN-y+2 points
+        const int sx = (y == pin_y && x > pin_x);   // points after the pin in its row move up one
+        if (y == pin_y && x == pin_x) return -1;
+        if (P == 1 || (y & 1) == 0) return x - sx;
+        // odd row: behind the PN-y+2 points of row y-1 (one fewer when the pin is there)
+        return (PN - y + 2) - (pin_y == y - 1) + x - sx;
     }
     // inverse of pos: lattice point of position p in level lev
     __device__ __forceinline__ void point(int lev, int p, int* x, int* y) const {
         if (P == 1) {
             *y = lev;
-            *x = p + (lev == 0);
+            *x = p + (lev == pin_y && p >= pin_x);
             return;
         }
-        int y0 = 2 * lev;
-        int len0 = PN - y0 + 1 - (lev == 0);
+        const int y0 = 2 * lev;
+        const int len0 = PN - y0 + 1 - (pin_y == y0);
         if (p < len0 || lev == N) {
             *y = y0;
-            *x = p + (lev == 0);
+            *x = p + (pin_y == y0 && p >= pin_x);
         } else {
+            const int q = p - len0;
             *y = y0 + 1;
-            *x = p - len0;
+            *x = q + (pin_y == y0 + 1 && q >= pin_x);
         }
     }
 };
@@ -105,6 +110,44 @@ __device__ __forceinline__ void element_nodes(int P, bool up, int i, int j, int 
         nx[4] = cx + ax; ny[4] = cy + ay;
         nx[5] = ax + bx; ny[5] = ay + by;
     }
+}
+
+// The pinned DOF of a local problem (Sec. 2: the local solutions are fixed up to a
+// constant; one DOF is set to zero, then the mean is removed): a lattice point of
+// levels 0 and 1 (level 0 alone when N = 1) on a fine triangle of largest kappa among
+// the triangles of fine rows 0 and 1, the first such point in DOF order; DOF 0 when kappa
+// is uniform there.  Pinning inside a stiff region keeps the pinned solution free of a
+// large constant offset on it; the face integrals would otherwise cancel that offset
+// in rounding (relative errors up to 1e5 times larger on high-contrast elements).
+// kap: the element's kappa in fine-triangle order (row j: up i = 0..N-j-1, down
+// i = 0..N-j-2).  Called by one thread.
+__device__ inline void choose_pin(int P, int N, const double* kap, int* pin_x, int* pin_y) {
+    const int PN = P * N;
+    const int ymax = N == 1 ? (P == 1 ? 0 : 1) : (P == 1 ? 1 : 3);   // lattice rows of the candidate levels
+    const int jmax = N == 1 ? 1 : 2;                                  // fine rows touching them
+    double best = -1.0;
+    for (int j = 0; j < jmax; ++j) {
+        const int rs = j * (2 * N - j);
+        for (int t = 0; t < 2 * (N - j) - 1; ++t) best = fmax(best, kap[rs + t]);
+    }
+    int bd = 1 << 30, bx = 0, by = 0;
+    for (int j = 0; j < jmax; ++j) {
+        const int rs = j * (2 * N - j);
+        for (int t = 0; t < 2 * (N - j) - 1; ++t) {
+            if (kap[rs + t] != best) continue;
+            const bool up = t < N - j;
+            int nx[6], ny[6];
+            element_nodes(P, up, up ? t : t - (N - j), j, nx, ny);
+            for (int a = 0; a < (P == 1 ? 3 : 6); ++a) {
+                const int x = nx[a], y = ny[a];
+                if (y > ymax) continue;
+                const int d = y * (PN + 1) - y * (y - 1) / 2 + x;
+                if (d < bd) { bd = d; bx = x; by = y; }
+            }
+        }
+    }
+    *pin_x = bx;
+    *pin_y = by;
 }
 
 // int_T phi_a / |T|: P1 1/3 at every vertex; P2 0 at vertices, 1/3 at midpoints.
@@ -355,6 +398,131 @@ __device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int 
                 }
                 Rhs[i * ldr + c] = acc;
             }
+        }
+        __syncthreads();
+    }
+}
+
+// The same factorisation for a window held in global memory (one too large for
+// shared memory).  Each panel of NB pivots is copied to shared memory (Ps: window
+// rows [p0, nr) x NB, row-major, 16-byte aligned; Rs: NB x ncols; invd: NB), its
+// NB x NB diagonal block is factored there by warp 0 together with the panel's
+// right-hand-side rows, the rows below it are solved against that block row by
+// row, the panel goes back to M and Rhs, and the trailing window is updated from
+// the shared copy: every trailing entry is read and written once per panel.  gram
+// (ncols x ncols, upper triangle; NULL: none) accumulates (L^{-1} Rhs)^T
+// (L^{-1} Rhs) over the b pivot rows.  Same results and contract as
+// blocked_cholesky_level (up to rounding order); no alignment asked of M or Rhs.
+// Ends with a block barrier.
+template <int NB>
+__device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rhs, int ldr, int rhs_rows, int ncols,
+                                    int* bad, double* Ps, double* Rs, double* invd, double* gram) {
+    for (int p0 = 0; p0 < b; p0 += NB) {
+        const int nbk = min(NB, b - p0), pe = p0 + nbk, np = nr - p0;
+        for (int t = threadIdx.x; t < np * NB; t += blockDim.x) {
+            const int i = t / NB, q = t - i * NB;
+            Ps[t] = (q < nbk && i >= q) ? M[(size_t)(p0 + i) * ld + p0 + q] : 0.0;
+        }
+        for (int t = threadIdx.x; t < NB * ncols; t += blockDim.x) {   // rows past nbk: zero
+            const int q = t / ncols, cc = t - q * ncols;
+            Rs[t] = q < nbk ? Rhs[(size_t)(p0 + q) * ldr + cc] : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // diagonal block (lane = row) and the panel's right-hand-side rows (lane = column)
+            const int lane = threadIdx.x;
+            for (int q = 0; q < nbk; ++q) {
+                const double d = Ps[q * NB + q];
+                const double inv = rsqrt_t<double>(d);
+                __syncwarp();
+                if (lane == 0) {
+                    if (!(d > 0.0) && *bad == 0) *bad = p0 + q + 1;
+                    Ps[q * NB + q] = d * inv;
+                    invd[q] = inv;
+                }
+                if (lane > q && lane < nbk) Ps[lane * NB + q] *= inv;
+                for (int cc = lane; cc < ncols; cc += 32) Rs[q * ncols + cc] *= inv;
+                __syncwarp();
+                if (lane > q && lane < nbk) {
+                    const double liq = Ps[lane * NB + q];
+                    for (int j = q + 1; j <= lane; ++j) Ps[lane * NB + j] -= liq * Ps[j * NB + q];
+                }
+                for (int q2 = q + 1; q2 < nbk; ++q2) {
+                    const double l2 = Ps[q2 * NB + q];
+                    for (int cc = lane; cc < ncols; cc += 32) Rs[q2 * ncols + cc] -= l2 * Rs[q * ncols + cc];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // rows below the diagonal block: l_i = (a_i - sum_{k<q} l_ik L_qk) / L_qq, one row per thread
+        for (int ii = nbk + threadIdx.x; ii < np; ii += blockDim.x) {
+            double l[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) l[q] = Ps[ii * NB + q];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (q < nbk) {
+                    double v = l[q];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (k < q) v -= l[k] * Ps[q * NB + k];
+                    l[q] = v * invd[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q) Ps[ii * NB + q] = l[q];
+        }
+        __syncthreads();
+        // panel back to M and Rhs (columns [p0, pe), rows [p0, pe) of Rhs)
+        for (int t = threadIdx.x; t < np * nbk; t += blockDim.x) {
+            const int i = t / nbk, q = t - i * nbk;
+            if (i >= q) M[(size_t)(p0 + i) * ld + p0 + q] = Ps[i * NB + q];
+        }
+        for (int t = threadIdx.x; t < nbk * ncols; t += blockDim.x) {
+            const int q = t / ncols, cc = t - q * ncols;
+            Rhs[(size_t)(p0 + q) * ldr + cc] = Rs[t];
+        }
+        if (gram) {
+            for (int t = threadIdx.x; t < ncols * (ncols + 1) / 2; t += blockDim.x) {
+                int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
+                while (c2 >= ncols - c1) { c2 -= ncols - c1; ++c1; }
+                c2 += c1;
+                double s = 0.0;
+                for (int q = 0; q < nbk; ++q) s += Rs[q * ncols + c1] * Rs[q * ncols + c2];
+                gram[c1 * ncols + c2] += s;
+            }
+        }
+        // trailing symmetric part: rows/cols [pe, nr), folded row pairs (pe+m-1-p, pe+p)
+        const int m = nr - pe;
+        if (m > 0) {
+            const int H = (m + 1) / 2, Wd = m + 1, total = H * Wd;
+#pragma unroll 2
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                const int p = e / Wd, cc = e - p * Wd;
+                const bool second = cc >= m - p;
+                const int i = pe + (second ? p : m - 1 - p);
+                const int j = pe + (second ? cc - (m - p) : cc);
+                if (second && m - 1 - p == p) continue;
+                double li[NB], lj[NB];
+                load_panel<NB>(Ps + (size_t)(i - p0) * NB, li);
+                load_panel<NB>(Ps + (size_t)(j - p0) * NB, lj);
+                double acc = M[(size_t)i * ld + j];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) acc -= li[q] * lj[q];
+                M[(size_t)i * ld + j] = acc;
+            }
+        }
+        // trailing right-hand-side rows [pe, rhs_rows)
+        const int rr = rhs_rows - pe;
+        for (int e = threadIdx.x; e < rr * ncols; e += blockDim.x) {
+            const int i = pe + e / ncols, cc = e - (e / ncols) * ncols;
+            double li[NB];
+            load_panel<NB>(Ps + (size_t)(i - p0) * NB, li);
+            double acc = Rhs[(size_t)i * ldr + cc];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) acc -= li[q] * Rs[q * ncols + cc];
+            Rhs[(size_t)i * ldr + cc] = acc;
         }
         __syncthreads();
     }

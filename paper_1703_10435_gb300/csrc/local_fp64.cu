@@ -4,7 +4,8 @@
 // What is computed.  With A the stiffness matrix of a(.,.)_K on the submesh,
 // m_w = int_K phi_w, and the loads N_i = -(s psi_i, phi_w)_{dK}, F = (f, phi_w)_K,
 // the zero-mean solutions are eta = z - (m^T z / |K|) 1 where z solves the
-// system pinned at DOF 0 with the compatible loads g~ = g - (1^T g / |K|) m.
+// system pinned at one DOF (choose_pin: inside the stiffest region touching the
+// first two levels) with the compatible loads g~ = g - (1^T g / |K|) m.
 // The face integrals of Eq. "mat_global" then reduce to a Gram matrix:
 //     A_K = -N~^T A_p^{-1} N~ = -Y^T Y,   E_K = Y^T y_f,
 // with Y = L^{-1} N~, y_f = L^{-1} f~ and A_p = L L^T (Cholesky of the pinned
@@ -21,6 +22,11 @@
 // level lev+1 and the forward-solved right-hand sides in one pass), accumulates
 // Y_lev^T Y_lev into the Gram matrix and moves the reduced level lev+1 to the
 // top of the window.
+//
+// Levels whose window does not fit in shared memory (P1 r = 7: 256 rows; P2 r = 5)
+// keep it in global memory instead, one workspace slot per block of a persistent
+// grid (one block per SM, so the slots stay in L2), and factor it panel by panel
+// through shared memory (wide_cholesky_level).
 #include <cuda_runtime.h>
 
 #include "local_common.cuh"
@@ -30,6 +36,8 @@ namespace mhm {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kThreadsWide = 512;   // wide window: one block per SM
+constexpr int kNBWide = 16;         // wide window: pivots per panel
 
 struct Fp64Args {
     DeviceMesh dm;
@@ -40,7 +48,9 @@ struct Fp64Args {
     int rows;      // window rows (largest b + b')
     int src_kind;
     double src_value, src_freq;
-    int64_t K0;
+    int64_t K0, K1;  // launch indices [K0, K1) within the level
+    double* win;     // wide window: slots of win_doubles per block (NULL: window in shared memory)
+    size_t win_doubles;
     double *AK, *EK, *BK, *FK;
     int32_t *status, *iters;
     const int32_t* kcount;   // launch indices >= *kcount do nothing (NULL: no bound)
@@ -57,6 +67,7 @@ struct KCtx {
     double cproj[kMaxNI + 1];  // projection coefficient of each right-hand side
     double FK;
     int bad;             // first failing pivot (+1), 0 if none
+    int pin_x, pin_y;    // the pinned lattice point (choose_pin)
 };
 
 // Sum over the block of one value per thread.
@@ -189,18 +200,30 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
     }
 }
 
-template <int RPL>
-__global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
+// Shared memory of the wide variant: the Gram matrix (R x R, rounded to an even count
+// so the panel stays 16-byte aligned), the panel (rows x kNBWide), its right-hand-side
+// rows (kNBWide x R) and the inverse pivots (kNBWide).
+__host__ __device__ inline size_t wide_gram_doubles(int R) { return ((size_t)R * R + 1) & ~(size_t)1; }
+inline size_t wide_smem_bytes(int rows, int R) {
+    return (wide_gram_doubles(R) + (size_t)rows * kNBWide + (size_t)kNBWide * R + kNBWide) * sizeof(double);
+}
+
+template <int RPL, bool WIDE>
+__global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) k_local_fp64(const Fp64Args g) {
     extern __shared__ double smem[];
     __shared__ KCtx c;
     __shared__ double red[32];
-    const int64_t ki = g.K0 + blockIdx.x;                          // launch index within the level
-    if (g.kcount && ki >= *g.kcount) return;                       // (whole block: no barrier passed)
-    const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;  // coarse element
-    const LevelGeom lg{g.P, g.N, g.PN};
     const int R = g.R;
-    double* W = smem;                                 // window: rows x ld
-    double* gram = smem + (size_t)g.rows * g.ld;      // R x R, upper triangle used
+    // window rows x ld: shared memory, or this block's workspace slot
+    double* W = WIDE ? g.win + (size_t)blockIdx.x * g.win_doubles : smem;
+    double* gram = WIDE ? smem : smem + (size_t)g.rows * g.ld;   // R x R, upper triangle used
+    double* Ps = smem + wide_gram_doubles(R);                      // (wide) panel
+    double* Rs = Ps + (size_t)g.rows * kNBWide;
+    double* invd = Rs + (size_t)kNBWide * R;
+    // launch indices within the level: one per block, or (wide) strided over the grid
+    for (int64_t ki = g.K0 + blockIdx.x; ki < g.K1; ki += gridDim.x) {
+    if (g.kcount && ki >= *g.kcount) break;                        // (whole block)
+    const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;  // coarse element
     const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
 
     // ---- per-K setup
@@ -225,8 +248,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
         element_stiffness(g.P, Xu, c.Sup);
         element_stiffness(g.P, Xd, c.Sdn);
         c.bad = 0;
+        choose_pin(g.P, g.N, kap, &c.pin_x, &c.pin_y);
     }
     __syncthreads();
+    const LevelGeom lg{g.P, g.N, g.PN, c.pin_x, c.pin_y};
     // F_K = (f, 1)_K and the projection coefficients (1^T g) / |K| of every right-hand side
     double FK;
     if (g.src_kind == MHM_SRC_CONST) {
@@ -273,17 +298,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
         }
         // Blocked right-looking Cholesky of the level's b pivots on the augmented window
         // rows; the right-hand-side columns (all window rows) are forward-substituted.
-        blocked_cholesky_level<double, 8, RPL, 2>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
-        // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
-        for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
-            int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
-            while (c2 >= R - c1) { c2 -= R - c1; ++c1; }
-            c2 += c1;
-            double s = 0.0;
-            for (int k = 0; k < b; ++k) s += W[k * g.ld + g.rhs0 + c1] * W[k * g.ld + g.rhs0 + c2];
-            gram[c1 * R + c2] += s;
+        if constexpr (WIDE) {
+            // Gram += Y^T Y accumulated panel by panel
+            wide_cholesky_level<kNBWide>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad, Ps, Rs, invd, gram);
+        } else {
+            blocked_cholesky_level<double, 8, RPL, 2>(W, g.ld, b, nr, W + g.rhs0, g.ld, nr, R, &c.bad);
+            // Gram += Y^T Y over the b rows of this level (upper triangle c1 <= c2)
+            for (int t = threadIdx.x; t < R * (R + 1) / 2; t += blockDim.x) {
+                int c1 = 0, c2 = t;   // t-th pair of the upper triangle, row by row
+                while (c2 >= R - c1) { c2 -= R - c1; ++c1; }
+                c2 += c1;
+                double s = 0.0;
+                for (int k = 0; k < b; ++k) s += W[k * g.ld + g.rhs0 + c1] * W[k * g.ld + g.rhs0 + c2];
+                gram[c1 * R + c2] += s;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (bn > 0) {
             // move the reduced level lev+1 (rows/cols [b, nr)) to the top; clear the next rows
             for (int t = threadIdx.x; t < bn * (bn + R); t += blockDim.x) {
@@ -318,6 +348,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_local_fp64(const Fp64Args g) {
         g.status[K] = c.bad ? MHM_ERR_INVALID_ARG : 0;
         if (g.iters) g.iters[K] = g.fallback ? -1 : 1;
     }
+    __syncthreads();   // the context, the Gram matrix and the window serve the next element
+    }
 }
 
 }  // namespace
@@ -333,10 +365,50 @@ int fp64_window_rows(const mhm_mesh* mesh, const Level& lv) {
     return size(0) + (N >= 1 ? size(1) : 0);
 }
 
+namespace {
+
+// Window of a level: rows, leading dimension (even: 16-byte rows), shared memory, and
+// whether it lives in global memory (more rows than the register panel holds, or more
+// than the shared memory).
+struct Fp64Shape {
+    int rows, ld, R;
+    size_t smem, win_doubles;
+    bool wide;
+};
+
+Fp64Shape fp64_shape(const mhm_mesh* mesh, const Level& lv) {
+    Fp64Shape sh;
+    sh.R = (int)mesh->NI + 1;
+    sh.rows = fp64_window_rows(mesh, lv);
+    sh.ld = sh.rows + sh.R;
+    if (sh.ld % 2 == 1) sh.ld += 1;
+    sh.smem = ((size_t)sh.rows * sh.ld + (size_t)sh.R * sh.R) * sizeof(double);
+    sh.wide = sh.rows > 128 || sh.smem > 220 * 1024;
+    sh.win_doubles = ((size_t)sh.rows * sh.ld + 31) & ~(size_t)31;   // 256-byte slots
+    if (sh.wide) sh.smem = wide_smem_bytes(sh.rows, sh.R);
+    return sh;
+}
+
+int sm_count(const mhm_mesh* mesh) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+size_t fp64_level_workspace(const mhm_mesh* mesh, const Level& lv) {
+    if (mesh->device < 0) return 0;
+    const Fp64Shape sh = fp64_shape(mesh, lv);
+    if (!sh.wide) return 0;
+    const int64_t slots = std::min<int64_t>(sm_count(mesh), std::max<int64_t>(lv.nK, 1));
+    return (size_t)slots * sh.win_doubles * sizeof(double);
+}
+
 static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                               int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
                               int32_t* status, int32_t* iters, const int32_t* list, const int32_t* count,
-                              cudaStream_t stream) {
+                              void* ws, size_t ws_bytes, cudaStream_t stream) {
     Fp64Args g;
     g.dm = mesh->dev(lv);
     g.kcount = count;
@@ -350,31 +422,49 @@ static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const doubl
     g.L = mesh->desc.l;
     g.dpf = mesh->dpf;
     g.NI = (int)mesh->NI;
-    g.R = g.NI + 1;
-    const int rows = fp64_window_rows(mesh, lv);
-    g.rows = rows;
-    g.rhs0 = rows;
-    g.ld = rows + g.R;
-    if (g.ld % 2 == 1) g.ld += 1;  // rows 16-byte aligned for the vector panel loads
+    const Fp64Shape sh = fp64_shape(mesh, lv);
+    g.R = sh.R;
+    g.rows = sh.rows;
+    g.rhs0 = sh.rows;
+    g.ld = sh.ld;
     g.src_kind = f.kind;
     g.src_value = f.value;
     g.src_freq = f.freq;
     g.K0 = K0;
+    g.K1 = K1;
+    g.win = nullptr;
+    g.win_doubles = sh.win_doubles;
     g.AK = AK; g.EK = EK; g.BK = BK; g.FK = FK;
     g.status = status;
     g.iters = iters;
-    const size_t smem = ((size_t)rows * g.ld + (size_t)g.R * g.R) * sizeof(double);
-    if (smem > 220 * 1024)
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window exceeds shared memory (r too large)");
-    if (rows > 128 || g.R > 64)
-        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window rows > 128 or more than 64 right-hand sides");
-    // register shape of the warp panel: window rows per lane
-    void (*kern)(const Fp64Args) = rows <= 64 ? k_local_fp64<2> : k_local_fp64<4>;
-    MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (sh.smem > 220 * 1024)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 window panel exceeds shared memory (r too large)");
+    if (g.R > 64)
+        return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch: FP64 path takes at most 64 right-hand sides");
     const int64_t nblk = K1 - K0;
     if (nblk <= 0) return MHM_OK;
+    void (*kern)(const Fp64Args);
+    int64_t grid = nblk;
+    int threads = kThreads;
+    if (sh.wide) {
+        // persistent grid: one block per SM and workspace slot
+        const int64_t fit = ws ? (int64_t)(ws_bytes / (sh.win_doubles * sizeof(double))) : 0;
+        grid = std::min<int64_t>(std::min<int64_t>(sm_count(mesh), fit), nblk);
+        if (grid < 1)
+            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: the FP64 window of this level needs a workspace of " +
+                                                 std::to_string(sh.win_doubles * sizeof(double)) + " bytes or more");
+        if (reinterpret_cast<uintptr_t>(ws) % 16 != 0)
+            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace must be 16-byte aligned");
+        g.win = static_cast<double*>(ws);
+        kern = k_local_fp64<4, true>;
+        threads = kThreadsWide;
+    } else {
+        // register shape of the warp panel: window rows per lane
+        kern = sh.rows <= 64 ? k_local_fp64<2, false> : k_local_fp64<4, false>;
+    }
+    MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
     timing_mark(mesh, MHM_KERNEL_LOCAL_FP64, stream, true);
-    kern<<<(unsigned)nblk, kThreads, smem, stream>>>(g);
+    kern<<<(unsigned)grid, threads, sh.smem, stream>>>(g);
     timing_mark(mesh, MHM_KERNEL_LOCAL_FP64, stream, false);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
@@ -382,15 +472,17 @@ static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const doubl
 
 mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK, int32_t* status,
-                             int32_t* iters, cudaStream_t stream) {
+                             int32_t* iters, void* ws, size_t ws_bytes, cudaStream_t stream) {
     // K0, K1: launch indices within the level (its K list, or K itself on a uniform mesh)
-    return launch_fp64(mesh, lv, kappa, f, K0, K1, AK, EK, BK, FK, status, iters, nullptr, nullptr, stream);
+    return launch_fp64(mesh, lv, kappa, f, K0, K1, AK, EK, BK, FK, status, iters, nullptr, nullptr, ws, ws_bytes,
+                       stream);
 }
 
 mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                                   const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
                                   double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream) {
-    return launch_fp64(mesh, lv, kappa, f, 0, max_n, AK, EK, BK, FK, status, iters, list, count, stream);
+    // re-solves of failed mixed elements: mixed levels always have a shared-memory window
+    return launch_fp64(mesh, lv, kappa, f, 0, max_n, AK, EK, BK, FK, status, iters, list, count, nullptr, 0, stream);
 }
 
 }  // namespace mhm

@@ -1814,21 +1814,10 @@ static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const Mixed
 }
 
 size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv) {
-    if (mesh->device < 0 || fp64_level(mesh, lv)) return 0;   // FP64 levels need no workspace
+    if (mesh->device < 0 || fp64_level(mesh, lv)) return 0;   // FP64 levels: fp64_level_workspace
     const MixedLayout L = mixed_layout(mesh, lv);
     if (L.smem > 220 * 1024 || !mixed_kernel(L)) return 0;
     return (level_workspace(mesh, lv, L) + 255) & ~(size_t)255;
-}
-
-size_t mixed_workspace_bytes(const mhm_mesh* mesh) {
-    if (mesh->device < 0) return 0;
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(mesh->device);
-    size_t bytes = 0;   // the levels may run at the same time: a region each
-    for (const Level& lv : mesh->levels) bytes += mixed_level_workspace(mesh, lv);
-    cudaSetDevice(cur);
-    return bytes;
 }
 
 mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
@@ -2005,9 +1994,9 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         level_range(lv, K0, K1, &i0, &i1);
         const int64_t nK = i1 - i0;
         if (nK <= 0) continue;
-        if (fp64_level(mesh, lv)) {   // the FP64 path needs no scratch
+        if (fp64_level(mesh, lv)) {   // a window wider than shared memory: as many blocks as the array holds
             const mhm_status st = launch_local_fp64(mesh, lv, kappa, *f, i0, i1, AK, EK, BK, FK, status, iters,
-                                                    (cudaStream_t)stream);
+                                                    scratch, kStaticScratch, (cudaStream_t)stream);
             if (st) return st;
             continue;
         }

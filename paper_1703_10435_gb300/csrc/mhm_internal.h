@@ -150,9 +150,16 @@ struct mhm_mesh {
 
 namespace mhm {
 // Launchers (defined in the .cu files).
+// FP64 local solves of launch indices [K0, K1) of level lv; a level whose window exceeds
+// shared memory keeps it in ws (fp64_level_workspace bytes; with less, fewer blocks)
 mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
-                             int32_t* status, int32_t* iters, cudaStream_t stream);
+                             int32_t* status, int32_t* iters, void* ws, size_t ws_bytes, cudaStream_t stream);
+size_t fp64_level_workspace(const mhm_mesh* mesh, const Level& lv);   // 0: window in shared memory
+int fp64_window_rows(const mhm_mesh* mesh, const Level& lv);
+// workspace region of one level at the given precision, and of all levels (one after the other)
+size_t level_workspace_bytes(const mhm_mesh* mesh, const Level& lv, int32_t precision);
+size_t local_workspace_bytes(const mhm_mesh* mesh, int32_t precision);
 mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                               const mhm_solve_opts& opts, int64_t K0, int64_t K1, double* AK,
                               double* EK, double* BK, double* FK, int32_t* status, int32_t* iters,
@@ -162,11 +169,12 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
 mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                                   const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
                                   double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream);
-size_t mixed_workspace_bytes(const mhm_mesh* mesh);   // the levels' regions, one after the other
 size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv);   // one level's region (0: FP64 level)
-// A level the MIXED precision runs on the FP64 path: P1 levels wider than 32 points.  Their
-// FP32 factor (levels of 64 points, jumps of 1e4 in kappa) is too inaccurate to drive the
-// FP64 refinement to the tolerance in a few passes, and its error estimate is not reliable.
+// A level the MIXED precision runs on the FP64 path: P1 levels wider than 32 points, and
+// levels whose window exceeds the mixed kernel's shared memory (P2 r >= 5).  The FP32 factor
+// of the wide P1 levels (levels of 64 points, jumps of 1e4 in kappa) is too inaccurate to
+// drive the FP64 refinement to the tolerance in a few passes, and its error estimate is not
+// reliable.
 bool fp64_level(const mhm_mesh* mesh, const Level& lv);
 // [i0, i1): the launch indices of level lv whose K lies in [K0, K1)
 void level_range(const Level& lv, int64_t K0, int64_t K1, int64_t* i0, int64_t* i1);

@@ -6,6 +6,9 @@
 // right-hand side, storing L_lev and L_{lev+1,lev} per level in scratch, then a
 // backward sweep by one warp.  Optional per-K squared L2 and broken-H1 errors
 // against an exact solution by the collapsed 4 x 4 Gauss rule per fine triangle.
+// Windows too large for shared memory (P1 r = 7, P2 r = 5) sit in the block's
+// scratch slot behind the stored factors and are factored panel by panel
+// (wide_cholesky_level).
 #include <cuda_runtime.h>
 
 #include "local_common.cuh"
@@ -15,6 +18,8 @@ namespace mhm {
 namespace {
 
 constexpr int kThreadsR = 128;
+constexpr int kThreadsRWide = 256;
+constexpr int kNBR = 16;   // wide window: pivots per panel
 
 struct RecArgs {
     DeviceMesh dm;
@@ -30,6 +35,7 @@ struct RecArgs {
     double ex[6];
     char* ws;
     size_t slot_bytes;
+    size_t win_offset;          // wide window: its byte offset in the slot (0: shared memory)
     int64_t nK;                 // launch indices of this level
     const int64_t* nod_off;     // first nodal value of each K in u_out (NULL: K * nloc)
     double* u_out;              // n_K * nloc (per-K levels: at nod_off)
@@ -43,7 +49,8 @@ struct RCtx {
     double flen[3];
     int sgn[3], rev[3];
     int bad;
-    double red[kThreadsR / 32];
+    int pin_x, pin_y;            // the pinned lattice point (choose_pin)
+    double red[kThreadsRWide / 32];
     double mz;
 };
 
@@ -120,15 +127,19 @@ __device__ double block_sum(double v, RCtx& c) {
     return s;
 }
 
-__global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
+template <bool WIDE>
+__global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruct(const RecArgs g) {
     extern __shared__ double smem[];
-    double* W = smem;                          // window rows x ld; column rhs is the right-hand side
-    double* zs = smem + (size_t)g.rows * g.ld; // nloc: the solution z (pinned DOF 0 = 0)
     __shared__ RCtx c;
-    const LevelGeom lg{g.P, g.N, g.PN};
     const int rhs = g.rhs;
     char* slot = g.ws + (size_t)blockIdx.x * g.slot_bytes;
     double* Fst = reinterpret_cast<double*>(slot);   // per level: L (b x b), C (bn x b), y (b)
+    // window rows x ld (column rhs is the right-hand side): shared memory or the slot
+    double* W = WIDE ? reinterpret_cast<double*>(slot + g.win_offset) : smem;
+    double* zs = WIDE ? smem : smem + (size_t)g.rows * g.ld;   // nloc: the solution z (pinned DOF 0 = 0)
+    double* Ps = smem + (((size_t)g.nloc + 1) & ~(size_t)1);   // (wide) panel, 16-byte aligned
+    double* Rs = Ps + (size_t)g.rows * kNBR;
+    double* invd = Rs + kNBR;
     const int nb = g.P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
 
     for (int64_t ki = blockIdx.x; ki < g.nK; ki += gridDim.x) {
@@ -162,8 +173,10 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
             }
             c.cl = cl;
             c.bad = 0;
+            choose_pin(g.P, g.N, kap, &c.pin_x, &c.pin_y);
         }
         __syncthreads();
+        const LevelGeom lg{g.P, g.N, g.PN, c.pin_x, c.pin_y};
         double fk = 0.0;
         if (g.src_kind == MHM_SRC_CONST) fk = g.src_value * c.area;
         else {
@@ -251,7 +264,10 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
                     __syncthreads();
                 }
             }
-            blocked_cholesky_level<double, 8, 4, 1>(W, g.ld, b, nr, W + rhs, g.ld, nr, 1, &c.bad);
+            if constexpr (WIDE)
+                wide_cholesky_level<kNBR>(W, g.ld, b, nr, W + rhs, g.ld, nr, 1, &c.bad, Ps, Rs, invd, nullptr);
+            else
+                blocked_cholesky_level<double, 8, 4, 1>(W, g.ld, b, nr, W + rhs, g.ld, nr, 1, &c.bad);
             // keep L_lev, L_{lev+1,lev} and y_lev for the backward sweep
             for (int t = threadIdx.x; t < b * b + bn * b + b; t += blockDim.x) {
                 double v;
@@ -279,7 +295,7 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
             const int lane = threadIdx.x;
             size_t off = foff;
             int bnext = 0, u0n = 0;
-            int ustart = g.nloc - 1;   // unknowns = local DOFs 1..nloc-1
+            int ustart = g.nloc - 1;   // unknowns 0..nloc-2 at zs[1 ..]
             for (int lev = g.nlev - 1; lev >= 0; --lev) {
                 const int b = lg.size(lev);
                 const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
@@ -304,7 +320,16 @@ __global__ void __launch_bounds__(kThreadsR) k_reconstruct(const RecArgs g) {
                 bnext = b;
                 u0n = ustart;
             }
-            if (lane == 0) zs[0] = 0.0;   // the pinned DOF
+            // zs[1 + u] holds unknown u; the unknowns are the local DOFs in order without the
+            // pinned one: shift the DOFs before it down by one and set the pinned DOF to 0
+            const int pd = lg.pin_y * (g.PN + 1) - lg.pin_y * (lg.pin_y - 1) / 2 + lg.pin_x;
+            for (int base = 0; base < pd; base += 32) {
+                const double v = base + lane < pd ? zs[base + lane + 1] : 0.0;
+                __syncwarp();
+                if (base + lane < pd) zs[base + lane] = v;
+                __syncwarp();
+            }
+            if (lane == 0) zs[pd] = 0.0;
         }
         __syncthreads();
         // zero mean: eta = z - (m^T z) / |K|, m_w = sum of int phi_w over the fine triangles
@@ -430,19 +455,29 @@ extern "C" mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa,
         g.nod_off = mesh->d_nod_off;
         g.u_out = u_nodal;
         g.err_out = err_sq;
-        const size_t smem = ((size_t)g.rows * g.ld + (size_t)g.nloc) * sizeof(double);
+        size_t smem = ((size_t)g.rows * g.ld + (size_t)g.nloc) * sizeof(double);
+        const bool wide = g.rows > 128 || smem > 220 * 1024;
+        g.win_offset = 0;
+        if (wide) {
+            // the window behind the stored factors in the slot; shared memory keeps z and the panel
+            g.win_offset = g.slot_bytes;
+            g.slot_bytes += (((size_t)g.rows * g.ld * sizeof(double)) + 255) & ~(size_t)255;
+            smem = ((((size_t)g.nloc + 1) & ~(size_t)1) + (size_t)g.rows * kNBR + 2 * kNBR) * sizeof(double);
+        }
         if (smem > 220 * 1024) return fail(MHM_ERR_UNSUPPORTED, "mhm_reconstruct: window exceeds shared memory");
-        MHM_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        void (*kern)(const RecArgs) = wide ? k_reconstruct<true> : k_reconstruct<false>;
+        const int threads = wide ? kThreadsRWide : kThreadsR;
+        MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_reconstruct, kThreadsR, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         int64_t grid = (int64_t)sms * (occ > 0 ? occ : 1);
         if (grid > lv.nK) grid = lv.nK;
         char* ws = nullptr;
         cudaError_t e = cudaMallocAsync((void**)&ws, (size_t)grid * g.slot_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: cudaMallocAsync");
         g.ws = ws;
-        k_reconstruct<<<(unsigned)grid, kThreadsR, smem, s>>>(g);
+        kern<<<(unsigned)grid, threads, smem, s>>>(g);
         e = cudaGetLastError();
         cudaFreeAsync(ws, s);
         if (e != cudaSuccess) return cuda_fail(e, "mhm_reconstruct: launch");

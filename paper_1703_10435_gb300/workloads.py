@@ -209,7 +209,7 @@ class Workload:
     dirichlet: tuple | None = None   # (a, b, c) for g = a + b x + c y, None = homogeneous
     seed: int = 0
     levels: str | None = None        # None: every K at r; "channels": level per K from the channel field
-    r_cap: int = 6                   # largest level a K gets ("channels")
+    r_cap: int = 7                   # largest level a K gets ("channels")
 
     @property
     def r_per_K(self):
@@ -261,8 +261,8 @@ WORKLOADS = {
     "c3_grf_mixed": Workload("c3_grf_mixed", 128, 128, 5, 1, 2, 2, "grf4", "const", 1.0),
     # 256x256 squares (131072 K), r=4 P2 (561 DOFs), m=3 l=1, GRF contrast 1e6, f = 1
     "c5_p2_large": Workload("c5_p2_large", 256, 256, 4, 2, 3, 1, "grf6", "const", 1.0),
-    # uneven levels: 64x64 squares, level per K from 16 channels of kappa = 1e4, P1, one
-    # subface with degree 2 multipliers on every face
+    # uneven levels 3..7: 64x64 squares, level per K from 16 channels of kappa = 1e4, P1,
+    # one subface with degree 2 multipliers on every face
     "c4_channels": Workload("c4_channels", 64, 64, 3, 1, 1, 2, "channels", "const", 1.0, levels="channels"),
 }
 
