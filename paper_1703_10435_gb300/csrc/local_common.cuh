@@ -405,23 +405,29 @@ __device__ void blocked_cholesky_level(T* M, int ld, int b, int nr, T* Rhs, int 
 
 // The same factorisation for a window held in global memory (one too large for
 // shared memory).  Each panel of NB pivots is copied to shared memory (Ps: window
-// rows [p0, nr) x NB, row-major, 16-byte aligned; Rs: NB x ncols; invd: NB), its
+// rows [p0, nr) x NB columns, 16-byte aligned; Rs: NB x ncols; invd: NB), its
 // NB x NB diagonal block is factored there by warp 0 together with the panel's
 // right-hand-side rows, the rows below it are solved against that block row by
 // row, the panel goes back to M and Rhs, and the trailing window is updated from
-// the shared copy: every trailing entry is read and written once per panel.  gram
+// the shared copy: every trailing entry is read and written once per panel.  Panel
+// rows are wide_panel_stride(NB) doubles apart (NB + 2: consecutive rows start four
+// banks apart, so the 16-byte loads of 8 rows cover all 32 banks).  gram
 // (ncols x ncols, upper triangle; NULL: none) accumulates (L^{-1} Rhs)^T
 // (L^{-1} Rhs) over the b pivot rows.  Same results and contract as
 // blocked_cholesky_level (up to rounding order); no alignment asked of M or Rhs.
 // Ends with a block barrier.
 template <int NB>
+__host__ __device__ constexpr int wide_panel_stride() { return NB + 2; }
+
+template <int NB>
 __device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rhs, int ldr, int rhs_rows, int ncols,
                                     int* bad, double* Ps, double* Rs, double* invd, double* gram) {
+    constexpr int PS = wide_panel_stride<NB>();
     for (int p0 = 0; p0 < b; p0 += NB) {
         const int nbk = min(NB, b - p0), pe = p0 + nbk, np = nr - p0;
         for (int t = threadIdx.x; t < np * NB; t += blockDim.x) {
             const int i = t / NB, q = t - i * NB;
-            Ps[t] = (q < nbk && i >= q) ? M[(size_t)(p0 + i) * ld + p0 + q] : 0.0;
+            Ps[i * PS + q] = (q < nbk && i >= q) ? M[(size_t)(p0 + i) * ld + p0 + q] : 0.0;
         }
         for (int t = threadIdx.x; t < NB * ncols; t += blockDim.x) {   // rows past nbk: zero
             const int q = t / ncols, cc = t - q * ncols;
@@ -432,23 +438,23 @@ __device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rh
             // diagonal block (lane = row) and the panel's right-hand-side rows (lane = column)
             const int lane = threadIdx.x;
             for (int q = 0; q < nbk; ++q) {
-                const double d = Ps[q * NB + q];
+                const double d = Ps[q * PS + q];
                 const double inv = rsqrt_t<double>(d);
                 __syncwarp();
                 if (lane == 0) {
                     if (!(d > 0.0) && *bad == 0) *bad = p0 + q + 1;
-                    Ps[q * NB + q] = d * inv;
+                    Ps[q * PS + q] = d * inv;
                     invd[q] = inv;
                 }
-                if (lane > q && lane < nbk) Ps[lane * NB + q] *= inv;
+                if (lane > q && lane < nbk) Ps[lane * PS + q] *= inv;
                 for (int cc = lane; cc < ncols; cc += 32) Rs[q * ncols + cc] *= inv;
                 __syncwarp();
                 if (lane > q && lane < nbk) {
-                    const double liq = Ps[lane * NB + q];
-                    for (int j = q + 1; j <= lane; ++j) Ps[lane * NB + j] -= liq * Ps[j * NB + q];
+                    const double liq = Ps[lane * PS + q];
+                    for (int j = q + 1; j <= lane; ++j) Ps[lane * PS + j] -= liq * Ps[j * PS + q];
                 }
                 for (int q2 = q + 1; q2 < nbk; ++q2) {
-                    const double l2 = Ps[q2 * NB + q];
+                    const double l2 = Ps[q2 * PS + q];
                     for (int cc = lane; cc < ncols; cc += 32) Rs[q2 * ncols + cc] -= l2 * Rs[q * ncols + cc];
                 }
                 __syncwarp();
@@ -459,25 +465,25 @@ __device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rh
         for (int ii = nbk + threadIdx.x; ii < np; ii += blockDim.x) {
             double l[NB];
 #pragma unroll
-            for (int q = 0; q < NB; ++q) l[q] = Ps[ii * NB + q];
+            for (int q = 0; q < NB; ++q) l[q] = Ps[ii * PS + q];
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
                 if (q < nbk) {
                     double v = l[q];
 #pragma unroll
                     for (int k = 0; k < NB; ++k)
-                        if (k < q) v -= l[k] * Ps[q * NB + k];
+                        if (k < q) v -= l[k] * Ps[q * PS + k];
                     l[q] = v * invd[q];
                 }
             }
 #pragma unroll
-            for (int q = 0; q < NB; ++q) Ps[ii * NB + q] = l[q];
+            for (int q = 0; q < NB; ++q) Ps[ii * PS + q] = l[q];
         }
         __syncthreads();
         // panel back to M and Rhs (columns [p0, pe), rows [p0, pe) of Rhs)
         for (int t = threadIdx.x; t < np * nbk; t += blockDim.x) {
             const int i = t / nbk, q = t - i * nbk;
-            if (i >= q) M[(size_t)(p0 + i) * ld + p0 + q] = Ps[i * NB + q];
+            if (i >= q) M[(size_t)(p0 + i) * ld + p0 + q] = Ps[i * PS + q];
         }
         for (int t = threadIdx.x; t < nbk * ncols; t += blockDim.x) {
             const int q = t / ncols, cc = t - q * ncols;
@@ -505,8 +511,8 @@ __device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rh
                 const int j = pe + (second ? cc - (m - p) : cc);
                 if (second && m - 1 - p == p) continue;
                 double li[NB], lj[NB];
-                load_panel<NB>(Ps + (size_t)(i - p0) * NB, li);
-                load_panel<NB>(Ps + (size_t)(j - p0) * NB, lj);
+                load_panel<NB>(Ps + (size_t)(i - p0) * PS, li);
+                load_panel<NB>(Ps + (size_t)(j - p0) * PS, lj);
                 double acc = M[(size_t)i * ld + j];
 #pragma unroll
                 for (int q = 0; q < NB; ++q) acc -= li[q] * lj[q];
@@ -518,7 +524,7 @@ __device__ void wide_cholesky_level(double* M, int ld, int b, int nr, double* Rh
         for (int e = threadIdx.x; e < rr * ncols; e += blockDim.x) {
             const int i = pe + e / ncols, cc = e - (e / ncols) * ncols;
             double li[NB];
-            load_panel<NB>(Ps + (size_t)(i - p0) * NB, li);
+            load_panel<NB>(Ps + (size_t)(i - p0) * PS, li);
             double acc = Rhs[(size_t)i * ldr + cc];
 #pragma unroll
             for (int q = 0; q < NB; ++q) acc -= li[q] * Rs[q * ncols + cc];

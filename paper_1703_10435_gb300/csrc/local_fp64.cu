@@ -201,11 +201,12 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
 }
 
 // Shared memory of the wide variant: the Gram matrix (R x R, rounded to an even count
-// so the panel stays 16-byte aligned), the panel (rows x kNBWide), its right-hand-side
+// so the panel stays 16-byte aligned), the panel (rows x wide_panel_stride), its right-hand-side
 // rows (kNBWide x R) and the inverse pivots (kNBWide).
 __host__ __device__ inline size_t wide_gram_doubles(int R) { return ((size_t)R * R + 1) & ~(size_t)1; }
 inline size_t wide_smem_bytes(int rows, int R) {
-    return (wide_gram_doubles(R) + (size_t)rows * kNBWide + (size_t)kNBWide * R + kNBWide) * sizeof(double);
+    return (wide_gram_doubles(R) + (size_t)rows * wide_panel_stride<kNBWide>() + (size_t)kNBWide * R + kNBWide) *
+           sizeof(double);
 }
 
 template <int RPL, bool WIDE>
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
     double* W = WIDE ? g.win + (size_t)blockIdx.x * g.win_doubles : smem;
     double* gram = WIDE ? smem : smem + (size_t)g.rows * g.ld;   // R x R, upper triangle used
     double* Ps = smem + wide_gram_doubles(R);                      // (wide) panel
-    double* Rs = Ps + (size_t)g.rows * kNBWide;
+    double* Rs = Ps + (size_t)g.rows * wide_panel_stride<kNBWide>();
     double* invd = Rs + (size_t)kNBWide * R;
     // launch indices within the level: one per block, or (wide) strided over the grid
     for (int64_t ki = g.K0 + blockIdx.x; ki < g.K1; ki += gridDim.x) {

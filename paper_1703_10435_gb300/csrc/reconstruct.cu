@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
     double* W = WIDE ? reinterpret_cast<double*>(slot + g.win_offset) : smem;
     double* zs = WIDE ? smem : smem + (size_t)g.rows * g.ld;   // nloc: the solution z (pinned DOF 0 = 0)
     double* Ps = smem + (((size_t)g.nloc + 1) & ~(size_t)1);   // (wide) panel, 16-byte aligned
-    double* Rs = Ps + (size_t)g.rows * kNBR;
+    double* Rs = Ps + (size_t)g.rows * wide_panel_stride<kNBR>();
     double* invd = Rs + kNBR;
     const int nb = g.P == 1 ? 3 : 6, npair = nb * (nb + 1) / 2;
 
@@ -462,7 +462,8 @@ extern "C" mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa,
             // the window behind the stored factors in the slot; shared memory keeps z and the panel
             g.win_offset = g.slot_bytes;
             g.slot_bytes += (((size_t)g.rows * g.ld * sizeof(double)) + 255) & ~(size_t)255;
-            smem = ((((size_t)g.nloc + 1) & ~(size_t)1) + (size_t)g.rows * kNBR + 2 * kNBR) * sizeof(double);
+            smem = ((((size_t)g.nloc + 1) & ~(size_t)1) + (size_t)g.rows * wide_panel_stride<kNBR>() + 2 * kNBR) *
+                   sizeof(double);
         }
         if (smem > 220 * 1024) return fail(MHM_ERR_UNSUPPORTED, "mhm_reconstruct: window exceeds shared memory");
         void (*kern)(const RecArgs) = wide ? k_reconstruct<true> : k_reconstruct<false>;

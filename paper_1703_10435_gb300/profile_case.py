@@ -5,6 +5,12 @@ twice (the second launch is the one to capture, the first warms caches and
 code), on cuda:0, and checks the status words.  Example:
 
     python -m paper_1703_10435_gb300.profile_case --precision mixed --n-k 152
+
+--level r puts every coarse triangle of the workload at refinement level r (its
+kappa field sampled at that level), e.g. the 256-row level windows of r = 7:
+
+    python -m paper_1703_10435_gb300.profile_case --workload c4_channels --level 7 \
+        --precision fp64 --n-k 152
 """
 from __future__ import annotations
 
@@ -16,6 +22,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="c2_hetero_fp64")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--n-k", type=int, default=152, help="coarse triangles K = 0 .. n_k - 1")
+    ap.add_argument("--level", type=int, default=None, help="uniform refinement level r for every K")
     args = ap.parse_args(argv)
 
     import torch
@@ -25,8 +32,13 @@ def main(argv=None):
 
     build.build()
     w = W.WORKLOADS[args.workload]
+    if args.level is not None:
+        import dataclasses
+        w = dataclasses.replace(w, r=args.level, levels=None)
     n = min(args.n_k, w.n_K)
-    kap = torch.as_tensor(W.kappa_for(w), device="cuda")
+    # kappa of K = 0 .. n - 1 only (the blocks sit at the same offsets as in the full field)
+    import numpy as np
+    kap = torch.as_tensor(W.kappa_for(w, np.arange(n)), device="cuda").reshape(-1)
     prec = mhm.MHM_MIXED if args.precision == "mixed" else mhm.MHM_FP64
     p = Pipeline.for_workload(w, 0, prec)
     opts = mhm.SolveOpts(8, 1e-12, 0, n)
