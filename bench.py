@@ -109,7 +109,8 @@ def oracle_sample(w, Ks, kap):
     from oracle.local import solve_local
     from oracle.mesh import build_mesh
     from oracle.run import source_fn
-    mesh = build_mesh(w.nx, w.ny, w.m, w.l)
+    lf = w.l_per_face(build_mesh(w.nx, w.ny, 1, 0).tri_edges) if w.face_degree else None
+    mesh = build_mesh(w.nx, w.ny, w.m, w.l if lf is None else lf)
     f = float(w.source_value) if w.source == "const" else source_fn("sinsin", w.source_value, w.source_freq)
     rk = w.r_per_K
     for i, K in enumerate(Ks):
@@ -163,8 +164,7 @@ def run_reference(args, w, rank, world):
         "value": value, "unit": "coarse elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_K": w.n_K, "r": w.r, "degree": w.degree, "m": w.m, "l": w.l,
-                   "sample_K_per_step": n_sample, "field": w.field},
+        "config": dict(workload_config(w), sample_K_per_step=n_sample, field=w.field),
         "cpu_baseline": {"value": value, "unit": "coarse elements/s", "cores": cores, "kind": "oracle",
                          "sample": "%d coarse triangles of the workload per step (K = 0..%d)" % (n_sample, n_sample - 1)},
         "e2e": {"value": value, "unit": "coarse elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -218,6 +218,22 @@ def level_counts(w):
     if rk is None:
         return {w.r: w.n_K}
     return {int(r): int((rk == r).sum()) for r in np.unique(rk)}
+
+
+def workload_config(w):
+    """The workload's shape for the config object: uniform r, or the elements per level and
+    the face degrees of a workload with a level per K."""
+    cfg = {"workload": w.name, "n_K": w.n_K, "degree": w.degree, "m": w.m}
+    if w.r_per_K is None:
+        cfg.update({"r": w.r, "n_local": w.n_local})
+    else:
+        cfg["elements_per_level"] = {str(r): c for r, c in level_counts(w).items()}
+    if w.face_degree is None:
+        cfg["l"] = w.l
+    else:
+        cfg["l_per_face"] = "1 + [max adjacent r >= 5] + [max adjacent r >= 7] (1..%d)" % w.l
+    cfg["rhs"] = w.n_I + 1
+    return cfg
 
 
 def mixed_level(w, r):
@@ -446,11 +462,11 @@ def run_ours(args, w, rank, world, local_rank):
         "value": value, "unit": "coarse elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mx / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_K": w.n_K, "r": w.r, "degree": w.degree, "n_local": w.n_local,
-                   "m": w.m, "l": w.l, "rhs": w.n_I + 1, "field": w.field, "seed": w.seed,
+        "config": dict(workload_config(w), **{
+                   "field": w.field, "seed": w.seed,
                    "precision": "mixed (FP32 factor and solves, FP64 residuals)",
                    "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "K-range shard per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "K-range shard per GPU" if world > 1 else "single GPU"}),
         "fp64_path": {"value": v64, "ms_per_step": t_64 / args.steps, "dtype": "f64", "roofline": roof_64},
         "mixed_over_fp64": value / v64,
         "error": err,

@@ -30,6 +30,11 @@
  *  - Lambda_H^{m,l}: m subfaces per face counted from the lower-id vertex,
  *    Legendre P_p (p = 0..l) of the subface coordinate in [-1,1]; global index
  *    offset(face) + q(l+1) + p; local index inside K runs over a = 0,1,2.
+ *    With a degree per face (mhm_mesh_desc.l_per_face) face e carries
+ *    m(l_e+1) multipliers, numbered the same way with its own l_e; inside K,
+ *    local face a keeps the slots a d .. a d + m(l_a+1) - 1 of a fixed stride
+ *    d = m(l_max+1) (N_I = 3d per K).  The slots past m(l_a+1) are unused:
+ *    their rows and columns of A_K, and their E_K and B_K entries, are zero.
  *  - Submesh: N = 2^r segments per face, local degree P (1 or 2); lattice
  *    point (i,j), i+j <= PN, is local DOF sum_{j'<j}(PN+1-j') + i.  kappa is
  *    given per fine triangle, per K in ascending order, and inside K row by
@@ -89,6 +94,10 @@ typedef struct {
                              * of each K (each local problem is on its own submesh; the
                              * multipliers live on the coarse faces); NULL: every K at r.
                              * Read during mhm_create_mesh only. */
+    const int8_t* l_per_face;  /* optional, host, n_faces = nx(ny+1) + ny(nx+1) + nx ny
+                                * entries >= 0 in the global face numbering: the multiplier
+                                * degree of each face (l is then ignored); NULL: every face
+                                * at l.  m(l_e+1) <= 16.  Read during mhm_create_mesh only. */
 } mhm_mesh_desc;
 
 typedef struct {
@@ -140,13 +149,14 @@ void mhm_destroy_mesh(mhm_mesh* mesh);
 /* Queries for sizes and for the integer structure (bit-exact parity). */
 #define MHM_Q_SIZES 0          /* int64[8]: n_K, n_faces, n_vertices, n_lambda, n_fine per K,
                                   n_local per K (with per-K levels: of the finest K),
-                                  N_I per K, skeleton nnz */
+                                  N_I per K (the slot stride, 3 m (l_max+1)), skeleton nnz */
 #define MHM_Q_TRI_VERTS 1      /* int32[n_K*3] vertex ids, CCW */
 #define MHM_Q_TRI_FACES 2      /* int32[n_K*3] face id of local face a */
 #define MHM_Q_TRI_SIGNS 3      /* int8[n_K*3]  s = n . n_F^K */
 #define MHM_Q_FACE_VERTS 4     /* int32[n_faces*2] vertex ids, lower first */
 #define MHM_Q_LAMBDA_OFFSET 5  /* int64[n_faces+1] first global multiplier of each face */
-#define MHM_Q_K_LAMBDA 6       /* int32[n_K*N_I] global multiplier id of each local one */
+#define MHM_Q_K_LAMBDA 6       /* int32[n_K*N_I] global multiplier id of each local slot
+                                  (-1: unused slot of a face below the largest degree) */
 #define MHM_Q_CSR_ROWPTR 7     /* int32[n_lambda+1] skeleton CSR row pointers */
 #define MHM_Q_CSR_COLS 8       /* int32[nnz] skeleton CSR column ids */
 #define MHM_Q_VERTEX_XY 9      /* double[n_vertices*2] */
@@ -154,6 +164,7 @@ void mhm_destroy_mesh(mhm_mesh* mesh);
 #define MHM_Q_R_OF_K 11        /* int8[n_K] refinement level of each K */
 #define MHM_Q_KAPPA_OFFSET 12  /* int64[n_K+1] first kappa value of each K (4^r_K values per K) */
 #define MHM_Q_NODAL_OFFSET 13  /* int64[n_K+1] first value of each K in mhm_reconstruct's u_nodal */
+#define MHM_Q_FACE_DEGREE 14   /* int8[n_faces] multiplier degree l_e of each face */
 /* Copies the queried table into host_out (bytes must be >= its size).
  * Errors: INVALID_ARG (unknown query, short buffer). */
 mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, size_t bytes);

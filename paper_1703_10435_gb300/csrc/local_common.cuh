@@ -150,6 +150,21 @@ __device__ inline void choose_pin(int P, int N, const double* kap, int* pin_x, i
     *pin_y = by;
 }
 
+// Degree + 1 of local face a of K (Lambda_H^{m,l} with a degree per face, Sec. 2).
+__device__ __forceinline__ int face_la1(const DeviceMesh& dm, int64_t K, int a) {
+    return dm.lface ? dm.lface[3 * K + a] + 1 : dm.lmax1;
+}
+
+// Row of the face-load table (rows q lmax1 + p, built for the largest degree) of local
+// slot jf = q la1 + p of a face of degree la1 - 1; -1 for the unused slots jf >= m la1
+// of a face below the largest degree (no load: zero rows and columns in A_K).
+__device__ __forceinline__ int face_row(int jf, int la1, int fm, int lmax1) {
+    if (la1 == lmax1) return jf;
+    if (jf >= fm * la1) return -1;
+    const int q = jf / la1;
+    return q * lmax1 + (jf - q * la1);
+}
+
 // int_T phi_a / |T|: P1 1/3 at every vertex; P2 0 at vertices, 1/3 at midpoints.
 __device__ __forceinline__ double element_mass_frac(int P, int a) {
     return (P == 1 || a >= 3) ? (1.0 / 3.0) : 0.0;

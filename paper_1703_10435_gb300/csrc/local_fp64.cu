@@ -63,7 +63,7 @@ struct KCtx {
     double area_fine;    // |T| of every fine triangle
     double area;         // |K|
     double flen[3];      // face lengths
-    int sgn[3], rev[3];
+    int sgn[3], rev[3], la1[3];  // la1: degree + 1 of each face
     double cproj[kMaxNI + 1];  // projection coefficient of each right-hand side
     double FK;
     int bad;             // first failing pivot (+1), 0 if none
@@ -141,8 +141,10 @@ __device__ void add_face_loads(const Fp64Args& g, const KCtx& c, const LevelGeom
         lg.point(lev, p, &x, &y);
         const int kl = face_position(g.PN, x, y, a);
         if (kl < 0) continue;
+        const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+        if (row < 0) continue;   // unused slot: no load
         const int k = c.rev[a] ? g.PN - kl : kl;
-        const double v = -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + k];
+        const double v = -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + k];
         W[(row0 + p) * g.ld + g.rhs0 + a * g.dpf + jf] += v;
     }
 }
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
             c.flen[a] = sqrt((Q0[0] - P0[0]) * (Q0[0] - P0[0]) + (Q0[1] - P0[1]) * (Q0[1] - P0[1]));
             c.sgn[a] = g.dm.sign[3 * K + a];
             c.rev[a] = g.dm.rev[3 * K + a];
+            c.la1[a] = face_la1(g.dm, K, a);
         }
         double Xu[3][2], Xd[3][2];
         fine_vertices(c, g.N, true, 0, 0, Xu);
@@ -276,7 +279,8 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
         if (col == g.NI) c.cproj[col] = FK / c.area;
         else {
             const int a = col / g.dpf, jf = col - a * g.dpf;
-            c.cproj[col] = -c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf] / c.area;
+            const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+            c.cproj[col] = row < 0 ? 0.0 : -c.sgn[a] * c.flen[a] * g.dm.btab_sum[row] / c.area;
         }
     }
     for (int t = threadIdx.x; t < R * R; t += blockDim.x) gram[t] = 0.0;
@@ -342,7 +346,8 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
     for (int j = threadIdx.x; j < NI; j += blockDim.x) {
         g.EK[K * NI + j] = gram[j * R + NI];
         const int a = j / g.dpf, jf = j - a * g.dpf;
-        g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
+        const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+        g.BK[K * NI + j] = row < 0 ? 0.0 : c.sgn[a] * c.flen[a] * g.dm.btab_sum[row];
     }
     if (threadIdx.x == 0) {
         g.FK[K] = FK;

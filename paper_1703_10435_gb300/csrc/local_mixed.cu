@@ -69,7 +69,7 @@ struct MCtx {
     double Sup[36], Sdn[36];
     double area_fine, area, FK;
     double flen[3];
-    int sgn[3], rev[3];
+    int sgn[3], rev[3], la1[3];   // la1: degree + 1 of each face
     double cproj[kMaxNI + 1];
     int bad;
     int col_done[kMaxNI + 1];
@@ -896,6 +896,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 c.flen[a] = sqrt((Q0[0] - P0[0]) * (Q0[0] - P0[0]) + (Q0[1] - P0[1]) * (Q0[1] - P0[1]));
                 c.sgn[a] = g.dm.sign[3 * K + a];
                 c.rev[a] = g.dm.rev[3 * K + a];
+                c.la1[a] = face_la1(g.dm, K, a);
             }
             double Xu[3][2], Xd[3][2];
             fine_xy(c, g.N, true, 0, 0, Xu);
@@ -937,7 +938,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             if (col == g.NI) c.cproj[col] = c.FK / c.area;
             else {
                 const int a = col / g.dpf, jf = col - a * g.dpf;
-                c.cproj[col] = -c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf] / c.area;
+                const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                c.cproj[col] = row < 0 ? 0.0 : -c.sgn[a] * c.flen[a] * g.dm.btab_sum[row] / c.area;
             }
         }
         __syncthreads();
@@ -1019,9 +1021,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     else {
                         const int a = col / g.dpf, jf = col - a * g.dpf;
                         const int kl = face_position(g.PN, X, Y, a);
-                        if (kl >= 0) {
+                        const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                        if (kl >= 0 && row >= 0) {
                             const int kk2 = c.rev[a] ? g.PN - kl : kl;
-                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk2];
+                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + kk2];
                         }
                     }
                     Rh[(size_t)u * R + col] = su * v;
@@ -1143,7 +1146,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                         if (u < 0) continue;
                         const int kk2 = c.rev[a] ? g.PN - kl : kl;
                         const double zs = sc[u] * Zh[(size_t)u * R + lane] * (-c.sgn[a] * c.flen[a]);
-                        for (int jf = 0; jf < g.dpf; ++jf) sb[jf] = fma(g.dm.btab[jf * (g.PN + 1) + kk2], zs, sb[jf]);
+                        for (int jf = 0; jf < g.dpf; ++jf) {
+                            const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                            if (row >= 0) sb[jf] = fma(g.dm.btab[row * (g.PN + 1) + kk2], zs, sb[jf]);
+                        }
                     }
                     for (int jf = 0; jf < g.dpf; ++jf) {
                         const int j = a * g.dpf + jf;
@@ -1161,7 +1167,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             for (int j = threadIdx.x; j < NI; j += blockDim.x) {
                 g.EK[K * NI + j] = xbuf[j * R + NI];
                 const int a = j / g.dpf, jf = j - a * g.dpf;
-                g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
+                const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                g.BK[K * NI + j] = row < 0 ? 0.0 : c.sgn[a] * c.flen[a] * g.dm.btab_sum[row];
             }
             if (threadIdx.x == 0) {
                 g.FK[K] = c.FK;
@@ -1198,9 +1205,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     else {
                         const int a = col / g.dpf, jf = col - a * g.dpf;
                         const int kl = face_position(g.PN, X, Y, a);
-                        if (kl >= 0) {
+                        const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                        if (kl >= 0 && row >= 0) {
                             const int kk = c.rev[a] ? g.PN - kl : kl;
-                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk];
+                            v += -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + kk];
                         }
                     }
                     G[(size_t)col * g.nunk + u] = v;
@@ -1463,9 +1471,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             for (int t = threadIdx.x; t < g.NI * R; t += blockDim.x) {
                 const int j = t / R, col = t - j * R;
                 const int a = j / g.dpf, jf = j - a * g.dpf;
+                const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
                 const double* zc = Z + (size_t)col * g.nunk;
                 double s = 0.0;
-                for (int kl = 0; kl <= g.PN; ++kl) {
+                for (int kl = 0; kl <= g.PN && row >= 0; ++kl) {
                     int X, Y;
                     if (a == 2) { X = kl; Y = 0; }
                     else if (a == 0) { X = g.PN - kl; Y = kl; }
@@ -1473,7 +1482,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     const int u = unk(g.PN, X, Y);
                     if (u < 0) continue;
                     const int kk = c.rev[a] ? g.PN - kl : kl;
-                    s += (-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk]) * zc[u];
+                    s += (-c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + kk]) * zc[u];
                 }
                 xbuf[j * R + col] += s - c.cproj[j] * c.mz[col];
             }
@@ -1486,7 +1495,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             for (int j = threadIdx.x; j < NI; j += blockDim.x) {
                 g.EK[K * NI + j] = xbuf[j * R + NI];
                 const int a = j / g.dpf, jf = j - a * g.dpf;
-                g.BK[K * NI + j] = c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf];
+                const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                g.BK[K * NI + j] = row < 0 ? 0.0 : c.sgn[a] * c.flen[a] * g.dm.btab_sum[row];
             }
             if (threadIdx.x == 0) {
                 g.FK[K] = c.FK;

@@ -80,7 +80,8 @@ mhm_status upload(const std::vector<T>& h, T** d) {
 void free_mesh_device(mhm_mesh* m) {
     void* ptrs[] = {m->d_geom, m->d_sign, m->d_rev, m->d_btab, m->d_btab_sum, m->d_gauss_x,
                     m->d_gauss_w, m->d_face_v, m->d_face_K, m->d_tri_f, m->d_vxy, m->d_lam_off,
-                    m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs, m->d_aug_rowptr, m->d_aug_cols, m->d_aug_src, m->d_k_lambda};
+                    m->d_csr_rowptr, m->d_nbr_ptr, m->d_nbrs, m->d_aug_rowptr, m->d_aug_cols, m->d_aug_src, m->d_k_lambda,
+                    m->d_lam_face, m->d_lface};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->d_kap_off) cudaFree(m->d_kap_off);
@@ -150,7 +151,17 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
         }
     }
     if (d.degree != 1 && d.degree != 2) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: degree must be 1 or 2");
-    if (d.m < 1 || d.l < 0 || d.m * (d.l + 1) > mhm::kMaxFaceDofs)
+    const int64_t n_faces = (int64_t)d.nx * (d.ny + 1) + (int64_t)d.ny * (d.nx + 1) + (int64_t)d.nx * d.ny;
+    int l_max = d.l;
+    if (d.l_per_face) {
+        l_max = 0;
+        for (int64_t e = 0; e < n_faces; ++e) {
+            if (d.l_per_face[e] < 0)
+                return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: every l_per_face must be >= 0");
+            l_max = std::max(l_max, (int)d.l_per_face[e]);
+        }
+    }
+    if (d.m < 1 || l_max < 0 || d.m * (l_max + 1) > mhm::kMaxFaceDofs)
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: m >= 1, l >= 0 and m(l+1) <= 16 required");
     // device < 0 builds the host tables only (queries work, compute calls return UNSUPPORTED).
     if (device >= 0) {
@@ -163,11 +174,13 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     mhm_mesh* m = new mhm_mesh();
     m->device = device;
     m->desc = d;
-    m->desc.r_per_K = nullptr;   // the caller's array is read here only
+    m->desc.r_per_K = nullptr;   // the caller's arrays are read here only
+    m->desc.l_per_face = nullptr;
+    m->desc.l = l_max;           // from here on: the largest face degree
     const int nx = d.nx, ny = d.ny;
     m->N = 1 << r_top;
     m->PN = d.degree * m->N;
-    m->dpf = d.m * (d.l + 1);
+    m->dpf = d.m * (l_max + 1);
     m->nv = (int64_t)(nx + 1) * (ny + 1);
     m->nK = 2LL * nx * ny;
     m->nfine = (int64_t)m->N * m->N;
@@ -250,15 +263,35 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
             m->tri_rev[3 * K + a] = m->tri_v[3 * K + (a + 1) % 3] > m->tri_v[3 * K + (a + 2) % 3] ? 1 : 0;
         }
 
-    // multiplier numbering
+    // multiplier numbering: face e carries m(l_e+1) multipliers; local face a of K keeps the
+    // slots [a dpf, a dpf + m(l_a+1)) of the stride dpf = m(l_max+1), the rest unused (-1)
+    if (m->ne != n_faces) {
+        delete m;
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: internal face count mismatch");
+    }
+    m->face_l.assign(m->ne, (int8_t)l_max);
+    if (d.l_per_face) m->face_l.assign(d.l_per_face, d.l_per_face + m->ne);
+    auto dofs = [&](int64_t e) { return (int64_t)d.m * (m->face_l[e] + 1); };
     m->lam_off.resize(m->ne + 1);
-    for (int64_t e = 0; e <= m->ne; ++e) m->lam_off[e] = e * m->dpf;
+    m->lam_off[0] = 0;
+    for (int64_t e = 0; e < m->ne; ++e) m->lam_off[e + 1] = m->lam_off[e] + dofs(e);
     m->nlam = m->lam_off[m->ne];
+    m->lam_face.resize(m->nlam);
+    for (int64_t e = 0; e < m->ne; ++e)
+        for (int64_t j = m->lam_off[e]; j < m->lam_off[e + 1]; ++j) m->lam_face[j] = (int32_t)e;
+    bool uniform_l = true;
+    for (int64_t e = 0; e < m->ne; ++e) uniform_l = uniform_l && m->face_l[e] == l_max;
+    if (!uniform_l) {
+        m->tri_l.resize(m->nK * 3);
+        for (int64_t K = 0; K < 3 * m->nK; ++K) m->tri_l[K] = m->face_l[m->tri_f[K]];
+    }
     m->k_lambda.resize(m->nK * m->NI);
     for (int64_t K = 0; K < m->nK; ++K)
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
+            const int64_t e = m->tri_f[3 * K + a];
             for (int u = 0; u < m->dpf; ++u)
-                m->k_lambda[K * m->NI + a * m->dpf + u] = (int32_t)(m->lam_off[m->tri_f[3 * K + a]] + u);
+                m->k_lambda[K * m->NI + a * m->dpf + u] = u < dofs(e) ? (int32_t)(m->lam_off[e] + u) : -1;
+        }
 
     // skeleton pattern: face e's rows couple with every face of its (one or two) K
     m->nbr_ptr.assign(m->ne + 1, 0);
@@ -285,19 +318,21 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
         int32_t off = 0;
         for (auto& kv : blocks) {
             kv.second.col_off = off;
-            off += m->dpf;
+            off += (int32_t)dofs(kv.second.f);
             m->nbrs.push_back(kv.second);
         }
         m->nbr_ptr[e + 1] = (int32_t)m->nbrs.size();
     }
     m->csr_rowptr.assign(m->nlam + 1, 0);
     for (int64_t e = 0; e < m->ne; ++e) {
-        int32_t len = (m->nbr_ptr[e + 1] - m->nbr_ptr[e]) * m->dpf;
-        for (int u = 0; u < m->dpf; ++u) {
+        int32_t len = 0;
+        for (int b = m->nbr_ptr[e]; b < m->nbr_ptr[e + 1]; ++b) len += (int32_t)dofs(m->nbrs[b].f);
+        for (int u = 0; u < dofs(e); ++u) {
             int64_t j = m->lam_off[e] + u;
             m->csr_rowptr[j + 1] = m->csr_rowptr[j] + len;
             for (int b = m->nbr_ptr[e]; b < m->nbr_ptr[e + 1]; ++b)
-                for (int v = 0; v < m->dpf; ++v) m->csr_cols.push_back((int32_t)(m->lam_off[m->nbrs[b].f] + v));
+                for (int v = 0; v < dofs(m->nbrs[b].f); ++v)
+                    m->csr_cols.push_back((int32_t)(m->lam_off[m->nbrs[b].f] + v));
         }
     }
     m->nnz = (int64_t)m->csr_cols.size();
@@ -309,7 +344,7 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
         const int64_t L = m->nlam;
         m->aug_rowptr.assign(L + m->nK + 1, 0);
         for (int64_t j = 0; j < L; ++j) {
-            const int64_t e = j / m->dpf, u = j - e * m->dpf;
+            const int64_t e = m->lam_face[j], u = j - m->lam_off[e];
             for (int32_t t = m->csr_rowptr[j]; t < m->csr_rowptr[j + 1]; ++t) {
                 m->aug_cols.push_back(m->csr_cols[t]);
                 m->aug_src.push_back(t);
@@ -326,7 +361,8 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
         }
         for (int64_t K = 0; K < m->nK; ++K) {
             std::vector<std::pair<int32_t, int64_t>> row;
-            for (int64_t i = 0; i < m->NI; ++i) row.emplace_back(m->k_lambda[K * m->NI + i], -(K * m->NI + i) - 1);
+            for (int64_t i = 0; i < m->NI; ++i)
+                if (m->k_lambda[K * m->NI + i] >= 0) row.emplace_back(m->k_lambda[K * m->NI + i], -(K * m->NI + i) - 1);
             std::sort(row.begin(), row.end());
             for (auto& pr : row) {
                 m->aug_cols.push_back(pr.first);
@@ -344,7 +380,8 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
         gauss_legendre01(n, &m->gauss_x[(n - 1) * mhm::kMaxGauss], &m->gauss_w[(n - 1) * mhm::kMaxGauss]);
 
     // face-load table of the mesh's (finest) level, and the levels
-    face_load_table(d.degree, m->N, d.m, d.l, m->gauss_x, m->gauss_w, m->btab, m->btab_sum);
+    // (rows q (l_max+1) + p: a face of lower degree uses the rows p <= l_e of each subface)
+    face_load_table(d.degree, m->N, d.m, l_max, m->gauss_x, m->gauss_w, m->btab, m->btab_sum);
     if (!d.r_per_K) {
         mhm::Level lv;
         lv.r = d.r;
@@ -376,7 +413,7 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
             lv.nK = (int64_t)lv.K.size();
             if (lv.nK == 0) continue;
             std::vector<double> bsum;
-            face_load_table(d.degree, lv.N, d.m, d.l, m->gauss_x, m->gauss_w, lv.btab, bsum);
+            face_load_table(d.degree, lv.N, d.m, l_max, m->gauss_x, m->gauss_w, lv.btab, bsum);
             m->levels.push_back(std::move(lv));
         }
     }
@@ -413,6 +450,8 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     if (!st) st = upload(m->aug_cols, &m->d_aug_cols);
     if (!st) st = upload(m->aug_src, &m->d_aug_src);
     if (!st) st = upload(m->k_lambda, &m->d_k_lambda);
+    if (!st) st = upload(m->lam_face, &m->d_lam_face);
+    if (!st) st = upload(m->tri_l, &m->d_lface);
     if (m->per_k_levels) {
         if (!st) st = upload(m->kap_off, &m->d_kap_off);
         if (!st) st = upload(m->nod_off, &m->d_nod_off);
@@ -472,6 +511,7 @@ extern "C" mhm_status mhm_mesh_query(const mhm_mesh* m, int32_t what, void* out,
         case MHM_Q_CSR_COLS: return copy_out(m->csr_cols, out, bytes);
         case MHM_Q_VERTEX_XY: return copy_out(m->vxy, out, bytes);
         case MHM_Q_FACE_NORMALS: return copy_out(m->normals, out, bytes);
+        case MHM_Q_FACE_DEGREE: return copy_out(m->face_l, out, bytes);
         case MHM_Q_R_OF_K: {
             if (m->per_k_levels) return copy_out(m->r_of_K, out, bytes);
             return copy_out(std::vector<int8_t>(m->nK, (int8_t)m->desc.r), out, bytes);

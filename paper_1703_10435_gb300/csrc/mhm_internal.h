@@ -52,6 +52,8 @@ struct DeviceMesh {
     const double* gauss_w;
     const int32_t* klist;    // coarse element of each launch index (NULL: the index itself)
     const int64_t* kap_off;  // first kappa value of each K (NULL: K * 4^r)
+    const int8_t* lface;     // n_K * 3: degree of local face a (NULL: every face at the largest degree)
+    int fm, lmax1;           // subfaces per face; largest degree + 1 (the table's row stride per subface)
 };
 
 // The coarse elements of one refinement level: the local-solve and reconstruction
@@ -81,7 +83,7 @@ struct mhm_mesh {
     mutable size_t tev_used = 0;
     mhm_mesh_desc desc{};
     int64_t nK = 0, ne = 0, nv = 0, nlam = 0, nfine = 0, nloc = 0, NI = 0, nnz = 0;
-    int32_t N = 1, PN = 1, dpf = 1;  // 2^r, P*N, dofs per face m(l+1)
+    int32_t N = 1, PN = 1, dpf = 1;  // 2^r, P*N, slots per face m(l_max+1) (the per-K stride)
 
     // host tables
     std::vector<double> vxy;          // nv*2
@@ -93,7 +95,10 @@ struct mhm_mesh {
     std::vector<int32_t> face_K;      // ne*2 (second = -1 on the boundary)
     std::vector<double> normals;      // ne*2
     std::vector<int64_t> lam_off;     // ne+1
-    std::vector<int32_t> k_lambda;    // nK*NI
+    std::vector<int32_t> lam_face;    // nlam: face of each global multiplier
+    std::vector<int8_t> face_l;       // ne: multiplier degree of each face
+    std::vector<int8_t> tri_l;        // nK*3: degree of local face a (non-uniform degrees only)
+    std::vector<int32_t> k_lambda;    // nK*NI (-1: unused slot)
     std::vector<int32_t> csr_rowptr;  // nlam+1
     std::vector<int32_t> csr_cols;    // nnz
     std::vector<int32_t> nbr_ptr;     // ne+1
@@ -125,6 +130,8 @@ struct mhm_mesh {
     int32_t* d_aug_cols = nullptr;
     int64_t* d_aug_src = nullptr;
     int32_t* d_k_lambda = nullptr;
+    int32_t* d_lam_face = nullptr;
+    int8_t* d_lface = nullptr;            // tri_l on the device (NULL: uniform degree)
 
     // refinement level per K (meshes built with r_per_K; uniform meshes leave these empty)
     bool per_k_levels = false;
@@ -140,11 +147,12 @@ struct mhm_mesh {
     mutable cudaEvent_t fork_ev = nullptr;
 
     mhm::DeviceMesh dev() const {
-        return mhm::DeviceMesh{d_geom, d_sign, d_rev, d_btab, d_btab_sum, d_gauss_x, d_gauss_w, nullptr, nullptr};
+        return mhm::DeviceMesh{d_geom,  d_sign,  d_rev,   d_btab, d_btab_sum,  d_gauss_x,
+                               d_gauss_w, nullptr, nullptr, d_lface, desc.m, desc.l + 1};
     }
     mhm::DeviceMesh dev(const mhm::Level& lv) const {
-        return mhm::DeviceMesh{d_geom, d_sign, d_rev, lv.d_btab ? lv.d_btab : d_btab, d_btab_sum, d_gauss_x,
-                               d_gauss_w, lv.d_K, d_kap_off};
+        return mhm::DeviceMesh{d_geom,    d_sign, d_rev,     lv.d_btab ? lv.d_btab : d_btab, d_btab_sum, d_gauss_x,
+                               d_gauss_w, lv.d_K, d_kap_off, d_lface,                        desc.m,     desc.l + 1};
     }
 };
 

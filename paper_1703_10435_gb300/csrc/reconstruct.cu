@@ -47,7 +47,7 @@ struct RCtx {
     double Sup[36], Sdn[36];
     double area, area_fine, FK, cl;
     double flen[3];
-    int sgn[3], rev[3];
+    int sgn[3], rev[3], la1[3];  // la1: degree + 1 of each face
     int bad;
     int pin_x, pin_y;            // the pinned lattice point (choose_pin)
     double red[kThreadsRWide / 32];
@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
                 c.flen[a] = sqrt((Q0[0] - P0[0]) * (Q0[0] - P0[0]) + (Q0[1] - P0[1]) * (Q0[1] - P0[1]));
                 c.sgn[a] = g.dm.sign[3 * K + a];
                 c.rev[a] = g.dm.rev[3 * K + a];
+                c.la1[a] = face_la1(g.dm, K, a);
             }
             double Xu[3][2], Xd[3][2];
             fine_xy(c, g.N, true, 0, 0, Xu);
@@ -169,7 +170,9 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
             double cl = 0.0;
             for (int i = 0; i < g.NI; ++i) {
                 const int a = i / g.dpf, jf = i - a * g.dpf;
-                cl += g.lambda[g.k_lambda[K * g.NI + i]] * (-c.sgn[a] * c.flen[a] * g.dm.btab_sum[jf] / c.area);
+                const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                if (row < 0) continue;   // unused slot
+                cl += g.lambda[g.k_lambda[K * g.NI + i]] * (-c.sgn[a] * c.flen[a] * g.dm.btab_sum[row] / c.area);
             }
             c.cl = cl;
             c.bad = 0;
@@ -213,9 +216,12 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
                         const int kl = face_position(g.PN, x, y, a);
                         if (kl < 0) continue;
                         const int kk = c.rev[a] ? g.PN - kl : kl;
-                        for (int jf = 0; jf < g.dpf; ++jf)
+                        for (int jf = 0; jf < g.dpf; ++jf) {
+                            const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+                            if (row < 0) continue;   // unused slot
                             v += g.lambda[g.k_lambda[K * g.NI + a * g.dpf + jf]] *
-                                 (-c.sgn[a] * c.flen[a] * g.dm.btab[jf * (g.PN + 1) + kk]);
+                                 (-c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + kk]);
+                        }
                     }
                     W[(row0 + p) * g.ld + rhs] += v;
                 }

@@ -19,6 +19,8 @@ struct SkelArgs {
     const double* AK;
     const double* EK;
     const int32_t* rowptr;
+    const int64_t* lam_off;   // first multiplier of each face
+    const int32_t* lam_face;  // face of each multiplier
     const int32_t* nbr_ptr;
     const FaceNbr* nbrs;
     const int32_t* face_K;
@@ -35,19 +37,23 @@ struct SkelArgs {
     double* E;
 };
 
-// One warp per skeleton row j = (face e, local dof u); lanes over the row's entries.
+// One warp per skeleton row j = (face e, local dof u); lanes over the row's entries, which
+// run over the neighbour faces f of e (m(l_f+1) columns each, from FaceNbr::col_off).  Local
+// slot u of a face sits at a dpf + u in the per-K blocks (stride dpf = m(l_max+1)).
 __global__ void k_skeleton_A(const SkelArgs g) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= g.nlam) return;
-    const int e = (int)(j / g.dpf), u = (int)(j - (int64_t)e * g.dpf);
+    const int e = g.lam_face[j], u = (int)(j - g.lam_off[e]);
     const int nb0 = g.nbr_ptr[e], nb1 = g.nbr_ptr[e + 1];
-    const int len = (nb1 - nb0) * g.dpf;
+    const int len = g.rowptr[j + 1] - g.rowptr[j];
     const int64_t out = g.rowptr[j];
     const int64_t nn = (int64_t)g.NI * g.NI;
     for (int c = lane; c < len; c += 32) {
-        const int blk = nb0 + c / g.dpf, v = c - (c / g.dpf) * g.dpf;
+        int blk = nb0;
+        while (blk + 1 < nb1 && g.nbrs[blk + 1].col_off <= c) ++blk;   // at most 5 blocks
         const FaceNbr nb = g.nbrs[blk];
+        const int v = c - nb.col_off;
         double val = g.AK[nb.K0 * nn + (int64_t)(nb.a0 * g.dpf + u) * g.NI + nb.b0 * g.dpf + v];
         if (nb.K1 >= 0) val += g.AK[nb.K1 * nn + (int64_t)(nb.a1 * g.dpf + u) * g.NI + nb.b1 * g.dpf + v];
         g.A[out + c] = val;
@@ -69,7 +75,7 @@ __device__ __forceinline__ double legendre_dev(int p, double xi) {
 __global__ void k_skeleton_E(const SkelArgs g) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.nlam) return;
-    const int e = (int)(j / g.dpf), u = (int)(j - (int64_t)e * g.dpf);
+    const int e = g.lam_face[j], u = (int)(j - g.lam_off[e]);
     double val = 0.0;
     for (int side = 0; side < 2; ++side) {
         const int K = g.face_K[2 * e + side];
@@ -79,8 +85,10 @@ __global__ void k_skeleton_E(const SkelArgs g) {
         val += g.EK[(int64_t)K * g.NI + a * g.dpf + u];
     }
     if (g.has_g && g.face_K[2 * e + 1] < 0) {
-        // (g, psi_{q,p})_F on subface q, Gauss-Legendre exact for degree l + 2
-        const int q = u / (g.L + 1), p = u - q * (g.L + 1);
+        // (g, psi_{q,p})_F on subface q, Gauss-Legendre exact for degree l + 2 (l_e + 1 =
+        // the face's multipliers / m)
+        const int le1 = (int)(g.lam_off[e + 1] - g.lam_off[e]) / g.M;
+        const int q = u / le1, p = u - q * le1;
         const int n = min(kMaxGauss, g.L / 2 + 3);
         const double* gx = g.gauss_x + (n - 1) * kMaxGauss;
         const double* gw = g.gauss_w + (n - 1) * kMaxGauss;
@@ -107,6 +115,8 @@ mhm_status launch_skeleton(const mhm_mesh* mesh, const double* AK, const double*
     g.AK = AK;
     g.EK = EK;
     g.rowptr = mesh->d_csr_rowptr;
+    g.lam_off = mesh->d_lam_off;
+    g.lam_face = mesh->d_lam_face;
     g.nbr_ptr = mesh->d_nbr_ptr;
     g.nbrs = mesh->d_nbrs;
     g.face_K = mesh->d_face_K;

@@ -30,7 +30,8 @@ MHM_SRC_CONST = 0
 MHM_SRC_SINSIN = 1
 
 Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q_K_LAMBDA, \
-    Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS, Q_R_OF_K, Q_KAPPA_OFFSET, Q_NODAL_OFFSET = range(14)
+    Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS, Q_R_OF_K, Q_KAPPA_OFFSET, Q_NODAL_OFFSET, \
+    Q_FACE_DEGREE = range(15)
 
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
@@ -47,7 +48,7 @@ MHM_EXACT_POLY = 2
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("r", ctypes.c_int32),
                 ("degree", ctypes.c_int32), ("m", ctypes.c_int32), ("l", ctypes.c_int32),
-                ("r_per_K", ctypes.c_void_p)]
+                ("r_per_K", ctypes.c_void_p), ("l_per_face", ctypes.c_void_p)]
 
 
 class Source(ctypes.Structure):
@@ -127,13 +128,17 @@ def _stream(stream):
 class Mesh:
     """Owning handle of an mhm_mesh (splitProblem)."""
 
-    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, r_per_K=None):
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, r_per_K=None, l_per_face=None):
         """r_per_K: optional refinement level of every K (sequence of n_K ints); r is
-        then ignored."""
-        rk = None
+        then ignored.  l_per_face: optional multiplier degree of every face (global face
+        numbering); l is then ignored."""
+        rk = lf = None
         if r_per_K is not None:
             rk = np.ascontiguousarray(np.asarray(r_per_K, dtype=np.int8))
-        self.desc = MeshDesc(nx, ny, r, degree, m, l, None if rk is None else rk.ctypes.data)
+        if l_per_face is not None:
+            lf = np.ascontiguousarray(np.asarray(l_per_face, dtype=np.int8))
+        self.desc = MeshDesc(nx, ny, r, degree, m, l, None if rk is None else rk.ctypes.data,
+                             None if lf is None else lf.ctypes.data)
         h = ctypes.c_void_p()
         _check(lib().mhm_create_mesh(ctypes.byref(self.desc), device, ctypes.byref(h)))
         self.handle = h
@@ -144,6 +149,7 @@ class Mesh:
         self.r_of_K = self.query(Q_R_OF_K, np.int8, self.n_K)
         self.kappa_offset = self.query(Q_KAPPA_OFFSET, np.int64, self.n_K + 1)   # 4^r_K values per K
         self.nodal_offset = self.query(Q_NODAL_OFFSET, np.int64, self.n_K + 1)   # n_local(r_K) values per K
+        self.face_degree = self.query(Q_FACE_DEGREE, np.int8, self.n_faces)
 
     def query(self, what, dtype, count):
         out = np.empty(count, dtype=dtype)
@@ -162,8 +168,8 @@ class Mesh:
             pass
 
 
-def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0, r_per_K=None) -> Mesh:
-    return Mesh(nx, ny, r, degree, m, l, device, r_per_K)
+def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0, r_per_K=None, l_per_face=None) -> Mesh:
+    return Mesh(nx, ny, r, degree, m, l, device, r_per_K, l_per_face)
 
 
 def mhm_local_workspace_size(mesh: Mesh, precision: int) -> int:

@@ -35,8 +35,9 @@ class _RawPtr:
 
 
 class Pipeline:
-    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64, r_per_K=None):
-        self.mesh = mhm.Mesh(nx, ny, r, degree, m, l, device, r_per_K)
+    def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64, r_per_K=None,
+                 l_per_face=None):
+        self.mesh = mhm.Mesh(nx, ny, r, degree, m, l, device, r_per_K, l_per_face)
         self.device = torch.device("cuda", device)
         self.precision = precision
         M = self.mesh
@@ -55,7 +56,14 @@ class Pipeline:
 
     @classmethod
     def for_workload(cls, w: Workload, device: int = 0, precision: int = mhm.MHM_FP64):
-        return cls(w.nx, w.ny, w.r, w.degree, w.m, w.l, device, precision, getattr(w, "r_per_K", None))
+        rk = w.r_per_K
+        lf = None
+        if w.face_degree is not None:
+            # the face numbering from a host-only mesh of the same T_H
+            h = mhm.Mesh(w.nx, w.ny, w.r, w.degree, w.m, w.l, -1, rk)
+            lf = w.l_per_face(h.query(mhm.Q_TRI_FACES, np.int32, 3 * h.n_K))
+            h.close()
+        return cls(w.nx, w.ny, w.r, w.degree, w.m, w.l, device, precision, rk, lf)
 
     def set_precision(self, precision: int):
         self.precision = precision

@@ -210,6 +210,8 @@ class Workload:
     seed: int = 0
     levels: str | None = None        # None: every K at r; "channels": level per K from the channel field
     r_cap: int = 7                   # largest level a K gets ("channels")
+    face_degree: str | None = None   # None: every face at l; "levels": l_e from the adjacent levels
+                                     # (face_degree_from_levels; l is then the largest degree)
 
     @property
     def r_per_K(self):
@@ -227,6 +229,19 @@ class Workload:
         for thr, lev in ((4 * H, 4), (2 * H, 5), (H, 6), (0.5 * H, 7)):
             r[d < thr] = lev
         return np.minimum(r, self.r_cap).astype(np.int8)
+
+    def l_per_face(self, tri_faces):
+        """Multiplier degree of every face (None: every face at l), given the global face
+        id of each K's local faces (n_K x 3, any consistent face numbering)."""
+        if self.face_degree is None:
+            return None
+        if self.face_degree != "levels":
+            raise ValueError(self.face_degree)
+        tf = np.asarray(tri_faces).reshape(-1, 3)
+        rk = self.r_per_K if self.r_per_K is not None else np.full(self.n_K, self.r, dtype=np.int8)
+        rmax = np.zeros(int(tf.max()) + 1, dtype=np.int64)
+        np.maximum.at(rmax, tf.ravel(), np.repeat(rk.astype(np.int64), 3))
+        return face_degree_from_levels(rmax)
 
     @property
     def n_K(self) -> int:
@@ -250,6 +265,14 @@ class Workload:
         return 3 * self.m * (self.l + 1)
 
 
+def face_degree_from_levels(r_adjacent_max):
+    """Degree of a face's multipliers from the largest refinement level among its (one or
+    two) coarse elements: 1 + [r >= 5] + [r >= 7], so finer submeshes meet richer
+    multiplier spaces."""
+    r = np.asarray(r_adjacent_max)
+    return (1 + (r >= 5).astype(np.int64) + (r >= 7).astype(np.int64)).astype(np.int8)
+
+
 WORKLOADS = {
     # 4x4 squares (32 K), r=3 P1, m=1 l=1, kappa = 1, u = sin(pi x) sin(pi y)
     "c1_sin": Workload("c1_sin", 4, 4, 3, 1, 1, 1, "one", "sinsin", 1.0, 1.0),
@@ -262,8 +285,9 @@ WORKLOADS = {
     # 256x256 squares (131072 K), r=4 P2 (561 DOFs), m=3 l=1, GRF contrast 1e6, f = 1
     "c5_p2_large": Workload("c5_p2_large", 256, 256, 4, 2, 3, 1, "grf6", "const", 1.0),
     # uneven levels 3..7: 64x64 squares, level per K from 16 channels of kappa = 1e4, P1,
-    # one subface with degree 2 multipliers on every face
-    "c4_channels": Workload("c4_channels", 64, 64, 3, 1, 1, 2, "channels", "const", 1.0, levels="channels"),
+    # one subface per face with degree 1..3 multipliers by the adjacent levels
+    "c4_channels": Workload("c4_channels", 64, 64, 3, 1, 1, 3, "channels", "const", 1.0, levels="channels",
+                            face_degree="levels"),
 }
 
 

@@ -38,6 +38,32 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def _degrees(tri_faces, rs):
+    """Per-face multiplier degrees by the level recipe on one side's own face numbering."""
+    tf = np.asarray(tri_faces).reshape(-1, 3)
+    rmax = np.zeros(int(tf.max()) + 1, dtype=np.int64)
+    np.maximum.at(rmax, tf.ravel(), np.repeat(np.asarray(rs, dtype=np.int64), 3))
+    return W.face_degree_from_levels(rmax)
+
+
+def _slots(mesh, K, m, d, blk):
+    """The oracle's per-K vector or matrix (local multipliers face by face, m(l_a+1) each)
+    in the library's slot layout: face a at a d .. a d + m(l_a+1) - 1, zeros elsewhere."""
+    idx = []
+    for a in range(3):
+        e = int(mesh.tri_edges[K, a])
+        idx.extend(a * d + np.arange(m * (int(mesh.l_e[e]) + 1)))
+    idx = np.asarray(idx)
+    blk = np.asarray(blk)
+    if blk.ndim == 2:
+        out = np.zeros((3 * d, 3 * d))
+        out[np.ix_(idx, idx)] = blk
+    else:
+        out = np.zeros(3 * d)
+        out[idx] = blk
+    return out
+
+
 def _fp64_bound(o, kap, base):
     """base, or the FP64 error bound 10 u cond(A) (u = 2^-53; cond on the mean-zero space,
     from the largest and the smallest non-zero eigenvalue) where that is larger: two FP64
@@ -139,9 +165,82 @@ def test_levels_solution_vs_oracle():
         assert _rel(uh[a:b], orec.local_u(o.mesh, K, loc, o.lam, o.u0)) < 1e-9, (K, int(rs[K]))
 
 
+@pytest.mark.parametrize("precision,tol", [(mhm.MHM_FP64, 1e-10), (mhm.MHM_MIXED, 1e-9)])
+def test_face_degrees_every_element_vs_oracle(precision, tol):
+    """A multiplier degree per face (1 + [r >= 5] + [r >= 7] over the adjacent levels, so
+    degrees 1..3 meet levels 1..7): every element's blocks against the oracle in the slot
+    layout (unused slots of lower-degree faces exactly zero)."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    m = 1
+    h = mhm.Mesh(nx, ny, 0, 1, m, 0, -1, rs)
+    lf = _degrees(h.query(mhm.Q_TRI_FACES, np.int32, 3 * h.n_K), rs)
+    mesh = build_mesh(nx, ny, m, _degrees(build_mesh(nx, ny, 1, 0).tri_edges, rs))
+    assert np.array_equal(lf, mesh.l_e) and set(lf.tolist()) == {1, 2, 3}
+    p = Pipeline(nx, ny, 0, 1, m, 3, 0, precision, r_per_K=rs, l_per_face=lf)
+    d = p.mesh.n_I // 3
+    kd = torch.as_tensor(np.concatenate(kap), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    p.local(kd, src)
+    torch.cuda.synchronize()
+    assert int(p.status.abs().sum()) == 0
+    NI = p.mesh.n_I
+    AK = p.AK.view(-1, NI, NI).cpu().numpy()
+    EK, BK = p.EK.view(-1, NI).cpu().numpy(), p.BK.view(-1, NI).cpu().numpy()
+    for K in range(len(rs)):
+        o = solve_local(mesh, K, int(rs[K]), 1, kap[K], 1.0)
+        oA, oE, oB = _slots(mesh, K, m, d, o.AK), _slots(mesh, K, m, d, o.EK), _slots(mesh, K, m, d, o.BK)
+        unused = _slots(mesh, K, m, d, np.ones(len(o.BK))) == 0.0
+        assert unused.sum() == 3 * d - len(o.BK)
+        assert np.all(AK[K][unused] == 0.0) and np.all(AK[K][:, unused] == 0.0), K
+        assert np.all(EK[K][unused] == 0.0) and np.all(BK[K][unused] == 0.0), K
+        tk = _fp64_bound(o, kap[K], tol) if rs[K] >= 7 else tol
+        assert _rel(AK[K], oA) < tk, (K, int(rs[K]), tk)
+        assert _rel(BK[K], oB) < 1e-13, K
+        scale = max(np.linalg.norm(o.EK), np.linalg.norm(o.AK) * abs(o.FK) / max(np.linalg.norm(o.BK), 1e-300), 1e-300)
+        assert np.linalg.norm(EK[K] - oE) / scale < tk, (K, int(rs[K]), tk)
+    if precision == mhm.MHM_MIXED:   # the allocation-free entry runs the same levels
+        AK2 = torch.empty_like(p.AK)
+        EK2, BK2, FK2 = torch.empty_like(p.EK), torch.empty_like(p.BK), torch.empty_like(p.FK)
+        st2 = torch.empty_like(p.status)
+        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, None, AK2, EK2, BK2, FK2, st2)
+        torch.cuda.synchronize()
+        assert int(st2.abs().sum()) == 0
+        assert _rel(AK2.cpu().numpy(), p.AK.cpu().numpy()) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(mhm.MHM_FP64, 1e-9), (mhm.MHM_MIXED, 1e-8)])
+def test_face_degrees_solution_vs_oracle(precision, tol):
+    """Degrees 1..3 per face through the whole pipeline (skeleton of mixed block sizes,
+    global solve, reconstruction): multipliers, u0 and u of every element against the
+    oracle; sinsin source."""
+    from oracle import reconstruct as orec
+    from oracle.run import source_fn
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    m = 1
+    h = mhm.Mesh(nx, ny, 0, 1, m, 0, -1, rs)
+    lf = _degrees(h.query(mhm.Q_TRI_FACES, np.int32, 3 * h.n_K), rs)
+    p = Pipeline(nx, ny, 0, 1, m, 3, 0, precision, r_per_K=rs, l_per_face=lf)
+    kd = torch.as_tensor(np.concatenate(kap), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_SINSIN, 1.0, 1.0)
+    p.step(kd, src, None, mhm.SolveOpts(10, 1e-13, 0, 0))
+    lam, u0 = p.solve_global()
+    u, _ = p.reconstruct(kd, src)
+    torch.cuda.synchronize()
+    assert int(p.status.abs().sum()) == 0
+    o = run(nx, ny, rs, 1, m, _degrees(build_mesh(nx, ny, 1, 0).tri_edges, rs), kap, source_fn("sinsin"))
+    assert _rel(lam.cpu().numpy(), o.lam) < tol
+    assert _rel(u0.cpu().numpy(), o.u0) < tol
+    uh = u.cpu().numpy()
+    for K, loc in enumerate(o.locals):
+        a, b = int(p.mesh.nodal_offset[K]), int(p.mesh.nodal_offset[K + 1])
+        assert _rel(uh[a:b], orec.local_u(o.mesh, K, loc, o.lam, o.u0)) < tol, (K, int(rs[K]))
+
+
 def test_channel_workload_full_size():
-    """The uneven channel workload (8192 K, levels 3..7): every level present, FP64 and
-    mixed agree, and sampled elements of each level match the oracle."""
+    """The uneven channel workload (8192 K, levels 3..7, face degrees 1..3): every level
+    present, FP64 and mixed agree, and sampled elements of each level match the oracle."""
     from paper_1703_10435_gb300.pipeline import Pipeline, source_of
     w = W.WORKLOADS["c4_channels"]
     rk = w.r_per_K
@@ -166,8 +265,10 @@ def test_channel_workload_full_size():
     # error bound 10 u cond(A_p) (u = 2^-53, cond on the mean-zero space) where that is
     # larger: a crossing level-6 element has cond ~2e7, where two FP64 solvers (dense
     # bordered LU here, pinned Cholesky on the GPU) can only agree to ~3e-9.
-    mesh = build_mesh(w.nx, w.ny, w.m, w.l)
+    mesh = build_mesh(w.nx, w.ny, w.m, w.l_per_face(build_mesh(w.nx, w.ny, 1, 0).tri_edges))
+    assert set(mesh.l_e.tolist()) == {1, 2, 3}
     NI = 3 * w.m * (w.l + 1)
+    d = NI // 3
     for r in (3, 4, 5, 6, 7):
         idx = np.flatnonzero(rk == r)
         picks = [int(idx[len(idx) // 2])]
@@ -180,7 +281,8 @@ def test_channel_workload_full_size():
             o = solve_local(mesh, K, r, 1, kap, 1.0)
             tol = _fp64_bound(o, kap, 1e-10)
             for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
-                assert _rel(out[prec][K].view(NI, NI).cpu().numpy(), o.AK) < tol, (r, K, prec, tol)
+                got = out[prec][K].view(NI, NI).cpu().numpy()
+                assert _rel(got, _slots(mesh, K, w.m, d, o.AK)) < tol, (r, K, prec, tol)
 
 
 @pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])

@@ -70,6 +70,41 @@ def test_skeleton_pattern_matches_oracle(lib):
     assert got == want
 
 
+@pytest.mark.parametrize("nx,ny,m", [(3, 2, 1), (4, 3, 2)])
+def test_per_face_degree_numbering_matches_oracle(lib, nx, ny, m):
+    """A multiplier degree per face: offsets, the per-K slots (face a at a d + u, d =
+    m(l_max+1), unused slots -1) and the skeleton pattern against the oracle's mesh."""
+    rng = np.random.default_rng(5 + nx)
+    ne = nx * (ny + 1) + ny * (nx + 1) + nx * ny
+    lf = rng.integers(0, 4, ne).astype(np.int8)
+    M = mhm.Mesh(nx, ny, 2, 1, m, 0, device=-1, l_per_face=lf)
+    o = build_mesh(nx, ny, m, lf)
+    d = m * (int(lf.max()) + 1)
+    assert (M.n_faces, M.n_lambda, M.n_I) == (o.n_e, o.n_lambda, 3 * d)
+    assert np.array_equal(M.face_degree, lf)
+    assert np.array_equal(M.query(mhm.Q_LAMBDA_OFFSET, np.int64, M.n_faces + 1), o.lam_offset)
+    kl = M.query(mhm.Q_K_LAMBDA, np.int32, M.n_K * M.n_I).reshape(M.n_K, M.n_I)
+    for K in range(M.n_K):
+        used = []
+        for a in range(3):
+            e = int(o.tri_edges[K, a])
+            n = m * (int(lf[e]) + 1)
+            assert np.array_equal(kl[K, a * d:a * d + n], o.lam_offset[e] + np.arange(n))
+            assert np.all(kl[K, a * d + n:(a + 1) * d] == -1)
+            used.extend(kl[K, a * d:a * d + n])
+        assert np.array_equal(used, o.local_lambda(K))
+    rowptr = M.query(mhm.Q_CSR_ROWPTR, np.int32, M.n_lambda + 1)
+    cols = M.query(mhm.Q_CSR_COLS, np.int32, M.nnz)
+    want = set()
+    for K in range(o.n_K):
+        ids = o.local_lambda(K)
+        want.update((int(a), int(b)) for a in ids for b in ids)
+    got = {(j, int(c)) for j in range(M.n_lambda) for c in cols[rowptr[j]:rowptr[j + 1]]}
+    assert got == want
+    for j in range(M.n_lambda):
+        assert np.all(np.diff(cols[rowptr[j]:rowptr[j + 1]]) > 0)
+
+
 def test_errors_are_reported(lib):
     with pytest.raises(mhm.MHMError) as e:
         mhm.Mesh(0, 1, 2, 1, 1, 1, device=-1)
