@@ -238,6 +238,37 @@ def test_face_degrees_solution_vs_oracle(precision, tol):
         assert _rel(uh[a:b], orec.local_u(o.mesh, K, loc, o.lam, o.u0)) < tol, (K, int(rs[K]))
 
 
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_face_degrees_exact_linear_pipeline(precision):
+    """Degrees 0..3 face by face, levels 2..4 element by element, kappa = 1 and
+    u = 1 + 2x - 3y: recovered exactly at every node (the flux is constant per face, so it
+    lies in every face's space; m(l_e+1) <= 4 against >= 5 trace nodes keeps the system
+    nonsingular)."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx = ny = 3
+    ne = nx * (ny + 1) + ny * (nx + 1) + nx * ny
+    rng = np.random.default_rng(10)
+    lf = rng.integers(0, 4, ne).astype(np.int8)
+    rs = rng.integers(2, 5, 2 * nx * ny).astype(np.int8)
+    p = Pipeline(nx, ny, 0, 1, 1, 3, 0, precision, r_per_K=rs, l_per_face=lf)
+    kd = torch.ones(int(p.mesh.kappa_offset[-1]), dtype=torch.float64, device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 0.0, 1.0)
+    gd = mhm.Dirichlet((mhm.ctypes.c_double * 6)(1.0, 2.0, -3.0, 0.0, 0.0, 0.0))
+    p.step(kd, src, gd)
+    p.solve_global()
+    ex = mhm.Exact(mhm.MHM_EXACT_POLY, (mhm.ctypes.c_double * 6)(1.0, 2.0, -3.0, 0.0, 0.0, 0.0))
+    u, err = p.reconstruct(kd, src, ex)
+    torch.cuda.synchronize()
+    assert int(p.status.abs().sum()) == 0
+    assert float(err.sum()) < 1e-18
+    o = run(nx, ny, rs, 1, 1, lf, [np.ones(4 ** int(r)) for r in rs], 0.0, g=lambda x, y: 1 + 2 * x - 3 * y)
+    uh = u.cpu().numpy()
+    for K, loc in enumerate(o.locals):
+        a, b = int(p.mesh.nodal_offset[K]), int(p.mesh.nodal_offset[K + 1])
+        xy = loc.sub.node_xy
+        assert np.abs(uh[a:b] - (1 + 2 * xy[:, 0] - 3 * xy[:, 1])).max() < 1e-10, K
+
+
 def test_channel_workload_full_size():
     """The uneven channel workload (8192 K, levels 3..7, face degrees 1..3): every level
     present, FP64 and mixed agree, and sampled elements of each level match the oracle."""

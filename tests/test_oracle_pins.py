@@ -378,3 +378,49 @@ def test_per_element_levels_exact_layered(P):
 
     o = run(nx, ny, rs, P, 1, 1, kap, 0.0, g=u)
     assert _max_nodal_error(o, u) < 1e-11 * cum[-1]
+
+
+def test_per_face_degree_uniform_equals_scalar():
+    """A per-face degree array with one value gives the scalar-degree run's system exactly."""
+    rng = np.random.default_rng(8)
+    kap = 10.0 ** rng.uniform(-1, 1, (8, 16))
+    a = run(2, 2, 2, 1, 2, 1, kap, 1.0)
+    ne = 2 * 3 + 2 * 3 + 4
+    b = run(2, 2, 2, 1, 2, np.ones(ne, dtype=np.int64), kap, 1.0)
+    assert np.array_equal(a.A.toarray(), b.A.toarray()) and np.array_equal(a.E, b.E)
+    assert np.array_equal(a.lam, b.lam)
+
+
+@pytest.mark.parametrize("m,lmax", [(1, 3), (2, 1)])
+def test_per_face_degree_exact_linear_and_layered(m, lmax):
+    """Degrees 0..lmax face by face, levels 2..4 element by element: kappa = 1 with u
+    linear, and layered kappa with u(y) = int 1/kappa (flux constant per face, so it lies in
+    every face's space), are both reproduced exactly.  Every face keeps m(l_e+1) <= 4
+    multipliers against the >= 5 trace nodes of a level-2 submesh (a richer multiplier
+    space than the trace makes the saddle-point system singular)."""
+    from paper_1703_10435_gb300 import workloads as W
+    nx = ny = 3
+    ne = nx * (ny + 1) + ny * (nx + 1) + nx * ny
+    rng = np.random.default_rng(9 + m)
+    lf = rng.integers(0, lmax + 1, ne)
+    rs = rng.integers(2, 5, 2 * nx * ny)
+    g = lambda x, y: 1 + 2 * x - 3 * y
+    o = run(nx, ny, rs, 1, m, lf, [np.ones(4 ** int(r)) for r in rs], 0.0, g=g)
+    assert sorted(set(int(v) for v in o.mesh.l_e)) == list(range(lmax + 1))
+    assert _max_nodal_error(o, g) < 1e-12
+    rmin = int(rs.min())
+    hs = 1.0 / (ny * (1 << rmin))
+    ks = 10.0 ** (-2 + 4 * W.uniform01(7, np.arange(ny * (1 << rmin), dtype=np.uint64), 0, 0))
+    kap = []
+    for K, r in enumerate(rs):
+        cen = W.fine_centroids(W.coarse_vertices(nx, ny), 1 << int(r))[K]
+        kap.append(ks[np.floor(cen[..., 1] / hs).astype(int)])
+    cum = np.concatenate([[0.0], np.cumsum(hs / ks)])
+
+    def u(x, y):
+        y = np.asarray(y, dtype=float)
+        s = np.clip(np.floor(y / hs).astype(int), 0, len(ks) - 1)
+        return cum[s] + (y - s * hs) / ks[s]
+
+    o = run(nx, ny, rs, 1, m, lf, kap, 0.0, g=u)
+    assert _max_nodal_error(o, u) < 1e-11 * cum[-1]
