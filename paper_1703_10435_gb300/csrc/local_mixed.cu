@@ -240,13 +240,17 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
         double w[7];
         int v[7];
         p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
+        uint32_t nz = 0;   // non-zero weights (zero: edges at right angles), tested on the integer pipe
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if ((__double_as_longlong(w[k]) << 1) != 0) nz |= 1u << k;
         for (int col = 0; col < g.R; ++col) {
             if (c.col_done[col]) continue;
             const double* Dc = D + col * ld;
             double a = 0.0;
 #pragma unroll
             for (int k = 0; k < 7; ++k)
-                if (w[k] != 0.0) a = fma(w[k], Dc[v[k]], a);   // zero weights: edges at right angles
+                if (nz >> k & 1) a = fma(w[k], Dc[v[k]], a);
             const double rn = Res[col * ld + u] - a;
             Res[col * ld + u] = rn;
             y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
@@ -774,10 +778,13 @@ __device__ __noinline__ void fused_residual(int PN, int nu, int R, const double*
         v[5] = unk(PN, X + 1, Y - 1);
         v[6] = unk(PN, X - 1, Y + 1);
         double a[7];
+        uint32_t nz = 0;   // stencil points with a non-zero weight, tested once per node on the
+                           // integer pipe (a double comparison would occupy the FP64 pipe)
 #pragma unroll
         for (int d = 0; d < 7; ++d) {
             a[d] = ah[(size_t)d * nu + u];
             if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
+            if ((__double_as_longlong(a[d]) << 1) != 0) nz |= 1u << d;   // a[d] != 0 (either zero sign)
         }
         for (int c0 = 0; c0 < R; c0 += 8) {
             double zr[8], rr[8];
@@ -797,7 +804,7 @@ __device__ __noinline__ void fused_residual(int PN, int nu, int R, const double*
                     double r = fma(-a[0], d0, rr[j]);
 #pragma unroll
                     for (int d = 1; d < 7; ++d)
-                        if (a[d] != 0.0) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
+                        if (nz >> d & 1) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
                     Rh[(size_t)u * R + col] = r;
                 }
             }
