@@ -226,23 +226,6 @@ __device__ __forceinline__ float d2f_bits(double d) {
     return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
-// Error-free transformations on the FP32 pipe (Knuth's TwoSum; the exact product error
-// by a fused multiply-add).  With them a value kept as an FP32 pair hi + lo (about 48
-// significant bits) is updated without FP64 instructions: on this GPU the FP32 pipe runs
-// 64 times the FP64 rate.  IEEE round-to-nearest FP32 arithmetic is required (no fast-math).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);   // a + b = s + e exactly
-}
-// A double as an FP32 pair: hi its truncation (exact, on the integer pipe), lo the rounded
-// remainder; |x - hi - lo| <= 2^-47 |x|.
-__device__ __forceinline__ float2 split_pair(double x) {
-    const float hi = d2f_bits(x);
-    return make_float2(hi, __double2float_rn(x - f2d_bits(hi)));
-}
-__device__ __forceinline__ double pair_value(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
-
 // Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
 // FP32 right-hand side y(u, :) = s_u Res(u, :): the sum over
 // the fine triangles T containing u of kappa_T S_T[a_u][b] D(b).  P1 uses the
@@ -656,7 +639,7 @@ __device__ __forceinline__ int4 schur_step_info(const LevelGeom& lg, int nlev, c
 // T_lev g_lev its result) in a fixed order.  Needs R <= 32: one output tile per warp,
 // warp w at (row tile w / NT, column tile w % NT) at every level.
 __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
-                                         const float* cw, const float2* Rh, float* opbuf, float* stage, double* eps,
+                                         const float* cw, const double* Rh, float* opbuf, float* stage, double* eps,
                                          MCtx& c) {
     const int R = g.R, NT = (R + 7) >> 3, nu = g.nunk;
     const int nsteps = 2 * g.nlev - 1;
@@ -680,11 +663,11 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     const bool issuer = threadIdx.x == kThreadsM - 32;
     if (issuer) issue(0);
     for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
-    // the right-hand side r = the high part of the pair Rh, in y (frozen columns keep their pending
-    // correction); node-major on both sides, so the reads are coalesced and all in flight together
+    // the right-hand side r = FP32 rounding of Rh, in y (frozen columns keep their pending correction);
+    // node-major on both sides, so the reads are coalesced and all in flight together
     for (int t = threadIdx.x; t < nu * R; t += kThreadsM) {
         const int col = t % R;
-        if (!(frozen >> col & 1)) y[t] = Rh[t].x;
+        if (!(frozen >> col & 1)) y[t] = d2f_bits(Rh[t]);
     }
     __syncthreads();
     float eacc0 = 0.0f, eacc1 = 0.0f;   // this lane's two columns (2 tq, 2 tq + 1 of its column tile)
@@ -776,14 +759,12 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
 }
 
 // One refinement pass of the level-Schur path, in scaled variables, for the columns
-// not done: Zh_u += y_u and Rh_u -= sum_v Ah_uv y_v over the stencil points v of u.  Zh, Rh
-// and the weights Ah are FP32 pairs hi + lo (about 48 bits); y is FP32, so a weight times y
-// is hi y + lo y, hi y exact as a product and its rounding error (fmaf), and every sum is
-// carried by TwoSum: all of it on the FP32 pipe.  A node's entries are read 8 columns at a
-// time before they are used, so that their loads are in flight together.  Thread per node;
-// `done` has bit col set for the columns to skip.
-__device__ __noinline__ void fused_residual(int PN, int nu, int R, const float2* __restrict__ ah, const float* y,
-                                            float2* __restrict__ Zh, float2* __restrict__ Rh, uint64_t done) {
+// not done: Zh_u += y_u and Rh_u -= sum_v Ah_uv y_v over the stencil points v of u,
+// accumulated in FP64 (y widened on the integer pipe).  A node's entries are read 8
+// columns at a time before they are used, so that their loads are in flight
+// together.  Thread per node; `done` has bit col set for the columns to skip.
+__device__ __noinline__ void fused_residual(int PN, int nu, int R, const double* __restrict__ ah, const float* y,
+                                            double* __restrict__ Zh, double* __restrict__ Rh, uint64_t done) {
     const uint32_t y_s = smem_u32(y);
     for (int u = threadIdx.x; u < nu; u += kThreadsM) {
         int X, Y;
@@ -796,46 +777,35 @@ __device__ __noinline__ void fused_residual(int PN, int nu, int R, const float2*
         v[4] = unk(PN, X, Y - 1);
         v[5] = unk(PN, X + 1, Y - 1);
         v[6] = unk(PN, X - 1, Y + 1);
-        float2 a[7];
-        uint32_t nz = 0;   // stencil points with a non-zero weight
+        double a[7];
+        uint32_t nz = 0;   // stencil points with a non-zero weight, tested once per node on the
+                           // integer pipe (a double comparison would occupy the FP64 pipe)
 #pragma unroll
         for (int d = 0; d < 7; ++d) {
             a[d] = ah[(size_t)d * nu + u];
-            if (v[d] < 0 || v[d] >= nu) { a[d] = make_float2(0.0f, 0.0f); v[d] = u; }   // (weight zero there)
-            if (((__float_as_uint(a[d].x) | __float_as_uint(a[d].y)) << 1) != 0) nz |= 1u << d;
+            if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
+            if ((__double_as_longlong(a[d]) << 1) != 0) nz |= 1u << d;   // a[d] != 0 (either zero sign)
         }
         for (int c0 = 0; c0 < R; c0 += 8) {
-            float2 zr[8], rr[8];
+            double zr[8], rr[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int col = c0 + j;
                 const bool on = col < R && !(done >> col & 1);
-                zr[j] = on ? Zh[(size_t)u * R + col] : make_float2(0.0f, 0.0f);
-                rr[j] = on ? Rh[(size_t)u * R + col] : make_float2(0.0f, 0.0f);
+                zr[j] = on ? Zh[(size_t)u * R + col] : 0.0;
+                rr[j] = on ? Rh[(size_t)u * R + col] : 0.0;
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int col = c0 + j;
                 if (col < R && !(done >> col & 1)) {
-                    const float y0 = lds1(y_s + 4u * (uint32_t)(u * R + col));
-                    float s, e;
-                    two_sum(zr[j].x, y0, s, e);
-                    e += zr[j].y;
-                    two_sum(s, e, zr[j].x, zr[j].y);
-                    Zh[(size_t)u * R + col] = zr[j];
-                    float rh = rr[j].x, rl = rr[j].y;
+                    const double d0 = f2d_bits(lds1(y_s + 4u * (uint32_t)(u * R + col)));
+                    Zh[(size_t)u * R + col] = zr[j] + d0;
+                    double r = fma(-a[0], d0, rr[j]);
 #pragma unroll
-                    for (int d = 0; d < 7; ++d)
-                        if (nz >> d & 1) {
-                            const float yd = d == 0 ? y0 : lds1(y_s + 4u * (uint32_t)(v[d] * R + col));
-                            const float p = a[d].x * yd;
-                            const float pe = fmaf(a[d].x, yd, -p);   // a.hi yd = p + pe exactly
-                            two_sum(rh, -p, s, e);
-                            rh = s;
-                            rl += (e - pe) - a[d].y * yd;
-                        }
-                    two_sum(rh, rl, s, e);
-                    Rh[(size_t)u * R + col] = make_float2(s, e);
+                    for (int d = 1; d < 7; ++d)
+                        if (nz >> d & 1) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
+                    Rh[(size_t)u * R + col] = r;
                 }
             }
         }
@@ -986,9 +956,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             //   Zh = S^-1 Z, Rh = S (G - A Z), Ah = S A S, S = diag(A_uu^-1/2).
             // A correction is Zh += y (the FP32 solve output, exactly), the residual update
             // Rh -= Ah y reads y at the stencil points, and z_j^T Res_i = Zh_j^T Rh_i.
-            // Rh and Zh as FP32 pairs (hi, lo) in the FP64 slot arrays (8 bytes each)
-            float2* Rh = reinterpret_cast<float2*>(G);
-            float2* Zh = reinterpret_cast<float2*>(Z);
+            double* Rh = G;
+            double* Zh = Z;
             double* smass = mass;   // s_u m_u
             const double* sc;
             const double* ah;       // 7 x nunk: self, E, W, N, S, SE, NW
@@ -1033,9 +1002,6 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 sc = scale;
                 ah = ahw;
             }
-            // the scaled stencil as FP32 pairs, in place (each entry read and rewritten by one thread)
-            float2* ah2 = reinterpret_cast<float2*>(const_cast<double*>(ah));
-            for (int t = threadIdx.x; t < 7 * nu; t += blockDim.x) ah2[t] = split_pair(ah[t]);
             // ---- right-hand sides Rh = S G (compatible loads, pinned DOF left out), S m, Zh = 0
             for (int u = threadIdx.x; u < nu; u += blockDim.x) {
                 int X, Y;
@@ -1068,8 +1034,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                             v += -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + kk2];
                         }
                     }
-                    Rh[(size_t)u * R + col] = split_pair(su * v);
-                    Zh[(size_t)u * R + col] = make_float2(0.0f, 0.0f);
+                    Rh[(size_t)u * R + col] = su * v;
+                    Zh[(size_t)u * R + col] = 0.0;
                 }
             }
             __syncthreads();
@@ -1093,7 +1059,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     uint64_t done = 0;
                     for (int col = 0; col < R; ++col)
                         if (c.col_done[col]) done |= 1ull << col;
-                    fused_residual(g.PN, nu, R, ah2, y, Zh, Rh, done);
+                    fused_residual(g.PN, nu, R, ah, y, Zh, Rh, done);
                 }
                 ++pass;
                 __syncthreads();
@@ -1129,7 +1095,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             const int converged = c.converged;
             // ---- outputs X[j][i] = N~_j^T z_i + z_j^T Res_i = (S N~_j)^T Zh_i + Zh_j^T Rh_i.
             // Lane = column, warps take node rows in turn: every row read is one coalesced
-            // load of R FP32 pairs.  The Gram Zh^T Rh (the correction, of the size of the error
+            // load of R doubles.  The Gram Zh^T Rh (the correction, of the size of the error
             // of Z) accumulates in FP32, one R x R partial per warp in shared memory; the mass
             // term (S m)^T Zh in FP64; partials are summed in a fixed warp order.
             {
@@ -1145,10 +1111,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
                 double mzp = 0.0;
                 for (int u = warp; u < nu; u += kWarpsM) {
-                    const float2 zp = lc ? Zh[(size_t)u * R + lane] : make_float2(0.0f, 0.0f);
-                    const float2 rp = lc ? Rh[(size_t)u * R + lane] : make_float2(0.0f, 0.0f);
-                    mzp = fma(smass[u], pair_value(zp), mzp);
-                    const float zf = zp.x, rf = rp.x;
+                    const double zh = lc ? Zh[(size_t)u * R + lane] : 0.0;
+                    const double rh = lc ? Rh[(size_t)u * R + lane] : 0.0;
+                    mzp = fma(smass[u], zh, mzp);
+                    const float zf = d2f_bits(zh), rf = d2f_bits(rh);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const float ri = __shfl_sync(0xffffffffu, rf, i);
@@ -1186,7 +1152,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                         const int u = unk(g.PN, X, Y);
                         if (u < 0) continue;
                         const int kk2 = c.rev[a] ? g.PN - kl : kl;
-                        const double zs = sc[u] * pair_value(Zh[(size_t)u * R + lane]) * (-c.sgn[a] * c.flen[a]);
+                        const double zs = sc[u] * Zh[(size_t)u * R + lane] * (-c.sgn[a] * c.flen[a]);
                         for (int jf = 0; jf < g.dpf; ++jf) {
                             const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
                             if (row >= 0) sb[jf] = fma(g.dm.btab[row * (g.PN + 1) + kk2], zs, sb[jf]);
