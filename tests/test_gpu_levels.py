@@ -269,6 +269,29 @@ def test_face_degrees_exact_linear_pipeline(precision):
         assert np.abs(uh[a:b] - (1 + 2 * xy[:, 0] - 3 * xy[:, 1])).max() < 1e-10, K
 
 
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_levels_k_ranges_equal_one_shot(precision):
+    """The K-range option (one rank's contiguous share of the elements) on a mesh of levels
+    1..7 and face degrees 1..3: two calls over an uneven split give the one-shot blocks bit
+    for bit (each level maps the range to its own element list)."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    h = mhm.Mesh(nx, ny, 0, 1, 1, 0, -1, rs)
+    lf = _degrees(h.query(mhm.Q_TRI_FACES, np.int32, 3 * h.n_K), rs)
+    kd = torch.as_tensor(np.concatenate(kap), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    one = Pipeline(nx, ny, 0, 1, 1, 3, 0, precision, r_per_K=rs, l_per_face=lf)
+    one.local(kd, src)
+    two = Pipeline(nx, ny, 0, 1, 1, 3, 0, precision, r_per_K=rs, l_per_face=lf)
+    n = two.mesh.n_K
+    split = n // 2 + 1
+    two.local(kd, src, mhm.SolveOpts(8, 1e-12, 0, split))
+    two.local(kd, src, mhm.SolveOpts(8, 1e-12, split, n))
+    torch.cuda.synchronize()
+    for name in ("AK", "EK", "BK", "FK", "status", "iters"):
+        assert torch.equal(getattr(one, name), getattr(two, name)), name
+
+
 def test_channel_workload_full_size():
     """The uneven channel workload (8192 K, levels 3..7, face degrees 1..3): every level
     present, FP64 and mixed agree, and sampled elements of each level match the oracle."""
