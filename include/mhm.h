@@ -263,11 +263,15 @@ mhm_status mhm_solve_global(const mhm_mesh* mesh, const double* A_vals_dev, cons
  * sum_i k_i eta_i + eta_f on every K, computed in FP64 as one zero-mean Neumann
  * solve per K with the combined load sum_i k_i N~_i + f~ (the k_i are the global
  * multipliers of K's local basis).  Writes u_nodal_dev[K*n_local + w] for every
- * local DOF w of K (lattice order); with a level per K, u_nodal_dev[MHM_Q_NODAL_OFFSET[K] + w].  If err_sq_dev is not NULL (it needs
+ * local DOF w of K (lattice order); with a level per K,
+ * u_nodal_dev[MHM_Q_NODAL_OFFSET[K] + w].  If err_sq_dev is not NULL (it needs
  * `exact`), also writes err_sq_dev[2K] = ||u_{H,h} - u||^2_{L2(K)} and
  * err_sq_dev[2K+1] = |u_{H,h} - u|^2_{H1(K)}, by the collapsed 4 x 4 Gauss rule
- * on every fine triangle.  Allocates temporary device memory.
- * Errors: INVALID_ARG, UNSUPPORTED (window beyond shared memory), CUDA. */
+ * on every fine triangle.  Allocates temporary device memory, stream-ordered: per
+ * resident block the level factors of one element (2/3 (PN+1)^3 doubles for P1, about
+ * 11 MB at r = 7, with its level window behind them when that exceeds shared memory),
+ * i.e. a few GB for a level-7 launch.
+ * Errors: INVALID_ARG, UNSUPPORTED (window panel beyond shared memory), OOM, CUDA. */
 mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
                            const double* lambda_dev, const double* u0_dev, const mhm_exact* exact,
                            double* u_nodal_dev, double* err_sq_dev, void* stream);
