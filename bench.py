@@ -58,10 +58,12 @@ def algorithmic_fmas(P, N, R):
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path: str | None = None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        # the raw samples (the JSON line carries their summary)
+        self.path = path or os.path.join(tempfile.gettempdir(), "clocks_bench_%d.csv" % index)
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -322,7 +324,7 @@ def run_ours(args, w, rank, world, local_rank):
 
     p64 = Pipeline.for_workload(w, local_rank, mhm.MHM_FP64)
     pmx = Pipeline.for_workload(w, local_rank, mhm.MHM_MIXED)
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(local_rank, args.clocks_csv)
     sampler.start()
     step64, local64, kern64 = time_path(p64, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
     stepmx, localmx, kernmx = time_path(pmx, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
@@ -493,6 +495,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="file for the raw nvidia-smi samples (default: temp dir)")
     ap.add_argument("--no-solution-check", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
