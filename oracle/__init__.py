@@ -9,16 +9,19 @@ library (only the seeded input arrays of ``workloads`` reach both).
 It follows the paper's statement of the method literally, in FP64:
 
 * ``mesh``        coarse triangulation T_H, faces, normals and the multiplier
-                  space Lambda_H^{m,l} (Sec. 2, definitions (i) and the
-                  global problem, Eq. "global");
+                  space Lambda_H^{m,l}, with a subface count and degree per
+                  face (Sec. 2, definitions (i) and the global problem,
+                  Eq. "global");
 * ``quadrature``  Gauss-Legendre rules on segments and a collapsed (Duffy)
                   Gauss rule on triangles;
 * ``fem``         the second-level space V_h(K): continuous Lagrange P1/P2 on
                   an r-times uniformly refined submesh (Sec. 2);
 * ``local``       solveLocalProblem (Sec. 3, Eqs. "etaf", "etai",
-                  "source_term"): assembly of a(.,.)_K, the zero-mean Neumann
-                  solves by a bordered dense system, and the face integrals
-                  (psi_j, eta_i) and (psi_j, eta_f) by quadrature of traces;
+                  "source_term") on a submesh of any level: assembly of
+                  a(.,.)_K, the zero-mean Neumann solves by the bordered system
+                  (dense LU with partial pivoting; sparse LU above 2200
+                  unknowns), and the face integrals (psi_j, eta_i) and
+                  (psi_j, eta_f) by quadrature of traces;
 * ``globalsys``   reduceLocalProblems: assembly and direct solve of the
                   saddle-point system (Eq. "mat_global");
 * ``reconstruct`` computeSolution (Eq. "u_Hh") and error norms.
