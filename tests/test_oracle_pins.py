@@ -424,3 +424,24 @@ def test_per_face_degree_exact_linear_and_layered(m, lmax):
 
     o = run(nx, ny, rs, 1, m, lf, kap, 0.0, g=u)
     assert _max_nodal_error(o, u) < 1e-11 * cum[-1]
+
+
+def test_per_face_degree_exact_quadratic_p2():
+    """P2 locals, levels 1..3 element by element, degrees 1..3 face by face: the flux of a
+    quadratic u is linear along every face, so it lies in every face's space (l_e >= 1), and
+    u is reproduced exactly (m(l_e+1) <= 4 against the >= 5 P2 trace nodes of a level-1
+    face keeps the system nonsingular).  Degree 0 on one face breaks the exactness."""
+    u = lambda x, y: x ** 2 - 2 * x * y + 3 * y ** 2 + x
+    nx = ny = 2
+    ne = nx * (ny + 1) + ny * (nx + 1) + nx * ny
+    rng = np.random.default_rng(12)
+    lf = rng.integers(1, 4, ne)
+    rs = rng.integers(1, 4, 2 * nx * ny)
+    kap = [np.ones(4 ** int(r)) for r in rs]
+    o = run(nx, ny, rs, 2, 1, lf, kap, -8.0, g=u)
+    assert sorted(set(int(v) for v in o.mesh.l_e)) == [1, 2, 3]
+    assert _max_nodal_error(o, u) < 1e-11
+    lf0 = lf.copy()
+    lf0[[e for e in range(ne) if not o.mesh.boundary[e]][0]] = 0   # one interior face at degree 0
+    o0 = run(nx, ny, rs, 2, 1, lf0, kap, -8.0, g=u)
+    assert _max_nodal_error(o0, u) > 1e-6
