@@ -209,6 +209,25 @@ mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, 
                                  int32_t* iters_dev, void* workspace_dev, size_t workspace_bytes,
                                  void* stream);
 
+/* mhm_local_solve_batch with kappa in HOST memory, in memory-admitted waves (the
+ * batch's kappa need not fit on the device): the elements of [opts->K_begin,
+ * opts->K_end) are cut into contiguous waves, each as long as its kappa fits in half
+ * of kappa_budget_bytes, and two device buffers of at most that size (from the
+ * stream-ordered allocator, freed on `stream` at the end) alternate: the copy of wave
+ * w + 1 runs on a library-owned copy stream while the solves of wave w run on
+ * `stream`.  kappa_host: the whole batch's kappa in the layout of kappa_dev (with a
+ * level per K, element K at MHM_Q_KAPPA_OFFSET[K]); pin it (cudaHostAlloc /
+ * cudaHostRegister) for the copies to overlap the solves; it must stay valid until
+ * the work on `stream` completes.  Outputs, workspace and precision as in
+ * mhm_local_solve_batch; *n_waves (may be NULL) gets the number of waves.  Not for
+ * stream capture.  Errors: INVALID_ARG (NULL pointers, bad range, one element's kappa
+ * above half the budget), OOM, and those of mhm_local_solve_batch. */
+mhm_status mhm_local_solve_waves(const mhm_mesh* mesh, const double* kappa_host, size_t kappa_budget_bytes,
+                                 const mhm_source* f, int32_t precision, const mhm_solve_opts* opts,
+                                 double* AK_dev, double* EK_dev, double* BK_dev, double* FK_dev,
+                                 int32_t* status_dev, int32_t* iters_dev, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream, int32_t* n_waves);
+
 /* Allocation-free variant of mhm_local_solve_batch with precision MHM_MIXED (the
  * paper has no counterpart: it is an interface for callers that cannot allocate
  * device memory while they run, e.g. a framework whose pool owns all device

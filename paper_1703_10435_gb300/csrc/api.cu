@@ -188,6 +188,85 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
     return MHM_OK;
 }
 
+extern "C" mhm_status mhm_local_solve_waves(const mhm_mesh* mesh, const double* kappa_host, size_t kappa_budget_bytes,
+                                            const mhm_source* f, int32_t precision, const mhm_solve_opts* opts,
+                                            double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                                            int32_t* iters, void* workspace, size_t ws_bytes, void* stream,
+                                            int32_t* n_waves) {
+    mhm_status st = enter(mesh, "mhm_local_solve_waves");
+    if (st) return st;
+    if (!kappa_host || !f) return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_waves: NULL pointer argument");
+    mhm_solve_opts o{};
+    o.it_max = 8;
+    o.tol = 1e-12;
+    if (opts) o = *opts;
+    const int64_t K0 = o.K_begin, K1 = o.K_end > 0 ? o.K_end : mesh->nK;
+    if (K0 < 0 || K1 > mesh->nK || K0 > K1)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_waves: K range out of bounds");
+    // first kappa value of K (per-K levels: the mesh's offsets; uniform: K 4^r)
+    auto koff = [&](int64_t K) { return mesh->per_k_levels ? mesh->kap_off[K] : K * mesh->nfine; };
+    // waves: contiguous K ranges, each as long as its kappa fits in one of the two buffers
+    const size_t half = kappa_budget_bytes / 2;
+    std::vector<int64_t> cut{K0};
+    while (cut.back() < K1) {
+        const int64_t a = cut.back();
+        int64_t b = a;
+        while (b < K1 && (size_t)(koff(b + 1) - koff(a)) * sizeof(double) <= half) ++b;
+        if (b == a)
+            return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_waves: the kappa of one element exceeds half the budget");
+        cut.push_back(b);
+    }
+    const int nw = (int)cut.size() - 1;
+    if (n_waves) *n_waves = nw;
+    if (nw == 0) return MHM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!mesh->wave_copy) {
+        MHM_CUDA_TRY(cudaStreamCreateWithFlags(&mesh->wave_copy, cudaStreamNonBlocking));
+        MHM_CUDA_TRY(cudaEventCreateWithFlags(&mesh->wave_start, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b) {
+            MHM_CUDA_TRY(cudaEventCreateWithFlags(&mesh->wave_copied[b], cudaEventDisableTiming));
+            MHM_CUDA_TRY(cudaEventCreateWithFlags(&mesh->wave_solved[b], cudaEventDisableTiming));
+        }
+    }
+    // the buffers come from the stream-ordered allocator on the caller's stream; the copy
+    // stream starts after them (and after the caller's earlier work)
+    double* buf[2] = {nullptr, nullptr};
+    const int nbuf = nw > 1 ? 2 : 1;
+    for (int b = 0; b < nbuf; ++b) {
+        int64_t most = 0;   // the largest wave this buffer holds
+        for (int w = b; w < nw; w += 2) most = std::max<int64_t>(most, koff(cut[w + 1]) - koff(cut[w]));
+        cudaError_t e = cudaMallocAsync((void**)&buf[b], (size_t)most * sizeof(double), s);
+        if (e != cudaSuccess) {
+            for (int i = 0; i < b; ++i) cudaFreeAsync(buf[i], s);
+            return cuda_fail(e, "mhm_local_solve_waves: cudaMallocAsync");
+        }
+    }
+    cudaError_t ce = cudaEventRecord(mesh->wave_start, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(mesh->wave_copy, mesh->wave_start, 0);
+    for (int w = 0; w < nw && !st && ce == cudaSuccess; ++w) {
+        const int b = w & 1;
+        const int64_t a = cut[w], e = cut[w + 1];
+        // buffer b is refilled once the solves of wave w - 2 are done with it
+        if (w >= 2) ce = cudaStreamWaitEvent(mesh->wave_copy, mesh->wave_solved[b], 0);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(buf[b], kappa_host + koff(a), (size_t)(koff(e) - koff(a)) * sizeof(double),
+                                 cudaMemcpyHostToDevice, mesh->wave_copy);
+        if (ce == cudaSuccess) ce = cudaEventRecord(mesh->wave_copied[b], mesh->wave_copy);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, mesh->wave_copied[b], 0);
+        if (ce != cudaSuccess) break;
+        mhm_solve_opts ow = o;
+        ow.K_begin = a;
+        ow.K_end = e;
+        // the kernels index kappa by the absolute offset of K: a base koff(a) elements before the buffer
+        st = mhm_local_solve_batch(mesh, buf[b] - koff(a), f, precision, &ow, AK, EK, BK, FK, status, iters,
+                                   workspace, ws_bytes, stream);
+        if (!st) ce = cudaEventRecord(mesh->wave_solved[b], s);
+    }
+    for (int b = 0; b < nbuf; ++b) cudaFreeAsync(buf[b], s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "mhm_local_solve_waves");
+    return st;
+}
+
 extern "C" mhm_status mhm_assemble_skeleton(const mhm_mesh* mesh, const double* AK, const double* EK,
                                             const mhm_dirichlet* g, double* A_vals, double* E, void* stream) {
     mhm_status st = enter(mesh, "mhm_assemble_skeleton");

@@ -483,6 +483,9 @@ extern "C" void mhm_destroy_mesh(mhm_mesh* m) {
     for (cudaStream_t ss : m->side) cudaStreamDestroy(ss);
     for (cudaEvent_t e : m->side_done) cudaEventDestroy(e);
     if (m->fork_ev) cudaEventDestroy(m->fork_ev);
+    if (m->wave_copy) cudaStreamDestroy(m->wave_copy);
+    for (cudaEvent_t e : {m->wave_start, m->wave_copied[0], m->wave_copied[1], m->wave_solved[0], m->wave_solved[1]})
+        if (e) cudaEventDestroy(e);
     cudaSetDevice(cur);
     delete m;
 }

@@ -145,6 +145,9 @@ struct mhm_mesh {
     mutable std::vector<cudaStream_t> side;
     mutable std::vector<cudaEvent_t> side_done;
     mutable cudaEvent_t fork_ev = nullptr;
+    // memory-admitted waves: the copy stream and its events (created on first use)
+    mutable cudaStream_t wave_copy = nullptr;
+    mutable cudaEvent_t wave_start = nullptr, wave_copied[2] = {nullptr, nullptr}, wave_solved[2] = {nullptr, nullptr};
 
     mhm::DeviceMesh dev() const {
         return mhm::DeviceMesh{d_geom,  d_sign,  d_rev,   d_btab, d_btab_sum,  d_gauss_x,

@@ -37,6 +37,7 @@ EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
     "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
+    "mhm_local_solve_waves",
 ]
 MHM_KERNEL_LOCAL_FP64, MHM_KERNEL_LOCAL_MIXED, MHM_KERNEL_SCHUR_FACTOR = range(3)
 MHM_N_KERNELS = 3
@@ -92,6 +93,8 @@ def lib():
         L.mhm_local_workspace_size.argtypes = [vp, i32, ctypes.POINTER(sz)]
         L.mhm_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source), i32, ctypes.POINTER(SolveOpts),
                                             vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.mhm_local_solve_waves.argtypes = [vp, vp, sz, ctypes.POINTER(Source), i32, ctypes.POINTER(SolveOpts),
+                                            vp, vp, vp, vp, vp, vp, vp, sz, vp, ctypes.POINTER(i32)]
         L.mhm_assemble_skeleton.argtypes = [vp, vp, vp, ctypes.POINTER(Dirichlet), vp, vp, vp]
         L.mhm_local_solve_batch_noalloc.argtypes = [vp, vp, ctypes.POINTER(Source), ctypes.POINTER(SolveOpts),
                                                     vp, vp, vp, vp, vp, vp, vp]
@@ -103,7 +106,8 @@ def lib():
         L.mhm_kernel_times.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
                      "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc",
-                     "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times"):
+                     "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
+                     "mhm_local_solve_waves"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -175,6 +179,22 @@ def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0, r_per_K=None, l_pe
 def mhm_local_workspace_size(mesh: Mesh, precision: int) -> int:
     n = ctypes.c_size_t()
     _check(lib().mhm_local_workspace_size(mesh.handle, precision, ctypes.byref(n)))
+    return int(n.value)
+
+
+def mhm_local_solve_waves(mesh: Mesh, kappa_host, budget_bytes: int, source: Source, precision,
+                          opts: SolveOpts | None, AK, EK, BK, FK, status, iters=None, workspace=None,
+                          stream=None) -> int:
+    """kappa_host: a contiguous float64 CPU tensor (pinned for overlapped copies) holding the
+    whole batch's kappa; returns the number of waves."""
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    if kappa_host.is_cuda or not kappa_host.is_contiguous():
+        raise ValueError("kappa_host must be a contiguous CPU tensor")
+    n = ctypes.c_int32(0)
+    _check(lib().mhm_local_solve_waves(mesh.handle, _ptr(kappa_host), int(budget_bytes), ctypes.byref(source),
+                                       precision, None if opts is None else ctypes.byref(opts),
+                                       _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters),
+                                       _ptr(workspace), ws_bytes, _stream(stream), ctypes.byref(n)))
     return int(n.value)
 
 

@@ -24,16 +24,6 @@ def dirichlet_of(w: Workload):
     return mhm.Dirichlet((mhm.ctypes.c_double * 6)(*c))
 
 
-class _RawPtr:
-    """A device address standing in for a tensor in the binding (kappa of one wave)."""
-
-    def __init__(self, addr):
-        self.addr = addr
-
-    def data_ptr(self):
-        return self.addr
-
-
 class Pipeline:
     def __init__(self, nx, ny, r, degree, m, l, device: int = 0, precision: int = mhm.MHM_FP64, r_per_K=None,
                  l_per_face=None):
@@ -101,30 +91,17 @@ class Pipeline:
         return uv, (None if err is None else err.view(M.n_K, 2))
 
     def local_waves(self, kappa_host, source, budget_bytes: int, opts=None, stream=None):
-        """Local solves in memory-admitted waves: kappa stays on the host (pinned) and is
-        streamed to the device in contiguous K ranges sized so that the kappa of one
-        wave fits in `budget_bytes`; each wave runs mhm_local_solve_batch on its range
-        (the per-K outputs are indexed by absolute K).  Returns the number of waves."""
-        import torch
-        M = self.mesh
-        per_K = M.n_fine * 8
-        wave = max(1, int(budget_bytes // per_K))
-        kh = torch.as_tensor(kappa_host).reshape(M.n_K, M.n_fine)
+        """Local solves with kappa on the host, in memory-admitted waves
+        (mhm_local_solve_waves): contiguous K ranges whose kappa fits in half of
+        `budget_bytes`, two device buffers alternating so that the copy of the next wave
+        overlaps the solves of the current one.  Returns the number of waves."""
+        kh = torch.as_tensor(kappa_host, dtype=torch.float64).reshape(-1).contiguous()
         if not kh.is_pinned():
             kh = kh.pin_memory()
-        buf = torch.empty((min(wave, M.n_K), M.n_fine), dtype=torch.float64, device=self.device)
-        # a kappa pointer for the device buffer, offset so that row K0 sits at the buffer start
-        n = 0
-        for K0 in range(0, M.n_K, wave):
-            K1 = min(M.n_K, K0 + wave)
-            buf[:K1 - K0].copy_(kh[K0:K1], non_blocking=True)
-            base = buf.data_ptr() - K0 * per_K
-            o = opts or mhm.SolveOpts(8, 1e-12, 0, 0)
-            o2 = mhm.SolveOpts(o.it_max, o.tol, K0, K1)
-            mhm.mhm_local_solve_batch(self.mesh, _RawPtr(base), source, self.precision, o2, self.AK, self.EK,
+        n = mhm.mhm_local_solve_waves(self.mesh, kh, budget_bytes, source, self.precision, opts, self.AK, self.EK,
                                       self.BK, self.FK, self.status, self.iters, self.workspace, stream)
-            torch.cuda.current_stream().synchronize()   # the buffer is reused by the next wave
-            n += 1
+        # the copies read kh until the work on the stream is done
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return n
 
     # host-side views for tests and reports

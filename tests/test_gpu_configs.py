@@ -56,6 +56,8 @@ def test_full_size_sampled_parity(name, tol):
 
 
 def test_waves_equal_one_shot():
+    """Memory-admitted waves (kappa on the host, two alternating device buffers of half the
+    budget): the one-shot result bit for bit, uniform and per-level meshes."""
     from paper_1703_10435_gb300.pipeline import Pipeline, source_of
     w = W.Workload("t", 8, 8, 5, 1, 2, 2, "log_uniform", "const", 1.0, seed=3)
     kap = W.kappa_for(w)
@@ -63,9 +65,21 @@ def test_waves_equal_one_shot():
     p1.local(torch.as_tensor(kap, device="cuda"), source_of(w))
     p2 = Pipeline.for_workload(w, 0, mhm.MHM_MIXED)
     nw = p2.local_waves(kap, source_of(w), budget_bytes=40 * w.n_fine * 8)
-    torch.cuda.synchronize()
-    assert nw == (w.n_K + 39) // 40
+    assert nw == (w.n_K + 19) // 20
     assert torch.equal(p1.AK, p2.AK) and torch.equal(p1.EK, p2.EK) and torch.equal(p1.status, p2.status)
+    # levels 3..6 per element (the waves follow the per-K kappa offsets), both precisions
+    rng = np.random.default_rng(4)
+    rs = rng.integers(3, 7, 2 * 4 * 4).astype(np.int8)
+    kl = np.concatenate([10.0 ** rng.uniform(-2, 2, 4 ** int(r)) for r in rs])
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
+        q1 = Pipeline(4, 4, 0, 1, 1, 2, 0, prec, r_per_K=rs)
+        q1.local(torch.as_tensor(kl, device="cuda"), src)
+        q2 = Pipeline(4, 4, 0, 1, 1, 2, 0, prec, r_per_K=rs)
+        n = q2.local_waves(kl, src, budget_bytes=2 * 3 * 4096 * 8)
+        assert n > 3
+        for name in ("AK", "EK", "BK", "FK", "status", "iters"):
+            assert torch.equal(getattr(q1, name), getattr(q2, name)), (prec, name)
 
 
 @pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
