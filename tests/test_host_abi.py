@@ -117,6 +117,17 @@ def test_errors_are_reported(lib):
     code = lib.mhm_local_solve_batch(M.handle, None, None, 0, None, None, None, None, None, None, None,
                                      None, 0, None)
     assert code == mhm.MHM_ERR_UNSUPPORTED
+    code = lib.mhm_local_solve_waves(M.handle, None, 0, None, 0, None, None, None, None, None, None, None,
+                                     None, 0, None, None)
+    assert code == mhm.MHM_ERR_UNSUPPORTED
+    # a degree per face: negative degrees and more than 16 multipliers per face are refused
+    ne = 2 * 3 + 2 * 3 + 4
+    with pytest.raises(mhm.MHMError) as e:
+        mhm.Mesh(2, 2, 2, 1, 1, 0, device=-1, l_per_face=[-1] + [1] * (ne - 1))
+    assert e.value.code == mhm.MHM_ERR_INVALID_ARG
+    with pytest.raises(mhm.MHMError) as e:
+        mhm.Mesh(2, 2, 2, 1, 4, 0, device=-1, l_per_face=[4] + [1] * (ne - 1))
+    assert e.value.code == mhm.MHM_ERR_INVALID_ARG
 
 
 def test_per_element_levels_queries():
