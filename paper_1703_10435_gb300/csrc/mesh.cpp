@@ -2,6 +2,7 @@
 // normals and signs, the multiplier space Lambda_H^{m,l} and the tables the
 // kernels read, built on the host and uploaded once.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <map>
 #include <utility>
@@ -322,6 +323,21 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
             m->nbrs.push_back(kv.second);
         }
         m->nbr_ptr[e + 1] = (int32_t)m->nbrs.size();
+    }
+    // the skeleton CSR and the saddle-point CSR index their entries in int32 (as do the
+    // sparse library calls of the global solve): refuse meshes beyond that
+    {
+        int64_t nnz = 0, bt = 0;
+        for (int64_t e = 0; e < m->ne; ++e) {
+            int64_t len = 0;
+            for (int b = m->nbr_ptr[e]; b < m->nbr_ptr[e + 1]; ++b) len += dofs(m->nbrs[b].f);
+            nnz += dofs(e) * len;
+            bt += dofs(e) * (m->face_K[2 * e + 1] >= 0 ? 2 : 1);
+        }
+        if (nnz + 2 * bt > (int64_t)INT32_MAX) {
+            delete m;
+            return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: skeleton system beyond 2^31 entries (mesh too large)");
+        }
     }
     m->csr_rowptr.assign(m->nlam + 1, 0);
     for (int64_t e = 0; e < m->ne; ++e) {
