@@ -1,14 +1,16 @@
 """Benchmark of the MHM hot path: local solves + skeleton assembly, coarse
-elements per second, on the heterogeneous workload (32x32 squares = 2048 coarse
-triangles, P1 locals refined 5 times = 561 DOFs, m = 2 subfaces with P2
-multipliers = 18 lambda right-hand sides + 1 source, log-uniform kappa with
-log10 kappa ~ U[-2, 2] per fine triangle, f = 1).
+elements per second, on the mixed-precision workload (128x128 squares = 32768
+coarse triangles, P1 locals refined 5 times = 561 DOFs, m = 2 subfaces with P2
+multipliers = 18 lambda right-hand sides + 1 source, kappa a Gaussian random
+field of correlation length 0.02 exponentiated to contrast 1e4, f = 1).
 
 One step = mhm_local_solve_batch + mhm_assemble_skeleton over all coarse
 triangles.  Both arithmetic paths are timed: the headline `value` is the
 mixed-precision path (FP32 factorisation and solves, FP64 residuals), the
 all-FP64 path is reported beside it, with the L2 difference of the
-reconstructed u between the two.  Prints one JSON line.
+multipliers and of the reconstructed u between the two, and a sample of
+coarse triangles checked against the FP64 oracle.  The 2048-element
+log-uniform workload is timed as a secondary line.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
@@ -28,7 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_hetero_fp64"
+WORKLOAD = "c3_grf_mixed"
+SECONDARY = "c2_hetero_fp64"
 
 
 def algorithmic_fmas(P, N, R):
@@ -184,32 +187,38 @@ def measured_peaks():
         return {}
 
 
-# Kernel sources whose hash a recorded ncu traffic figure belongs to.
+# Kernel sources whose hash a recorded ncu traffic figure belongs to; the summary of
+# kernel k on workload w is profiles/<k>_<short name of w>.md.
 TRAFFIC_SOURCES = {
-    "k_local_mixed": ("k_local_mixed_c2.md", ["local_mixed.cu", "local_common.cuh", "mhm_internal.h"]),
-    "k_local_fp64": ("k_local_fp64_c2.md", ["local_fp64.cu", "local_common.cuh", "mhm_internal.h"]),
+    "k_local_mixed": ["local_mixed.cu", "local_common.cuh", "mhm_internal.h"],
+    "k_local_fp64": ["local_fp64.cu", "local_common.cuh", "mhm_internal.h"],
 }
+PROFILE_TAG = {"c2_hetero_fp64": "c2", "c3_grf_mixed": "c3", "c5_p2_large": "c5", "c4_channels": "c4"}
+
+
+def sources_sha256(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1703_10435_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` on
-    the 2048-element workload, from the ncu summary under profiles/, or None when the
-    kernel's sources changed since that capture (hash mismatch) or for other workloads."""
-    import hashlib
-    if workload != "c2_hetero_fp64" or kernel not in TRAFFIC_SOURCES:
+    `workload`, from its ncu summary under profiles/ ("traffic_bytes_per_launch", per launch
+    of the bench's launch shape), or None when there is none or the kernel's sources changed
+    since that capture (hash mismatch)."""
+    if kernel not in TRAFFIC_SOURCES or workload not in PROFILE_TAG:
         return None
-    md, srcs = TRAFFIC_SOURCES[kernel]
-    root = os.path.dirname(os.path.abspath(__file__))
     try:
-        text = open(os.path.join(root, "profiles", md)).read()
-        h = hashlib.sha256()
-        for f in srcs:
-            with open(os.path.join(root, "paper_1703_10435_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
+        text = open(os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, PROFILE_TAG[workload]))).read()
+        sha = sources_sha256(kernel)
     except OSError:
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith(("traffic_bytes", "sources_sha")))
-    if fields.get("sources_sha256", "").strip() != h.hexdigest():
+    if fields.get("sources_sha256", "").strip() != sha or "traffic_bytes_per_launch" not in fields:
         return None
     return float(fields["traffic_bytes_per_launch"])
 
@@ -302,121 +311,259 @@ def time_path(p, kap, src, gd, steps, warmup, flush, stream, barrier):
     return step_ms, local_ms, kern
 
 
+def oracle_locals(w, Ks, kaps):
+    """The oracle's local contributions and local solutions of the coarse triangles Ks
+    (a worker): per K (A_K, E_K, B_K, F_K, eta)."""
+    from oracle.local import solve_local
+    from oracle.mesh import build_mesh
+    from oracle.run import source_fn
+    mesh = build_mesh(w.nx, w.ny, w.m, w.l)
+    f = float(w.source_value) if w.source == "const" else source_fn("sinsin", w.source_value, w.source_freq)
+    out = []
+    for i, K in enumerate(Ks):
+        o = solve_local(mesh, int(K), w.r, w.degree, kaps[i], f)
+        out.append((o.AK, o.EK, o.BK, o.FK, o.eta))
+    return out
+
+
+def block_error(AK, EK, BK, FK, o):
+    """Largest entry error of one K's blocks against the oracle's: A_K entries against
+    sqrt(|A_ii| |A_jj|) (A_K is a Gram matrix), E_K and B_K against the block's largest
+    entry (E_K against |A_K| |F_K| / |B_K| when it vanishes, as for a constant f), F_K
+    relative."""
+    oA, oE, oB, oF = o[0], o[1], o[2], o[3]
+    d = np.sqrt(np.abs(np.diag(oA)))
+    eA = float((np.abs(AK - oA) / np.maximum(np.outer(d, d), 1e-300)).max())
+    bmax = max(float(np.abs(oB).max()), 1e-300)
+    sE = max(float(np.abs(oE).max()), float(np.abs(oA).max()) * abs(oF) / bmax, 1e-300)
+    return max(eA, float(np.abs(EK - oE).max()) / sE, float(np.abs(BK - oB).max()) / bmax,
+               abs(FK - oF) / max(abs(oF), 1e-300))
+
+
+def run_workload(args, w, rank, world, local_rank, dev, barrier, steps, warmup, flush, full):
+    """Times both paths on workload w; with `full`, also the end-to-end run, the solution
+    errors and the oracle sample.  Returns a dict of results (rank 0) or None."""
+    import torch
+    import torch.distributed as dist
+    from paper_1703_10435_gb300 import mhm
+    from paper_1703_10435_gb300 import workloads as W
+    from paper_1703_10435_gb300.pipeline import Pipeline, dirichlet_of, source_of
+
+    kap = W.kappa_for_torch(w, dev).reshape(-1).contiguous()
+    src, gd = source_of(w), dirichlet_of(w)
+    stream = torch.cuda.current_stream()
+    p64 = Pipeline.for_workload(w, local_rank, mhm.MHM_FP64)
+    pmx = Pipeline.for_workload(w, local_rank, mhm.MHM_MIXED)
+    sampler = ClockSampler(local_rank, args.clocks_csv) if full else None
+    if sampler:
+        sampler.start()
+    step64, local64, kern64 = time_path(p64, kap, src, gd, steps, warmup, flush, stream, barrier)
+    stepmx, localmx, kernmx = time_path(pmx, kap, src, gd, steps, warmup, flush, stream, barrier)
+    clocks = sampler.stop() if sampler else None
+    for p in (p64, pmx):
+        assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
+    t_mx, t_64 = float(stepmx.sum()), float(step64.sum())
+    res = {"w": w, "p64": p64, "pmx": pmx, "kap": kap, "stepmx": stepmx, "localmx": localmx, "kern64": kern64,
+           "kernmx": kernmx, "clocks": clocks, "t_mx": t_mx, "t_64": t_64}
+    if full:
+        # end to end through the C ABI with host buffers (mixed path): kappa H2D in,
+        # skeleton system (A, E, B, F) D2H out
+        kap_pin = kap.cpu().pin_memory()
+        outs = [pmx.A_vals, pmx.E, pmx.BK, pmx.FK]
+        outs_pin = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        kap_dev2 = torch.empty_like(kap)
+        res["h2d"] = kap_pin.numel() * 8
+        res["d2h"] = sum(o.numel() * o.element_size() for o in outs)
+        for _ in range(2):
+            kap_dev2.copy_(kap_pin, non_blocking=True)
+            pmx.step(kap_dev2, src, gd)
+            for o, h in zip(outs, outs_pin):
+                h.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            kap_dev2.copy_(kap_pin, non_blocking=True)
+            pmx.step(kap_dev2, src, gd)
+            for o, h in zip(outs, outs_pin):
+                h.copy_(o, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["t_e2e"] = e0.elapsed_time(e1)
+        del kap_dev2
+    if world > 1:
+        tt = torch.tensor([res["t_mx"], res["t_64"], res.get("t_e2e", 0.0)], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        res["t_mx"], res["t_64"], res["t_e2e"] = [float(v) for v in tt]
+    if full and not args.no_solution_check:
+        res["error"] = solution_errors(args, w, p64, pmx, kap, src)
+    return res if rank == 0 else None
+
+
+class MemSampler:
+    """Samples the device's used memory (cudaMemGetInfo) from a thread during a call."""
+
+    def __init__(self, dev):
+        import threading
+        self.dev, self.peak, self.stop_ev = dev, 0, threading.Event()
+        self.t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        import torch
+        torch.cuda.set_device(self.dev)
+        while not self.stop_ev.is_set():
+            free, total = torch.cuda.mem_get_info(self.dev)
+            self.peak = max(self.peak, total - free)
+            time.sleep(0.005)
+
+    def __enter__(self):
+        import torch
+        free, total = torch.cuda.mem_get_info(self.dev)
+        self.base = total - free
+        self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop_ev.set()
+        self.t.join()
+
+
+def solution_errors(args, w, p64, pmx, kap, src):
+    """Multipliers, u0 and reconstructed u of the mixed path against the FP64 path (whole
+    batch), and a sample of coarse triangles against the FP64 oracle: the per-K blocks of
+    both paths entry by entry, and u on those K from the oracle's local solutions combined
+    with the path's own multipliers (Eq. "u_Hh")."""
+    import torch
+    from oracle.mesh import build_mesh
+    from paper_1703_10435_gb300 import workloads as W
+    dev = kap.device
+    out = {}
+    sols = {}
+    from paper_1703_10435_gb300 import mhm
+    for name, p in (("fp64", p64), ("mixed", pmx)):
+        torch.cuda.synchronize()
+        g0 = time.perf_counter()
+        try:
+            with MemSampler(dev) as ms:
+                lam, u0 = p.solve_global()
+                torch.cuda.synchronize()
+        except mhm.MHMError as e:
+            out["global_solve_error_" + name] = str(e)
+            return out
+        g1 = time.perf_counter()
+        u, _ = p.reconstruct(kap, src)
+        torch.cuda.synchronize()
+        g2 = time.perf_counter()
+        sols[name] = (lam.clone(), u0.clone(), u)
+        out["global_solve_s_" + name] = g1 - g0
+        out["reconstruct_s_" + name] = g2 - g1
+        out["global_solve_device_bytes_above_base_" + name] = int(ms.peak - ms.base)
+    (l64, z64, u64), (lmx, zmx, umx) = sols["fp64"], sols["mixed"]
+    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    out.update({"u_rel_l2_mixed_vs_fp64": rel(umx, u64), "lambda_rel_l2_mixed_vs_fp64": rel(lmx, l64),
+                "u0_rel_l2_mixed_vs_fp64": rel(zmx, z64), "n_lambda": int(l64.numel()), "n_K": int(z64.numel())})
+    if w.r_per_K is not None or args.oracle_sample <= 0:
+        return out
+    # the oracle on a sample of coarse triangles (first, last and seeded picks)
+    rng = np.random.default_rng(7)
+    Ks = sorted(set([0, w.n_K - 1] + [int(k) for k in rng.integers(0, w.n_K, args.oracle_sample - 2)]))
+    kap_np = W.kappa_for(w, np.asarray(Ks))
+    cores = min(os.cpu_count() or 1, len(Ks))
+    pool = make_pool(cores)
+    chunks = np.array_split(np.arange(len(Ks)), cores)
+    futs = [pool.submit(oracle_locals, w, [Ks[i] for i in c], kap_np[c]) for c in chunks if len(c)]
+    orc = [o for fu in futs for o in fu.result()]
+    pool.shutdown()
+    mesh = build_mesh(w.nx, w.ny, w.m, w.l)
+    nI = w.n_I
+    samp = {"K": Ks, "kappa_max_abs_diff": float(np.abs(kap.view(w.n_K, -1)[Ks].cpu().numpy() - kap_np).max())}
+    for name, p in (("fp64", p64), ("mixed", pmx)):
+        AK, EK, BK, FK = p.blocks()
+        lam, u0, u = sols[name]
+        lam, u0 = lam.cpu().numpy(), u0.cpu().numpy()
+        uK = u.view(w.n_K, -1)[Ks].cpu().numpy()
+        be, ue = 0.0, []
+        for i, (K, o) in enumerate(zip(Ks, orc)):
+            be = max(be, block_error(AK[K], EK[K], BK[K], FK[K], o))
+            eta = o[4]
+            uo = u0[K] + eta[:, :nI] @ lam[mesh.local_lambda(K)] + eta[:, nI]
+            ue.append((np.sum((uK[i] - uo) ** 2), np.sum(uo ** 2)))
+        ue = np.asarray(ue)
+        samp["blocks_max_entry_err_" + name] = be
+        samp["u_rel_l2_vs_oracle_" + name] = float(math.sqrt(ue[:, 0].sum() / ue[:, 1].sum()))
+    samp["what"] = ("per-K blocks A_K, E_K, B_K, F_K entry by entry against the oracle's (A_K per entry against "
+                    "sqrt(|A_ii||A_jj|)); u on these K: the oracle's local solutions combined with the path's own "
+                    "multipliers and u0, against the path's reconstructed u")
+    out["oracle_sample"] = samp
+    return out
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_1703_10435_gb300 import build, mhm
     from paper_1703_10435_gb300 import workloads as W
-    from paper_1703_10435_gb300.pipeline import Pipeline, dirichlet_of, source_of
 
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    kap_host = W.kappa_for(w)
-    kap = torch.as_tensor(kap_host, device=dev).contiguous()
-    src, gd = source_of(w), dirichlet_of(w)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2 (129 MB)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    p64 = Pipeline.for_workload(w, local_rank, mhm.MHM_FP64)
-    pmx = Pipeline.for_workload(w, local_rank, mhm.MHM_MIXED)
-    sampler = ClockSampler(local_rank, args.clocks_csv)
-    sampler.start()
-    step64, local64, kern64 = time_path(p64, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
-    stepmx, localmx, kernmx = time_path(pmx, kap, src, gd, args.steps, args.warmup, flush, stream, barrier)
-    clocks = sampler.stop()
-    for p in (p64, pmx):
-        assert int(p.status.abs().sum()) == 0, "local solve status nonzero"
-    itv = pmx.iters.cpu().numpy()
-    passes = float(itv[itv > 0].mean()) if np.any(itv > 0) else 0.0   # elements refined in mixed precision
-
-    # end to end through the C ABI with host buffers (mixed path): kappa H2D in,
-    # skeleton system (A, E, B, F) D2H out
-    kap_pin = torch.as_tensor(kap_host).pin_memory()
-    outs = [pmx.A_vals, pmx.E, pmx.BK, pmx.FK]
-    outs_pin = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-    kap_dev2 = torch.empty_like(kap)
-    h2d = kap_pin.numel() * 8
-    d2h = sum(o.numel() * o.element_size() for o in outs)
-    for _ in range(2):
-        kap_dev2.copy_(kap_pin, non_blocking=True)
-        pmx.step(kap_dev2, src, gd)
-        for o, h in zip(outs, outs_pin):
-            h.copy_(o, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        kap_dev2.copy_(kap_pin, non_blocking=True)
-        pmx.step(kap_dev2, src, gd)
-        for o, h in zip(outs, outs_pin):
-            h.copy_(o, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1)
-
-    t_mx, t_64 = float(stepmx.sum()), float(step64.sum())
-    if world > 1:
-        tt = torch.tensor([t_mx, t_64, t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_mx, t_64, t_e2e = [float(v) for v in tt]
-
-    # L2 difference of the reconstructed u (and of the multipliers) between the two paths
-    err = None
-    if not args.no_solution_check:
-        g0 = time.perf_counter()
-        lam64, _ = p64.solve_global()
-        lammx, _ = pmx.solve_global()
-        u64, _ = p64.reconstruct(kap, src)
-        umx, _ = pmx.reconstruct(kap, src)
-        torch.cuda.synchronize()
-        g1 = time.perf_counter()
-        err = {"u_rel_l2_mixed_vs_fp64": float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)),
-               "lambda_rel_l2_mixed_vs_fp64": float(torch.linalg.norm(lammx - lam64) / torch.linalg.norm(lam64)),
-               "global_solve_and_reconstruct_s_both_paths": g1 - g0}
+    r = run_workload(args, w, rank, world, local_rank, dev, barrier, args.steps, args.warmup, flush, True)
+    sec = None
+    if args.secondary and args.secondary != w.name:
+        w2 = W.WORKLOADS[args.secondary]
+        r2 = run_workload(args, w2, rank, world, local_rank, dev, barrier, args.steps, args.warmup, flush, False)
+        if rank == 0:
+            u2 = world * w2.n_K * args.steps
+            sec = {"workload": w2.name, "config": workload_config(w2), "value": u2 / (r2["t_mx"] * 1e-3),
+                   "fp64_value": u2 / (r2["t_64"] * 1e-3), "mixed_over_fp64": r2["t_64"] / r2["t_mx"],
+                   "ms_per_step": r2["t_mx"] / args.steps, "unit": "coarse elements/s"}
+            del r2
     if rank != 0:
         return
+    p64, pmx, kern64, kernmx = r["p64"], r["pmx"], r["kern64"], r["kernmx"]
+    t_mx, t_64, t_e2e = r["t_mx"], r["t_64"], r["t_e2e"]
+    clocks, localmx = r["clocks"], r["localmx"]
+    itv = pmx.iters.cpu().numpy()
+    passes = float(itv[itv > 0].mean()) if np.any(itv > 0) else 0.0   # elements refined in mixed precision
 
     units = world * w.n_K * args.steps
     value, v64, e2e = units / (t_mx * 1e-3), units / (t_64 * 1e-3), units / (t_e2e * 1e-3)
     pipes = mhm.mhm_measure_pipes(local_rank)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     clk = clocks["sm_max_mhz"] if clocks else 2070.0
-    # GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal over 152 SMs at 2.07 GHz);
-    # 128 FP32 FMA per clock per SM
+    # GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal over 152 SMs at 2.07 GHz)
     peak64 = 2 * 2 * sms * clk * 1e6 / 1e12
-    peak32 = 2 * 128 * sms * clk * 1e6 / 1e12
     # Kernel durations over the timed region: the library's CUDA events around each
     # local-solve launch, on the launching stream.
-    # Algorithmic work per step, summed over the refinement levels (one launch per level
-    # and step); achieved = work per step / kernel time per step (= per launch when a
-    # step is one launch).
+    # Algorithmic work per step, summed over the refinement levels; achieved = work per
+    # step / kernel time per step.
     lv = level_counts(w)
     R = w.n_I + 1
-    it_all = pmx.iters.cpu().numpy()
     rk = w.r_per_K if w.r_per_K is not None else np.full(w.n_K, w.r)
-    fl64 = 2.0 * sum(c * algorithmic_fmas(w.degree, 1 << r, R) for r, c in lv.items())
+    fl64 = 2.0 * sum(c * algorithmic_fmas(w.degree, 1 << rr, R) for rr, c in lv.items())
     t_k64 = kern64["k_local_fp64"][1] * 1e-3 / args.steps if "k_local_fp64" in kern64 else None
     t_kmx = kernmx["k_local_mixed"][1] * 1e-3 / args.steps if "k_local_mixed" in kernmx else None
     t_kfac = kernmx["k_schur_factor"][1] * 1e-3 / args.steps if "k_schur_factor" in kernmx else None
     n64, nmx, nfac = [kern.get(k, (0, 0.0))[0] for kern, k in ((kern64, "k_local_fp64"), (kernmx, "k_local_mixed"),
                                                                 (kernmx, "k_schur_factor"))]
     fl_res, fl_tc = 0.0, 0.0
-    for r, c in lv.items():
-        if not mixed_level(w, r):
+    for rr, c in lv.items():
+        if not mixed_level(w, rr):
             continue
-        it = it_all[rk == r]
+        it = itv[rk == rr]
         p_r = float(it[it > 0].mean()) if np.any(it > 0) else 0.0
-        res = residual_fmas_per_pass(w, 1 << r)
+        res = residual_fmas_per_pass(w, 1 << rr)
         if res is not None:
             fl_res += 2.0 * res * p_r * c
         if w.degree == 1:
-            N = 1 << r
+            N = 1 << rr
             sizes = [N + 1 - l_ - (l_ == 0) for l_ in range(N + 1)]
             fl_tc += 2.0 * R * (2 * sum(b * b for b in sizes) - sizes[-1] ** 2) * p_r * c
     fl_res = fl_res or None
@@ -429,17 +576,20 @@ def run_ours(args, w, rank, world, local_rank):
               "achieved": fl_tc / t_kmx / 1e12, "peak": peak_tf32, "unit": "TFLOP/s",
               "frac": (fl_tc / t_kmx / 1e12 / peak_tf32) if peak_tf32 else None,
               "peak_source": "MEASURED_PEAKS.json bf16 burst x 1.1/2.25 (nominal tf32/bf16)"}
+    launch_kmx = t_kmx * args.steps / nmx if (t_kmx and nmx) else None
     roof_mx = {"kernel": "k_local_mixed", "bound": "alu", "pipe": "fp64 (refinement residuals)",
                "achieved": (fl_res / t_kmx / 1e12) if (fl_res and t_kmx) else None, "peak": peak64, "unit": "TFLOP/s",
                "frac": (fl_res / t_kmx / 1e12 / peak64) if (fl_res and t_kmx) else None,
                "traffic": recorded_traffic("k_local_mixed", w.name),
+               "traffic_unit": "bytes per launch (%d K per launch)" % (w.n_K * args.steps // max(nmx, 1)),
                "flops_per_step": fl_res, "kernel_ms_per_step": t_kmx * 1e3 if t_kmx else None, "launches": nmx,
+               "kernel_ms_per_launch": launch_kmx * 1e3 if launch_kmx else None,
                "refinement_passes_mean": passes,
                "peak_source": "2 FP64 FMA/clk/SM x SMs x max SM clock", "peak_measured_microbench": pipes["fp64_gflops"] / 1e3,
                "tensor": tc,
                "factor_kernel": {"kernel": "k_schur_factor", "kernel_ms_per_step": t_kfac * 1e3 if t_kfac else None,
                                  "launches": nfac},
-               "levels": {str(r): c for r, c in lv.items()},
+               "levels": {str(k): c for k, c in lv.items()},
                "fp64_equivalent_local_solve_tflops": fl64 / (float(localmx.mean()) * 1e-3) / 1e12}
     roof_64 = {"kernel": "k_local_fp64", "bound": "alu", "pipe": "fp64",
                "achieved": fl64 / t_k64 / 1e12 if t_k64 else None, "peak": peak64, "unit": "TFLOP/s",
@@ -471,17 +621,19 @@ def run_ours(args, w, rank, world, local_rank):
                    "parallelism": "K-range shard per GPU" if world > 1 else "single GPU"}),
         "fp64_path": {"value": v64, "ms_per_step": t_64 / args.steps, "dtype": "f64", "roofline": roof_64},
         "mixed_over_fp64": value / v64,
-        "error": err,
+        "error": r.get("error"),
         "local_solve_ms": float(localmx.mean()),
-        "skeleton_ms": float((stepmx - localmx).mean()),
+        "skeleton_ms": float((r["stepmx"] - localmx).mean()),
         "roofline": roof_mx,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e, "unit": "coarse elements/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e, "unit": "coarse elements/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
         # our kernels in the timed region of the headline (mixed) path: the local-solve
         # launches recorded by the library plus the two skeleton kernels per step
         "gpu_launches": sum(n for n, _ in kernmx.values()) + 2 * args.steps,
         "clocks": clocks,
         "pipes_gflops": pipes,
+        "secondary": sec,
     }
     print(json.dumps(line), flush=True)
 
@@ -497,6 +649,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="file for the raw nvidia-smi samples (default: temp dir)")
     ap.add_argument("--no-solution-check", action="store_true")
+    ap.add_argument("--secondary", default=SECONDARY, help="second workload timed beside the headline ('' = none)")
+    ap.add_argument("--oracle-sample", type=int, default=12, help="coarse triangles checked against the oracle")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -77,9 +77,22 @@ typedef int32_t mhm_status;
 #define MHM_FP64 0   /* factorisation, solves and face integrals in FP64 */
 #define MHM_MIXED 1  /* FP32 factorisation and solves, FP64 residuals and refinement */
 
-/* Source term f of -div(kappa grad u) = f. */
+/* Source term f of -div(kappa grad u) = f (Eq. "etaf": the load (f, phi_w)_K of the
+ * source subproblem, and F_K = (f, 1)_K of Eq. "mat_global").  The integrals over every
+ * fine triangle use the collapsed (Duffy) 4 x 4 Gauss rule: with a_i, w_i (i = 0..3) the
+ * 4-point Gauss-Legendre nodes and weights on [0, 1], point k = 4 i + j of a fine triangle
+ * with vertices (X0, X1, X2) (the kappa order below lists them: "up" (i,j),(i+1,j),(i,j+1),
+ * "down" (i+1,j),(i+1,j+1),(i,j+1)) is X0 + xi (X1 - X0) + eta (X2 - X0) with xi = a_i,
+ * eta = a_j (1 - a_i), weight w_i w_j (1 - a_i) times twice the triangle's area. */
 #define MHM_SRC_CONST 0   /* f = value */
 #define MHM_SRC_SINSIN 1  /* f = value * 2 (freq pi)^2 sin(freq pi x) sin(freq pi y) */
+#define MHM_SRC_QUAD 2    /* f given by its values at those 16 points of every fine triangle:
+                           * values_dev (device, caller-owned, read during the call's work
+                           * on the stream) holds 16 doubles per fine triangle in the layout
+                           * of kappa, i.e. the 16 values of fine triangle t of K start at
+                           * 16 (kappa offset of K + t); value and freq are ignored.  Any f
+                           * whose point values the caller can evaluate (paper Sec. 4.2,
+                           * Eq. "source_term": (f, w)_K for a general f). */
 
 typedef struct mhm_mesh mhm_mesh;
 
@@ -104,6 +117,7 @@ typedef struct {
     int32_t kind;     /* MHM_SRC_* */
     double value;
     double freq;
+    const double* values_dev;  /* MHM_SRC_QUAD only (else ignored, may be NULL) */
 } mhm_source;
 
 /* Dirichlet data g = c[0] + c[1] x + c[2] y + c[3] x^2 + c[4] x y + c[5] y^2 on
@@ -165,6 +179,9 @@ void mhm_destroy_mesh(mhm_mesh* mesh);
 #define MHM_Q_KAPPA_OFFSET 12  /* int64[n_K+1] first kappa value of each K (4^r_K values per K) */
 #define MHM_Q_NODAL_OFFSET 13  /* int64[n_K+1] first value of each K in mhm_reconstruct's u_nodal */
 #define MHM_Q_FACE_DEGREE 14   /* int8[n_faces] multiplier degree l_e of each face */
+#define MHM_Q_SYSTEM_NNZ 15    /* int64[2]: entries of the saddle-point system [A B^T; B 0] as counted
+                                  before the tables are built (mhm_create_mesh refuses meshes whose
+                                  count exceeds 2^31 - 1: the CSR tables index in int32), and as built */
 /* Copies the queried table into host_out (bytes must be >= its size).
  * Errors: INVALID_ARG (unknown query, short buffer). */
 mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, size_t bytes);
@@ -294,6 +311,29 @@ mhm_status mhm_solve_global(const mhm_mesh* mesh, const double* A_vals_dev, cons
 mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
                            const double* lambda_dev, const double* u0_dev, const mhm_exact* exact,
                            double* u_nodal_dev, double* err_sq_dev, void* stream);
+
+/* ---------------------------------------------------------------- status --- */
+
+/* Outcome word of the local solves on a mesh: a device word owned by the mesh that the
+ * kernels of mhm_local_solve_batch, mhm_local_solve_waves and
+ * mhm_local_solve_batch_noalloc update in stream order (atomic OR), so that a caller learns
+ * of failures without reading the per-K status array:
+ *   bit (1u << c)  some element finished with the final per-K status c: MHM_ERR_NOT_CONVERGED
+ *                  (refinement hit it_max), MHM_ERR_INVALID_ARG (non-positive pivot),
+ *                  MHM_ERR_TIMEOUT (a bounded wait for the staged operators ran out);
+ *                  with the default FP64 re-solve of failed mixed elements, only the
+ *                  outcome of the re-solve counts;
+ *   MHM_STATUS_REFINED_IN_FP64  some elements whose mixed refinement failed were solved
+ *                  again by the FP64 path (their status is then OK; informational). */
+#define MHM_STATUS_REFINED_IN_FP64 (1u << 16)
+
+/* Waits for the work queued on `stream` (a cudaStream_t, NULL = legacy default stream),
+ * reads the mesh's outcome word into *word_out (may be NULL) and clears it.  Returns the
+ * most severe final code recorded since the last read (MHM_ERR_TIMEOUT, then
+ * MHM_ERR_INVALID_ARG, then MHM_ERR_NOT_CONVERGED), MHM_OK if none; the calls of the
+ * recorded solves must have been issued on `stream` or ordered before its current work.
+ * Errors: INVALID_ARG (NULL or host-only mesh), CUDA. */
+mhm_status mhm_sync_status(const mhm_mesh* mesh, void* stream, uint32_t* word_out);
 
 /* ------------------------------------------------------------------ misc --- */
 

@@ -85,6 +85,15 @@ size_t local_workspace_bytes(const mhm_mesh* mesh, int32_t precision) {
     return bytes;
 }
 
+mhm_status check_source(const mhm_source* f, const char* who) {
+    if (!f) return fail(MHM_ERR_INVALID_ARG, std::string(who) + ": NULL source");
+    if (f->kind != MHM_SRC_CONST && f->kind != MHM_SRC_SINSIN && f->kind != MHM_SRC_QUAD)
+        return fail(MHM_ERR_INVALID_ARG, std::string(who) + ": unknown source kind");
+    if (f->kind == MHM_SRC_QUAD && !f->values_dev)
+        return fail(MHM_ERR_INVALID_ARG, std::string(who) + ": MHM_SRC_QUAD needs values_dev");
+    return MHM_OK;
+}
+
 // Makes the mesh's device current; fails for host-only meshes.
 static mhm_status enter(const mhm_mesh* mesh, const char* who) {
     if (!mesh) return fail(MHM_ERR_INVALID_ARG, std::string(who) + ": NULL mesh");
@@ -118,8 +127,8 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
     if (st) return st;
     if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: NULL pointer argument");
-    if (f->kind != MHM_SRC_CONST && f->kind != MHM_SRC_SINSIN)
-        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown source kind");
+    st = check_source(f, "mhm_local_solve_batch");
+    if (st) return st;
     mhm_solve_opts o{};
     o.it_max = 8;
     o.tol = 1e-12;
@@ -196,6 +205,8 @@ extern "C" mhm_status mhm_local_solve_waves(const mhm_mesh* mesh, const double* 
     mhm_status st = enter(mesh, "mhm_local_solve_waves");
     if (st) return st;
     if (!kappa_host || !f) return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_waves: NULL pointer argument");
+    st = check_source(f, "mhm_local_solve_waves");
+    if (st) return st;
     mhm_solve_opts o{};
     o.it_max = 8;
     o.tol = 1e-12;
@@ -262,8 +273,15 @@ extern "C" mhm_status mhm_local_solve_waves(const mhm_mesh* mesh, const double* 
                                    workspace, ws_bytes, stream);
         if (!st) ce = cudaEventRecord(mesh->wave_solved[b], s);
     }
+    // every copy queued on the copy stream is ordered before the frees on `s`, whichever
+    // call above failed: join the copy stream into `s` first (if even that fails, wait for
+    // the copy stream on the host rather than free a buffer a copy may still write)
+    cudaError_t je = cudaEventRecord(mesh->wave_start, mesh->wave_copy);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(s, mesh->wave_start, 0);
+    if (je != cudaSuccess) cudaStreamSynchronize(mesh->wave_copy);
     for (int b = 0; b < nbuf; ++b) cudaFreeAsync(buf[b], s);
     if (ce != cudaSuccess) return cuda_fail(ce, "mhm_local_solve_waves");
+    if (je != cudaSuccess) return cuda_fail(je, "mhm_local_solve_waves: joining the copy stream");
     return st;
 }
 
@@ -328,6 +346,21 @@ extern "C" mhm_status mhm_measure_pipes(int32_t device, double* out) {
     out[1] = time_fma<float, 16>(sms, 1 << 16);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mhm_measure_pipes");
+    return MHM_OK;
+}
+
+extern "C" mhm_status mhm_sync_status(const mhm_mesh* mesh, void* stream, uint32_t* word_out) {
+    if (!mesh || mesh->device < 0 || !mesh->d_sword)
+        return fail(MHM_ERR_INVALID_ARG, "mhm_sync_status: NULL or host-only mesh");
+    MHM_CUDA_TRY(cudaSetDevice(mesh->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t w = 0;
+    MHM_CUDA_TRY(cudaMemcpyAsync(&w, mesh->d_sword, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    MHM_CUDA_TRY(cudaMemsetAsync(mesh->d_sword, 0, sizeof(uint32_t), s));
+    MHM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (word_out) *word_out = w;
+    for (int c : {MHM_ERR_TIMEOUT, MHM_ERR_INVALID_ARG, MHM_ERR_NOT_CONVERGED})
+        if (w & (1u << c)) return c;
     return MHM_OK;
 }
 

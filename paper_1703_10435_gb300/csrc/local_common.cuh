@@ -176,6 +176,23 @@ __device__ __forceinline__ double source_value(int kind, double value, double fr
     return c * sinpi(freq * x) * sinpi(freq * y);
 }
 
+// f at point k = 4 i + j of the collapsed 4 x 4 Gauss rule of a fine triangle: the caller's
+// value there (MHM_SRC_QUAD; fq holds the triangle's 16 values), else the analytic source.
+__device__ __forceinline__ double source_at(int kind, double value, double freq, double x, double y,
+                                            const double* fq, int k) {
+    if (kind == MHM_SRC_QUAD) return fq[k];
+    return source_value(kind, value, freq, x, y);
+}
+
+// The 16 point values of f on fine triangle (up, i, j) of the element whose kappa starts at
+// kap (the values array is laid out like kappa with 16 values per fine triangle), or NULL
+// when f is not given by values.
+__device__ __forceinline__ const double* quad_of(const double* vals, const double* kappa, const double* kap, int N,
+                                                 bool up, int i, int j) {
+    if (!vals) return nullptr;
+    return vals + 16 * ((kap - kappa) + (int64_t)j * (2 * N - j) + (up ? i : (N - j) + i));
+}
+
 // Faces of lattice point (x, y): bit a set if it lies on local face a
 // (face 2: y = 0, face 0: x + y = PN, face 1: x = 0), with the face-local
 // position k_loc along the face (from vertex a+1 towards vertex a+2).

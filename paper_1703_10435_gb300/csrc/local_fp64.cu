@@ -47,6 +47,8 @@ struct Fp64Args {
     int rhs0;      // first right-hand-side column of the window
     int rows;      // window rows (largest b + b')
     int src_kind;
+    const double* src_vals;   // MHM_SRC_QUAD: 16 values per fine triangle, laid out like kappa
+    uint32_t* sword;          // the mesh's outcome word (mhm_sync_status)
     double src_value, src_freq;
     int64_t K0, K1;  // launch indices [K0, K1) within the level
     double* win;     // wide window: slots of win_doubles per block (NULL: window in shared memory)
@@ -89,7 +91,7 @@ __device__ double block_sum(double v, double* red) {
 
 // Cell integral of f phi_a over fine triangle (X0, X1, X2) by the collapsed
 // 4 x 4 Gauss rule; phi_a = -1 means the integral of f itself.
-__device__ double cell_source(const Fp64Args& g, const double X[3][2], int P, int a) {
+__device__ double cell_source(const Fp64Args& g, const double X[3][2], int P, int a, const double* fq) {
     const double* gx = g.dm.gauss_x + 3 * kMaxGauss;
     const double* gw = g.dm.gauss_w + 3 * kMaxGauss;
     const double adet = fabs((X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[2][0] - X[0][0]) * (X[1][1] - X[0][1]));
@@ -111,7 +113,7 @@ __device__ double cell_source(const Fp64Args& g, const double X[3][2], int P, in
                     else phi = 4.0 * l0 * l1;
                 }
             }
-            s += w * adet * source_value(g.src_kind, g.src_value, g.src_freq, x, y) * phi;
+            s += w * adet * source_at(g.src_kind, g.src_value, g.src_freq, x, y, fq, 4 * i + j) * phi;
         }
     return s;
 }
@@ -192,7 +194,7 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
                     else {
                         double X[3][2];
                         fine_vertices(c, N, up, i, j, X);
-                        v += cell_source(g, X, P, a);
+                        v += cell_source(g, X, P, a, quad_of(g.src_vals, g.kappa, kap, N, up, i, j));
                     }
                 }
                 W[ra * g.ld + g.rhs0 + col] += v;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
             const int i = up ? o : o - (g.N - j);
             double X[3][2];
             fine_vertices(c, g.N, up, i, j, X);
-            s += cell_source(g, X, g.P, -1);
+            s += cell_source(g, X, g.P, -1, quad_of(g.src_vals, g.kappa, kap, g.N, up, i, j));
         }
         FK = block_sum(s, red);
     }
@@ -353,6 +355,8 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
         g.FK[K] = FK;
         g.status[K] = c.bad ? MHM_ERR_INVALID_ARG : 0;
         if (g.iters) g.iters[K] = g.fallback ? -1 : 1;
+        if (g.sword && (c.bad || g.fallback))
+            atomicOr(g.sword, (c.bad ? 1u << MHM_ERR_INVALID_ARG : 0u) | (g.fallback ? MHM_STATUS_REFINED_IN_FP64 : 0u));
     }
     __syncthreads();   // the context, the Gram matrix and the window serve the next element
     }
@@ -411,6 +415,16 @@ size_t fp64_level_workspace(const mhm_mesh* mesh, const Level& lv) {
     return (size_t)slots * sh.win_doubles * sizeof(double);
 }
 
+size_t fp64_slot_bytes(const mhm_mesh* mesh, const Level& lv) {
+    const Fp64Shape sh = fp64_shape(mesh, lv);
+    return sh.wide ? sh.win_doubles * sizeof(double) : 0;
+}
+
+bool fp64_level_launchable(const mhm_mesh* mesh, const Level& lv) {
+    const Fp64Shape sh = fp64_shape(mesh, lv);
+    return sh.smem <= 220 * 1024 && sh.R <= 64;
+}
+
 static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,
                               int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
                               int32_t* status, int32_t* iters, const int32_t* list, const int32_t* count,
@@ -434,6 +448,8 @@ static mhm_status launch_fp64(const mhm_mesh* mesh, const Level& lv, const doubl
     g.rhs0 = sh.rows;
     g.ld = sh.ld;
     g.src_kind = f.kind;
+    g.src_vals = f.kind == MHM_SRC_QUAD ? f.values_dev : nullptr;
+    g.sword = mesh->d_sword;
     g.src_value = f.value;
     g.src_freq = f.freq;
     g.K0 = K0;

@@ -43,6 +43,9 @@ struct MixedArgs {
     int stage_floats;             // floats of one staged solve operand (fragment order)
     int ldr;                      // leading dimension of the level right-hand sides (multiple of 4)
     int src_kind;
+    const double* src_vals;       // MHM_SRC_QUAD: 16 values per fine triangle, laid out like kappa
+    uint32_t* sword;              // the mesh's outcome word (mhm_sync_status)
+    int word_final;               // 1: a failed status is final (no FP64 re-solve follows)
     double src_value, src_freq;
     int64_t K0, K1;
     int it_max;
@@ -103,7 +106,7 @@ __device__ __forceinline__ void fine_xy(const MCtx& c, int N, bool up, int i, in
     }
 }
 
-__device__ double cell_src(const MixedArgs& g, const double X[3][2], int P, int a) {
+__device__ double cell_src(const MixedArgs& g, const double X[3][2], int P, int a, const double* fq) {
     const double* gx = g.dm.gauss_x + 3 * kMaxGauss;
     const double* gw = g.dm.gauss_w + 3 * kMaxGauss;
     const double adet = fabs((X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[2][0] - X[0][0]) * (X[1][1] - X[0][1]));
@@ -125,7 +128,7 @@ __device__ double cell_src(const MixedArgs& g, const double X[3][2], int P, int 
                     else phi = 4.0 * l0 * l1;
                 }
             }
-            s += w * adet * source_value(g.src_kind, g.src_value, g.src_freq, x, y) * phi;
+            s += w * adet * source_at(g.src_kind, g.src_value, g.src_freq, x, y, fq, 4 * i + j) * phi;
         }
     return s;
 }
@@ -929,7 +932,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 const bool up = o < g.N - j;
                 double X[3][2];
                 fine_xy(c, g.N, up, up ? o : o - (g.N - j), j, X);
-                s += cell_src(g, X, g.P, -1);
+                s += cell_src(g, X, g.P, -1, quad_of(g.src_vals, g.kappa, kap, g.N, up, up ? o : o - (g.N - j), j));
             }
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if ((threadIdx.x & 31) == 0) c.red[threadIdx.x >> 5] = s;
@@ -1017,7 +1020,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     else {
                         double Xv[3][2];
                         fine_xy(c, g.N, tup[t], ti[t], tj[t], Xv);
-                        fh += cell_src(g, Xv, 1, ta[t]);
+                        fh += cell_src(g, Xv, 1, ta[t], quad_of(g.src_vals, g.kappa, kap, g.N, tup[t], ti[t], tj[t]));
                     }
                 }
                 const double su = sc[u];
@@ -1179,8 +1182,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
             if (threadIdx.x == 0) {
                 g.FK[K] = c.FK;
-                g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                const int code = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                g.status[K] = code;
                 if (g.iters) g.iters[K] = pass;
+                if (code && g.sword && g.word_final) atomicOr(g.sword, 1u << code);
             }
             __syncthreads();
         } else {
@@ -1201,7 +1206,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                     else {
                         double Xv[3][2];
                         fine_xy(c, g.N, tup[t], ti[t], tj[t], Xv);
-                        fh += cell_src(g, Xv, g.P, ta[t]);
+                        fh += cell_src(g, Xv, g.P, ta[t], quad_of(g.src_vals, g.kappa, kap, g.N, tup[t], ti[t], tj[t]));
                     }
                 }
                 mass[u] = m;
@@ -1507,8 +1512,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             }
             if (threadIdx.x == 0) {
                 g.FK[K] = c.FK;
-                g.status[K] = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                const int code = c.timeout ? MHM_ERR_TIMEOUT : c.bad ? MHM_ERR_INVALID_ARG : (converged ? 0 : MHM_ERR_NOT_CONVERGED);
+                g.status[K] = code;
                 if (g.iters) g.iters[K] = pass;
+                if (code && g.sword && g.word_final) atomicOr(g.sword, 1u << code);
             }
             __syncthreads();
         }
@@ -1781,6 +1788,9 @@ MixedArgs mixed_args(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L
     g.stage_floats = L.stage_floats;
     g.ldr = L.ldr;
     g.src_kind = f.kind;
+    g.src_vals = f.kind == MHM_SRC_QUAD ? f.values_dev : nullptr;
+    g.sword = mesh->d_sword;
+    g.word_final = o.no_fallback != 0;
     g.src_value = f.value;
     g.src_freq = f.freq;
     g.it_max = o.it_max;
@@ -1969,8 +1979,10 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: mesh has no usable device");
     if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: NULL pointer argument");
-    if (f->kind != MHM_SRC_CONST && f->kind != MHM_SRC_SINSIN)
-        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: unknown source kind");
+    {
+        const mhm_status sst = check_source(f, "mhm_local_solve_batch_noalloc");
+        if (sst) return sst;
+    }
     MHM_CUDA_TRY(cudaSetDevice(mesh->device));
     mhm_solve_opts o{};
     o.it_max = 8;
@@ -1981,8 +1993,20 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: K range out of bounds");
     if (o.it_max < 1 || !(o.tol > 0.0))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch_noalloc: it_max >= 1 and tol > 0 required");
+    // every level is checked before any is launched: the call either runs all of them or
+    // launches nothing
     for (const Level& lv : mesh->levels) {
-        if (fp64_level(mesh, lv)) continue;
+        if (fp64_level(mesh, lv)) {
+            if (!fp64_level_launchable(mesh, lv))
+                return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: FP64 window panel exceeds shared memory");
+            const size_t need = fp64_slot_bytes(mesh, lv);
+            if (need > kStaticScratch)
+                return fail(MHM_ERR_INVALID_ARG,
+                            "mhm_local_solve_batch_noalloc: one coarse element's FP64 window needs " +
+                                std::to_string(need) + " bytes of scratch, above the fixed " +
+                                std::to_string(kStaticScratch) + " bytes");
+            continue;
+        }
         const MixedLayout L = mixed_layout(mesh, lv, false);   // factor inside the solve kernel
         if (L.smem > 220 * 1024 || !mixed_kernel(L))
             return fail(MHM_ERR_UNSUPPORTED, "mhm_local_solve_batch_noalloc: buffers exceed shared memory (r too large)");
@@ -2023,6 +2047,7 @@ extern "C" mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const 
         if (grid > fit) grid = fit;
         if (grid > nK) grid = nK;
         MixedArgs g = mixed_args(mesh, lv, L, kappa, *f, o, AK, EK, BK, FK, status, iters, (char*)scratch);
+        g.word_final = 1;
         g.K0 = i0;
         g.K1 = i1;
         mixed_kernel(L)<<<(unsigned)grid, kThreadsM, L.smem, (cudaStream_t)stream>>>(g);

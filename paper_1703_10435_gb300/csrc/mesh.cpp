@@ -87,6 +87,8 @@ void free_mesh_device(mhm_mesh* m) {
         if (p) cudaFree(p);
     if (m->d_kap_off) cudaFree(m->d_kap_off);
     if (m->d_nod_off) cudaFree(m->d_nod_off);
+    if (m->d_sword) cudaFree(m->d_sword);
+    m->d_sword = nullptr;
     for (mhm::Level& lv : m->levels) {
         if (lv.d_K) cudaFree(lv.d_K);
         if (lv.d_btab) cudaFree(lv.d_btab);
@@ -334,6 +336,7 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
             nnz += dofs(e) * len;
             bt += dofs(e) * (m->face_K[2 * e + 1] >= 0 ? 2 : 1);
         }
+        m->sys_count = nnz + 2 * bt;
         if (nnz + 2 * bt > (int64_t)INT32_MAX) {
             delete m;
             return mhm::fail(MHM_ERR_INVALID_ARG, "mhm_create_mesh: skeleton system beyond 2^31 entries (mesh too large)");
@@ -468,6 +471,7 @@ extern "C" mhm_status mhm_create_mesh(const mhm_mesh_desc* desc, int32_t device,
     if (!st) st = upload(m->k_lambda, &m->d_k_lambda);
     if (!st) st = upload(m->lam_face, &m->d_lam_face);
     if (!st) st = upload(m->tri_l, &m->d_lface);
+    if (!st) st = upload(std::vector<uint32_t>{0u}, &m->d_sword);
     if (m->per_k_levels) {
         if (!st) st = upload(m->kap_off, &m->d_kap_off);
         if (!st) st = upload(m->nod_off, &m->d_nod_off);
@@ -531,6 +535,10 @@ extern "C" mhm_status mhm_mesh_query(const mhm_mesh* m, int32_t what, void* out,
         case MHM_Q_VERTEX_XY: return copy_out(m->vxy, out, bytes);
         case MHM_Q_FACE_NORMALS: return copy_out(m->normals, out, bytes);
         case MHM_Q_FACE_DEGREE: return copy_out(m->face_l, out, bytes);
+        case MHM_Q_SYSTEM_NNZ: {
+            const std::vector<int64_t> v{m->sys_count, m->aug_nnz};
+            return copy_out(v, out, bytes);
+        }
         case MHM_Q_R_OF_K: {
             if (m->per_k_levels) return copy_out(m->r_of_K, out, bytes);
             return copy_out(std::vector<int8_t>(m->nK, (int8_t)m->desc.r), out, bytes);

@@ -19,6 +19,8 @@ mhm_status fail(mhm_status code, const std::string& msg);
 void timing_begin(const mhm_mesh* m);
 void timing_mark(const mhm_mesh* m, int kernel, cudaStream_t s, bool start);
 mhm_status cuda_fail(cudaError_t e, const char* what);
+// Checks a source descriptor (known kind; MHM_SRC_QUAD carries its values).
+mhm_status check_source(const mhm_source* f, const char* who);
 
 #define MHM_CUDA_TRY(expr)                                              \
     do {                                                                \
@@ -107,6 +109,7 @@ struct mhm_mesh {
     // saddle-point system [A B^T; B 0] in CSR: pattern and, per entry, the source of its
     // value (>= 0: index into the skeleton CSR values; < 0: -(index into BK) - 1)
     int64_t aug_nnz = 0;
+    int64_t sys_count = 0;   // the saddle-point entries as counted by the int32 guard of mhm_create_mesh
     std::vector<int32_t> aug_rowptr, aug_cols;
     std::vector<int64_t> aug_src;
 
@@ -132,6 +135,9 @@ struct mhm_mesh {
     int32_t* d_k_lambda = nullptr;
     int32_t* d_lam_face = nullptr;
     int8_t* d_lface = nullptr;            // tri_l on the device (NULL: uniform degree)
+    // outcome word of the local solves (mhm_sync_status): bit c for a final per-K status c,
+    // MHM_STATUS_REFINED_IN_FP64 for FP64 re-solves; written by the kernels with atomicOr
+    uint32_t* d_sword = nullptr;
 
     // refinement level per K (meshes built with r_per_K; uniform meshes leave these empty)
     bool per_k_levels = false;
@@ -167,6 +173,8 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double
                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK, double* FK,
                              int32_t* status, int32_t* iters, void* ws, size_t ws_bytes, cudaStream_t stream);
 size_t fp64_level_workspace(const mhm_mesh* mesh, const Level& lv);   // 0: window in shared memory
+size_t fp64_slot_bytes(const mhm_mesh* mesh, const Level& lv);        // one block's window slot (0: shared memory)
+bool fp64_level_launchable(const mhm_mesh* mesh, const Level& lv);    // panel fits shared memory, R <= 64
 int fp64_window_rows(const mhm_mesh* mesh, const Level& lv);
 // workspace region of one level at the given precision, and of all levels (one after the other)
 size_t level_workspace_bytes(const mhm_mesh* mesh, const Level& lv, int32_t precision);

@@ -30,6 +30,7 @@ struct RecArgs {
     int P, N, PN, dpf, NI, nlev, nloc;
     int rows, ld, rhs;          // window rows, leading dimension, right-hand-side column
     int src_kind;
+    const double* src_vals;   // MHM_SRC_QUAD: 16 values per fine triangle, laid out like kappa
     double src_value, src_freq;
     int ex_kind;                // 0 none, 1 sin sin, 2 quadratic polynomial
     double ex[6];
@@ -85,7 +86,7 @@ __device__ __forceinline__ void basis_eval(int P, double l0, double l1, double l
 }
 
 // Integral of f phi_a (a >= 0) or of f (a < 0) over a fine triangle, 4 x 4 collapsed Gauss.
-__device__ double cell_source(const RecArgs& g, const double X[3][2], int a) {
+__device__ double cell_source(const RecArgs& g, const double X[3][2], int a, const double* fq) {
     const double* gx = g.dm.gauss_x + 3 * kMaxGauss;
     const double* gw = g.dm.gauss_w + 3 * kMaxGauss;
     const double adet = fabs((X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[2][0] - X[0][0]) * (X[1][1] - X[0][1]));
@@ -97,7 +98,7 @@ __device__ double cell_source(const RecArgs& g, const double X[3][2], int a) {
             const double y = X[0][1] + xi * (X[1][1] - X[0][1]) + eta * (X[2][1] - X[0][1]);
             double phi[6], dx[6], dy[6];
             basis_eval(g.P, 1.0 - xi - eta, xi, eta, phi, dx, dy);
-            s += w * adet * source_value(g.src_kind, g.src_value, g.src_freq, x, y) * (a >= 0 ? phi[a] : 1.0);
+            s += w * adet * source_at(g.src_kind, g.src_value, g.src_freq, x, y, fq, 4 * i + j) * (a >= 0 ? phi[a] : 1.0);
         }
     return s;
 }
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
                 const bool up = o < g.N - j;
                 double X[3][2];
                 fine_xy(c, g.N, up, up ? o : o - (g.N - j), j, X);
-                s += cell_source(g, X, -1);
+                s += cell_source(g, X, -1, quad_of(g.src_vals, g.kappa, kap, g.N, up, up ? o : o - (g.N - j), j));
             }
             fk = block_sum(s, c);
         }
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsRWide : kThreadsR) k_reconstruc
                             else {
                                 double X[3][2];
                                 fine_xy(c, g.N, up, i, lev, X);
-                                v += cell_source(g, X, a);
+                                v += cell_source(g, X, a, quad_of(g.src_vals, g.kappa, kap, g.N, up, i, lev));
                             }
                             W[ra * g.ld + rhs] += v;
                         }
@@ -419,6 +420,10 @@ extern "C" mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa,
     if (mesh->device < 0) return fail(MHM_ERR_UNSUPPORTED, "mhm_reconstruct: mesh was created without a device");
     if (!kappa || !f || !lambda || !u0 || !u_nodal) return fail(MHM_ERR_INVALID_ARG, "mhm_reconstruct: NULL pointer argument");
     if (err_sq && !exact) return fail(MHM_ERR_INVALID_ARG, "mhm_reconstruct: err_sq needs an exact solution");
+    {
+        const mhm_status sst = check_source(f, "mhm_reconstruct");
+        if (sst) return sst;
+    }
     if (exact && exact->kind != MHM_EXACT_SINSIN && exact->kind != MHM_EXACT_POLY)
         return fail(MHM_ERR_INVALID_ARG, "mhm_reconstruct: unknown exact-solution kind");
     MHM_CUDA_TRY(cudaSetDevice(mesh->device));
@@ -447,6 +452,7 @@ extern "C" mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa,
         g.rhs = g.rows;                      // right-hand side right after the symmetric part
         g.ld = (g.rows + 2) & ~1;            // even: 16-byte rows for the vector panel loads
         g.src_kind = f->kind;
+        g.src_vals = f->kind == MHM_SRC_QUAD ? f->values_dev : nullptr;
         g.src_value = f->value;
         g.src_freq = f->freq;
         g.ex_kind = exact ? (exact->kind == MHM_EXACT_SINSIN ? 1 : 2) : 0;

@@ -28,16 +28,18 @@ MHM_FP64 = 0
 MHM_MIXED = 1
 MHM_SRC_CONST = 0
 MHM_SRC_SINSIN = 1
+MHM_SRC_QUAD = 2
+MHM_STATUS_REFINED_IN_FP64 = 1 << 16
 
 Q_SIZES, Q_TRI_VERTS, Q_TRI_FACES, Q_TRI_SIGNS, Q_FACE_VERTS, Q_LAMBDA_OFFSET, Q_K_LAMBDA, \
     Q_CSR_ROWPTR, Q_CSR_COLS, Q_VERTEX_XY, Q_FACE_NORMALS, Q_R_OF_K, Q_KAPPA_OFFSET, Q_NODAL_OFFSET, \
-    Q_FACE_DEGREE = range(15)
+    Q_FACE_DEGREE, Q_SYSTEM_NNZ = range(16)
 
 EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
     "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
-    "mhm_local_solve_waves",
+    "mhm_local_solve_waves", "mhm_sync_status",
 ]
 MHM_KERNEL_LOCAL_FP64, MHM_KERNEL_LOCAL_MIXED, MHM_KERNEL_SCHUR_FACTOR = range(3)
 MHM_N_KERNELS = 3
@@ -53,7 +55,18 @@ class MeshDesc(ctypes.Structure):
 
 
 class Source(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("freq", ctypes.c_double)]
+    """mhm_source: kind, value, freq, and for MHM_SRC_QUAD the device pointer of the point
+    values (keep the tensor alive while the calls that use it run)."""
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("freq", ctypes.c_double),
+                ("values_dev", ctypes.c_void_p)]
+
+
+def quad_source(values) -> Source:
+    """A source given by its values at the 16 collapsed-Gauss points of every fine triangle
+    (a contiguous float64 device tensor laid out like kappa, 16 values per fine triangle)."""
+    src = Source(MHM_SRC_QUAD, 0.0, 0.0, ctypes.c_void_p(values.data_ptr()))
+    src._values = values   # keeps the tensor alive with the struct
+    return src
 
 
 class Dirichlet(ctypes.Structure):
@@ -104,6 +117,8 @@ def lib():
         L.mhm_measure_pipes.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mhm_set_timing.argtypes = [vp, i32]
         L.mhm_kernel_times.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+        L.mhm_sync_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+        L.mhm_sync_status.restype = i32
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
                      "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc",
                      "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
@@ -251,3 +266,14 @@ def mhm_kernel_times(mesh: Mesh):
     ms = (ctypes.c_double * MHM_N_KERNELS)()
     _check(lib().mhm_kernel_times(mesh.handle, n, ms))
     return {KERNEL_NAMES[k]: (int(n[k]), float(ms[k])) for k in range(MHM_N_KERNELS) if n[k] > 0}
+
+
+def mhm_sync_status(mesh: Mesh, stream=None):
+    """(most severe final code recorded since the last read, the outcome word); waits for the
+    work on `stream` and clears the word.  The code is returned, not raised."""
+    w = ctypes.c_uint32(0)
+    code = lib().mhm_sync_status(mesh.handle, _stream(stream), ctypes.byref(w))
+    if code not in (MHM_OK, MHM_ERR_NOT_CONVERGED, MHM_ERR_INVALID_ARG, MHM_ERR_TIMEOUT) or (
+            code == MHM_ERR_INVALID_ARG and not w.value):
+        _check(code)
+    return code, int(w.value)

@@ -6,6 +6,11 @@ code), on cuda:0, and checks the status words.  Example:
 
     python -m paper_1703_10435_gb300.profile_case --precision mixed --n-k 152
 
+The first 8192 coarse triangles of the 32768-element random-field workload are one
+factor + solve launch pair of the bench's mixed path:
+
+    python -m paper_1703_10435_gb300.profile_case --workload c3_grf_mixed --n-k 8192
+
 --level r puts every coarse triangle of the workload at refinement level r (its
 kappa field sampled at that level), e.g. the 256-row level windows of r = 7:
 
@@ -36,9 +41,13 @@ def main(argv=None):
         import dataclasses
         w = dataclasses.replace(w, r=args.level, levels=None)
     n = min(args.n_k, w.n_K)
-    # kappa of K = 0 .. n - 1 only (the blocks sit at the same offsets as in the full field)
     import numpy as np
-    kap = torch.as_tensor(W.kappa_for(w, np.arange(n)), device="cuda").reshape(-1)
+    if w.field in ("grf4", "grf6") and w.r_per_K is None:
+        # random Fourier field: evaluated on the device (the blocks of K >= n are not read)
+        kap = W.kappa_for_torch(w, torch.device("cuda")).reshape(-1)
+    else:
+        # kappa of K = 0 .. n - 1 only (the blocks sit at the same offsets as in the full field)
+        kap = torch.as_tensor(W.kappa_for(w, np.arange(n)), device="cuda").reshape(-1)
     prec = mhm.MHM_MIXED if args.precision == "mixed" else mhm.MHM_FP64
     p = Pipeline.for_workload(w, 0, prec)
     opts = mhm.SolveOpts(8, 1e-12, 0, n)

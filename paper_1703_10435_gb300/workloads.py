@@ -105,6 +105,40 @@ def fine_centroids(verts: np.ndarray, N: int) -> np.ndarray:
     return v0 + lat[None, :, 0, None] * e1 + lat[None, :, 1, None] * e2
 
 
+def duffy_points_ref() -> np.ndarray:
+    """(16, 2) reference points (xi, eta) of the collapsed 4 x 4 Gauss rule, point 4 i + j at
+    xi = a_i, eta = a_j (1 - a_i) with a the 4-point Gauss-Legendre nodes on [0, 1] (the
+    point order of a source given by its values, MHM_SRC_QUAD)."""
+    a = 0.5 * (np.polynomial.legendre.leggauss(4)[0] + 1.0)
+    return np.array([(a[i], a[j] * (1.0 - a[i])) for i in range(4) for j in range(4)])
+
+
+def fine_triangle_lattice(N: int) -> np.ndarray:
+    """(N*N, 3, 2) lattice coordinates (units of 1/N) of the fine-triangle vertices in the
+    kappa order: "up" (i,j),(i+1,j),(i,j+1), then "down" (i+1,j),(i+1,j+1),(i,j+1)."""
+    out = []
+    for j in range(N):
+        for i in range(N - j):
+            out.append(((i, j), (i + 1, j), (i, j + 1)))
+        for i in range(N - 1 - j):
+            out.append(((i + 1, j), (i + 1, j + 1), (i, j + 1)))
+    return np.asarray(out, dtype=np.float64)
+
+
+def source_points(verts: np.ndarray, N: int) -> np.ndarray:
+    """(N_K, N*N, 16, 2) physical positions of the 16 source points of every fine triangle
+    of the coarse triangles `verts` (N_K, 3, 2) at N = 2^r, in the layout of a source given
+    by its values: X0 + xi (X1 - X0) + eta (X2 - X0) per fine triangle (X0, X1, X2)."""
+    lat = fine_triangle_lattice(N) / N                                    # (T, 3, 2)
+    ref = duffy_points_ref()                                              # (16, 2)
+    bary = lat[:, 0, None, :] + ref[None, :, 0, None] * (lat[:, 1] - lat[:, 0])[:, None, :] \
+        + ref[None, :, 1, None] * (lat[:, 2] - lat[:, 0])[:, None, :]     # (T, 16, 2) in (s, t)
+    v0 = verts[:, 0, None, None, :]
+    e1 = (verts[:, 1] - verts[:, 0])[:, None, None, :]
+    e2 = (verts[:, 2] - verts[:, 0])[:, None, None, :]
+    return v0 + bary[None, ..., 0, None] * e1 + bary[None, ..., 1, None] * e2
+
+
 # ---------------------------------------------------------------------------
 # Coefficient fields
 # ---------------------------------------------------------------------------

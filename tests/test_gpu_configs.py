@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 from oracle.local import solve_local
 from oracle.mesh import build_mesh
 from paper_1703_10435_gb300 import mhm, workloads as W
+from _blocks import assert_blocks
 
 pytestmark = pytest.mark.gpu
 
@@ -43,9 +44,10 @@ def test_full_size_sampled_parity(name, tol):
     assert np.abs(kap_np - kap[Ks].cpu().numpy()).max() <= 1e-12 * kap_np.max()
     mesh = build_mesh(w.nx, w.ny, w.m, w.l)
     AK = pm.AK.view(w.n_K, w.n_I, w.n_I)
+    EK, BK, FK = pm.EK.view(w.n_K, w.n_I), pm.BK.view(w.n_K, w.n_I), pm.FK
     for i, K in enumerate(Ks):
         o = solve_local(mesh, int(K), w.r, w.degree, kap_np[i], float(w.source_value))
-        assert _rel(AK[K].cpu().numpy(), o.AK) < tol, K
+        assert_blocks(AK[K].cpu().numpy(), EK[K].cpu().numpy(), BK[K].cpu().numpy(), float(FK[K]), o, tol, K)
     # the whole batch against the FP64 path
     p64 = Pipeline.for_workload(w, 0, mhm.MHM_FP64)
     p64.local(kap, source_of(w))
@@ -107,3 +109,43 @@ def test_cuda_graph_replay(precision):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(p.A_vals, ref)
+
+
+def test_waves_sub_range_and_refusals():
+    """Memory-admitted waves over a K range strictly inside a per-level mesh (the kappa base
+    is offset by the first element's kappa offset) equal mhm_local_solve_batch over the same
+    range bit for bit, and leave the elements outside it untouched; a budget below two
+    elements' kappa and a NULL kappa_host are refused with INVALID_ARG."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    rng = np.random.default_rng(8)
+    rs = rng.integers(3, 6, 2 * 4 * 4).astype(np.int8)
+    kl = np.concatenate([10.0 ** rng.uniform(-2, 2, 4 ** int(r)) for r in rs])
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    K0, K1 = 5, 27
+    opts = mhm.SolveOpts(8, 1e-12, K0, K1)
+    for prec in (mhm.MHM_FP64, mhm.MHM_MIXED):
+        q1 = Pipeline(4, 4, 0, 1, 1, 2, 0, prec, r_per_K=rs)
+        q1.local(torch.as_tensor(kl, device="cuda"), src, opts)
+        q2 = Pipeline(4, 4, 0, 1, 1, 2, 0, prec, r_per_K=rs)
+        q2.AK.fill_(7.0)
+        n = q2.local_waves(kl, src, budget_bytes=2 * 3 * 1024 * 8, opts=opts)
+        assert n > 2
+        NI = q1.mesh.n_I
+        for name, stride in (("AK", NI * NI), ("EK", NI), ("BK", NI), ("FK", 1), ("status", 1), ("iters", 1)):
+            a, b = getattr(q1, name), getattr(q2, name)
+            assert torch.equal(a[K0 * stride:K1 * stride], b[K0 * stride:K1 * stride]), (prec, name)
+        assert float(q2.AK[:K0 * NI * NI].sub(7.0).abs().max()) == 0.0
+        assert float(q2.AK[K1 * NI * NI:].sub(7.0).abs().max()) == 0.0
+    q = Pipeline(4, 4, 0, 1, 1, 2, 0, mhm.MHM_MIXED, r_per_K=rs)
+    big = 4 ** int(rs.max()) * 8
+    with pytest.raises(mhm.MHMError) as ei:
+        q.local_waves(kl, src, budget_bytes=2 * big - 8)
+    assert ei.value.code == mhm.MHM_ERR_INVALID_ARG
+    L = mhm.lib()
+    n = mhm.ctypes.c_int32(0)
+    ws = q.workspace
+    code = L.mhm_local_solve_waves(q.mesh.handle, None, 1 << 30, mhm.ctypes.byref(src), mhm.MHM_MIXED, None,
+                                   mhm._ptr(q.AK), mhm._ptr(q.EK), mhm._ptr(q.BK), mhm._ptr(q.FK),
+                                   mhm._ptr(q.status), mhm._ptr(q.iters), mhm._ptr(ws),
+                                   0 if ws is None else ws.numel(), mhm._stream(None), mhm.ctypes.byref(n))
+    assert code == mhm.MHM_ERR_INVALID_ARG

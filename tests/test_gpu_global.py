@@ -98,12 +98,37 @@ def test_multipliers_and_solution_vs_oracle(name, P, r, m, l, nx, field):
 
 
 @pytest.mark.parametrize("field", ["log_uniform", "grf4"])
-def test_mixed_vs_fp64_solution(field):
-    """Mixed-precision local solves: multipliers and the reconstructed u agree with
-    the all-FP64 path within 1e-8 relative (L2 norm of u)."""
+def test_mixed_vs_fp64_and_oracle_solution(field):
+    """Mixed-precision local solves on a heterogeneous 8 x 8 mesh (128 K, P1 r = 5, 561
+    unknowns per K): multipliers, u0 and the reconstructed nodal u within 1e-8 relative
+    (L2) of the FP64 oracle, and of the GPU's all-FP64 path."""
     w = W.Workload("t", 8, 8, 5, 1, 2, 2, field, "const", 1.0, seed=6)
     kap = W.kappa_for(w)
     p64, u64, _ = _gpu_all(w, kap, mhm.MHM_FP64)
     pm, um, _ = _gpu_all(w, kap, mhm.MHM_MIXED)
+    assert int(pm.iters.max()) >= 2               # the mixed path did refine
     assert _rel(pm.lam.cpu().numpy(), p64.lam.cpu().numpy()) < 1e-8
     assert _rel(um, u64) < 1e-8
+    o = run(w.nx, w.ny, w.r, 1, w.m, w.l, kap, 1.0)
+    uo = np.stack([orec.local_u(o.mesh, K, loc, o.lam, o.u0) for K, loc in enumerate(o.locals)])
+    for u_, p_ in ((um, pm), (u64, p64)):
+        assert _rel(p_.lam.cpu().numpy(), o.lam) < 1e-8
+        assert _rel(p_.u0.cpu().numpy(), o.u0) < 1e-8
+        assert _rel(u_, uo) < 1e-8
+
+
+def test_quad_source_solution_vs_oracle():
+    """f = exp(x) cos(3y) + 1/(1+x+y), given by its point values (MHM_SRC_QUAD), through the
+    whole pipeline (local solves, skeleton, global solve, computeSolution) against the oracle
+    evaluating the same f: multipliers, u0 and nodal u within 1e-10."""
+    f = lambda x, y: np.exp(x) * np.cos(3.0 * y) + 1.0 / (1.0 + x + y)
+    w = W.Workload("t", 3, 3, 3, 1, 2, 1, "log_uniform", "const", 1.0, seed=5)
+    kap = W.kappa_for(w)
+    pts = W.source_points(W.coarse_vertices(w.nx, w.ny), w.N)
+    vals = torch.as_tensor(f(pts[..., 0], pts[..., 1]).reshape(-1), device="cuda").contiguous()
+    p, u, _ = _gpu_all(w, kap, src=mhm.quad_source(vals))
+    o = run(w.nx, w.ny, w.r, 1, w.m, w.l, kap, f)
+    assert _rel(p.lam.cpu().numpy(), o.lam) < 1e-10
+    assert _rel(p.u0.cpu().numpy(), o.u0) < 1e-10
+    uo = np.stack([orec.local_u(o.mesh, K, loc, o.lam, o.u0) for K, loc in enumerate(o.locals)])
+    assert _rel(u, uo) < 1e-10

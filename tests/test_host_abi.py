@@ -154,3 +154,24 @@ def test_per_element_levels_reject_out_of_range():
     from paper_1703_10435_gb300 import mhm
     with pytest.raises(mhm.MHMError):
         mhm.Mesh(1, 1, 0, 1, 1, 1, device=-1, r_per_K=[3, 8])
+
+
+@pytest.mark.parametrize("nx,ny,m,l,per_face", [(1, 1, 1, 0, False), (3, 2, 4, 3, False), (4, 3, 2, 2, True)])
+def test_system_count_equals_built_pattern(lib, nx, ny, m, l, per_face):
+    """The entry count behind mhm_create_mesh's int32 guard equals the saddle-point CSR
+    the mesh then builds (uniform degree and a degree per face)."""
+    lf = None
+    if per_face:
+        ne = nx * (ny + 1) + ny * (nx + 1) + nx * ny
+        lf = np.random.default_rng(3).integers(0, l + 1, ne)
+    M = mhm.Mesh(nx, ny, 2, 1, m, l, -1, None, lf)
+    counted, built = M.query(mhm.Q_SYSTEM_NNZ, np.int64, 2)
+    assert counted == built > 0
+
+
+def test_mesh_beyond_int32_entries_refused(lib):
+    """760 x 760 squares with 16 multipliers per face: about 2.2e9 saddle-point entries,
+    beyond int32 indexing; refused with INVALID_ARG before any table of that size exists."""
+    with pytest.raises(mhm.MHMError) as ei:
+        mhm.Mesh(760, 760, 1, 1, 4, 3, -1)
+    assert ei.value.code == mhm.MHM_ERR_INVALID_ARG and "2^31" in str(ei.value)

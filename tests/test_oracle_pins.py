@@ -15,6 +15,7 @@ from oracle.local import assemble_stiffness, cell_integrals, solve_local
 from oracle.mesh import build_mesh
 from oracle.quadrature import duffy_triangle, gauss_legendre_01
 from oracle.run import run, source_fn
+from _golden import dirichlet_moment, legendre_golden
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -445,3 +446,38 @@ def test_per_face_degree_exact_quadratic_p2():
     lf0[[e for e in range(ne) if not o.mesh.boundary[e]][0]] = 0   # one interior face at degree 0
     o0 = run(nx, ny, rs, 2, 1, lf0, kap, -8.0, g=u)
     assert _max_nodal_error(o0, u) > 1e-6
+
+
+# --------------------------------------------------------------- Legendre basis
+def test_legendre_golden_values_norms_moments():
+    """The multiplier basis P_p of Lambda_H^{m,l} (Sec. 2, definition (i)) against the
+    closed forms: point values (a wrong recurrence coefficient or normalisation moves
+    P_2(1/2) = -1/8 and P_3(1/2) = -7/16), the norms 2/(2p+1) and the moments."""
+    from oracle.mesh import legendre
+    gold = legendre_golden()
+    for row in gold["values"]:
+        x, vals = row[0], row[1:]
+        for p, v in enumerate(vals):
+            assert float(legendre(p, x)) == pytest.approx(v, abs=1e-15), (p, x)
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    for p, v in gold["norms"].items():
+        assert float(np.sum(wg * legendre(p, xg) ** 2)) == pytest.approx(v, rel=1e-14)
+    for (k, p), v in gold["moments"].items():
+        assert float(np.sum(wg * xg ** k * legendre(p, xg))) == pytest.approx(v, abs=1e-14)
+
+
+@pytest.mark.parametrize("m,l", [(1, 0), (2, 2), (3, 3)])
+def test_dirichlet_term_face_moments(m, l):
+    """The oracle's boundary term (g, psi_j)_F (Eq. "global" with u = g on the boundary)
+    for g = x^2 + y^2 equals the closed form built from the Legendre moments: pins the
+    basis normalisation, the direction of xi on every boundary face and the subface
+    coordinates."""
+    gold = legendre_golden()
+    mesh = build_mesh(2, 3, m, l)
+    G = globalsys.dirichlet_term(mesh, lambda x, y: x * x + y * y, 4)
+    for e in range(mesh.n_e):
+        for q in range(m):
+            for p in range(l + 1):
+                j = mesh.lam_offset[e] + q * (l + 1) + p
+                want = dirichlet_moment(mesh, e, q, p, m, gold) if mesh.boundary[e] else 0.0
+                assert G[j] == pytest.approx(want, abs=1e-14), (e, q, p)
