@@ -148,6 +148,23 @@ typedef struct {
                            * 1: they keep their failure status.  MIXED runs P1
                            * levels wider than 32 points (r >= 6) and P2 levels of
                            * r >= 5 on the FP64 path. */
+    /* MIXED, P1 levels of at most 32 points: keep the local factorisations across calls
+     * (the paper factors each local matrix once and reuses it while kappa does not change,
+     * Sec. 3).  factor_store: device memory of mhm_factor_store_size bytes (caller-owned);
+     * NULL: no store.  factor_reuse 0: the call factors every element of the range and
+     * keeps the factors in the store; 1: the call skips the factorisation and solves with
+     * the factors the store holds, which must come from an earlier call on the same mesh
+     * with the same kappa over these elements (any source f).  Other levels are factored
+     * on every call. */
+    void* factor_store;
+    size_t factor_store_bytes;
+    int32_t factor_reuse;
+    /* MIXED: path of a tuning cache file (NULL: none).  For every level of the mesh without
+     * a launch shape yet, the call looks the shape up in the file under the key (degree,
+     * level r, right-hand sides, device name, SM count); on a miss it runs mhm_autotune's
+     * search on this call's inputs (synchronously: not for stream capture) and appends the
+     * result to the file. */
+    const char* tuner_cache;
 } mhm_solve_opts;
 
 /* ------------------------------------------------------------------ mesh --- */
@@ -194,6 +211,10 @@ mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, si
  * only); wider windows (P1 r = 7, P2 r = 5) live in one slot per SM of
  * rows x (rows + N_I + 1) doubles.  MHM_MIXED adds its per-level buffers. */
 mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes);
+
+/* Bytes of the factor store that mhm_solve_opts.factor_store points to: 0 when no level
+ * of the mesh keeps its factors (FP64-only meshes, P2, P1 levels wider than 32 points). */
+mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes);
 
 /* solveLocalProblem for K in [opts->K_begin, opts->K_end) (all K by default):
  * for each K, assembles A = [a(phi_j, phi_i)] with a(u,w) = (kappa grad u,
@@ -266,6 +287,42 @@ mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kap
                                          const mhm_solve_opts* opts, double* AK_dev, double* EK_dev,
                                          double* BK_dev, double* FK_dev, int32_t* status_dev,
                                          int32_t* iters_dev, void* stream);
+
+/* ------------------------------------------------------------ autotuner --- */
+
+/* Launch shape of the mixed-precision local solves of one refinement level (P1 levels of
+ * at most 32 points, the level-Schur path).  Every field changes speed only: the results
+ * are the same bit for bit under every shape. */
+typedef struct {
+    int32_t chunk;          /* elements per factor + solve launch pair: 256..8192 */
+    int32_t blocks_per_sm;  /* resident solve blocks per SM: 1..3 */
+    int32_t op_buffers;     /* level operators staged ahead in shared memory: 2..4 (the copy
+                             * of level step s + op_buffers - 1 is issued at step s) */
+    int32_t l2_prefetch;    /* L2 prefetch distance in level steps beyond the staged ones (0: none) */
+    int32_t prefetch_all;   /* 1: prefetch an element's whole operator set into L2 at each solve */
+    int32_t op_policy;      /* L2 policy of the operator copies: 0 default, 1 evict first, 2 evict last */
+    double ms_per_K;        /* mhm_autotune: measured milliseconds per element of this shape
+                             * (0 for a shape set by hand or the default) */
+} mhm_tuning;
+
+/* Sets / reads the launch shape of level r (0..7) of the mesh.  Errors: INVALID_ARG (NULL,
+ * r out of range, a field out of range). */
+mhm_status mhm_set_tuning(mhm_mesh* mesh, int32_t r, const mhm_tuning* t);
+mhm_status mhm_get_tuning(const mhm_mesh* mesh, int32_t r, mhm_tuning* t);
+
+/* Autotuner of the launch shapes: for every level of the mesh that runs the level-Schur
+ * mixed path, a coordinate search over the fields of mhm_tuning: each field in turn over
+ * its candidate values, the others fixed at the best so far, two sweeps;, every candidate
+ * timed with CUDA events on `stream` over the level's first elements (up to 16384) with
+ * this call's inputs; the fastest shape is set on the mesh and, with cache_path, appended
+ * to that file under its key (degree, level r, right-hand sides, device name, SM count).
+ * Arguments as in mhm_local_solve_batch (precision MIXED); the outputs hold the last
+ * candidate's results (identical under every shape).  Synchronous.  Errors: those of
+ * mhm_local_solve_batch, INVALID_ARG (cache file not writable). */
+mhm_status mhm_autotune(mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f, const mhm_solve_opts* opts,
+                        double* AK_dev, double* EK_dev, double* BK_dev, double* FK_dev, int32_t* status_dev,
+                        int32_t* iters_dev, void* workspace_dev, size_t workspace_bytes, const char* cache_path,
+                        void* stream);
 
 /* -------------------------------------------------------------- skeleton --- */
 

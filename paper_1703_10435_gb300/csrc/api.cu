@@ -74,6 +74,15 @@ size_t level_workspace_bytes(const mhm_mesh* mesh, const Level& lv, int32_t prec
     return (b + 255) & ~(size_t)255;
 }
 
+size_t level_region_offset(const mhm_mesh* mesh, const Level& lv, int32_t precision) {
+    size_t off = 0;
+    for (const Level& l2 : mesh->levels) {
+        if (&l2 == &lv) break;
+        off += level_workspace_bytes(mesh, l2, precision);
+    }
+    return off;
+}
+
 size_t local_workspace_bytes(const mhm_mesh* mesh, int32_t precision) {
     if (mesh->device < 0) return 0;
     int cur = 0;
@@ -119,6 +128,16 @@ extern "C" mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t pre
     return fail(MHM_ERR_INVALID_ARG, "mhm_local_workspace_size: unknown precision");
 }
 
+extern "C" mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes) {
+    if (!mesh || !bytes) return fail(MHM_ERR_INVALID_ARG, "mhm_factor_store_size: NULL argument");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (mesh->device >= 0) cudaSetDevice(mesh->device);
+    *bytes = factor_store_layout(mesh, nullptr, nullptr);
+    cudaSetDevice(cur);
+    return MHM_OK;
+}
+
 extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa, const mhm_source* f,
                                             int32_t precision, const mhm_solve_opts* opts, double* AK,
                                             double* EK, double* BK, double* FK, int32_t* status,
@@ -143,10 +162,25 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: unknown precision");
     if (precision == MHM_MIXED && (o.it_max < 1 || !(o.tol > 0.0)))
         return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: it_max >= 1 and tol > 0 required");
+    if (precision != MHM_MIXED) {
+        o.factor_store = nullptr;   // the FP64 path keeps no factors
+        o.factor_reuse = 0;
+    } else if (o.factor_reuse && !o.factor_store) {
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: factor_reuse needs a factor_store");
+    } else if (o.factor_store && o.factor_store_bytes < factor_store_layout(mesh, nullptr, nullptr)) {
+        return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: factor_store smaller than mhm_factor_store_size");
+    } else if (o.factor_store && factor_store_layout(mesh, nullptr, nullptr) == 0) {
+        o.factor_store = nullptr;   // no level keeps factors
+        o.factor_reuse = 0;
+    }
     {
         const size_t need = local_workspace_bytes(mesh, precision);
         if (ws_bytes < need || (need > 0 && !workspace))
             return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: workspace smaller than mhm_local_workspace_size");
+    }
+    if (precision == MHM_MIXED && o.tuner_cache) {
+        st = tune_from_cache_or_search(mesh, kappa, *f, o, AK, EK, BK, FK, status, iters, workspace, ws_bytes, s);
+        if (st) return st;
     }
     // One launch sequence per refinement level.  The levels are independent (disjoint
     // elements and outputs), so with several of them the first runs on the caller's stream

@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kThreadsM = 256;
 constexpr int kWarpsM = kThreadsM / 32;
+constexpr int kMaxOpBufs = 4;   // level-Schur solves: shared-memory ring of staged level operators
 
 struct MixedArgs {
     DeviceMesh dm;
@@ -56,15 +57,22 @@ struct MixedArgs {
     int kap_in_smem;
     double *AK, *EK, *BK, *FK;
     int32_t *status, *iters;
-    // level-Schur operators computed by the factor kernel for the chunk [Kc0, K1)
+    // level-Schur operators computed by the factor kernel for the chunk [Kc0, K1); the
+    // per-K arrays below start at launch index Kbase (the chunk's first, or 0 for a factor
+    // store that holds the whole level)
     float* Tall;                  // t_stride floats per K
     float* cwall;                 // 4 nunk floats per K
     int* fbad;                    // pivot flag per K
     double* scall;                // s_u = A_uu^-1/2, nunk per K
     double* ahall;                // scaled stencil S A S: 7 x nunk per K (self, E, W, N, S, SE, NW)
-    int64_t Kc0;
+    int64_t Kc0, Kbase;
     size_t t_stride;
     int* kcounter;                // dynamic K assignment (zeroed before the launch); NULL: static
+    // level-Schur solves (tuning knobs): operator buffers in the shared-memory ring (2..4;
+    // the copy of step s + nbuf - 1 is issued at step s), L2 prefetch distance in steps
+    // (0: none), prefetch of the element's whole operator set into L2 at the start of each
+    // solve, and the L2 policy of the operator copies (0 default, 1 evict first, 2 evict last)
+    int nbuf, l2pf, pf_all, op_policy;
 };
 
 struct MCtx {
@@ -88,8 +96,8 @@ struct MCtx {
     float epsred[2][32];          // level-Schur solve: per row-tile partial sums of g^T T g per column
     int64_t nextK;
     double mz[kMaxNI + 1];
-    alignas(8) uint64_t bar[2];
-    uint32_t phase[2];
+    alignas(8) uint64_t bar[kMaxOpBufs];
+    uint32_t phase[kMaxOpBufs];
     int timeout;
 };
 
@@ -650,21 +658,35 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     const uint32_t y_s = smem_u32(y), op_s = smem_u32(opbuf), st_s = smem_u32(stage);
     const float* cwS = cw + 2 * nu;
     const float* cwSE = cw + 3 * nu;
-    uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
+    uint32_t ph = 0;   // bit b: parity of buffer b's next wait
+    for (int b = 0; b < kMaxOpBufs; ++b) ph |= (c.phase[b] & 1u) << b;
     uint64_t frozen = 0;
     for (int col = 0; col < R; ++col)
         if (c.col_frozen[col]) frozen |= 1ull << col;
     const int si0 = threadIdx.x / R, sc0 = threadIdx.x - si0 * R, srq = kThreadsM / R, srr = kThreadsM - srq * R;
+    const int nb = g.nbuf;   // ring of staged operators: step st uses buffer st % nb
+    const uint64_t pol = g.op_policy == 1 ? l2_policy_evict_first() : l2_policy_evict_last();
+    auto op_bytes = [&](int st) { return (uint32_t)frag_op_floats(sinfo[st].x & 0xff, sinfo[st].x & 0xff) * 4u; };
     auto issue = [&](int st) {
-        const int4 si = sinfo[st];
-        const uint32_t bytes = (uint32_t)frag_op_floats(si.x & 0xff, si.x & 0xff) * 4u;
+        const uint32_t bytes = op_bytes(st);
+        const int b = st % nb;
         fence_proxy_async_shared();
-        mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
-        bulk_copy_g2s(opbuf + (size_t)(st & 1) * g.opmax, F + si.w, bytes, &c.bar[st & 1]);
+        mbar_arrive_expect_tx(&c.bar[b], bytes);
+        if (g.op_policy) bulk_copy_g2s_hint(opbuf + (size_t)b * g.opmax, F + sinfo[st].w, bytes, &c.bar[b], pol);
+        else bulk_copy_g2s(opbuf + (size_t)b * g.opmax, F + sinfo[st].w, bytes, &c.bar[b]);
     };
     // lane 0 of the last warp issues the copies (it holds no output tile while a level has <= 7 tiles)
     const bool issuer = threadIdx.x == kThreadsM - 32;
-    if (issuer) issue(0);
+    if (issuer) {
+        if (g.pf_all) {
+            // the element's operators (one contiguous array, forward steps in level order)
+            const int l = nsteps / 2;   // the last level's step
+            bulk_prefetch_l2(F, (uint32_t)(sinfo[l].w * 4u + op_bytes(l)));
+        } else {
+            for (int st = nb - 1; st < nsteps && st < nb - 1 + g.l2pf; ++st) bulk_prefetch_l2(F + sinfo[st].w, op_bytes(st));
+        }
+        for (int st = 0; st < nb - 1 && st < nsteps; ++st) issue(st);
+    }
     for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
     // the right-hand side r = FP32 rounding of Rh, in y (frozen columns keep their pending correction);
     // node-major on both sides, so the reads are coalesced and all in flight together
@@ -679,7 +701,12 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
         const int b = si.x & 0xff, dir = si.x >> 8;
         const int ulev = si.y & 0xffff, uo = si.y >> 16;
         const int bo = si.z & 0xffff, lev = si.z >> 16;
-        if (issuer && st + 1 < nsteps) issue(st + 1);
+        // buffer (st + nb - 1) % nb was last read in step st - 1, which ended with a barrier
+        if (issuer && st + nb - 1 < nsteps) issue(st + nb - 1);
+        if (issuer && g.l2pf && !g.pf_all && st + nb - 1 + g.l2pf < nsteps) {
+            const int sp = st + nb - 1 + g.l2pf;
+            bulk_prefetch_l2(F + sinfo[sp].w, op_bytes(sp));
+        }
         // B (b x R) in fragment order: forward r_lev - C_lev v_{lev-1} (r = the FP32 rounding of
         // the scaled residual Rh); backward C_{lev+1}^T x_{lev+1}
         {
@@ -708,12 +735,12 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
                 if (col >= R) { col -= R; ++i; }
             }
         }
-        const uint32_t par = (st & 1) ? ph1 : ph0;
-        if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
-        if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        const int bu = st % nb;
+        if (!mbar_wait_bounded(&c.bar[bu], (ph >> bu) & 1u)) c.timeout = 1;
+        ph ^= 1u << bu;
         __syncthreads();
         const int KT = (b + 7) >> 3, MT = (b + 15) >> 4;
-        const uint32_t op0 = op_s + (uint32_t)((st & 1) * g.opmax) * 4u;
+        const uint32_t op0 = op_s + (uint32_t)(bu * g.opmax) * 4u;
         for (int q = warp; q < MT * NT; q += kWarpsM) {
             const int mt = q / NT, nt = q - mt * NT;
             const uint32_t aa = op0 + (uint32_t)(((mt * KT) * 32 + lane) * 16);
@@ -755,10 +782,8 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
     }
     __syncthreads();
     if (threadIdx.x < R) eps[threadIdx.x] = (double)c.epsred[0][threadIdx.x] + (double)c.epsred[1][threadIdx.x];
-    if (threadIdx.x == 0) {
-        c.phase[0] = ph0;
-        c.phase[1] = ph1;
-    }
+    if (threadIdx.x == 0)
+        for (int b = 0; b < kMaxOpBufs; ++b) c.phase[b] = (ph >> b) & 1u;
 }
 
 // One refinement pass of the level-Schur path, in scaled variables, for the columns
@@ -838,8 +863,8 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
     int4* sinfo = reinterpret_cast<int4*>(smem_raw + g.off_sinfo);      // 2 nlev solve steps
     double* kap_s = reinterpret_cast<double*>(smem_raw + g.off_kap_smem);   // kappa of the current K (if staged)
     double* scale = reinterpret_cast<double*>(g.ws + (size_t)blockIdx.x * g.slot_bytes + g.off_scale);   // 1/sqrt(diag A_p)
-    float* opbuf = W;                                                   // 2 x opmax staging (solves only)
-    float* stage = W + 2 * (size_t)g.opmax;                             // staged solve operand(s) (solves only)
+    float* opbuf = W;                                                   // nbuf x opmax staging (solves only)
+    float* stage = W + (size_t)(SCHUR ? g.nbuf : 2) * g.opmax;          // staged solve operand(s) (solves only)
     float* cw = reinterpret_cast<float*>(smem_raw + g.off_cw);          // level-Schur path: 4 x nunk couplings
     __shared__ MCtx c;
     const LevelGeom lg{g.P, g.N, g.PN};
@@ -872,10 +897,10 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             for (int st = 0; st < 2 * g.nlev - 1; ++st) sinfo[st] = schur_step_info(lg, g.nlev, loff, u0, st);
         else
             for (int st = 0; st < 2 * g.nlev; ++st) sinfo[st] = solve_step_info(lg, g.nlev, loff, u0, st);
-        mbar_init(&c.bar[0], 1);
-        mbar_init(&c.bar[1], 1);
-        c.phase[0] = 0;
-        c.phase[1] = 0;
+        for (int b = 0; b < kMaxOpBufs; ++b) {
+            mbar_init(&c.bar[b], 1);
+            c.phase[b] = 0;
+        }
     }
     __syncthreads();
 
@@ -967,7 +992,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             const int nu = g.nunk;
             if constexpr (MODE == 2) {
                 __syncthreads();
-                const int64_t kk = ki - g.Kc0;
+                const int64_t kk = ki - g.Kbase;
                 F = g.Tall + kk * (int64_t)g.t_stride;
                 sc = g.scall + kk * (int64_t)nu;
                 ah = g.ahall + kk * 7 * (int64_t)nu;
@@ -1230,7 +1255,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
             if constexpr (MODE == 2) {
                 // ---- precomputed level-Schur operators of this K: couplings to shared memory
                 __syncthreads();
-                const int64_t kk = ki - g.Kc0;
+                const int64_t kk = ki - g.Kbase;
                 F = g.Tall + kk * (int64_t)g.t_stride;
                 const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
                 for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
@@ -1556,7 +1581,7 @@ __global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedA
     const int nu = g.nunk;
     double* scale = reinterpret_cast<double*>(fs_raw + kFactorWarps * sizeof(FactorSmem)) + (size_t)warp * nu;
     const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
-    const int64_t kk = ki - g.Kc0;
+    const int64_t kk = ki - g.Kbase;
     float* cw = g.cwall + kk * 4 * (int64_t)nu;
     float* T = g.Tall + kk * (int64_t)g.t_stride;
     if (lane == 0) {
@@ -1631,7 +1656,6 @@ struct MixedLayout {
     int kap_in_smem, rpl, cpl;
     bool schur;   // P1 with levels of at most kSchurMax unknowns: level-Schur factorisation
     int mode;     // kernel MODE (0 generic, 1 Schur in the kernel, 2 Schur by k_schur_factor)
-    size_t chunk_k_bytes;   // MODE 2: scratch per K of a chunk (T, couplings, pivot flag)
 };
 
 constexpr int64_t kChunkMax = 8192;   // MODE 2: coarse triangles per factor + solve launch pair
@@ -1676,8 +1700,6 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     const int R = (int)mesh->NI + 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     L.off_G = L.mode == 2 ? 0 : al(f * sizeof(float));   // MODE 2 keeps the operators outside the slots
-    L.chunk_k_bytes = al(f * sizeof(float)) + al((size_t)4 * L.nunk * sizeof(float)) + 256 +
-                      al((size_t)L.nunk * sizeof(double)) + al((size_t)7 * L.nunk * sizeof(double));
     L.off_Z = L.off_G + al((size_t)L.nunk * R * sizeof(double));
     L.off_mass = L.off_Z + al((size_t)L.nunk * R * sizeof(double));
     L.off_scale = L.off_mass + al((size_t)L.nunk * sizeof(double));
@@ -1695,7 +1717,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     if (L.schur) {
         // one staged operand of K = b; the factorisation's S and T (kSchurMax x kSLd each)
         L.stage_floats = ((bmax + 7) / 8) * ((R + 7) / 8) * 64;
-        win = std::max((size_t)2 * L.opmax + (size_t)L.stage_floats, (size_t)R * R * 2);
+        win = std::max((size_t)kMaxOpBufs * L.opmax + (size_t)L.stage_floats, (size_t)R * R * 2);
         if (L.mode == 1) win = std::max(win, (size_t)2 * kSchurMax * kSLd + 2 * kSchurMax);   // S, T, pivot rows
     } else {
         L.stage_floats = ktmax * ((R + 7) / 8) * 64;
@@ -1760,8 +1782,13 @@ int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
 
 namespace {
 
+// the workspace holds chunk regions of kChunkMax elements; a tuned chunk is at most that
 int64_t chunk_of(const Level& lv, const MixedLayout& L) {
     return L.mode == 2 ? std::min<int64_t>(lv.nK, kChunkMax) : 0;
+}
+int64_t tuned_chunk(const Level& lv, const MixedLayout& L) {
+    return L.mode == 2 ? std::min<int64_t>(chunk_of(lv, L), std::max(256, std::min<int>(lv.tune.chunk, (int)kChunkMax)))
+                       : 0;
 }
 
 MixedArgs mixed_args(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L, const double* kappa,
@@ -1811,10 +1838,38 @@ MixedArgs mixed_args(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L
     g.status = status;
     g.iters = iters;
     g.t_stride = L.factor_floats;
+    g.nbuf = std::max(2, std::min(kMaxOpBufs, lv.tune.nbuf));
+    g.l2pf = std::max(0, lv.tune.l2pf);
+    g.pf_all = lv.tune.pf_all != 0;
+    g.op_policy = std::max(0, std::min(2, lv.tune.op_policy));
     return g;
 }
 
 }  // namespace
+
+// Per-K arrays of the factor kernel's output for n coarse elements starting at base: T_lev
+// of every level (fragment order), the FP32 couplings, the pivot flags, the FP64 scaling
+// and the scaled stencil, each array 256-byte aligned.
+static size_t region_bytes(int64_t n, const MixedLayout& L) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return (size_t)n * al(L.factor_floats * sizeof(float)) + al((size_t)n * 4 * L.nunk * sizeof(float)) +
+           al((size_t)n * sizeof(int)) + al((size_t)n * L.nunk * sizeof(double)) +
+           al((size_t)n * 7 * L.nunk * sizeof(double));
+}
+
+static void region_ptrs(char* base, int64_t n, const MixedLayout& L, MixedArgs& g) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* p = base;
+    g.Tall = reinterpret_cast<float*>(p);
+    p += (size_t)n * al(L.factor_floats * sizeof(float));
+    g.cwall = reinterpret_cast<float*>(p);
+    p += al((size_t)n * 4 * L.nunk * sizeof(float));
+    g.fbad = reinterpret_cast<int*>(p);
+    p += al((size_t)n * sizeof(int));
+    g.scall = reinterpret_cast<double*>(p);
+    p += al((size_t)n * L.nunk * sizeof(double));
+    g.ahall = reinterpret_cast<double*>(p);
+}
 
 // The K of launch indices [i0, i1) whose status is not OK, appended to list (order of
 // arrival; each K's result does not depend on it).
@@ -1835,9 +1890,30 @@ static int chunk_buffers(const Level& lv, const MixedLayout& L) {
 }
 
 static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L) {
-    return (size_t)mixed_slots(mesh, L) * L.slot_bytes +
-           (size_t)chunk_buffers(lv, L) * chunk_of(lv, L) * L.chunk_k_bytes + 256 + 256 +
-           (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
+    return (size_t)mixed_slots(mesh, L) * L.slot_bytes + (size_t)chunk_buffers(lv, L) * region_bytes(chunk_of(lv, L), L) +
+           256 + 256 + (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
+}
+
+// Factor store (kept level-Schur factors): the MODE 2 levels one after the other, each a
+// region of all its elements.  Returns the store's size; *offset gets lv's region (or
+// SIZE_MAX for a level without one).
+size_t factor_store_layout(const mhm_mesh* mesh, const Level* lv, size_t* offset) {
+    size_t bytes = 0;
+    if (offset) *offset = SIZE_MAX;
+    if (mesh->device < 0) return 0;
+    for (const Level& l2 : mesh->levels) {
+        if (fp64_level(mesh, l2)) continue;
+        const MixedLayout L = mixed_layout(mesh, l2);
+        if (L.mode != 2) continue;
+        if (&l2 == lv && offset) *offset = bytes;
+        bytes += (region_bytes(l2.nK, L) + 255) & ~(size_t)255;
+    }
+    return bytes;
+}
+
+bool schur_split_level(const mhm_mesh* mesh, const Level& lv) {
+    if (mesh->device < 0 || fp64_level(mesh, lv)) return false;
+    return mixed_layout(mesh, lv).mode == 2;
 }
 
 size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv) {
@@ -1863,7 +1939,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
     // dynamic assignment of coarse triangles to blocks: a counter behind the scratch,
     // zeroed in stream order before every solve launch
     const int nbuf = chunk_buffers(lv, L);
-    int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)nbuf * chunk * L.chunk_k_bytes);
+    int* counter = reinterpret_cast<int*>((char*)workspace + slots_bytes + (size_t)nbuf * region_bytes(chunk, L));
     MixedArgs g = mixed_args(mesh, lv, L, kappa, f, opts, AK, EK, BK, FK, status, iters, (char*)workspace);
     const int64_t nK = K1 - K0;
     if (nK <= 0) return MHM_OK;
@@ -1896,7 +1972,14 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
     // region c % 2 is refilled once the solve of chunk c - 2 is done with it.
     const size_t fsmem = factor_smem_bytes(L.nunk);
     MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-    const bool pipelined = K1 - K0 > chunk;   // then nbuf == 2 (the level has more than one chunk)
+    // the tuned chunk steps through the range; factor launches run one chunk ahead on the
+    // level's stream when there are two chunk regions (or a factor store, whose regions
+    // never repeat), otherwise in the caller's stream order
+    const int64_t tchunk = tuned_chunk(lv, L);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
+    const int tslots = std::max(1, std::min(slots, sms * std::max(1, lv.tune.blocks_per_sm)));
+    const bool pipelined = K1 - K0 > tchunk && (nbuf == 2 || opts.factor_store != nullptr);
     if (pipelined) {
         if (!lv.fstream) {
             MHM_CUDA_TRY(cudaStreamCreateWithFlags(&lv.fstream, cudaStreamNonBlocking));
@@ -1910,35 +1993,43 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         MHM_CUDA_TRY(cudaStreamWaitEvent(lv.fstream, lv.fstart, 0));
     }
     cudaStream_t fs = pipelined ? lv.fstream : stream;
+    // a factor store keeps every element's factors of the level (factor_reuse 0: the factor
+    // launches fill it; 1: they are skipped and the solves read what it holds)
+    char* store = nullptr;
+    if (opts.factor_store) {
+        size_t off = SIZE_MAX;
+        factor_store_layout(mesh, &lv, &off);
+        if (off == SIZE_MAX) return fail(MHM_ERR_INVALID_ARG, "mhm_local_solve_batch: level without a factor store region");
+        store = (char*)opts.factor_store + off;
+    }
+    const bool reuse = store && opts.factor_reuse;
     int c = 0;
-    for (int64_t c0 = K0; c0 < K1; c0 += chunk, ++c) {
-        const int64_t c1 = std::min(K1, c0 + chunk);
+    for (int64_t c0 = K0; c0 < K1; c0 += tchunk, ++c) {
+        const int64_t c1 = std::min(K1, c0 + tchunk);
         const int b = pipelined ? (c & 1) : 0;
-        char* cbase = (char*)workspace + slots_bytes + (size_t)b * chunk * L.chunk_k_bytes;
-        const size_t tb = (size_t)chunk * ((L.factor_floats * sizeof(float) + 255) & ~(size_t)255);
-        g.Tall = reinterpret_cast<float*>(cbase);
-        g.cwall = reinterpret_cast<float*>(cbase + tb);
-        g.fbad = reinterpret_cast<int*>(cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float));
-        {
-            char* p = cbase + tb + (size_t)chunk * 4 * L.nunk * sizeof(float) +
-                      (((size_t)chunk * sizeof(int) + 255) & ~(size_t)255);
-            g.scall = reinterpret_cast<double*>(p);
-            g.ahall = reinterpret_cast<double*>(p + (((size_t)chunk * L.nunk * sizeof(double) + 255) & ~(size_t)255));
+        if (store) {
+            region_ptrs(store, lv.nK, L, g);
+            g.Kbase = 0;
+        } else {
+            region_ptrs((char*)workspace + slots_bytes + (size_t)b * region_bytes(chunk, L), chunk, L, g);
+            g.Kbase = c0;
         }
         g.Kc0 = c0;
         g.K0 = c0;
         g.K1 = c1;
-        if (pipelined && c >= 2) MHM_CUDA_TRY(cudaStreamWaitEvent(fs, lv.mdone[b], 0));
-        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, true);
-        k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, fs>>>(g);
-        timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, false);
-        MHM_CUDA_TRY(cudaGetLastError());
-        if (pipelined) {
-            MHM_CUDA_TRY(cudaEventRecord(lv.fdone[b], fs));
-            MHM_CUDA_TRY(cudaStreamWaitEvent(stream, lv.fdone[b], 0));
+        if (!reuse) {
+            if (pipelined && c >= 2 && !store) MHM_CUDA_TRY(cudaStreamWaitEvent(fs, lv.mdone[b], 0));
+            timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, true);
+            k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, fs>>>(g);
+            timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, false);
+            MHM_CUDA_TRY(cudaGetLastError());
+            if (pipelined) {
+                MHM_CUDA_TRY(cudaEventRecord(lv.fdone[b], fs));
+                MHM_CUDA_TRY(cudaStreamWaitEvent(stream, lv.fdone[b], 0));
+            }
         }
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
-        const int grid = (int)(c1 - c0 < slots ? c1 - c0 : slots);
+        const int grid = (int)(c1 - c0 < tslots ? c1 - c0 : tslots);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
         mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);

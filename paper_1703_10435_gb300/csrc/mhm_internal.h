@@ -58,6 +58,18 @@ struct DeviceMesh {
     int fm, lmax1;           // subfaces per face; largest degree + 1 (the table's row stride per subface)
 };
 
+// Launch shape of the mixed-precision local solves of one refinement level (the
+// autotuner's choices; defaults below): see mhm_tuning in mhm.h.
+struct Tuning {
+    int chunk = 8192;        // elements per factor + solve launch pair (<= kChunkMax)
+    int blocks_per_sm = 3;   // resident solve blocks per SM (<= the kernel's occupancy)
+    int nbuf = 2;            // staged level operators in the shared-memory ring (2..4)
+    int l2pf = 0;            // L2 prefetch distance in level steps (0: none)
+    int pf_all = 0;          // 1: prefetch the element's whole operator set into L2 per solve
+    int op_policy = 0;       // L2 policy of the operator copies: 0 default, 1 evict first, 2 evict last
+    int tuned = 0;           // 1: set by the autotuner or a tuning cache
+};
+
 // The coarse elements of one refinement level: the local-solve and reconstruction
 // kernels run one launch per level (uniform meshes have a single level).
 struct Level {
@@ -69,6 +81,7 @@ struct Level {
     double* d_btab = nullptr;      // NULL: the mesh's table (uniform mesh)
     // mixed path, several chunks: the factor launches run on their own stream, one chunk
     // ahead of the solve launches (created on first use)
+    mutable Tuning tune;
     mutable cudaStream_t fstream = nullptr;
     mutable cudaEvent_t fstart = nullptr, fdone[2] = {nullptr, nullptr}, mdone[2] = {nullptr, nullptr};
 };
@@ -189,6 +202,16 @@ mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const d
                                   const int32_t* list, const int32_t* count, int64_t max_n, double* AK, double* EK,
                                   double* BK, double* FK, int32_t* status, int32_t* iters, cudaStream_t stream);
 size_t mixed_level_workspace(const mhm_mesh* mesh, const Level& lv);   // one level's region (0: FP64 level)
+// bytes of the factor store of the whole mesh; *offset: level lv's region (SIZE_MAX: none)
+size_t factor_store_layout(const mhm_mesh* mesh, const Level* lv, size_t* offset);
+// A level on the level-Schur mixed path with the separate factor kernel (the tuned path).
+bool schur_split_level(const mhm_mesh* mesh, const Level& lv);
+// Offset of level lv's region in the local-solve workspace of `precision`.
+size_t level_region_offset(const mhm_mesh* mesh, const Level& lv, int32_t precision);
+// Launch shapes from a tuning cache, or from a search on this call's inputs (tuner_cache).
+mhm_status tune_from_cache_or_search(const mhm_mesh* mesh, const double* kappa, const mhm_source& f,
+                                     const mhm_solve_opts& o, double* AK, double* EK, double* BK, double* FK,
+                                     int32_t* status, int32_t* iters, void* ws, size_t ws_bytes, cudaStream_t s);
 // A level the MIXED precision runs on the FP64 path: P1 levels wider than 32 points, and
 // levels whose window exceeds the mixed kernel's shared memory (P2 r >= 5).  The FP32 factor
 // of the wide P1 levels (levels of 64 points, jumps of 1e4 in kappa) is too inaccurate to

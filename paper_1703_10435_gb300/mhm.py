@@ -39,7 +39,8 @@ EXPORTED = [
     "mhm_create_mesh", "mhm_destroy_mesh", "mhm_mesh_query", "mhm_local_workspace_size",
     "mhm_local_solve_batch", "mhm_assemble_skeleton", "mhm_last_error", "mhm_measure_pipes",
     "mhm_local_solve_batch_noalloc", "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
-    "mhm_local_solve_waves", "mhm_sync_status",
+    "mhm_local_solve_waves", "mhm_sync_status", "mhm_factor_store_size", "mhm_set_tuning", "mhm_get_tuning",
+    "mhm_autotune",
 ]
 MHM_KERNEL_LOCAL_FP64, MHM_KERNEL_LOCAL_MIXED, MHM_KERNEL_SCHUR_FACTOR = range(3)
 MHM_N_KERNELS = 3
@@ -79,7 +80,35 @@ class Exact(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("it_max", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("K_begin", ctypes.c_int64), ("K_end", ctypes.c_int64), ("no_fallback", ctypes.c_int32)]
+                ("K_begin", ctypes.c_int64), ("K_end", ctypes.c_int64), ("no_fallback", ctypes.c_int32),
+                ("factor_store", ctypes.c_void_p), ("factor_store_bytes", ctypes.c_size_t),
+                ("factor_reuse", ctypes.c_int32), ("tuner_cache", ctypes.c_char_p)]
+
+
+class Tuning(ctypes.Structure):
+    """mhm_tuning: launch shape of the mixed local solves of one level."""
+    _fields_ = [("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("op_buffers", ctypes.c_int32),
+                ("l2_prefetch", ctypes.c_int32), ("prefetch_all", ctypes.c_int32), ("op_policy", ctypes.c_int32),
+                ("ms_per_K", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def solve_opts(it_max=8, tol=1e-12, K_begin=0, K_end=0, no_fallback=0, factor_store=None, factor_reuse=0,
+               tuner_cache=None):
+    """mhm_solve_opts with an optional factor store (a uint8 device tensor of at least
+    mhm_factor_store_size bytes) and tuning cache path."""
+    o = SolveOpts(it_max, tol, K_begin, K_end, no_fallback)
+    if tuner_cache is not None:
+        o._cache = str(tuner_cache).encode()
+        o.tuner_cache = o._cache
+    if factor_store is not None:
+        o.factor_store = ctypes.c_void_p(factor_store.data_ptr())
+        o.factor_store_bytes = factor_store.numel() * factor_store.element_size()
+        o.factor_reuse = factor_reuse
+        o._store = factor_store   # keeps the tensor alive with the struct
+    return o
 
 
 class MHMError(RuntimeError):
@@ -118,6 +147,14 @@ def lib():
         L.mhm_set_timing.argtypes = [vp, i32]
         L.mhm_kernel_times.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
         L.mhm_sync_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+        L.mhm_factor_store_size.argtypes = [vp, ctypes.POINTER(sz)]
+        L.mhm_factor_store_size.restype = i32
+        L.mhm_set_tuning.argtypes = [vp, i32, ctypes.POINTER(Tuning)]
+        L.mhm_get_tuning.argtypes = [vp, i32, ctypes.POINTER(Tuning)]
+        L.mhm_autotune.argtypes = [vp, vp, ctypes.POINTER(Source), ctypes.POINTER(SolveOpts), vp, vp, vp, vp, vp, vp,
+                                   vp, sz, ctypes.c_char_p, vp]
+        for name in ("mhm_set_tuning", "mhm_get_tuning", "mhm_autotune"):
+            getattr(L, name).restype = i32
         L.mhm_sync_status.restype = i32
         for name in ("mhm_create_mesh", "mhm_mesh_query", "mhm_local_workspace_size", "mhm_local_solve_batch",
                      "mhm_assemble_skeleton", "mhm_measure_pipes", "mhm_local_solve_batch_noalloc",
@@ -189,6 +226,12 @@ class Mesh:
 
 def mhm_create_mesh(nx, ny, r, degree, m, l, device: int = 0, r_per_K=None, l_per_face=None) -> Mesh:
     return Mesh(nx, ny, r, degree, m, l, device, r_per_K, l_per_face)
+
+
+def mhm_factor_store_size(mesh: Mesh) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().mhm_factor_store_size(mesh.handle, ctypes.byref(n)))
+    return int(n.value)
 
 
 def mhm_local_workspace_size(mesh: Mesh, precision: int) -> int:
@@ -277,3 +320,21 @@ def mhm_sync_status(mesh: Mesh, stream=None):
             code == MHM_ERR_INVALID_ARG and not w.value):
         _check(code)
     return code, int(w.value)
+
+
+def mhm_set_tuning(mesh: Mesh, r: int, t: Tuning):
+    _check(lib().mhm_set_tuning(mesh.handle, r, ctypes.byref(t)))
+
+
+def mhm_get_tuning(mesh: Mesh, r: int) -> Tuning:
+    t = Tuning()
+    _check(lib().mhm_get_tuning(mesh.handle, r, ctypes.byref(t)))
+    return t
+
+
+def mhm_autotune(mesh: Mesh, kappa, source: Source, opts: SolveOpts | None, AK, EK, BK, FK, status, iters=None,
+                 workspace=None, cache_path=None, stream=None):
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().mhm_autotune(mesh.handle, _ptr(kappa), ctypes.byref(source), None if opts is None else ctypes.byref(opts),
+                              _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters), _ptr(workspace),
+                              ws_bytes, None if cache_path is None else str(cache_path).encode(), _stream(stream)))

@@ -86,6 +86,10 @@ def _fp64_bound(o, kap, base):
     return max(base, 10 * 2.0 ** -53 * hi / lo)
 
 
+# the mixed path at the refinement tolerance of the other mixed parity tests (1e-13)
+OPTS_PARITY = mhm.SolveOpts(10, 1e-13, 0, 0)
+
+
 @pytest.mark.parametrize("precision,tol", [(mhm.MHM_FP64, 1e-10), (mhm.MHM_MIXED, 1e-9)])
 def test_levels_every_element_vs_oracle(precision, tol):
     from paper_1703_10435_gb300.pipeline import Pipeline
@@ -94,7 +98,7 @@ def test_levels_every_element_vs_oracle(precision, tol):
     p = Pipeline(nx, ny, 0, 1, m, l, 0, precision, r_per_K=rs)
     kd = torch.as_tensor(np.concatenate(kap), device="cuda")
     src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
-    p.local(kd, src)
+    p.local(kd, src, OPTS_PARITY)
     torch.cuda.synchronize()
     assert int(p.status.abs().sum()) == 0
     NI = p.mesh.n_I
@@ -111,7 +115,7 @@ def test_levels_every_element_vs_oracle(precision, tol):
         AK2 = torch.empty_like(p.AK)
         EK2, BK2, FK2 = torch.empty_like(p.EK), torch.empty_like(p.BK), torch.empty_like(p.FK)
         st2 = torch.empty_like(p.status)
-        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, None, AK2, EK2, BK2, FK2, st2)
+        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, OPTS_PARITY, AK2, EK2, BK2, FK2, st2)
         torch.cuda.synchronize()
         assert int(st2.abs().sum()) == 0
         assert _rel(AK2.cpu().numpy(), p.AK.cpu().numpy()) < tol
@@ -184,7 +188,7 @@ def test_face_degrees_every_element_vs_oracle(precision, tol):
     d = p.mesh.n_I // 3
     kd = torch.as_tensor(np.concatenate(kap), device="cuda")
     src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
-    p.local(kd, src)
+    p.local(kd, src, OPTS_PARITY)
     torch.cuda.synchronize()
     assert int(p.status.abs().sum()) == 0
     NI = p.mesh.n_I
@@ -206,7 +210,7 @@ def test_face_degrees_every_element_vs_oracle(precision, tol):
         AK2 = torch.empty_like(p.AK)
         EK2, BK2, FK2 = torch.empty_like(p.EK), torch.empty_like(p.BK), torch.empty_like(p.FK)
         st2 = torch.empty_like(p.status)
-        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, None, AK2, EK2, BK2, FK2, st2)
+        mhm.mhm_local_solve_batch_noalloc(p.mesh, kd, src, OPTS_PARITY, AK2, EK2, BK2, FK2, st2)
         torch.cuda.synchronize()
         assert int(st2.abs().sum()) == 0
         assert _rel(AK2.cpu().numpy(), p.AK.cpu().numpy()) < tol
