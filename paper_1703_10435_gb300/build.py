@@ -54,7 +54,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcusolver", "-lcusparse"]
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcusolver", "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -499,6 +499,8 @@ extern "C" void mhm_destroy_mesh(mhm_mesh* m) {
     cudaGetDevice(&cur);
     cudaSetDevice(m->device);
     free_mesh_device(m);
+    mhm::free_nd_plan(m->nd);
+    m->nd = nullptr;
     for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
     for (cudaStream_t ss : m->side) cudaStreamDestroy(ss);
     for (cudaEvent_t e : m->side_done) cudaEventDestroy(e);

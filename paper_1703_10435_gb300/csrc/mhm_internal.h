@@ -70,6 +70,11 @@ struct Tuning {
     int tuned = 0;           // 1: set by the autotuner or a tuning cache
 };
 
+// Multifrontal factorisation plan of the global saddle-point system (mhm_solve_global):
+// built on the first call, kept by the mesh.
+struct NDPlan;
+void free_nd_plan(NDPlan* p);
+
 // The coarse elements of one refinement level: the local-solve and reconstruction
 // kernels run one launch per level (uniform meshes have a single level).
 struct Level {
@@ -151,6 +156,8 @@ struct mhm_mesh {
     // outcome word of the local solves (mhm_sync_status): bit c for a final per-K status c,
     // MHM_STATUS_REFINED_IN_FP64 for FP64 re-solves; written by the kernels with atomicOr
     uint32_t* d_sword = nullptr;
+    // nested-dissection factorisation of the saddle-point system (mhm_solve_global)
+    mutable mhm::NDPlan* nd = nullptr;
 
     // refinement level per K (meshes built with r_per_K; uniform meshes leave these empty)
     bool per_k_levels = false;
