@@ -295,7 +295,7 @@ mhm_status mhm_local_solve_batch_noalloc(const mhm_mesh* mesh, const double* kap
  * are the same bit for bit under every shape. */
 typedef struct {
     int32_t chunk;          /* elements per factor + solve launch pair: 256..8192 */
-    int32_t blocks_per_sm;  /* resident solve blocks per SM: 1..3 */
+    int32_t blocks_per_sm;  /* resident solve blocks per SM: 1..4 (4: a 64-register build of the kernel) */
     int32_t op_buffers;     /* level operators staged ahead in shared memory: 2..4 (the copy
                              * of level step s + op_buffers - 1 is issued at step s) */
     int32_t l2_prefetch;    /* L2 prefetch distance in level steps beyond the staged ones (0: none) */

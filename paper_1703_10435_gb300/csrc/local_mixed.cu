@@ -852,8 +852,8 @@ __device__ __noinline__ void cholesky_level_f32(float* M, int ld, int b, int nr,
 
 // MODE 0: generic level operators (Cholesky); 1: level Schur complements factored in
 // this kernel; 2: level Schur operators precomputed by k_schur_factor.
-template <int RPL, int CPL, int MODE>
-__global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g) {
+template <int RPL, int CPL, int MODE, int MINB>
+__global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs g) {
     constexpr bool SCHUR = MODE >= 1;
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
@@ -996,8 +996,7 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed(const MixedArgs g)
                 F = g.Tall + kk * (int64_t)g.t_stride;
                 sc = g.scall + kk * (int64_t)nu;
                 ah = g.ahall + kk * 7 * (int64_t)nu;
-                const float* src = g.cwall + kk * 4 * (int64_t)nu;
-                for (int t = threadIdx.x; t < 4 * nu; t += blockDim.x) cw[t] = src[t];
+                cw = g.cwall + kk * 4 * (int64_t)nu;   // read in place (L1), no shared copy
                 if (threadIdx.x == 0) c.bad = g.fbad[kk];
             } else {
                 double* ahw = reinterpret_cast<double*>(slot + g.off_D);
@@ -1717,7 +1716,9 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     if (L.schur) {
         // one staged operand of K = b; the factorisation's S and T (kSchurMax x kSLd each)
         L.stage_floats = ((bmax + 7) / 8) * ((R + 7) / 8) * 64;
-        win = std::max((size_t)kMaxOpBufs * L.opmax + (size_t)L.stage_floats, (size_t)R * R * 2);
+        // the ring of the level's tuned depth (the allocation-free entry keeps the default)
+        const int nring = std::max(2, std::min(kMaxOpBufs, lv.tune.nbuf));
+        win = std::max((size_t)nring * L.opmax + (size_t)L.stage_floats, (size_t)R * R * 2);
         if (L.mode == 1) win = std::max(win, (size_t)2 * kSchurMax * kSLd + 2 * kSchurMax);   // S, T, pivot rows
     } else {
         L.stage_floats = ktmax * ((R + 7) / 8) * 64;
@@ -1742,7 +1743,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     L.off_sinfo = off;
     off += (size_t)2 * L.nlev * 16;
     L.off_cw = off;
-    if (L.schur) off += (size_t)4 * L.nunk * sizeof(float);
+    if (L.mode == 1) off += (size_t)4 * L.nunk * sizeof(float);   // MODE 2 reads the couplings in place
     L.smem = (off + 15) & ~(size_t)15;
     // register shape of the warp panel: rows (window) and right-hand-side columns per lane
     int ncols = 0;
@@ -1759,14 +1760,18 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
 
 using MixedKernel = void (*)(const MixedArgs);
 
-MixedKernel mixed_kernel(const MixedLayout& L) {
-    if (L.mode == 2) return k_local_mixed<2, 3, 2>;
-    if (L.mode == 1) return k_local_mixed<2, 3, 1>;
-    if (L.rpl == 2) return k_local_mixed<2, 3, 0>;
-    if (L.rpl == 4) return k_local_mixed<4, 4, 0>;
+// four resident blocks per SM: the level-Schur solve kernel compiled for 64 registers
+MixedKernel mixed_kernel(const MixedLayout& L, int blocks_per_sm = 3) {
+    if (L.mode == 2) return blocks_per_sm >= 4 ? k_local_mixed<2, 3, 2, 4> : k_local_mixed<2, 3, 2, 3>;
+    if (L.mode == 1) return k_local_mixed<2, 3, 1, 3>;
+    if (L.rpl == 2) return k_local_mixed<2, 3, 0, 3>;
+    if (L.rpl == 4) return k_local_mixed<4, 4, 0, 3>;
     return nullptr;
 }
 
+// Resident blocks per SM of the kernel for this layout: the slots of the workspace.  The
+// level-Schur path sizes them for the four-block variant (its shape may be tuned after the
+// workspace was allocated).
 int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
     int dev = mesh->device, sms = 0, per = 0;
     MixedKernel k = mixed_kernel(L);
@@ -1775,6 +1780,7 @@ int mixed_slots(const mhm_mesh* mesh, const MixedLayout& L) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreadsM, L.smem) != cudaSuccess || per < 1)
         per = 1;
+    if (L.mode == 2) per = std::max(per, 4);
     return sms * per;
 }
 
@@ -1979,6 +1985,8 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
     const int tslots = std::max(1, std::min(slots, sms * std::max(1, lv.tune.blocks_per_sm)));
+    const MixedKernel kern = mixed_kernel(L, lv.tune.blocks_per_sm);
+    MHM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     const bool pipelined = K1 - K0 > tchunk && (nbuf == 2 || opts.factor_store != nullptr);
     if (pipelined) {
         if (!lv.fstream) {
@@ -2031,7 +2039,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
         const int grid = (int)(c1 - c0 < tslots ? c1 - c0 : tslots);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
-        mixed_kernel(L)<<<grid, kThreadsM, L.smem, stream>>>(g);
+        kern<<<grid, kThreadsM, L.smem, stream>>>(g);
         timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
         MHM_CUDA_TRY(cudaGetLastError());
         if (pipelined) MHM_CUDA_TRY(cudaEventRecord(lv.mdone[b], stream));

@@ -63,7 +63,7 @@ struct DeviceMesh {
 struct Tuning {
     int chunk = 8192;        // elements per factor + solve launch pair (<= kChunkMax)
     int blocks_per_sm = 3;   // resident solve blocks per SM (<= the kernel's occupancy)
-    int nbuf = 4;            // staged level operators in the shared-memory ring (2..4)
+    int nbuf = 2;            // staged level operators in the shared-memory ring (2..4)
     int l2pf = 0;            // L2 prefetch distance in level steps (0: none)
     int pf_all = 0;          // 1: prefetch the element's whole operator set into L2 per solve
     int op_policy = 1;       // L2 policy of the operator copies: 0 default, 1 evict first, 2 evict last

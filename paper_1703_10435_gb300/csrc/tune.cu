@@ -52,7 +52,7 @@ mhm_tuning to_public(const Tuning& u, double ms) {
 }
 
 bool valid(const mhm_tuning& t) {
-    return t.chunk >= 256 && t.chunk <= 8192 && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 3 && t.op_buffers >= 2 &&
+    return t.chunk >= 256 && t.chunk <= 8192 && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 && t.op_buffers >= 2 &&
            t.op_buffers <= 4 && t.l2_prefetch >= 0 && t.l2_prefetch <= 64 && (t.prefetch_all == 0 || t.prefetch_all == 1) &&
            t.op_policy >= 0 && t.op_policy <= 2;
 }
@@ -151,7 +151,7 @@ mhm_status search_level(const mhm_mesh* mesh, const Level& lv, const double* kap
     };
     const std::vector<Field> fields = {{&Tuning::nbuf, {2, 3, 4}},          {&Tuning::pf_all, {0, 1}},
                                        {&Tuning::l2pf, {0, 2, 4, 8}},       {&Tuning::op_policy, {0, 1, 2}},
-                                       {&Tuning::blocks_per_sm, {2, 3}},    {&Tuning::chunk, {2048, 4096, 8192}}};
+                                       {&Tuning::blocks_per_sm, {2, 3, 4}},    {&Tuning::chunk, {2048, 4096, 8192}}};
     for (int sweep = 0; sweep < 2 && !st; ++sweep) {
         for (const Field& fd : fields) {
             for (int v : fd.values) {

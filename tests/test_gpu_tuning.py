@@ -30,7 +30,7 @@ def _case():
     return w, kd, Pipeline.for_workload(w, 0, mhm.MHM_MIXED)
 
 
-@pytest.mark.parametrize("shape", [(256, 1, 2, 0, 0, 0), (1024, 2, 3, 4, 0, 1), (8192, 3, 4, 0, 1, 2),
+@pytest.mark.parametrize("shape", [(256, 1, 2, 0, 0, 0), (1024, 2, 3, 4, 0, 1), (8192, 3, 4, 0, 1, 2), (4096, 4, 2, 0, 0, 1),
                                    (512, 3, 4, 8, 0, 2)])
 def test_every_shape_same_result(shape):
     w, kd, p = _case()
@@ -80,7 +80,7 @@ def test_autotune_and_cache(tmp_path):
 
 def test_invalid_shapes_refused():
     w, kd, p = _case()
-    for bad in [(100, 3, 2, 0, 0, 0), (1024, 4, 2, 0, 0, 0), (1024, 3, 5, 0, 0, 0), (1024, 3, 2, -1, 0, 0),
+    for bad in [(100, 3, 2, 0, 0, 0), (1024, 5, 2, 0, 0, 0), (1024, 3, 5, 0, 0, 0), (1024, 3, 2, -1, 0, 0),
                 (1024, 3, 2, 0, 2, 0), (1024, 3, 2, 0, 0, 3)]:
         with pytest.raises(mhm.MHMError) as ei:
             mhm.mhm_set_tuning(p.mesh, 5, mhm.Tuning(*bad, 0.0))
