@@ -131,23 +131,50 @@ __device__ __forceinline__ void fine_vertices(const KCtx& c, int N, bool up, int
     }
 }
 
-// Boundary loads N_i = -(s psi_i, phi_w) of the points of level `lev`, placed at
-// window row offset `row0`.
-__device__ void add_face_loads(const Fp64Args& g, const KCtx& c, const LevelGeom& lg, int lev, int row0,
+// Mass m_w = int_K phi_w of lattice point (x, y) of the (P N)-lattice: a third of the fine
+// triangles around a P1 vertex; for P2 a third of the (one or two) triangles sharing an edge
+// midpoint, zero at a vertex.
+__device__ __forceinline__ double node_mass(int P, int N, int x, int y, double area_fine) {
+    auto up_ok = [&](int i, int j) { return i >= 0 && j >= 0 && i + j <= N - 1; };
+    auto dn_ok = [&](int i, int j) { return i >= 0 && j >= 0 && i + j <= N - 2; };
+    int n = 0;
+    if (P == 1) {
+        n = up_ok(x, y) + up_ok(x - 1, y) + up_ok(x, y - 1) + dn_ok(x - 1, y - 1) + dn_ok(x - 1, y) + dn_ok(x, y - 1);
+    } else if ((x & 1) && !(y & 1)) {          // horizontal edge midpoint
+        n = up_ok((x - 1) >> 1, y >> 1) + dn_ok((x - 1) >> 1, (y >> 1) - 1);
+    } else if (!(x & 1) && (y & 1)) {          // vertical edge midpoint
+        n = up_ok(x >> 1, (y - 1) >> 1) + dn_ok((x >> 1) - 1, (y - 1) >> 1);
+    } else if ((x & 1) && (y & 1)) {           // diagonal edge midpoint
+        n = up_ok((x - 1) >> 1, (y - 1) >> 1) + dn_ok((x - 1) >> 1, (y - 1) >> 1);
+    }
+    return n * (area_fine / 3.0);
+}
+
+// Right-hand sides at the nodes of level lev (window rows row0 + p), once per node and
+// column: the face load -(s psi_j, phi_w)_{dK} of multiplier column j on the nodes of its
+// face, the compatible projection -(1^T g / |K|) m_w of every column, and a constant
+// source's load f m_w (other sources' loads are added triangle by triangle in add_fine_row).
+__device__ void add_node_loads(const Fp64Args& g, const KCtx& c, const LevelGeom& lg, int lev, int row0,
                                double* W) {
-    const int b = lg.size(lev);
-    const int work = b * 3 * g.dpf;
-    for (int t = threadIdx.x; t < work; t += blockDim.x) {
-        const int p = t / (3 * g.dpf), rem = t - p * 3 * g.dpf, a = rem / g.dpf, jf = rem - a * g.dpf;
+    const int b = lg.size(lev), R = g.R;
+    for (int t = threadIdx.x; t < b * R; t += blockDim.x) {
+        const int p = t / R, col = t - p * R;
         int x, y;
         lg.point(lev, p, &x, &y);
-        const int kl = face_position(g.PN, x, y, a);
-        if (kl < 0) continue;
-        const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
-        if (row < 0) continue;   // unused slot: no load
-        const int k = c.rev[a] ? g.PN - kl : kl;
-        const double v = -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + k];
-        W[(row0 + p) * g.ld + g.rhs0 + a * g.dpf + jf] += v;
+        const double m = node_mass(g.P, g.N, x, y, c.area_fine);
+        double v = -c.cproj[col] * m;
+        if (col == g.NI) {
+            if (g.src_kind == MHM_SRC_CONST) v += g.src_value * m;
+        } else {
+            const int a = col / g.dpf, jf = col - a * g.dpf;
+            const int kl = face_position(g.PN, x, y, a);
+            const int row = face_row(jf, c.la1[a], g.dm.fm, g.dm.lmax1);
+            if (kl >= 0 && row >= 0) {   // (an unused slot of a lower-degree face has no load)
+                const int k = c.rev[a] ? g.PN - kl : kl;
+                v += -c.sgn[a] * c.flen[a] * g.dm.btab[row * (g.PN + 1) + k];
+            }
+        }
+        W[(row0 + p) * g.ld + g.rhs0 + col] += v;
     }
 }
 
@@ -163,7 +190,7 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
         const int parity = cls & 1;
         const int ntri = up ? N - j : N - 1 - j;
         const int ncls = (ntri - parity + 1) / 2;
-        const int per = npair + nb * g.R;
+        const int per = npair + (g.src_kind == MHM_SRC_CONST ? 0 : nb);   // (the source load per vertex)
         for (int t = threadIdx.x; t < ncls * per; t += blockDim.x) {
             const int ti = t / per, item = t - ti * per;
             const int i = parity + 2 * ti;
@@ -183,21 +210,14 @@ __device__ void add_fine_row(const Fp64Args& g, const KCtx& c, const LevelGeom& 
                 const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
                 W[hi * g.ld + lo] += kt * S[a * nb + bb];
             } else {
-                const int it = item - npair, a = it / g.R, col = it - a * g.R;
+                // (f, phi_a)_T of a source that is not constant, in the source column
+                const int a = item - npair;
                 const int pa = lg.pos(nx[a], ny[a]);
                 if (pa < 0) continue;
                 const int ra = pa + (lg.level_of_row(ny[a]) == j ? 0 : b);
-                const double mass = c.area_fine * element_mass_frac(P, a);
-                double v = -c.cproj[col] * mass;
-                if (col == g.NI) {
-                    if (g.src_kind == MHM_SRC_CONST) v += g.src_value * mass;
-                    else {
-                        double X[3][2];
-                        fine_vertices(c, N, up, i, j, X);
-                        v += cell_source(g, X, P, a, quad_of(g.src_vals, g.kappa, kap, N, up, i, j));
-                    }
-                }
-                W[ra * g.ld + g.rhs0 + col] += v;
+                double X[3][2];
+                fine_vertices(c, N, up, i, j, X);
+                W[ra * g.ld + g.rhs0 + g.NI] += cell_source(g, X, P, a, quad_of(g.src_vals, g.kappa, kap, N, up, i, j));
             }
         }
         __syncthreads();
@@ -289,7 +309,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
     const int b0 = lg.size(0), b1 = lg.size(1);
     for (int t = threadIdx.x; t < (b0 + b1) * g.ld; t += blockDim.x) W[t] = 0.0;
     __syncthreads();
-    add_face_loads(g, c, lg, 0, 0, W);
+    add_node_loads(g, c, lg, 0, 0, W);
     __syncthreads();
 
     // ---- level sweep
@@ -299,7 +319,7 @@ __global__ void __launch_bounds__(WIDE ? kThreadsWide : kThreads, WIDE ? 1 : 4) 
         const int bn = lev + 1 < nlev ? lg.size(lev + 1) : 0;
         const int nr = b + bn;
         if (bn > 0) {
-            add_face_loads(g, c, lg, lev + 1, b, W);
+            add_node_loads(g, c, lg, lev + 1, b, W);
             __syncthreads();
             add_fine_row(g, c, lg, lev, b, kap, W);  // ends with a barrier
         }
