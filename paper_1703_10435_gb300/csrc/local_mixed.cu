@@ -217,6 +217,82 @@ __device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su
         if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
 }
 
+// The assembled P2 row of unknown u at point (X, Y) of the (2N)-lattice: the weights
+// of u and of the points it shares a fine triangle with (19 around a vertex, 9 around
+// an edge midpoint), summed over those triangles (x = X >> 1, y = Y >> 1 indexes the
+// N-lattice), and their unknown indices.  Returns the number of entries (u first).
+// An entry outside K, the pinned DOF, or of zero weight gets weight 0 and index u.
+__device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su, const double* Sd, const double* kap,
+                                      int X, int Y, int u, double w[19], int v[19]) {
+    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
+    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
+    const int x = X >> 1, y = Y >> 1;
+    int n;
+    if (!(X & 1) && !(Y & 1)) {   // vertex
+        const double k0 = kup(x, y), k1 = kup(x - 1, y), k2 = kup(x, y - 1), k3 = kdn(x - 1, y - 1), k4 = kdn(x - 1, y), k5 = kdn(x, y - 1);
+        w[0] = k0 * Su[0] + k1 * Su[7] + k2 * Su[14] + k3 * Sd[7] + k4 * Sd[0] + k5 * Sd[14];  v[0] = u;
+        w[1] = k2 * Su[12] + k3 * Sd[6];  v[1] = unk(PN, X, Y - 2);
+        w[2] = k2 * Su[17];  v[2] = unk(PN, X + 1, Y - 2);
+        w[3] = k2 * Su[13] + k5 * Sd[12];  v[3] = unk(PN, X + 2, Y - 2);
+        w[4] = k3 * Sd[10];  v[4] = unk(PN, X - 1, Y - 1);
+        w[5] = k2 * Su[16] + k3 * Sd[11];  v[5] = unk(PN, X, Y - 1);
+        w[6] = k2 * Su[15] + k5 * Sd[16];  v[6] = unk(PN, X + 1, Y - 1);
+        w[7] = k5 * Sd[17];  v[7] = unk(PN, X + 2, Y - 1);
+        w[8] = k1 * Su[6] + k3 * Sd[8];  v[8] = unk(PN, X - 2, Y);
+        w[9] = k1 * Su[11] + k3 * Sd[9];  v[9] = unk(PN, X - 1, Y);
+        w[10] = k0 * Su[5] + k5 * Sd[15];  v[10] = unk(PN, X + 1, Y);
+        w[11] = k0 * Su[1] + k5 * Sd[13];  v[11] = unk(PN, X + 2, Y);
+        w[12] = k1 * Su[10];  v[12] = unk(PN, X - 2, Y + 1);
+        w[13] = k1 * Su[9] + k4 * Sd[4];  v[13] = unk(PN, X - 1, Y + 1);
+        w[14] = k0 * Su[4] + k4 * Sd[5];  v[14] = unk(PN, X, Y + 1);
+        w[15] = k0 * Su[3];  v[15] = unk(PN, X + 1, Y + 1);
+        w[16] = k1 * Su[8] + k4 * Sd[2];  v[16] = unk(PN, X - 2, Y + 2);
+        w[17] = k4 * Sd[3];  v[17] = unk(PN, X - 1, Y + 2);
+        w[18] = k0 * Su[2] + k4 * Sd[1];  v[18] = unk(PN, X, Y + 2);
+        n = 19;
+    } else if ((X & 1) && !(Y & 1)) {   // horizontal
+        const double k0 = kup(x, y), k1 = kdn(x, y - 1);
+        w[0] = k0 * Su[35] + k1 * Sd[21];  v[0] = u;
+        w[1] = k1 * Sd[18];  v[1] = unk(PN, X + 1, Y - 2);
+        w[2] = k1 * Sd[22];  v[2] = unk(PN, X, Y - 1);
+        w[3] = k1 * Sd[23];  v[3] = unk(PN, X + 1, Y - 1);
+        w[4] = k0 * Su[30] + k1 * Sd[20];  v[4] = unk(PN, X - 1, Y);
+        w[5] = k0 * Su[31] + k1 * Sd[19];  v[5] = unk(PN, X + 1, Y);
+        w[6] = k0 * Su[34];  v[6] = unk(PN, X - 1, Y + 1);
+        w[7] = k0 * Su[33];  v[7] = unk(PN, X, Y + 1);
+        w[8] = k0 * Su[32];  v[8] = unk(PN, X - 1, Y + 2);
+        n = 9;
+    } else if (!(X & 1) && (Y & 1)) {   // vertical
+        const double k0 = kup(x, y), k1 = kdn(x - 1, y);
+        w[0] = k0 * Su[28] + k1 * Sd[35];  v[0] = u;
+        w[1] = k0 * Su[24] + k1 * Sd[30];  v[1] = unk(PN, X, Y - 1);
+        w[2] = k0 * Su[29];  v[2] = unk(PN, X + 1, Y - 1);
+        w[3] = k0 * Su[25];  v[3] = unk(PN, X + 2, Y - 1);
+        w[4] = k1 * Sd[34];  v[4] = unk(PN, X - 1, Y);
+        w[5] = k0 * Su[27];  v[5] = unk(PN, X + 1, Y);
+        w[6] = k1 * Sd[32];  v[6] = unk(PN, X - 2, Y + 1);
+        w[7] = k1 * Sd[33];  v[7] = unk(PN, X - 1, Y + 1);
+        w[8] = k0 * Su[26] + k1 * Sd[31];  v[8] = unk(PN, X, Y + 1);
+        n = 9;
+    } else {   // diagonal
+        const double k0 = kup(x, y), k1 = kdn(x, y);
+        w[0] = k0 * Su[21] + k1 * Sd[28];  v[0] = u;
+        w[1] = k0 * Su[18];  v[1] = unk(PN, X - 1, Y - 1);
+        w[2] = k0 * Su[23];  v[2] = unk(PN, X, Y - 1);
+        w[3] = k0 * Su[19] + k1 * Sd[24];  v[3] = unk(PN, X + 1, Y - 1);
+        w[4] = k0 * Su[22];  v[4] = unk(PN, X - 1, Y);
+        w[5] = k1 * Sd[29];  v[5] = unk(PN, X + 1, Y);
+        w[6] = k0 * Su[20] + k1 * Sd[26];  v[6] = unk(PN, X - 1, Y + 1);
+        w[7] = k1 * Sd[27];  v[7] = unk(PN, X, Y + 1);
+        w[8] = k1 * Sd[25];  v[8] = unk(PN, X + 1, Y + 1);
+        n = 9;
+    }
+    for (int k = n; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
+    for (int k = 1; k < n; ++k)
+        if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
+    return n;
+}
+
 // Conversions between FP32 and FP64 by rearranging the IEEE-754 fields on the
 // integer pipe (a hardware conversion occupies the FP64 pipe here, at the rate of
 // an FP64 multiply-add).  f2d_bits is exact for zero and normal numbers (FP32
@@ -238,53 +314,33 @@ __device__ __forceinline__ float d2f_bits(double d) {
 }
 
 // Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
-// FP32 right-hand side y(u, :) = s_u Res(u, :): the sum over
-// the fine triangles T containing u of kappa_T S_T[a_u][b] D(b).  P1 uses the
-// assembled 7-point row of the lattice (6 triangles, 7 coefficients); P2 sums
-// element by element.
+// FP32 right-hand side y(u, :) = s_u Res(u, :), from the assembled row of u (the sum
+// over the fine triangles T containing u of kappa_T S_T[a_u][b]): 7 entries for P1,
+// up to 19 for P2.
 __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* kap, int u, const double* D,
                                double* Res, float* y, const double s_u) {
     int X, Y;
     lattice_of_unk(g.PN, u, &X, &Y);
     const size_t ld = (size_t)g.nunk;
+    double w[19];
+    int v[19];
     if (g.P == 1) {
-        double w[7];
-        int v[7];
         p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
-        uint32_t nz = 0;   // non-zero weights (zero: edges at right angles), tested on the integer pipe
-#pragma unroll
-        for (int k = 0; k < 7; ++k)
-            if ((__double_as_longlong(w[k]) << 1) != 0) nz |= 1u << k;
-        for (int col = 0; col < g.R; ++col) {
-            if (c.col_done[col]) continue;
-            const double* Dc = D + col * ld;
-            double a = 0.0;
-#pragma unroll
-            for (int k = 0; k < 7; ++k)
-                if (nz >> k & 1) a = fma(w[k], Dc[v[k]], a);
-            const double rn = Res[col * ld + u] - a;
-            Res[col * ld + u] = rn;
-            y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
-        }
-        return;
+        for (int k = 7; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
+    } else {
+        p2_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
     }
-    int ti[6], tj[6], ta[6];
-    bool tup[6];
-    const int n = incident(g.P, g.N, X, Y, ti, tj, tup, ta);
+    uint32_t nz = 0;   // non-zero weights (zero: edges at right angles), tested on the integer pipe
+#pragma unroll
+    for (int k = 0; k < 19; ++k)
+        if ((__double_as_longlong(w[k]) << 1) != 0) nz |= 1u << k;
     for (int col = 0; col < g.R; ++col) {
         if (c.col_done[col]) continue;
         const double* Dc = D + col * ld;
         double a = 0.0;
-        for (int t = 0; t < n; ++t) {
-            int nx[6], ny[6];
-            element_nodes(2, tup[t], ti[t], tj[t], nx, ny);
-            const double kt = kap[kap_index(g.N, tup[t], ti[t], tj[t])];
-            const double* S = tup[t] ? c.Sup : c.Sdn;
-            for (int b = 0; b < 6; ++b) {
-                const int ub = unk(g.PN, nx[b], ny[b]);
-                if (ub >= 0) a = fma(kt * S[ta[t] * 6 + b], Dc[ub], a);
-            }
-        }
+#pragma unroll
+        for (int k = 0; k < 19; ++k)
+            if (nz >> k & 1) a = fma(w[k], Dc[v[k]], a);
         const double rn = Res[col * ld + u] - a;
         Res[col * ld + u] = rn;
         y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
