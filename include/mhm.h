@@ -148,7 +148,8 @@ typedef struct {
                            * 1: they keep their failure status.  MIXED runs P1
                            * levels wider than 32 points (r >= 6) and P2 levels of
                            * r >= 5 on the FP64 path. */
-    /* MIXED, P1 levels of at most 32 points: keep the local factorisations across calls
+    /* MIXED, P1 levels of at most 32 points and P2 levels of r <= 4: keep the local
+     * factorisations across calls
      * (the paper factors each local matrix once and reuses it while kappa does not change,
      * Sec. 3).  factor_store: device memory of mhm_factor_store_size bytes (caller-owned);
      * NULL: no store.  factor_reuse 0: the call factors every element of the range and
@@ -213,7 +214,8 @@ mhm_status mhm_mesh_query(const mhm_mesh* mesh, int32_t what, void* host_out, si
 mhm_status mhm_local_workspace_size(const mhm_mesh* mesh, int32_t precision, size_t* bytes);
 
 /* Bytes of the factor store that mhm_solve_opts.factor_store points to: 0 when no level
- * of the mesh keeps its factors (FP64-only meshes, P2, P1 levels wider than 32 points). */
+ * of the mesh keeps its factors (FP64-only meshes: P1 levels wider than 32 points, P2
+ * levels of r >= 5). */
 mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes);
 
 /* solveLocalProblem for K in [opts->K_begin, opts->K_end) (all K by default):

@@ -228,6 +228,8 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
     auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
     const int x = X >> 1, y = Y >> 1;
     int n;
+#pragma unroll
+    for (int k = 9; k < 19; ++k) { w[k] = 0.0; v[k] = u; }   // (a midpoint's row has 9 entries)
     if (!(X & 1) && !(Y & 1)) {   // vertex
         const double k0 = kup(x, y), k1 = kup(x - 1, y), k2 = kup(x, y - 1), k3 = kdn(x - 1, y - 1), k4 = kdn(x - 1, y), k5 = kdn(x, y - 1);
         w[0] = k0 * Su[0] + k1 * Su[7] + k2 * Su[14] + k3 * Sd[7] + k4 * Sd[0] + k5 * Sd[14];  v[0] = u;
@@ -287,10 +289,21 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
         w[8] = k1 * Sd[25];  v[8] = unk(PN, X + 1, Y + 1);
         n = 9;
     }
-    for (int k = n; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
-    for (int k = 1; k < n; ++k)
+#pragma unroll
+    for (int k = 1; k < 19; ++k)
         if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
     return n;
+}
+
+// The assembled row of degree P (entries past the P1 row's seven: weight 0, index u).
+__device__ __forceinline__ void assembled_row(int P, int N, int PN, int nunk, const double* Su, const double* Sd,
+                                              const double* kap, int X, int Y, int u, double w[19], int v[19]) {
+    if (P == 2) {
+        p2_row(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+        return;
+    }
+    p1_row(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+    for (int k = 7; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
 }
 
 // Conversions between FP32 and FP64 by rearranging the IEEE-754 fields on the
@@ -324,12 +337,7 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
     const size_t ld = (size_t)g.nunk;
     double w[19];
     int v[19];
-    if (g.P == 1) {
-        p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
-        for (int k = 7; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
-    } else {
-        p2_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
-    }
+    assembled_row(g.P, g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
     uint32_t nz = 0;   // non-zero weights (zero: edges at right angles), tested on the integer pipe
 #pragma unroll
     for (int k = 0; k < 19; ++k)
@@ -343,7 +351,7 @@ __device__ void apply_residual(const MixedArgs& g, const MCtx& c, const double* 
             if (nz >> k & 1) a = fma(w[k], Dc[v[k]], a);
         const double rn = Res[col * ld + u] - a;
         Res[col * ld + u] = rn;
-        y[(size_t)u * g.Rp + col] = (float)(rn * s_u);
+        y[(size_t)u * g.Rp + col] = d2f_bits(rn * s_u);
     }
 }
 
@@ -906,11 +914,12 @@ __device__ __noinline__ void cholesky_level_f32(float* M, int ld, int b, int nr,
     blocked_cholesky_level<float, 8, RPL, CPL>(M, ld, b, nr, Rhs, ldr, rhs_rows, ncols, bad);
 }
 
-// MODE 0: generic level operators (Cholesky); 1: level Schur complements factored in
-// this kernel; 2: level Schur operators precomputed by k_schur_factor.
+// MODE 0: generic level operators (Cholesky) factored in this kernel; 1: level Schur
+// complements factored in this kernel; 2: level Schur operators precomputed by
+// k_schur_factor; 3: generic level operators precomputed by k_schur_factor_gen.
 template <int RPL, int CPL, int MODE, int MINB>
 __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs g) {
-    constexpr bool SCHUR = MODE >= 1;
+    constexpr bool SCHUR = MODE == 1 || MODE == 2;
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
     float* y = W + (size_t)g.wfloats;                                    // nunk x R
@@ -1307,32 +1316,13 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
                 }
             }
 
-            if constexpr (MODE == 2) {
-                // ---- precomputed level-Schur operators of this K: couplings to shared memory
+            if constexpr (MODE == 3) {
+                // ---- the level operators of this K, precomputed by the factor kernel
                 __syncthreads();
                 const int64_t kk = ki - g.Kbase;
                 F = g.Tall + kk * (int64_t)g.t_stride;
-                const float* src = g.cwall + kk * 4 * (int64_t)g.nunk;
-                for (int t = threadIdx.x; t < 4 * g.nunk; t += blockDim.x) cw[t] = src[t];
                 if (threadIdx.x == 0) c.bad = g.fbad[kk];
                 __syncthreads();
-            } else if constexpr (MODE == 1) {
-                // ---- FP32 factorisation by level Schur complements: scaled couplings first
-                __syncthreads();   // (publishes scale[] to the block)
-                for (int u = threadIdx.x; u < g.nunk; u += blockDim.x) {
-                    int X, Y;
-                    lattice_of_unk(g.PN, u, &X, &Y);
-                    double w[7];
-                    int v[7];
-                    p1_row(g.N, g.PN, g.nunk, c.Sup, c.Sdn, kap, X, Y, u, w, v);
-                    const double su = scale[u];
-                    cw[u] = (float)(w[1] * su * scale[v[1]]);
-                    cw[g.nunk + u] = (float)(w[2] * su * scale[v[2]]);
-                    cw[2 * g.nunk + u] = (float)(w[4] * su * scale[v[4]]);
-                    cw[3 * g.nunk + u] = (float)(w[5] * su * scale[v[5]]);
-                }
-                __syncthreads();
-                schur_factor(g, loff, u0, cw, W, W + kSchurMax * kSLd, W + 2 * kSchurMax * kSLd, F, c);
             } else {
                 // ---- FP32 factorisation by levels (window rows: level lev, then lev+1)
                 const int b0 = lg.size(0), b1 = g.nlev > 1 ? lg.size(1) : 0;
@@ -1449,7 +1439,7 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
             const int total = g.nunk * R;
             for (int t = threadIdx.x; t < g.nunk * g.Rp; t += blockDim.x) {
                 const int u = t / g.Rp, col = t - u * g.Rp;
-                y[t] = col < R ? (float)(Res[(size_t)col * g.nunk + u] * scale[u]) : 0.0f;
+                y[t] = col < R ? d2f_bits(Res[(size_t)col * g.nunk + u] * scale[u]) : 0.0f;
             }
             for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
             __syncthreads();
@@ -1480,7 +1470,7 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
                 for (int t = threadIdx.x; t < total; t += blockDim.x) {
                     const int col = t / g.nunk, u = t - col * g.nunk;
                     if (c.col_done[col]) continue;
-                    const double d = (double)y[(size_t)u * g.Rp + col] * scale[u];
+                    const double d = f2d_bits(y[(size_t)u * g.Rp + col]) * scale[u];
                     D64[t] = d;
                     Z[t] += d;
                 }
@@ -1704,16 +1694,291 @@ size_t factor_smem_bytes(int nunk) {
     return kFactorWarps * (sizeof(FactorSmem) + (size_t)nunk * sizeof(double));
 }
 
+// ---------------------------------------------------------------------------
+// Levels of the generic path (P2: two lattice rows per level, at most 64 unknowns;
+// P1 with more right-hand sides than the P1 level-Schur solve takes): the level-Schur
+// factorisation as its own kernel, one 64-thread block per coarse triangle (thread p
+// holds row p of the level's matrix).  In scaled variables Ah = S A_p S,
+// S = diag(A_p)^-1/2, with C_lev = Ah_{lev,lev-1}, S_0 = Ah_00,
+// S_lev = Ah_{lev,lev} - C_lev T_{lev-1} C_lev^T and T_lev = S_lev^-1 (the block LDL^T
+// of Ah by levels, as on the P1 path), it writes the operators of the generic level
+// solves, the neighbouring level's rows first:
+//   forward   v_lev = Fw_lev [v_{lev-1}; r_lev],  Fw_lev = [-T_lev C_lev | T_lev]
+//   backward  x_lev = Bw_lev [x_{lev+1}; v_lev],  Bw_lev = [-T_lev C_{lev+1}^T | I]
+// The couplings come from the assembled rows.  Only a level's first lattice row
+// couples to the level below (a P2 fine row's triangles span lattice rows 2j..2j+2),
+// so C_lev T_{lev-1} C_lev^T fills the leading first-row block of S_lev.
+constexpr int kGenMax = 64;            // largest level of this factorisation
+constexpr int kGenRow = 32;            // largest first lattice row of a level
+constexpr int kGenThreads = 64;
+constexpr int kGenLd = kGenMax + 4;    // tile row stride in floats (16-byte aligned rows)
+constexpr int kTabF = 4;               // couplings of a node into the level above it
+constexpr int kTabQ = 8;               // couplings of a first-row node into the level below it
+
+struct GenSmem {
+    alignas(16) float T[kGenMax * kGenLd];     // S_lev, then T_lev (row-major)
+    alignas(16) float rowbuf[2 * kGenMax];     // pivot rows of the Gauss-Jordan steps
+    float Q[kGenMax * (kGenRow + 1)];          // T_lev C_{lev+1}^T, first-row columns of lev + 1
+    float M[kGenRow * (kGenRow + 1)];          // C_{lev+1} T_lev C_{lev+1}^T, first-row block
+    int fpos[kGenMax * kTabF];                 // per column of lev - 1: positions in lev and
+    float fc[kGenMax * kTabF];                 //   couplings (position -1: none)
+    int qpos[kGenRow * kTabQ];                 // per first-row node of lev + 1: the same into lev
+    float qc[kGenRow * kTabQ];
+    double Su[36], Sd[36];                     // element stiffness of the two fine shapes
+    int bad;
+};
+
+// T = S^-1 in place (b x b, b <= kGenMax, rows of stride kGenLd in shared memory) by
+// Gauss-Jordan elimination without pivoting (S is SPD); thread p holds row p in
+// registers.  Pivots go in blocks of 8 with the row array kept rotated so that the
+// block's pivot columns sit at positions 0..7 (the array turns left by 8 after each
+// block), which keeps every register index static.  Row k travels through shared
+// memory; each row applies a[j] -= g r[j] with g = a_pk / a_kk, or 1 - 1/a_kk in row
+// k (which turns it into r / a_kk), then a_pk = -g (1 / a_kk in row k).  Ends with a
+// block barrier.
+__device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b, int lev, int* bad) {
+    const int p = threadIdx.x;
+    float a[kGenMax];
+#pragma unroll
+    for (int j = 0; j < kGenMax; j += 4) {
+        const float4 v = p < b ? *reinterpret_cast<const float4*>(T + p * kGenLd + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[j] = v.x; a[j + 1] = v.y; a[j + 2] = v.z; a[j + 3] = v.w;
+    }
+    const int nblk = (b + 7) >> 3;
+    for (int kb = 0; kb < nblk; ++kb) {
+        uint32_t cm = 0;   // chunk m (positions 8m..8m+7) holds columns 8 ((kb + m) mod 8) + 0..7
+#pragma unroll
+        for (int m = 0; m < kGenMax / 8; ++m)
+            if ((((kb + m) & 7) << 3) < b) cm |= 1u << m;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = kb * 8 + kk;
+            if (k < b) {
+                float* rb = rowbuf + (k & 1) * kGenMax;
+                if (p == k) {
+#pragma unroll
+                    for (int j = 0; j < kGenMax; j += 4)
+                        *reinterpret_cast<float4*>(rb + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+                }
+                __syncthreads();
+                if (p < b) {
+                    const float piv = rb[kk];
+                    if (p == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
+                    const float d = __frcp_rn(piv);
+                    const float gk = p == k ? 1.0f - d : a[kk] * d;
+#pragma unroll
+                    for (int m = 0; m < kGenMax / 8; ++m) {
+                        if (cm >> m & 1) {
+#pragma unroll
+                            for (int t = 0; t < 8; t += 4) {
+                                const float4 r4 = *reinterpret_cast<const float4*>(rb + 8 * m + t);
+                                a[8 * m + t] = fmaf(-gk, r4.x, a[8 * m + t]);
+                                a[8 * m + t + 1] = fmaf(-gk, r4.y, a[8 * m + t + 1]);
+                                a[8 * m + t + 2] = fmaf(-gk, r4.z, a[8 * m + t + 2]);
+                                a[8 * m + t + 3] = fmaf(-gk, r4.w, a[8 * m + t + 3]);
+                            }
+                        }
+                    }
+                    a[kk] = p == k ? d : -gk;
+                }
+            }
+        }
+        float t8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t8[j] = a[j];
+#pragma unroll
+        for (int j = 0; j < kGenMax - 8; ++j) a[j] = a[j + 8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[kGenMax - 8 + j] = t8[j];
+    }
+    // position j now holds column (8 nblk + j) mod kGenMax
+    __syncthreads();
+    if (p < b) {
+#pragma unroll
+        for (int j = 0; j < kGenMax; ++j) {
+            const int col = (8 * nblk + j) & (kGenMax - 1);
+            if (col < b) T[p * kGenLd + col] = a[j];
+        }
+    }
+    __syncthreads();
+}
+
+// Number of unknowns in the first lattice row of level lev (the pinned DOF 0 excluded).
+__device__ __forceinline__ int first_row_size(const LevelGeom& lg, int lev) {
+    if (lg.P == 1 || lev == lg.N) return lg.size(lev);
+    return lg.PN - 2 * lev + 1 - (lev == 0);
+}
+
+// Couplings of unknown u into the unknowns [lo, lo + n): up to cap (position, scaled
+// FP32 weight) pairs, position -1 after the last.
+__device__ __forceinline__ void coupling_table(const MixedArgs& g, const GenSmem& s, const double* kap,
+                                               const double* scale, int u, int lo, int n, int cap, int* pos, float* cf) {
+    int X, Y;
+    lattice_of_unk(g.PN, u, &X, &Y);
+    double w[19];
+    int v[19];
+    assembled_row(g.P, g.N, g.PN, g.nunk, s.Su, s.Sd, kap, X, Y, u, w, v);
+    const double su = scale[u];
+    int m = 0;
+#pragma unroll
+    for (int k = 1; k < 19; ++k)
+        if (v[k] != u && v[k] >= lo && v[k] < lo + n && m < cap) {
+            pos[m] = v[k] - lo;
+            cf[m] = (float)(w[k] * su * scale[v[k]]);
+            ++m;
+        }
+    for (; m < cap; ++m) { pos[m] = -1; cf[m] = 0.0f; }
+}
+
+// An operator of b rows and Kc columns to global memory in fragment order (one float4 per
+// lane and 16 x 8 tile, the layout of write_frag_op), entry (i, k) from val(i, k) inside
+// the operator and 0 in the padding.
+template <class Val>
+__device__ __forceinline__ void write_frag_gen(float* dst, int b, int Kc, const Val& val) {
+    const int KT = (Kc + 7) >> 3, MT = (b + 15) >> 4, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    auto at = [&](int i, int k) { return (i < b && k < Kc) ? val(i, k) : 0.0f; };
+    for (int tile = warp; tile < MT * KT; tile += kGenThreads / 32) {
+        const int mt = tile / KT, kt = tile - mt * KT;
+        const int i0 = mt * 16 + g, k0 = kt * 8 + t;
+        reinterpret_cast<float4*>(dst)[tile * 32 + lane] =
+            make_float4(at(i0, k0), at(i0 + 8, k0), at(i0, k0 + 4), at(i0 + 8, k0 + 4));
+    }
+}
+
+__global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArgs g) {
+    extern __shared__ unsigned char gs_raw[];
+    GenSmem& s = *reinterpret_cast<GenSmem*>(gs_raw);
+    double* scale = reinterpret_cast<double*>(gs_raw + sizeof(GenSmem));   // nunk
+    const int64_t ki = g.Kc0 + blockIdx.x;   // launch index within the level
+    if (ki >= g.K1) return;
+    const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;
+    const int p = threadIdx.x, nu = g.nunk;
+    const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
+    const int64_t kk = ki - g.Kbase;
+    float* F = g.Tall + kk * (int64_t)g.t_stride;
+    if (p == 0) {
+        // the two fine-triangle shapes (up and down) of the uniform refinement
+        double V[3][2];
+        for (int v = 0; v < 3; ++v) {
+            V[v][0] = g.dm.geom[6 * K + 2 * v];
+            V[v][1] = g.dm.geom[6 * K + 2 * v + 1];
+        }
+        const double e1x = (V[1][0] - V[0][0]) / g.N, e1y = (V[1][1] - V[0][1]) / g.N;
+        const double e2x = (V[2][0] - V[0][0]) / g.N, e2y = (V[2][1] - V[0][1]) / g.N;
+        const double Xu[3][2] = {{V[0][0], V[0][1]}, {V[0][0] + e1x, V[0][1] + e1y}, {V[0][0] + e2x, V[0][1] + e2y}};
+        const double Xd[3][2] = {{V[0][0] + e1x, V[0][1] + e1y},
+                                 {V[0][0] + e1x + e2x, V[0][1] + e1y + e2y},
+                                 {V[0][0] + e2x, V[0][1] + e2y}};
+        element_stiffness(g.P, Xu, s.Su);
+        element_stiffness(g.P, Xd, s.Sd);
+        s.bad = 0;
+    }
+    __syncthreads();
+    for (int u = p; u < nu; u += kGenThreads) {
+        int X, Y;
+        lattice_of_unk(g.PN, u, &X, &Y);
+        double w[19];
+        int v[19];
+        assembled_row(g.P, g.N, g.PN, nu, s.Su, s.Sd, kap, X, Y, u, w, v);
+        scale[u] = 1.0 / sqrt(w[0]);
+    }
+    __syncthreads();
+    const LevelGeom lg{g.P, g.N, g.PN};
+    int ul = 0, o = 0;   // first unknown of the level, operator offset
+    for (int lev = 0; lev < g.nlev; ++lev) {
+        const int b = lg.size(lev);
+        const int bp = lev > 0 ? lg.size(lev - 1) : 0;
+        const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
+        const int l0 = first_row_size(lg, lev), l0n = bn > 0 ? first_row_size(lg, lev + 1) : 0;
+        // S_lev: row p from the assembled row of its unknown, less the Schur update
+        if (p < b) {
+            float* row = s.T + p * kGenLd;
+            for (int j = 0; j < kGenMax; ++j) row[j] = 0.0f;
+            const int u = ul + p;
+            int X, Y;
+            lattice_of_unk(g.PN, u, &X, &Y);
+            double w[19];
+            int v[19];
+            assembled_row(g.P, g.N, g.PN, nu, s.Su, s.Sd, kap, X, Y, u, w, v);
+            const double su = scale[u];
+#pragma unroll
+            for (int k = 0; k < 19; ++k)
+                if (v[k] >= ul && v[k] < ul + b) row[v[k] - ul] += (float)(w[k] * su * scale[v[k]]);
+            if (lev > 0 && p < l0)
+                for (int q = 0; q < l0; ++q) row[q] -= s.M[p * (kGenRow + 1) + q];
+        }
+        // couplings of the level below into this level (columns of C_lev)
+        for (int k = p; k < bp; k += kGenThreads)
+            coupling_table(g, s, kap, scale, ul - bp + k, ul, b, kTabF, s.fpos + k * kTabF, s.fc + k * kTabF);
+        // couplings of the next level's first row into this level (rows of C_{lev+1})
+        for (int q = p; q < l0n; q += kGenThreads)
+            coupling_table(g, s, kap, scale, ul + b + q, ul, b, kTabQ, s.qpos + q * kTabQ, s.qc + q * kTabQ);
+        __syncthreads();
+        gauss_jordan_gen(s.T, s.rowbuf, b, lev, &s.bad);
+        // Fw_lev = [-T C_lev | T] in fragment order
+        write_frag_gen(F + o, b, bp + b, [&](int i, int k) {
+            if (k >= bp) return s.T[i * kGenLd + (k - bp)];
+            float acc = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kTabF; ++m) {
+                const int q = s.fpos[k * kTabF + m];
+                if (q >= 0) acc = fmaf(s.T[i * kGenLd + q], s.fc[k * kTabF + m], acc);
+            }
+            return -acc;
+        });
+        o += frag_op_floats(b, bp + b);
+        // Q = T C_{lev+1}^T on the next level's first-row columns
+        for (int t = p; t < b * l0n; t += kGenThreads) {
+            const int i = t / l0n, q = t - i * l0n;
+            float acc = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kTabQ; ++m) {
+                const int a = s.qpos[q * kTabQ + m];
+                if (a >= 0) acc = fmaf(s.T[i * kGenLd + a], s.qc[q * kTabQ + m], acc);
+            }
+            s.Q[i * (kGenRow + 1) + q] = acc;
+        }
+        __syncthreads();
+        // Bw_lev = [-Q | I] in fragment order (zero on the next level's other rows)
+        write_frag_gen(F + o, b, bn + b, [&](int i, int k) {
+            if (k >= bn) return (k - bn == i) ? 1.0f : 0.0f;
+            return k < l0n ? -s.Q[i * (kGenRow + 1) + k] : 0.0f;
+        });
+        o += frag_op_floats(b, bn + b);
+        // M = C_{lev+1} Q on the next level's first-row block
+        for (int t = p; t < l0n * l0n; t += kGenThreads) {
+            const int i = t / l0n, q = t - i * l0n;
+            float acc = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kTabQ; ++m) {
+                const int a = s.qpos[i * kTabQ + m];
+                if (a >= 0) acc = fmaf(s.qc[i * kTabQ + m], s.Q[a * (kGenRow + 1) + q], acc);
+            }
+            s.M[i * (kGenRow + 1) + q] = acc;
+        }
+        __syncthreads();
+        ul += b;
+    }
+    if (p == 0) g.fbad[kk] = s.bad;
+}
+
+size_t gen_factor_smem_bytes(int nunk) {
+    return sizeof(GenSmem) + (size_t)nunk * sizeof(double);
+}
+
 struct MixedLayout {
     int nlev, nunk, wrows, wld, wfloats, yfloats, bmax, opmax, ldr, Rp, stage_floats;
     size_t factor_floats, slot_bytes, off_G, off_Z, off_mass, off_scale, off_D, smem;
     size_t off_kap_smem, off_scale_smem, off_sinfo, off_cw;
     int kap_in_smem, rpl, cpl;
     bool schur;   // P1 with levels of at most kSchurMax unknowns: level-Schur factorisation
-    int mode;     // kernel MODE (0 generic, 1 Schur in the kernel, 2 Schur by k_schur_factor)
+    int mode;     // kernel MODE (0 generic, 1 Schur in the kernel, 2 Schur by k_schur_factor,
+                  // 3 generic by k_schur_factor_gen)
 };
 
-constexpr int64_t kChunkMax = 8192;   // MODE 2: coarse triangles per factor + solve launch pair
+constexpr int64_t kChunkMax = 8192;      // MODE 2: coarse triangles per factor + solve launch pair
+constexpr int64_t kChunkMaxGen = 4096;   // MODE 3 (about 4x the operator floats per element)
 
 // split: the level-Schur path factors in k_schur_factor (MODE 2) instead of in the
 // solve kernel (MODE 1; the allocation-free entry, whose scratch cannot hold the
@@ -1731,7 +1996,10 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     int bmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) bmax = std::max(bmax, size(lev));
     L.schur = P == 1 && bmax <= kSchurMax && mesh->NI + 1 <= 32;
-    L.mode = L.schur ? (split ? 2 : 1) : 0;
+    int row0 = 0;   // largest first lattice row of a level (unknowns)
+    for (int lev = 0; lev < L.nlev; ++lev)
+        row0 = std::max(row0, P == 1 || lev == N ? size(lev) : 2 * N - 2 * lev + 1 - (lev == 0));
+    L.mode = L.schur ? (split ? 2 : 1) : (split && bmax <= kGenMax && row0 <= kGenRow ? 3 : 0);
     size_t f = 0;
     int opmax = 0;
     for (int lev = 0; lev < L.nlev; ++lev) {
@@ -1754,7 +2022,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     L.wld = (L.wrows + 4) & ~3;   // rows 16-byte aligned for the vector panel loads
     const int R = (int)mesh->NI + 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    L.off_G = L.mode == 2 ? 0 : al(f * sizeof(float));   // MODE 2 keeps the operators outside the slots
+    L.off_G = L.mode >= 2 ? 0 : al(f * sizeof(float));   // MODEs 2 and 3 keep the operators outside the slots
     L.off_Z = L.off_G + al((size_t)L.nunk * R * sizeof(double));
     L.off_mass = L.off_Z + al((size_t)L.nunk * R * sizeof(double));
     L.off_scale = L.off_mass + al((size_t)L.nunk * sizeof(double));
@@ -1778,6 +2046,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
         if (L.mode == 1) win = std::max(win, (size_t)2 * kSchurMax * kSLd + 2 * kSchurMax);   // S, T, pivot rows
     } else {
         L.stage_floats = ktmax * ((R + 7) / 8) * 64;
+        if (L.mode == 3) win = (size_t)R * R * 2;   // no factorisation window: operators and operands only
         if (win < (size_t)2 * L.opmax + (size_t)2 * L.stage_floats) win = (size_t)2 * L.opmax + (size_t)2 * L.stage_floats;
     }
     win = (win + 3) & ~(size_t)3;
@@ -1785,7 +2054,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     size_t yf = (size_t)L.nunk * L.Rp;
     if (yf < (size_t)2 * R * 64) yf = (size_t)2 * R * 64;   // also holds two R x 64 staging chunks
     L.ldr = (2 * bmax + 3) & ~3;
-    if (!L.schur && yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
+    if (L.mode == 0 && yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
     if (L.schur) yf = std::max(yf, (size_t)(10 * R * R + 16 * R + 8));      // and the output partials
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
     size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
@@ -1820,6 +2089,7 @@ using MixedKernel = void (*)(const MixedArgs);
 MixedKernel mixed_kernel(const MixedLayout& L, int blocks_per_sm = 3) {
     if (L.mode == 2) return blocks_per_sm >= 4 ? k_local_mixed<2, 3, 2, 4> : k_local_mixed<2, 3, 2, 3>;
     if (L.mode == 1) return k_local_mixed<2, 3, 1, 3>;
+    if (L.mode == 3) return k_local_mixed<2, 3, 3, 2>;
     if (L.rpl == 2) return k_local_mixed<2, 3, 0, 3>;
     if (L.rpl == 4) return k_local_mixed<4, 4, 0, 3>;
     return nullptr;
@@ -1846,10 +2116,10 @@ namespace {
 
 // the workspace holds chunk regions of kChunkMax elements; a tuned chunk is at most that
 int64_t chunk_of(const Level& lv, const MixedLayout& L) {
-    return L.mode == 2 ? std::min<int64_t>(lv.nK, kChunkMax) : 0;
+    return L.mode == 2 ? std::min<int64_t>(lv.nK, kChunkMax) : L.mode == 3 ? std::min<int64_t>(lv.nK, kChunkMaxGen) : 0;
 }
 int64_t tuned_chunk(const Level& lv, const MixedLayout& L) {
-    return L.mode == 2 ? std::min<int64_t>(chunk_of(lv, L), std::max(256, std::min<int>(lv.tune.chunk, (int)kChunkMax)))
+    return L.mode >= 2 ? std::min<int64_t>(chunk_of(lv, L), std::max(256, std::min<int>(lv.tune.chunk, (int)kChunkMax)))
                        : 0;
 }
 
@@ -1909,13 +2179,14 @@ MixedArgs mixed_args(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L
 
 }  // namespace
 
-// Per-K arrays of the factor kernel's output for n coarse elements starting at base: T_lev
-// of every level (fragment order), the FP32 couplings, the pivot flags, the FP64 scaling
-// and the scaled stencil, each array 256-byte aligned.
+// Per-K arrays of the factor kernel's output for n coarse elements starting at base: the
+// level operators (fragment order), the pivot flags and, for MODE 2, the FP32 couplings,
+// the FP64 scaling and the scaled stencil, each array 256-byte aligned.
 static size_t region_bytes(int64_t n, const MixedLayout& L) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return (size_t)n * al(L.factor_floats * sizeof(float)) + al((size_t)n * 4 * L.nunk * sizeof(float)) +
-           al((size_t)n * sizeof(int)) + al((size_t)n * L.nunk * sizeof(double)) +
+    const size_t ops = (size_t)n * al(L.factor_floats * sizeof(float)) + al((size_t)n * sizeof(int));
+    if (L.mode == 3) return ops;
+    return ops + al((size_t)n * 4 * L.nunk * sizeof(float)) + al((size_t)n * L.nunk * sizeof(double)) +
            al((size_t)n * 7 * L.nunk * sizeof(double));
 }
 
@@ -1924,6 +2195,13 @@ static void region_ptrs(char* base, int64_t n, const MixedLayout& L, MixedArgs& 
     char* p = base;
     g.Tall = reinterpret_cast<float*>(p);
     p += (size_t)n * al(L.factor_floats * sizeof(float));
+    if (L.mode == 3) {
+        g.fbad = reinterpret_cast<int*>(p);
+        g.cwall = nullptr;
+        g.scall = nullptr;
+        g.ahall = nullptr;
+        return;
+    }
     g.cwall = reinterpret_cast<float*>(p);
     p += al((size_t)n * 4 * L.nunk * sizeof(float));
     g.fbad = reinterpret_cast<int*>(p);
@@ -1948,7 +2226,7 @@ __global__ void k_collect_failed(const int32_t* klist, int64_t i0, int64_t i1, c
 // chunk regions of a level: two (factor of chunk c+1 beside the solve of chunk c) when
 // the level spans several chunks
 static int chunk_buffers(const Level& lv, const MixedLayout& L) {
-    return (L.mode == 2 && lv.nK > kChunkMax) ? 2 : 1;
+    return (L.mode >= 2 && lv.nK > chunk_of(lv, L)) ? 2 : 1;
 }
 
 static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const MixedLayout& L) {
@@ -1956,8 +2234,8 @@ static size_t level_workspace(const mhm_mesh* mesh, const Level& lv, const Mixed
            256 + 256 + (((size_t)lv.nK * sizeof(int32_t) + 255) & ~(size_t)255);
 }
 
-// Factor store (kept level-Schur factors): the MODE 2 levels one after the other, each a
-// region of all its elements.  Returns the store's size; *offset gets lv's region (or
+// Factor store (kept level-Schur factors): the MODE 2 and 3 levels one after the other,
+// each a region of all its elements.  Returns the store's size; *offset gets lv's region (or
 // SIZE_MAX for a level without one).
 size_t factor_store_layout(const mhm_mesh* mesh, const Level* lv, size_t* offset) {
     size_t bytes = 0;
@@ -1966,7 +2244,7 @@ size_t factor_store_layout(const mhm_mesh* mesh, const Level* lv, size_t* offset
     for (const Level& l2 : mesh->levels) {
         if (fp64_level(mesh, l2)) continue;
         const MixedLayout L = mixed_layout(mesh, l2);
-        if (L.mode != 2) continue;
+        if (L.mode < 2) continue;
         if (&l2 == lv && offset) *offset = bytes;
         bytes += (region_bytes(l2.nK, L) + 255) & ~(size_t)255;
     }
@@ -2017,7 +2295,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         MHM_CUDA_TRY(cudaGetLastError());
         return launch_local_fp64_list(mesh, lv, kappa, f, flist, fcount, nK, AK, EK, BK, FK, status, iters, stream);
     };
-    if (L.mode != 2) {
+    if (L.mode < 2) {
         g.K0 = K0;
         g.K1 = K1;
         MHM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
@@ -2028,12 +2306,15 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         MHM_CUDA_TRY(cudaGetLastError());
         return fallback();
     }
-    // MODE 2: per chunk, the factor kernel writes T, couplings, scaling, scaled stencil and
-    // pivot flags into a chunk region behind the slots; the solve kernel reads them.  With
-    // several chunks the factor launches run on the level's own stream, one chunk ahead:
-    // region c % 2 is refilled once the solve of chunk c - 2 is done with it.
-    const size_t fsmem = factor_smem_bytes(L.nunk);
-    MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    // MODEs 2 and 3: per chunk, the factor kernel writes the level operators and pivot flags
+    // (MODE 2 also the couplings, scaling and scaled stencil) into a chunk region behind the
+    // slots; the solve kernel reads them.  With several chunks the factor launches run on
+    // the level's own stream, one chunk ahead: region c % 2 is refilled once the solve of
+    // chunk c - 2 is done with it.
+    const bool gen = L.mode == 3;
+    const size_t fsmem = gen ? gen_factor_smem_bytes(L.nunk) : factor_smem_bytes(L.nunk);
+    if (gen) MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    else MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     // the tuned chunk steps through the range; factor launches run one chunk ahead on the
     // level's stream when there are two chunk regions (or a factor store, whose regions
     // never repeat), otherwise in the caller's stream order
@@ -2084,7 +2365,8 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         if (!reuse) {
             if (pipelined && c >= 2 && !store) MHM_CUDA_TRY(cudaStreamWaitEvent(fs, lv.mdone[b], 0));
             timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, true);
-            k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, fs>>>(g);
+            if (gen) k_schur_factor_gen<<<(unsigned)(c1 - c0), kGenThreads, fsmem, fs>>>(g);
+            else k_schur_factor<<<(unsigned)((c1 - c0 + kFactorWarps - 1) / kFactorWarps), 32 * kFactorWarps, fsmem, fs>>>(g);
             timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, fs, false);
             MHM_CUDA_TRY(cudaGetLastError());
             if (pipelined) {

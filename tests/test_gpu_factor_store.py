@@ -35,10 +35,11 @@ def _fresh(w, kd, src, K0=0, K1=0):
     return p
 
 
-@pytest.mark.parametrize("nx,ny", [(8, 8), (64, 72)])   # one chunk; 9216 elements = two chunks
-def test_factor_store_reuse_with_new_source(nx, ny):
+# one chunk; two chunks (P1: 9216 elements of 8192 per chunk, P2: 4608 of 4096)
+@pytest.mark.parametrize("nx,ny,P,r", [(8, 8, 1, 5), (64, 72, 1, 5), (8, 8, 2, 3), (48, 48, 2, 4)])
+def test_factor_store_reuse_with_new_source(nx, ny, P, r):
     from paper_1703_10435_gb300.pipeline import Pipeline
-    w = W.Workload("t", nx, ny, 5, 1, 2, 2, "log_uniform", "const", 1.0, seed=12)
+    w = W.Workload("t", nx, ny, r, P, 2, 2, "log_uniform", "const", 1.0, seed=12)
     kd = W.kappa_for_torch(w, torch.device("cuda")).reshape(-1).contiguous()
     f1 = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
     f2 = mhm.Source(mhm.MHM_SRC_SINSIN, 1.0, 2.0)
@@ -65,7 +66,7 @@ def test_factor_store_reuse_with_new_source(nx, ny):
         mesh = build_mesh(w.nx, w.ny, w.m, w.l)
         f = source_fn("sinsin", 1.0, 2.0)
         for K in (0, 37, w.n_K - 1):
-            o = solve_local(mesh, K, w.r, 1, kap[K], f)
+            o = solve_local(mesh, K, w.r, w.degree, kap[K], f)
             assert_blocks(AK[K], EK[K], BK[K], FK[K], o, 1e-9, K)
 
 
