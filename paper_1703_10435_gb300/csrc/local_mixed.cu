@@ -914,6 +914,164 @@ __device__ __noinline__ void cholesky_level_f32(float* M, int ld, int b, int nr,
     blocked_cholesky_level<float, 8, RPL, CPL>(M, ld, b, nr, Rhs, ldr, rhs_rows, ncols, bad);
 }
 
+// ---------------------------------------------------------------------------
+// Generic levels (P2: two lattice rows per level, at most 64 unknowns; P1 with more
+// right-hand sides than the P1 level-Schur solve takes): the block LDL^T of Ah = S A_p S
+// by levels, as on the P1 path, factored by k_schur_factor_gen.  Only a level's first
+// lattice row couples to the level below (a P2 fine row's triangles span lattice rows
+// 2j..2j+2), and the couplings come from the assembled rows, kept as tables:
+//   forward   v_lev = T_lev (r_lev - C_lev v_{lev-1})
+//   backward  x_lev = v_lev - T_lev (C_{lev+1}^T x_{lev+1})
+// An element's operator block: T_lev of every level in fragment order, then per level
+// lev >= 1 the forward table (kTabQ entries per first-row node of lev: its couplings into
+// lev - 1), then per level lev <= nlev - 2 the backward table (kTabF entries per node of
+// lev: its couplings into lev + 1); an entry is two floats, the position in the other
+// level (int bits; -1: none) and the scaled FP32 weight.
+constexpr int kGenMax = 64;            // largest level of this path
+constexpr int kGenRow = 32;            // largest first lattice row of a level
+constexpr int kTabF = 4;               // couplings of a node into the level above it
+constexpr int kTabQ = 8;               // couplings of a first-row node into the level below it
+
+// Number of unknowns in the first lattice row of level lev (the pinned DOF 0 excluded).
+__device__ __forceinline__ int first_row_size(const LevelGeom& lg, int lev) {
+    if (lg.P == 1 || lev == lg.N) return lg.size(lev);
+    return lg.PN - 2 * lev + 1 - (lev == 0);
+}
+
+// Offsets (floats) of level lev's T, forward table and backward table in the operator block.
+__device__ inline void gen_offsets(const LevelGeom& lg, int nlev, int lev, int* t_off, int* f_off, int* b_off) {
+    int t = 0, tl = 0, fl = 0, bl = 0, fsum = 0, bsum = 0;
+    for (int l = 0; l < nlev; ++l) {
+        const int b = lg.size(l);
+        if (l == lev) { tl = t; fl = fsum; bl = bsum; }
+        t += frag_op_floats(b, b);
+        if (l >= 1) fsum += 2 * kTabQ * first_row_size(lg, l);
+        if (l + 1 < nlev) bsum += 2 * kTabF * b;
+    }
+    *t_off = tl;
+    *f_off = t + fl;
+    *b_off = t + fsum + bl;
+}
+
+// Per solve step: (b | dir << 8 | l0 << 16, ulev | uo << 16, table offset, T offset); l0 is
+// the forward step's first-row size (0 at level 0), uo the first unknown of the other level.
+__device__ inline int4 gen_step_info(const LevelGeom& lg, int nlev, const int* u0, int st) {
+    const int dir = st >= nlev, lev = dir ? 2 * nlev - 2 - st : st;
+    int t_off, f_off, b_off;
+    gen_offsets(lg, nlev, lev, &t_off, &f_off, &b_off);
+    const int b = lg.size(lev);
+    if (!dir) {
+        const int l0 = lev > 0 ? first_row_size(lg, lev) : 0;
+        return make_int4(b | (l0 << 16), u0[lev] | ((lev > 0 ? u0[lev - 1] : 0) << 16), lev > 0 ? f_off : 0, t_off);
+    }
+    return make_int4(b | (1 << 8), u0[lev] | (u0[lev + 1] << 16), b_off, t_off);
+}
+
+// Forward + backward solve of the generic path for every column still refining, in place
+// in y (node-major: y[u * R + col]): per level step the operand is staged from y through
+// the coupling tables, then one b x b by b x R product with T_lev on the tensor cores
+// (three-term TF32 split, as in solve_factor); T_lev streams into two shared-memory
+// buffers by bulk copies, one step ahead.
+__device__ __noinline__ void solve_gen(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
+                                       float* opbuf, float* stage, MCtx& c) {
+    const int R = g.R, NT = (R + 7) >> 3;
+    const int nsteps = 2 * g.nlev - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const uint32_t y_s = smem_u32(y), op_s = smem_u32(opbuf), st_s = smem_u32(stage);
+    uint32_t ph0 = c.phase[0], ph1 = c.phase[1];
+    const int si0 = threadIdx.x / R, sc0 = threadIdx.x - si0 * R, srq = kThreadsM / R, srr = kThreadsM - srq * R;
+    uint64_t frozen = 0;
+    for (int col = 0; col < R; ++col)
+        if (c.col_frozen[col]) frozen |= 1ull << col;
+    auto issue = [&](int st) {
+        const int4 si = sinfo[st];
+        const int b = si.x & 0xff;
+        const uint32_t bytes = (uint32_t)frag_op_floats(b, b) * 4u;
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&c.bar[st & 1], bytes);
+        bulk_copy_g2s(opbuf + (size_t)(st & 1) * g.opmax, F + si.w, bytes, &c.bar[st & 1]);
+    };
+    const bool issuer = threadIdx.x == kThreadsM - 32;
+    if (issuer) issue(0);
+    for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding stays 0
+    __syncthreads();
+    for (int st = 0; st < nsteps; ++st) {
+        const int4 si = sinfo[st];
+        const int b = si.x & 0xff, dir = (si.x >> 8) & 1, l0 = si.x >> 16;
+        const int ulev = si.y & 0xffff, uo = si.y >> 16;
+        const float2* tab = reinterpret_cast<const float2*>(F + si.z);
+        // the other buffer was last read in step st - 1, which ended with a barrier
+        if (issuer && st + 1 < nsteps) issue(st + 1);
+        // operand (b x R, fragment order): forward r_lev - C_lev v_{lev-1}, backward
+        // C_{lev+1}^T x_{lev+1}
+        {
+            int i = si0, col = sc0;
+            for (int t = threadIdx.x; t < b * R; t += kThreadsM) {
+                float v = 0.0f;
+                if (dir == 0) {
+                    v = lds1(y_s + 4u * (uint32_t)((ulev + i) * R + col));
+                    if (i < l0) {
+#pragma unroll
+                        for (int m = 0; m < kTabQ; ++m) {
+                            const float2 e = tab[i * kTabQ + m];
+                            const int pos = __float_as_int(e.x);
+                            if (pos >= 0) v = fmaf(-e.y, lds1(y_s + 4u * (uint32_t)((uo + pos) * R + col)), v);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < kTabF; ++m) {
+                        const float2 e = tab[i * kTabF + m];
+                        const int pos = __float_as_int(e.x);
+                        if (pos >= 0) v = fmaf(e.y, lds1(y_s + 4u * (uint32_t)((uo + pos) * R + col)), v);
+                    }
+                }
+                sts1(st_s + 4u * frag_b_pos(i, col, NT), v);
+                i += srq;
+                col += srr;
+                if (col >= R) { col -= R; ++i; }
+            }
+        }
+        const uint32_t par = (st & 1) ? ph1 : ph0;
+        if (!mbar_wait_bounded(&c.bar[st & 1], par)) c.timeout = 1;
+        if (st & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        __syncthreads();
+        const int KT = (b + 7) >> 3, MT = (b + 15) >> 4;
+        const uint32_t op0 = op_s + (uint32_t)((st & 1) * g.opmax) * 4u;
+        for (int q = warp; q < MT * NT; q += kWarpsM) {
+            const int mt = q / NT, nt = q - mt * NT;
+            const uint32_t aa = op0 + (uint32_t)(((mt * KT) * 32 + lane) * 16);
+            const uint32_t ba = st_s + (uint32_t)((nt * 32 + lane) * 8);
+            const uint32_t bstep = (uint32_t)(NT * 32 * 8);
+            float cv[4];
+            switch (KT) {
+                case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
+                case 2: tile_product<2>(aa, ba, bstep, KT, cv); break;
+                case 3: tile_product<3>(aa, ba, bstep, KT, cv); break;
+                case 4: tile_product<4>(aa, ba, bstep, KT, cv); break;
+                case 5: tile_product<5>(aa, ba, bstep, KT, cv); break;
+                case 6: tile_product<6>(aa, ba, bstep, KT, cv); break;
+                case 7: tile_product<7>(aa, ba, bstep, KT, cv); break;
+                default: tile_product<8>(aa, ba, bstep, KT, cv); break;
+            }
+            // forward: y_lev = result; backward: y_lev -= result (columns still refining)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = mt * 16 + gq + 8 * (e >> 1), col = nt * 8 + 2 * tq + (e & 1);
+                if (i < b && col < R && !(frozen >> col & 1)) {
+                    const uint32_t ya = y_s + 4u * (uint32_t)((ulev + i) * R + col);
+                    sts1(ya, dir == 0 ? cv[e] : lds1(ya) - cv[e]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        c.phase[0] = ph0;
+        c.phase[1] = ph1;
+    }
+}
+
 // MODE 0: generic level operators (Cholesky) factored in this kernel; 1: level Schur
 // complements factored in this kernel; 2: level Schur operators precomputed by
 // k_schur_factor; 3: generic level operators precomputed by k_schur_factor_gen.
@@ -960,6 +1118,8 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
         u0[g.nlev] = u;
         if (SCHUR)
             for (int st = 0; st < 2 * g.nlev - 1; ++st) sinfo[st] = schur_step_info(lg, g.nlev, loff, u0, st);
+        else if (MODE == 3)
+            for (int st = 0; st < 2 * g.nlev - 1; ++st) sinfo[st] = gen_step_info(lg, g.nlev, u0, st);
         else
             for (int st = 0; st < 2 * g.nlev; ++st) sinfo[st] = solve_step_info(lg, g.nlev, loff, u0, st);
         for (int b = 0; b < kMaxOpBufs; ++b) {
@@ -1444,7 +1604,8 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
             for (int t = threadIdx.x; t < total; t += blockDim.x) Z[t] = 0.0;
             __syncthreads();
             // gamma_c = G_c^T M G_c ~ ||z_c||^2_{A_p}
-            solve_factor(g, F, sinfo, y, opbuf, stage, c);
+            if constexpr (MODE == 3) solve_gen(g, F, sinfo, y, opbuf, stage, c);
+            else solve_factor(g, F, sinfo, y, opbuf, stage, c);
             __syncthreads();
             column_dot(g, Res, y, scale, c.gamma, c);
             __syncthreads();
@@ -1490,7 +1651,8 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
                 }
                 __syncthreads();
                 if (c.all_done) break;
-                solve_factor(g, F, sinfo, y, opbuf, stage, c);
+                if constexpr (MODE == 3) solve_gen(g, F, sinfo, y, opbuf, stage, c);
+                else solve_factor(g, F, sinfo, y, opbuf, stage, c);
                 __syncthreads();
                 column_dot(g, Res, y, scale, c.eps, c);
                 __syncthreads();
@@ -1695,35 +1857,21 @@ size_t factor_smem_bytes(int nunk) {
 }
 
 // ---------------------------------------------------------------------------
-// Levels of the generic path (P2: two lattice rows per level, at most 64 unknowns;
-// P1 with more right-hand sides than the P1 level-Schur solve takes): the level-Schur
-// factorisation as its own kernel, one 64-thread block per coarse triangle (thread p
-// holds row p of the level's matrix).  In scaled variables Ah = S A_p S,
-// S = diag(A_p)^-1/2, with C_lev = Ah_{lev,lev-1}, S_0 = Ah_00,
-// S_lev = Ah_{lev,lev} - C_lev T_{lev-1} C_lev^T and T_lev = S_lev^-1 (the block LDL^T
-// of Ah by levels, as on the P1 path), it writes the operators of the generic level
-// solves, the neighbouring level's rows first:
-//   forward   v_lev = Fw_lev [v_{lev-1}; r_lev],  Fw_lev = [-T_lev C_lev | T_lev]
-//   backward  x_lev = Bw_lev [x_{lev+1}; v_lev],  Bw_lev = [-T_lev C_{lev+1}^T | I]
-// The couplings come from the assembled rows.  Only a level's first lattice row
-// couples to the level below (a P2 fine row's triangles span lattice rows 2j..2j+2),
-// so C_lev T_{lev-1} C_lev^T fills the leading first-row block of S_lev.
-constexpr int kGenMax = 64;            // largest level of this factorisation
-constexpr int kGenRow = 32;            // largest first lattice row of a level
+// The generic path's level-Schur factorisation (see solve_gen) as its own kernel, one
+// 64-thread block per coarse triangle, thread p holding row p of the level's matrix:
+// S_0 = Ah_00, S_lev = Ah_{lev,lev} - C_lev T_{lev-1} C_lev^T (on the leading first-row
+// block), T_lev = S_lev^-1 by Gauss-Jordan elimination in FP32, written with the coupling
+// tables into the element's operator block.
 constexpr int kGenThreads = 64;
 constexpr int kGenLd = kGenMax + 4;    // tile row stride in floats (16-byte aligned rows)
-constexpr int kTabF = 4;               // couplings of a node into the level above it
-constexpr int kTabQ = 8;               // couplings of a first-row node into the level below it
 
 struct GenSmem {
     alignas(16) float T[kGenMax * kGenLd];     // S_lev, then T_lev (row-major)
     alignas(16) float rowbuf[2 * kGenMax];     // pivot rows of the Gauss-Jordan steps
     float Q[kGenMax * (kGenRow + 1)];          // T_lev C_{lev+1}^T, first-row columns of lev + 1
     float M[kGenRow * (kGenRow + 1)];          // C_{lev+1} T_lev C_{lev+1}^T, first-row block
-    int fpos[kGenMax * kTabF];                 // per column of lev - 1: positions in lev and
-    float fc[kGenMax * kTabF];                 //   couplings (position -1: none)
-    int qpos[kGenRow * kTabQ];                 // per first-row node of lev + 1: the same into lev
-    float qc[kGenRow * kTabQ];
+    int qpos[kGenRow * kTabQ];                 // per first-row node of lev + 1: positions in lev
+    float qc[kGenRow * kTabQ];                 //   and couplings (position -1: none)
     double Su[36], Sd[36];                     // element stiffness of the two fine shapes
     int bad;
 };
@@ -1803,12 +1951,6 @@ __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b,
     __syncthreads();
 }
 
-// Number of unknowns in the first lattice row of level lev (the pinned DOF 0 excluded).
-__device__ __forceinline__ int first_row_size(const LevelGeom& lg, int lev) {
-    if (lg.P == 1 || lev == lg.N) return lg.size(lev);
-    return lg.PN - 2 * lev + 1 - (lev == 0);
-}
-
 // Couplings of unknown u into the unknowns [lo, lo + n): up to cap (position, scaled
 // FP32 weight) pairs, position -1 after the last.
 __device__ __forceinline__ void coupling_table(const MixedArgs& g, const GenSmem& s, const double* kap,
@@ -1885,7 +2027,7 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
     }
     __syncthreads();
     const LevelGeom lg{g.P, g.N, g.PN};
-    int ul = 0, o = 0;   // first unknown of the level, operator offset
+    int ul = 0;   // first unknown of the level
     for (int lev = 0; lev < g.nlev; ++lev) {
         const int b = lg.size(lev);
         const int bp = lev > 0 ? lg.size(lev - 1) : 0;
@@ -1908,26 +2050,35 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
             if (lev > 0 && p < l0)
                 for (int q = 0; q < l0; ++q) row[q] -= s.M[p * (kGenRow + 1) + q];
         }
-        // couplings of the level below into this level (columns of C_lev)
-        for (int k = p; k < bp; k += kGenThreads)
-            coupling_table(g, s, kap, scale, ul - bp + k, ul, b, kTabF, s.fpos + k * kTabF, s.fc + k * kTabF);
-        // couplings of the next level's first row into this level (rows of C_{lev+1})
-        for (int q = p; q < l0n; q += kGenThreads)
-            coupling_table(g, s, kap, scale, ul + b + q, ul, b, kTabQ, s.qpos + q * kTabQ, s.qc + q * kTabQ);
+        int t_off, f_off, b_off;
+        // backward table of the level below: its nodes' couplings into this level
+        if (lev > 0) {
+            gen_offsets(lg, g.nlev, lev - 1, &t_off, &f_off, &b_off);
+            for (int k = p; k < bp; k += kGenThreads) {
+                int pos[kTabF];
+                float cf[kTabF];
+                coupling_table(g, s, kap, scale, ul - bp + k, ul, b, kTabF, pos, cf);
+                float2* e = reinterpret_cast<float2*>(F + b_off) + k * kTabF;
+#pragma unroll
+                for (int m = 0; m < kTabF; ++m) e[m] = make_float2(__int_as_float(pos[m]), cf[m]);
+            }
+        }
+        // the next level's first-row couplings into this level (rows of C_{lev+1}): its
+        // forward table, and kept for the Schur update
+        if (l0n > 0) {
+            gen_offsets(lg, g.nlev, lev + 1, &t_off, &f_off, &b_off);
+            for (int q = p; q < l0n; q += kGenThreads) {
+                coupling_table(g, s, kap, scale, ul + b + q, ul, b, kTabQ, s.qpos + q * kTabQ, s.qc + q * kTabQ);
+                float2* e = reinterpret_cast<float2*>(F + f_off) + q * kTabQ;
+#pragma unroll
+                for (int m = 0; m < kTabQ; ++m) e[m] = make_float2(__int_as_float(s.qpos[q * kTabQ + m]), s.qc[q * kTabQ + m]);
+            }
+        }
         __syncthreads();
         gauss_jordan_gen(s.T, s.rowbuf, b, lev, &s.bad);
-        // Fw_lev = [-T C_lev | T] in fragment order
-        write_frag_gen(F + o, b, bp + b, [&](int i, int k) {
-            if (k >= bp) return s.T[i * kGenLd + (k - bp)];
-            float acc = 0.0f;
-#pragma unroll
-            for (int m = 0; m < kTabF; ++m) {
-                const int q = s.fpos[k * kTabF + m];
-                if (q >= 0) acc = fmaf(s.T[i * kGenLd + q], s.fc[k * kTabF + m], acc);
-            }
-            return -acc;
-        });
-        o += frag_op_floats(b, bp + b);
+        // T_lev in fragment order
+        gen_offsets(lg, g.nlev, lev, &t_off, &f_off, &b_off);
+        write_frag_gen(F + t_off, b, b, [&](int i, int k) { return s.T[i * kGenLd + k]; });
         // Q = T C_{lev+1}^T on the next level's first-row columns
         for (int t = p; t < b * l0n; t += kGenThreads) {
             const int i = t / l0n, q = t - i * l0n;
@@ -1940,12 +2091,6 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
             s.Q[i * (kGenRow + 1) + q] = acc;
         }
         __syncthreads();
-        // Bw_lev = [-Q | I] in fragment order (zero on the next level's other rows)
-        write_frag_gen(F + o, b, bn + b, [&](int i, int k) {
-            if (k >= bn) return (k - bn == i) ? 1.0f : 0.0f;
-            return k < l0n ? -s.Q[i * (kGenRow + 1) + k] : 0.0f;
-        });
-        o += frag_op_floats(b, bn + b);
         // M = C_{lev+1} Q on the next level's first-row block
         for (int t = p; t < l0n * l0n; t += kGenThreads) {
             const int i = t / l0n, q = t - i * l0n;
@@ -2005,10 +2150,15 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     for (int lev = 0; lev < L.nlev; ++lev) {
         const int b = size(lev), bn = lev + 1 < L.nlev ? size(lev + 1) : 0;
         const int bp = lev > 0 ? size(lev - 1) : 0;
-        if (L.schur) {
+        if (L.schur || L.mode == 3) {
             const int t = frag_op_floats(b, b);
             f += (size_t)t;
             opmax = std::max(opmax, t);
+            if (L.mode == 3) {   // coupling tables: forward (first rows of levels >= 1), backward
+                const int l0 = P == 1 || lev == N ? b : 2 * N - 2 * lev + 1 - (lev == 0);
+                if (lev >= 1) f += (size_t)2 * kTabQ * l0;
+                if (lev + 1 < L.nlev) f += (size_t)2 * kTabF * b;
+            }
         } else {
             const int fw = frag_op_floats(b, b + bp), bw = frag_op_floats(b, b + bn);
             f += (size_t)fw + bw;
@@ -2046,8 +2196,13 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
         if (L.mode == 1) win = std::max(win, (size_t)2 * kSchurMax * kSLd + 2 * kSchurMax);   // S, T, pivot rows
     } else {
         L.stage_floats = ktmax * ((R + 7) / 8) * 64;
-        if (L.mode == 3) win = (size_t)R * R * 2;   // no factorisation window: operators and operands only
-        if (win < (size_t)2 * L.opmax + (size_t)2 * L.stage_floats) win = (size_t)2 * L.opmax + (size_t)2 * L.stage_floats;
+        if (L.mode == 3) {
+            // no factorisation window: two operator buffers and one staged operand of K = b
+            L.stage_floats = ((bmax + 7) / 8) * ((R + 7) / 8) * 64;
+            win = std::max((size_t)R * R * 2, (size_t)2 * L.opmax + (size_t)L.stage_floats);
+        }
+        if (win < (size_t)2 * L.opmax + (size_t)2 * L.stage_floats && L.mode != 3)
+            win = (size_t)2 * L.opmax + (size_t)2 * L.stage_floats;
     }
     win = (win + 3) & ~(size_t)3;
     L.wfloats = (int)win;
