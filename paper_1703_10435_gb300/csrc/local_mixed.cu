@@ -195,17 +195,48 @@ __device__ __forceinline__ void lattice_of_unk(int PN, int u, int* X, int* Y) {
     *Y = y;
 }
 
+// Conversions between FP32 and FP64 by rearranging the IEEE-754 fields on the
+// integer pipe (a hardware conversion occupies the FP64 pipe here, at the rate of
+// an FP64 multiply-add).  f2d_bits is exact for zero and normal numbers (FP32
+// subnormals flush to zero); d2f_bits truncates the significand (round toward
+// zero) and flushes magnitudes below the FP32 normal range to zero.  Only finite
+// values of FP32 range pass through them.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint32_t hi = e ? (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu) : (b & 0x80000000u);
+    const uint32_t lo = e ? (b << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (e <= 0) return __uint_as_float(hi & 0x80000000u);
+    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// x == 0 (either sign) tested on the integer pipe (a floating-point comparison of doubles
+// occupies the FP64 pipe)
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(float x) { return (__float_as_uint(x) << 1) == 0; }
+
+// kappa in the arithmetic of an assembled row (FP32: converted on the integer pipe)
+template <typename T> __device__ __forceinline__ T kappa_as(double k);
+template <> __device__ __forceinline__ double kappa_as<double>(double k) { return k; }
+template <> __device__ __forceinline__ float kappa_as<float>(double k) { return d2f_bits(k); }
+
 // The assembled P1 row of unknown u at lattice point (x, yl): the weights of u and
 // of its six lattice neighbours (east, west, north, south, south-east, north-west:
 // the edges of the six fine triangles around it) and their unknown indices.  A
 // neighbour outside K, the pinned DOF, or an edge of zero weight (a right angle)
 // gets weight 0 and index u.
-__device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su, const double* Sd, const double* kap,
-                                       int x, int yl, int u, double w[7], int v[7]) {
-    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
-    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
-    const double k1 = kup(x, yl), k2 = kup(x - 1, yl), k3 = kup(x, yl - 1);
-    const double k4 = kdn(x - 1, yl - 1), k5 = kdn(x - 1, yl), k6 = kdn(x, yl - 1);
+template <typename T>
+__device__ __forceinline__ void p1_row(int N, int PN, int nunk, const T* Su, const T* Sd, const double* kap,
+                                       int x, int yl, int u, T w[7], int v[7]) {
+    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kappa_as<T>(kap[kap_index(N, true, i, j)]) : T(0); };
+    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kappa_as<T>(kap[kap_index(N, false, i, j)]) : T(0); };
+    const T k1 = kup(x, yl), k2 = kup(x - 1, yl), k3 = kup(x, yl - 1);
+    const T k4 = kdn(x - 1, yl - 1), k5 = kdn(x - 1, yl), k6 = kdn(x, yl - 1);
     w[0] = k1 * Su[0] + k2 * Su[4] + k3 * Su[8] + k4 * Sd[4] + k5 * Sd[0] + k6 * Sd[8];  v[0] = u;
     w[1] = k1 * Su[1] + k6 * Sd[7];  v[1] = unk(PN, x + 1, yl);        // east
     w[2] = k2 * Su[3] + k4 * Sd[5];  v[2] = unk(PN, x - 1, yl);        // west
@@ -214,7 +245,7 @@ __device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su
     w[5] = k3 * Su[7] + k6 * Sd[6];  v[5] = unk(PN, x + 1, yl - 1);    // south-east
     w[6] = k2 * Su[5] + k5 * Sd[2];  v[6] = unk(PN, x - 1, yl + 1);    // north-west
     for (int k = 1; k < 7; ++k)
-        if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
+        if (is_zero(w[k]) || v[k] < 0 || v[k] >= nunk) { w[k] = T(0); v[k] = u; }
 }
 
 // The assembled P2 row of unknown u at point (X, Y) of the (2N)-lattice: the weights
@@ -222,16 +253,17 @@ __device__ __forceinline__ void p1_row(int N, int PN, int nunk, const double* Su
 // an edge midpoint), summed over those triangles (x = X >> 1, y = Y >> 1 indexes the
 // N-lattice), and their unknown indices.  Returns the number of entries (u first).
 // An entry outside K, the pinned DOF, or of zero weight gets weight 0 and index u.
-__device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su, const double* Sd, const double* kap,
-                                      int X, int Y, int u, double w[19], int v[19]) {
-    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kap[kap_index(N, true, i, j)] : 0.0; };
-    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kap[kap_index(N, false, i, j)] : 0.0; };
+template <typename T>
+__device__ __forceinline__ int p2_row(int N, int PN, int nunk, const T* Su, const T* Sd, const double* kap,
+                                      int X, int Y, int u, T w[19], int v[19]) {
+    auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kappa_as<T>(kap[kap_index(N, true, i, j)]) : T(0); };
+    auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kappa_as<T>(kap[kap_index(N, false, i, j)]) : T(0); };
     const int x = X >> 1, y = Y >> 1;
     int n;
 #pragma unroll
-    for (int k = 9; k < 19; ++k) { w[k] = 0.0; v[k] = u; }   // (a midpoint's row has 9 entries)
+    for (int k = 9; k < 19; ++k) { w[k] = T(0); v[k] = u; }   // (a midpoint's row has 9 entries)
     if (!(X & 1) && !(Y & 1)) {   // vertex
-        const double k0 = kup(x, y), k1 = kup(x - 1, y), k2 = kup(x, y - 1), k3 = kdn(x - 1, y - 1), k4 = kdn(x - 1, y), k5 = kdn(x, y - 1);
+        const T k0 = kup(x, y), k1 = kup(x - 1, y), k2 = kup(x, y - 1), k3 = kdn(x - 1, y - 1), k4 = kdn(x - 1, y), k5 = kdn(x, y - 1);
         w[0] = k0 * Su[0] + k1 * Su[7] + k2 * Su[14] + k3 * Sd[7] + k4 * Sd[0] + k5 * Sd[14];  v[0] = u;
         w[1] = k2 * Su[12] + k3 * Sd[6];  v[1] = unk(PN, X, Y - 2);
         w[2] = k2 * Su[17];  v[2] = unk(PN, X + 1, Y - 2);
@@ -253,7 +285,7 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
         w[18] = k0 * Su[2] + k4 * Sd[1];  v[18] = unk(PN, X, Y + 2);
         n = 19;
     } else if ((X & 1) && !(Y & 1)) {   // horizontal
-        const double k0 = kup(x, y), k1 = kdn(x, y - 1);
+        const T k0 = kup(x, y), k1 = kdn(x, y - 1);
         w[0] = k0 * Su[35] + k1 * Sd[21];  v[0] = u;
         w[1] = k1 * Sd[18];  v[1] = unk(PN, X + 1, Y - 2);
         w[2] = k1 * Sd[22];  v[2] = unk(PN, X, Y - 1);
@@ -265,7 +297,7 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
         w[8] = k0 * Su[32];  v[8] = unk(PN, X - 1, Y + 2);
         n = 9;
     } else if (!(X & 1) && (Y & 1)) {   // vertical
-        const double k0 = kup(x, y), k1 = kdn(x - 1, y);
+        const T k0 = kup(x, y), k1 = kdn(x - 1, y);
         w[0] = k0 * Su[28] + k1 * Sd[35];  v[0] = u;
         w[1] = k0 * Su[24] + k1 * Sd[30];  v[1] = unk(PN, X, Y - 1);
         w[2] = k0 * Su[29];  v[2] = unk(PN, X + 1, Y - 1);
@@ -277,7 +309,7 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
         w[8] = k0 * Su[26] + k1 * Sd[31];  v[8] = unk(PN, X, Y + 1);
         n = 9;
     } else {   // diagonal
-        const double k0 = kup(x, y), k1 = kdn(x, y);
+        const T k0 = kup(x, y), k1 = kdn(x, y);
         w[0] = k0 * Su[21] + k1 * Sd[28];  v[0] = u;
         w[1] = k0 * Su[18];  v[1] = unk(PN, X - 1, Y - 1);
         w[2] = k0 * Su[23];  v[2] = unk(PN, X, Y - 1);
@@ -291,39 +323,20 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const double* Su,
     }
 #pragma unroll
     for (int k = 1; k < 19; ++k)
-        if (w[k] == 0.0 || v[k] < 0 || v[k] >= nunk) { w[k] = 0.0; v[k] = u; }
+        if (is_zero(w[k]) || v[k] < 0 || v[k] >= nunk) { w[k] = T(0); v[k] = u; }
     return n;
 }
 
 // The assembled row of degree P (entries past the P1 row's seven: weight 0, index u).
-__device__ __forceinline__ void assembled_row(int P, int N, int PN, int nunk, const double* Su, const double* Sd,
-                                              const double* kap, int X, int Y, int u, double w[19], int v[19]) {
+template <typename T>
+__device__ __forceinline__ void assembled_row(int P, int N, int PN, int nunk, const T* Su, const T* Sd,
+                                              const double* kap, int X, int Y, int u, T w[19], int v[19]) {
     if (P == 2) {
-        p2_row(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+        p2_row<T>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
         return;
     }
-    p1_row(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
-    for (int k = 7; k < 19; ++k) { w[k] = 0.0; v[k] = u; }
-}
-
-// Conversions between FP32 and FP64 by rearranging the IEEE-754 fields on the
-// integer pipe (a hardware conversion occupies the FP64 pipe here, at the rate of
-// an FP64 multiply-add).  f2d_bits is exact for zero and normal numbers (FP32
-// subnormals flush to zero); d2f_bits truncates the significand (round toward
-// zero) and flushes magnitudes below the FP32 normal range to zero.  Only finite
-// values of FP32 range pass through them.
-__device__ __forceinline__ double f2d_bits(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xffu;
-    const uint32_t hi = e ? (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu) : (b & 0x80000000u);
-    const uint32_t lo = e ? (b << 29) : 0u;
-    return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ float d2f_bits(double d) {
-    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
-    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-    if (e <= 0) return __uint_as_float(hi & 0x80000000u);
-    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    p1_row<T>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+    for (int k = 7; k < 19; ++k) { w[k] = T(0); v[k] = u; }
 }
 
 // Res(u, :) -= (A_p D)(u, :) for the columns still refining, in FP64, and the next
@@ -364,7 +377,7 @@ __device__ __noinline__ void column_dot(const MixedArgs& g, const double* Res, c
         if (c.col_frozen[col]) continue;
         const double* rc = Res + (size_t)col * g.nunk;
         float a = 0.0f;   // an error estimate: FP32 is ample
-        for (int u = lane; u < g.nunk; u += 32) a = fmaf((float)rc[u] * (float)s[u], y[(size_t)u * g.Rp + col], a);
+        for (int u = lane; u < g.nunk; u += 32) a = fmaf(d2f_bits(rc[u]) * d2f_bits(s[u]), y[(size_t)u * g.Rp + col], a);
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) out[col] = (double)a;
     }
@@ -1697,8 +1710,8 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
                 __syncthreads();
                 for (int t = threadIdx.x; t < R * kChunk; t += blockDim.x) {
                     const int col = t / kChunk, uu = t - col * kChunk;
-                    zs[t] = uu < cnt ? (float)Z[(size_t)col * g.nunk + base + uu] : 0.0f;
-                    rs[t] = uu < cnt ? (float)Res[(size_t)col * g.nunk + base + uu] : 0.0f;
+                    zs[t] = uu < cnt ? d2f_bits(Z[(size_t)col * g.nunk + base + uu]) : 0.0f;
+                    rs[t] = uu < cnt ? d2f_bits(Res[(size_t)col * g.nunk + base + uu]) : 0.0f;
                 }
                 __syncthreads();
                 for (int q = 0; q * kThreadsM + (int)threadIdx.x < npair; ++q) {
@@ -1873,6 +1886,7 @@ struct GenSmem {
     int qpos[kGenRow * kTabQ];                 // per first-row node of lev + 1: positions in lev
     float qc[kGenRow * kTabQ];                 //   and couplings (position -1: none)
     double Su[36], Sd[36];                     // element stiffness of the two fine shapes
+    float Suf[36], Sdf[36];                    // (FP32: the factor's assembled rows)
     int bad;
 };
 
@@ -1952,21 +1966,22 @@ __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b,
 }
 
 // Couplings of unknown u into the unknowns [lo, lo + n): up to cap (position, scaled
-// FP32 weight) pairs, position -1 after the last.
+// weight) pairs, position -1 after the last.  The factorisation assembles and scales in
+// FP32 (it is an FP32 approximation of Ah; the refinement residual stays FP64).
 __device__ __forceinline__ void coupling_table(const MixedArgs& g, const GenSmem& s, const double* kap,
-                                               const double* scale, int u, int lo, int n, int cap, int* pos, float* cf) {
+                                               const float* scale, int u, int lo, int n, int cap, int* pos, float* cf) {
     int X, Y;
     lattice_of_unk(g.PN, u, &X, &Y);
-    double w[19];
+    float w[19];
     int v[19];
-    assembled_row(g.P, g.N, g.PN, g.nunk, s.Su, s.Sd, kap, X, Y, u, w, v);
-    const double su = scale[u];
+    assembled_row<float>(g.P, g.N, g.PN, g.nunk, s.Suf, s.Sdf, kap, X, Y, u, w, v);
+    const float su = scale[u];
     int m = 0;
 #pragma unroll
     for (int k = 1; k < 19; ++k)
         if (v[k] != u && v[k] >= lo && v[k] < lo + n && m < cap) {
             pos[m] = v[k] - lo;
-            cf[m] = (float)(w[k] * su * scale[v[k]]);
+            cf[m] = w[k] * su * scale[v[k]];
             ++m;
         }
     for (; m < cap; ++m) { pos[m] = -1; cf[m] = 0.0f; }
@@ -1991,7 +2006,7 @@ __device__ __forceinline__ void write_frag_gen(float* dst, int b, int Kc, const 
 __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArgs g) {
     extern __shared__ unsigned char gs_raw[];
     GenSmem& s = *reinterpret_cast<GenSmem*>(gs_raw);
-    double* scale = reinterpret_cast<double*>(gs_raw + sizeof(GenSmem));   // nunk
+    float* scale = reinterpret_cast<float*>(gs_raw + sizeof(GenSmem));   // nunk
     const int64_t ki = g.Kc0 + blockIdx.x;   // launch index within the level
     if (ki >= g.K1) return;
     const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;
@@ -2017,13 +2032,18 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
         s.bad = 0;
     }
     __syncthreads();
+    if (p < 36) {
+        s.Suf[p] = d2f_bits(s.Su[p]);
+        s.Sdf[p] = d2f_bits(s.Sd[p]);
+    }
+    __syncthreads();
     for (int u = p; u < nu; u += kGenThreads) {
         int X, Y;
         lattice_of_unk(g.PN, u, &X, &Y);
-        double w[19];
+        float w[19];
         int v[19];
-        assembled_row(g.P, g.N, g.PN, nu, s.Su, s.Sd, kap, X, Y, u, w, v);
-        scale[u] = 1.0 / sqrt(w[0]);
+        assembled_row<float>(g.P, g.N, g.PN, nu, s.Suf, s.Sdf, kap, X, Y, u, w, v);
+        scale[u] = 1.0f / sqrtf(w[0]);
     }
     __syncthreads();
     const LevelGeom lg{g.P, g.N, g.PN};
@@ -2040,13 +2060,13 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
             const int u = ul + p;
             int X, Y;
             lattice_of_unk(g.PN, u, &X, &Y);
-            double w[19];
+            float w[19];
             int v[19];
-            assembled_row(g.P, g.N, g.PN, nu, s.Su, s.Sd, kap, X, Y, u, w, v);
-            const double su = scale[u];
+            assembled_row<float>(g.P, g.N, g.PN, nu, s.Suf, s.Sdf, kap, X, Y, u, w, v);
+            const float su = scale[u];
 #pragma unroll
             for (int k = 0; k < 19; ++k)
-                if (v[k] >= ul && v[k] < ul + b) row[v[k] - ul] += (float)(w[k] * su * scale[v[k]]);
+                if (v[k] >= ul && v[k] < ul + b) row[v[k] - ul] += w[k] * su * scale[v[k]];
             if (lev > 0 && p < l0)
                 for (int q = 0; q < l0; ++q) row[q] -= s.M[p * (kGenRow + 1) + q];
         }
@@ -2109,7 +2129,7 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
 }
 
 size_t gen_factor_smem_bytes(int nunk) {
-    return sizeof(GenSmem) + (size_t)nunk * sizeof(double);
+    return sizeof(GenSmem) + (size_t)nunk * sizeof(float);
 }
 
 struct MixedLayout {
