@@ -224,14 +224,15 @@ __device__ __forceinline__ bool is_zero(float x) { return (__float_as_uint(x) <<
 template <typename T> __device__ __forceinline__ T kappa_as(double k);
 template <> __device__ __forceinline__ double kappa_as<double>(double k) { return k; }
 template <> __device__ __forceinline__ float kappa_as<float>(double k) { return d2f_bits(k); }
+template <typename T> __device__ __forceinline__ T kappa_as(float k) { return (T)k; }
 
 // The assembled P1 row of unknown u at lattice point (x, yl): the weights of u and
 // of its six lattice neighbours (east, west, north, south, south-east, north-west:
 // the edges of the six fine triangles around it) and their unknown indices.  A
 // neighbour outside K, the pinned DOF, or an edge of zero weight (a right angle)
 // gets weight 0 and index u.
-template <typename T>
-__device__ __forceinline__ void p1_row(int N, int PN, int nunk, const T* Su, const T* Sd, const double* kap,
+template <typename T, typename KT = double>
+__device__ __forceinline__ void p1_row(int N, int PN, int nunk, const T* Su, const T* Sd, const KT* kap,
                                        int x, int yl, int u, T w[7], int v[7]) {
     auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kappa_as<T>(kap[kap_index(N, true, i, j)]) : T(0); };
     auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kappa_as<T>(kap[kap_index(N, false, i, j)]) : T(0); };
@@ -253,8 +254,8 @@ __device__ __forceinline__ void p1_row(int N, int PN, int nunk, const T* Su, con
 // an edge midpoint), summed over those triangles (x = X >> 1, y = Y >> 1 indexes the
 // N-lattice), and their unknown indices.  Returns the number of entries (u first).
 // An entry outside K, the pinned DOF, or of zero weight gets weight 0 and index u.
-template <typename T>
-__device__ __forceinline__ int p2_row(int N, int PN, int nunk, const T* Su, const T* Sd, const double* kap,
+template <typename T, typename KT = double>
+__device__ __forceinline__ int p2_row(int N, int PN, int nunk, const T* Su, const T* Sd, const KT* kap,
                                       int X, int Y, int u, T w[19], int v[19]) {
     auto kup = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 1) ? kappa_as<T>(kap[kap_index(N, true, i, j)]) : T(0); };
     auto kdn = [&](int i, int j) { return (i >= 0 && j >= 0 && i + j <= N - 2) ? kappa_as<T>(kap[kap_index(N, false, i, j)]) : T(0); };
@@ -328,14 +329,14 @@ __device__ __forceinline__ int p2_row(int N, int PN, int nunk, const T* Su, cons
 }
 
 // The assembled row of degree P (entries past the P1 row's seven: weight 0, index u).
-template <typename T>
+template <typename T, typename KT = double>
 __device__ __forceinline__ void assembled_row(int P, int N, int PN, int nunk, const T* Su, const T* Sd,
-                                              const double* kap, int X, int Y, int u, T w[19], int v[19]) {
+                                              const KT* kap, int X, int Y, int u, T w[19], int v[19]) {
     if (P == 2) {
-        p2_row<T>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+        p2_row<T, KT>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
         return;
     }
-    p1_row<T>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
+    p1_row<T, KT>(N, PN, nunk, Su, Sd, kap, X, Y, u, w, v);
     for (int k = 7; k < 19; ++k) { w[k] = T(0); v[k] = u; }
 }
 
@@ -1879,10 +1880,10 @@ constexpr int kGenThreads = 64;
 constexpr int kGenLd = kGenMax + 4;    // tile row stride in floats (16-byte aligned rows)
 
 struct GenSmem {
-    alignas(16) float T[kGenMax * kGenLd];     // S_lev, then T_lev (row-major)
+    alignas(16) float T[kGenMax * kGenLd];     // S_lev, then T_lev (row-major), then the next level's
+                                               // Schur update C T C^T (first-row block)
     alignas(16) float rowbuf[2 * kGenMax];     // pivot rows of the Gauss-Jordan steps
     float Q[kGenMax * (kGenRow + 1)];          // T_lev C_{lev+1}^T, first-row columns of lev + 1
-    float M[kGenRow * (kGenRow + 1)];          // C_{lev+1} T_lev C_{lev+1}^T, first-row block
     int qpos[kGenRow * kTabQ];                 // per first-row node of lev + 1: positions in lev
     float qc[kGenRow * kTabQ];                 //   and couplings (position -1: none)
     double Su[36], Sd[36];                     // element stiffness of the two fine shapes
@@ -1968,7 +1969,7 @@ __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b,
 // Couplings of unknown u into the unknowns [lo, lo + n): up to cap (position, scaled
 // weight) pairs, position -1 after the last.  The factorisation assembles and scales in
 // FP32 (it is an FP32 approximation of Ah; the refinement residual stays FP64).
-__device__ __forceinline__ void coupling_table(const MixedArgs& g, const GenSmem& s, const double* kap,
+__device__ __forceinline__ void coupling_table(const MixedArgs& g, const GenSmem& s, const float* kap,
                                                const float* scale, int u, int lo, int n, int cap, int* pos, float* cf) {
     int X, Y;
     lattice_of_unk(g.PN, u, &X, &Y);
@@ -2007,11 +2008,13 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
     extern __shared__ unsigned char gs_raw[];
     GenSmem& s = *reinterpret_cast<GenSmem*>(gs_raw);
     float* scale = reinterpret_cast<float*>(gs_raw + sizeof(GenSmem));   // nunk
+    float* kap = scale + g.nunk;                                           // N^2 (FP32)
     const int64_t ki = g.Kc0 + blockIdx.x;   // launch index within the level
     if (ki >= g.K1) return;
     const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;
     const int p = threadIdx.x, nu = g.nunk;
-    const double* kap = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
+    const double* kapg = g.kappa + (g.dm.kap_off ? g.dm.kap_off[K] : K * (int64_t)g.N * g.N);
+    for (int t = p; t < g.N * g.N; t += kGenThreads) kap[t] = d2f_bits(kapg[t]);
     const int64_t kk = ki - g.Kbase;
     float* F = g.Tall + kk * (int64_t)g.t_stride;
     if (p == 0) {
@@ -2053,10 +2056,13 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
         const int bp = lev > 0 ? lg.size(lev - 1) : 0;
         const int bn = lev + 1 < g.nlev ? lg.size(lev + 1) : 0;
         const int l0 = first_row_size(lg, lev), l0n = bn > 0 ? first_row_size(lg, lev + 1) : 0;
-        // S_lev: row p from the assembled row of its unknown, less the Schur update
+        // S_lev: row p from the assembled row of its unknown, less the Schur update (which the
+        // level before left in the first-row block of the tile)
         if (p < b) {
             float* row = s.T + p * kGenLd;
-            for (int j = 0; j < kGenMax; ++j) row[j] = 0.0f;
+            const int keep = lev > 0 && p < l0 ? l0 : 0;
+            for (int j = 0; j < keep; ++j) row[j] = -row[j];
+            for (int j = keep; j < kGenMax; ++j) row[j] = 0.0f;
             const int u = ul + p;
             int X, Y;
             lattice_of_unk(g.PN, u, &X, &Y);
@@ -2067,8 +2073,6 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
 #pragma unroll
             for (int k = 0; k < 19; ++k)
                 if (v[k] >= ul && v[k] < ul + b) row[v[k] - ul] += w[k] * su * scale[v[k]];
-            if (lev > 0 && p < l0)
-                for (int q = 0; q < l0; ++q) row[q] -= s.M[p * (kGenRow + 1) + q];
         }
         int t_off, f_off, b_off;
         // backward table of the level below: its nodes' couplings into this level
@@ -2111,7 +2115,7 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
             s.Q[i * (kGenRow + 1) + q] = acc;
         }
         __syncthreads();
-        // M = C_{lev+1} Q on the next level's first-row block
+        // C_{lev+1} Q on the next level's first-row block, into the tile (T_lev is written out)
         for (int t = p; t < l0n * l0n; t += kGenThreads) {
             const int i = t / l0n, q = t - i * l0n;
             float acc = 0.0f;
@@ -2120,7 +2124,7 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
                 const int a = s.qpos[i * kTabQ + m];
                 if (a >= 0) acc = fmaf(s.qc[i * kTabQ + m], s.Q[a * (kGenRow + 1) + q], acc);
             }
-            s.M[i * (kGenRow + 1) + q] = acc;
+            s.T[i * kGenLd + q] = acc;
         }
         __syncthreads();
         ul += b;
@@ -2128,8 +2132,8 @@ __global__ void __launch_bounds__(kGenThreads) k_schur_factor_gen(const MixedArg
     if (p == 0) g.fbad[kk] = s.bad;
 }
 
-size_t gen_factor_smem_bytes(int nunk) {
-    return sizeof(GenSmem) + (size_t)nunk * sizeof(float);
+size_t gen_factor_smem_bytes(int nunk, int N) {
+    return sizeof(GenSmem) + (size_t)(nunk + N * N) * sizeof(float);
 }
 
 struct MixedLayout {
@@ -2487,7 +2491,7 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
     // the level's own stream, one chunk ahead: region c % 2 is refilled once the solve of
     // chunk c - 2 is done with it.
     const bool gen = L.mode == 3;
-    const size_t fsmem = gen ? gen_factor_smem_bytes(L.nunk) : factor_smem_bytes(L.nunk);
+    const size_t fsmem = gen ? gen_factor_smem_bytes(L.nunk, lv.N) : factor_smem_bytes(L.nunk);
     if (gen) MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     else MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     // the tuned chunk steps through the range; factor launches run one chunk ahead on the
