@@ -197,6 +197,39 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         r0.push_back(i0);
         r1.push_back(i1);
     }
+    // MIXED: the level-Schur levels go together into one persistent launch pair on the
+    // caller's stream (coarse elements of uneven refinement level, bucketed by size),
+    // beside the other levels' launch sequences
+    std::vector<const Level*> group;
+    std::vector<int64_t> g0, g1;
+    std::vector<char*> gregion;
+    if (precision == MHM_MIXED) {
+        for (size_t i = 0; i < run.size(); ++i)
+            if (!fp64_level(mesh, *run[i]) && schur_split_level(mesh, *run[i])) {
+                group.push_back(run[i]);
+                g0.push_back(r0[i]);
+                g1.push_back(r1[i]);
+                gregion.push_back((char*)workspace + level_region_offset(mesh, *run[i], precision));
+            }
+        if (levels_launchable(mesh, group, g0, g1, o)) {
+            std::vector<const Level*> rest;
+            std::vector<int64_t> q0, q1;
+            for (size_t i = 0; i < run.size(); ++i)
+                if (std::find(group.begin(), group.end(), run[i]) == group.end()) {
+                    rest.push_back(run[i]);
+                    q0.push_back(r0[i]);
+                    q1.push_back(r1[i]);
+                }
+            run.swap(rest);
+            r0.swap(q0);
+            r1.swap(q1);
+            run.insert(run.begin(), nullptr);   // the group, on the caller's stream
+            r0.insert(r0.begin(), 0);
+            r1.insert(r1.begin(), 0);
+        } else {
+            group.clear();
+        }
+    }
     const size_t nside = run.empty() ? 0 : run.size() - 1;
     if (nside > 0) {
         while (mesh->side.size() < nside) {
@@ -210,20 +243,24 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
         if (!mesh->fork_ev) MHM_CUDA_TRY(cudaEventCreateWithFlags(&mesh->fork_ev, cudaEventDisableTiming));
         MHM_CUDA_TRY(cudaEventRecord(mesh->fork_ev, s));
     }
-    size_t offset = 0;
     for (size_t i = 0; i < run.size(); ++i) {
-        const Level& lv = *run[i];
         cudaStream_t si = i == 0 ? s : mesh->side[i - 1];
         if (i > 0) MHM_CUDA_TRY(cudaStreamWaitEvent(si, mesh->fork_ev, 0));
-        const size_t need = level_workspace_bytes(mesh, lv, precision);
-        void* region = need ? (char*)workspace + offset : nullptr;
-        if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
-            st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, region, need, si);
+        if (!run[i]) {
+            st = launch_local_mixed_levels(mesh, group, g0, g1, gregion, kappa, *f, o, AK, EK, BK, FK, status, iters,
+                                           si);
         } else {
-            st = launch_local_mixed(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters, region,
-                                    need, si);
+            const Level& lv = *run[i];
+            const size_t need = level_workspace_bytes(mesh, lv, precision);
+            void* region = need ? (char*)workspace + level_region_offset(mesh, lv, precision) : nullptr;
+            if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
+                st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, region, need,
+                                       si);
+            } else {
+                st = launch_local_mixed(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters, region,
+                                        need, si);
+            }
         }
-        offset += need;
         if (st) return st;
         if (i > 0) MHM_CUDA_TRY(cudaEventRecord(mesh->side_done[i - 1], si));
     }

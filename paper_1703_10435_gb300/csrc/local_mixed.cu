@@ -223,7 +223,6 @@ __device__ __forceinline__ bool is_zero(float x) { return (__float_as_uint(x) <<
 // kappa in the arithmetic of an assembled row (FP32: converted on the integer pipe)
 template <typename T> __device__ __forceinline__ T kappa_as(double k);
 template <> __device__ __forceinline__ double kappa_as<double>(double k) { return k; }
-template <> __device__ __forceinline__ float kappa_as<float>(double k) { return d2f_bits(k); }
 template <typename T> __device__ __forceinline__ T kappa_as(float k) { return (T)k; }
 
 // The assembled P1 row of unknown u at lattice point (x, yl): the weights of u and
@@ -1089,8 +1088,9 @@ __device__ __noinline__ void solve_gen(const MixedArgs& g, const float* F, const
 // MODE 0: generic level operators (Cholesky) factored in this kernel; 1: level Schur
 // complements factored in this kernel; 2: level Schur operators precomputed by
 // k_schur_factor; 3: generic level operators precomputed by k_schur_factor_gen.
-template <int RPL, int CPL, int MODE, int MINB>
-__global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs g) {
+// The blocks of the launch take the coarse elements of one level (g) from its queue.
+template <int RPL, int CPL, int MODE>
+__device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
     constexpr bool SCHUR = MODE == 1 || MODE == 2;
     extern __shared__ unsigned char smem_raw[];
     float* W = reinterpret_cast<float*>(smem_raw);                    // FP32 window
@@ -1775,6 +1775,29 @@ __global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const MixedArgs
     }
 }
 
+template <int RPL, int CPL, int MODE, int MINB>
+__global__ void __launch_bounds__(kThreadsM, MINB) k_local_mixed(const __grid_constant__ MixedArgs g) {
+    mixed_blocks<RPL, CPL, MODE>(g);
+}
+
+// Coarse elements of uneven refinement level in one persistent launch: the level-Schur
+// levels of a mesh are buckets of work (one per local size, the largest first); every
+// block drains the current bucket's queue (its counter) and moves on to the next, so no
+// block idles while a bucket has elements left.
+constexpr int kMaxLevelLaunch = 5;
+struct MixedLevels {
+    int n;
+    int block0[kMaxLevelLaunch + 1];   // factor launch: first block of each level
+    MixedArgs lv[kMaxLevelLaunch];
+};
+
+__global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed_levels(const __grid_constant__ MixedLevels P) {
+    for (int l = 0; l < P.n; ++l) {
+        mixed_blocks<2, 3, 2>(P.lv[l]);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The level-Schur factorisation as its own kernel: one warp per coarse triangle
 // (four per 128-thread block).  Each factorisation is a long chain of small
@@ -1792,10 +1815,11 @@ struct FactorSmem {   // per warp
     int bad;
 };
 
-__global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedArgs g) {
+// blk: the block's index among the level's factor blocks
+__device__ __forceinline__ void schur_factor_block(const MixedArgs& g, int blk) {
     extern __shared__ unsigned char fs_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ki = g.Kc0 + (int64_t)blockIdx.x * kFactorWarps + warp;   // launch index within the level
+    const int64_t ki = g.Kc0 + (int64_t)blk * kFactorWarps + warp;   // launch index within the level
     if (ki >= g.K1) return;
     const int64_t K = g.dm.klist ? (int64_t)g.dm.klist[ki] : ki;
     FactorSmem& fs = reinterpret_cast<FactorSmem*>(fs_raw)[warp];
@@ -1864,6 +1888,17 @@ __global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const MixedA
         ul += b;
     }
     if (lane == 0) g.fbad[kk] = fs.bad;
+}
+
+__global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor(const __grid_constant__ MixedArgs g) {
+    schur_factor_block(g, blockIdx.x);
+}
+
+// The factorisations of several levels in one launch (blocks [block0[l], block0[l + 1]) take level l).
+__global__ void __launch_bounds__(32 * kFactorWarps) k_schur_factor_levels(const __grid_constant__ MixedLevels P) {
+    int l = 0;
+    while (l + 1 < P.n && (int)blockIdx.x >= P.block0[l + 1]) ++l;
+    schur_factor_block(P.lv[l], (int)blockIdx.x - P.block0[l]);
 }
 
 size_t factor_smem_bytes(int nunk) {
@@ -2562,6 +2597,93 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
         if (pipelined) MHM_CUDA_TRY(cudaEventRecord(lv.mdone[b], stream));
     }
     return fallback();
+}
+
+// Several level-Schur levels in one factor launch and one persistent solve launch (see
+// k_local_mixed_levels); each level keeps its own workspace region (slots, one chunk
+// region, queue counter), and its failed elements are re-solved in FP64 afterwards.
+bool levels_launchable(const mhm_mesh* mesh, const std::vector<const Level*>& lvs, const std::vector<int64_t>& r0,
+                       const std::vector<int64_t>& r1, const mhm_solve_opts& opts) {
+    if (lvs.size() < 2 || lvs.size() > (size_t)kMaxLevelLaunch || opts.factor_store) return false;
+    for (size_t i = 0; i < lvs.size(); ++i) {
+        if (!schur_split_level(mesh, *lvs[i])) return false;
+        const MixedLayout L = mixed_layout(mesh, *lvs[i]);
+        if (r1[i] - r0[i] > chunk_of(*lvs[i], L)) return false;   // one chunk region per level
+    }
+    return true;
+}
+
+mhm_status launch_local_mixed_levels(const mhm_mesh* mesh, const std::vector<const Level*>& lvs,
+                                     const std::vector<int64_t>& r0, const std::vector<int64_t>& r1,
+                                     const std::vector<char*>& regions, const double* kappa, const mhm_source& f,
+                                     const mhm_solve_opts& opts, double* AK, double* EK, double* BK, double* FK,
+                                     int32_t* status, int32_t* iters, cudaStream_t stream) {
+    const int n = (int)lvs.size();
+    // buckets in order of decreasing work (elements x unknowns)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::vector<MixedLayout> Ls(n);
+    for (int i = 0; i < n; ++i) Ls[i] = mixed_layout(mesh, *lvs[i]);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)(r1[a] - r0[a]) * Ls[a].nunk > (double)(r1[b] - r0[b]) * Ls[b].nunk;
+    });
+    MixedLevels P{};
+    P.n = n;
+    size_t smem = 0, fsmem = 0;
+    int min_slots = INT32_MAX, fblocks = 0;
+    std::vector<int*> counters(n);
+    for (int j = 0; j < n; ++j) {
+        const int i = order[j];
+        const Level& lv = *lvs[i];
+        const MixedLayout& L = Ls[i];
+        const int slots = mixed_slots(mesh, L);
+        min_slots = std::min(min_slots, slots);
+        const size_t slots_bytes = (size_t)slots * L.slot_bytes;
+        const int64_t chunk = chunk_of(lv, L);
+        const int nbuf = chunk_buffers(lv, L);
+        counters[j] = reinterpret_cast<int*>(regions[i] + slots_bytes + (size_t)nbuf * region_bytes(chunk, L));
+        MixedArgs g = mixed_args(mesh, lv, L, kappa, f, opts, AK, EK, BK, FK, status, iters, regions[i]);
+        region_ptrs(regions[i] + slots_bytes, chunk, L, g);
+        g.Kbase = g.Kc0 = g.K0 = r0[i];
+        g.K1 = r1[i];
+        g.kcounter = counters[j];
+        P.lv[j] = g;
+        P.block0[j] = fblocks;
+        fblocks += (int)((r1[i] - r0[i] + kFactorWarps - 1) / kFactorWarps);
+        smem = std::max(smem, L.smem);
+        fsmem = std::max(fsmem, factor_smem_bytes(L.nunk));
+        MHM_CUDA_TRY(cudaMemsetAsync(counters[j], 0, sizeof(int), stream));
+    }
+    P.block0[n] = fblocks;
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_schur_factor_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local_mixed_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->device);
+    const int grid = std::min(min_slots, sms * 3);
+    timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, true);
+    k_schur_factor_levels<<<(unsigned)fblocks, 32 * kFactorWarps, fsmem, stream>>>(P);
+    timing_mark(mesh, MHM_KERNEL_SCHUR_FACTOR, stream, false);
+    MHM_CUDA_TRY(cudaGetLastError());
+    timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, true);
+    k_local_mixed_levels<<<grid, kThreadsM, smem, stream>>>(P);
+    timing_mark(mesh, MHM_KERNEL_LOCAL_MIXED, stream, false);
+    MHM_CUDA_TRY(cudaGetLastError());
+    if (opts.no_fallback) return MHM_OK;
+    // elements whose refinement failed: solved again by the FP64 path, level by level
+    for (int j = 0; j < n; ++j) {
+        const int i = order[j];
+        int32_t* fcount = reinterpret_cast<int32_t*>((char*)counters[j] + 256);
+        int32_t* flist = reinterpret_cast<int32_t*>((char*)counters[j] + 512);
+        const int64_t nK = r1[i] - r0[i];
+        MHM_CUDA_TRY(cudaMemsetAsync(fcount, 0, sizeof(int32_t), stream));
+        const int64_t nb = std::min<int64_t>((nK + 255) / 256, 1024);
+        k_collect_failed<<<(unsigned)nb, 256, 0, stream>>>(P.lv[j].dm.klist, r0[i], r1[i], status, flist, fcount);
+        MHM_CUDA_TRY(cudaGetLastError());
+        const mhm_status st =
+            launch_local_fp64_list(mesh, *lvs[i], kappa, f, flist, fcount, nK, AK, EK, BK, FK, status, iters, stream);
+        if (st) return st;
+    }
+    return MHM_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -203,6 +203,15 @@ mhm_status launch_local_mixed(const mhm_mesh* mesh, const Level& lv, const doubl
                               const mhm_solve_opts& opts, int64_t K0, int64_t K1, double* AK,
                               double* EK, double* BK, double* FK, int32_t* status, int32_t* iters,
                               void* workspace, size_t ws_bytes, cudaStream_t stream);
+// Several level-Schur levels (launch index ranges [r0[i], r1[i]), workspace regions) in one
+// factor launch and one persistent solve launch; levels_launchable says whether they qualify.
+bool levels_launchable(const mhm_mesh* mesh, const std::vector<const Level*>& lvs, const std::vector<int64_t>& r0,
+                       const std::vector<int64_t>& r1, const mhm_solve_opts& opts);
+mhm_status launch_local_mixed_levels(const mhm_mesh* mesh, const std::vector<const Level*>& lvs,
+                                     const std::vector<int64_t>& r0, const std::vector<int64_t>& r1,
+                                     const std::vector<char*>& regions, const double* kappa, const mhm_source& f,
+                                     const mhm_solve_opts& opts, double* AK, double* EK, double* BK, double* FK,
+                                     int32_t* status, int32_t* iters, cudaStream_t stream);
 // FP64 local solves of the K in list[0 .. *count) (device count, at most max_n) of level lv:
 // the re-solve of elements whose mixed refinement failed (their iters entry becomes -1).
 mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,

@@ -398,3 +398,37 @@ def test_p2_r5_wide_window_vs_oracle(precision):
         o = solve_local(mesh, K, r, 2, kap[K], 1.0)
         tk = _fp64_bound(o, kap[K], 1e-10)
         assert_blocks(AK[K], EK[K], BK[K], FK[K], o, tk, (K, tk))
+
+
+def test_mixed_levels_in_one_persistent_launch():
+    """Coarse elements of five refinement levels on the mixed level-Schur path go into one
+    factor launch and one persistent solve launch (the levels as work buckets, the largest
+    first), with the blocks of the single-level launches: a mesh whose elements all sit at
+    one level runs those, so the same elements at the same level agree to rounding (the
+    two kernels are separate compilations of the same code)."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    keep = rs <= 5                     # the level-Schur levels only (6 and 7 run in FP64)
+    rs2 = np.where(keep, rs, 5).astype(np.int8)
+    kap2 = [k if kp else 10.0 ** np.random.default_rng(K).uniform(-2, 2, 4 ** 5) for K, (k, kp) in
+            enumerate(zip(kap, keep))]
+    p = Pipeline(nx, ny, 0, 1, 1, 2, 0, mhm.MHM_MIXED, r_per_K=rs2)
+    kd = torch.as_tensor(np.concatenate(kap2), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    mhm.mhm_set_timing(p.mesh, True)
+    p.local(kd, src, mhm.SolveOpts(10, 1e-13, 0, 0))
+    times = mhm.mhm_kernel_times(p.mesh)
+    assert times["k_local_mixed"][0] == 1 and times["k_schur_factor"][0] == 1, times
+    assert int(p.status.abs().sum()) == 0
+    # each element against a mesh that holds only its own level (single-level launches)
+    NI = p.mesh.n_I
+    for r in sorted(set(rs2.tolist())):
+        idx = np.flatnonzero(rs2 == r)
+        q = Pipeline(nx, ny, 0, 1, 1, 2, 0, mhm.MHM_MIXED, r_per_K=np.full_like(rs2, r))
+        kq = [kap2[K] if rs2[K] == r else np.ones(4 ** r) for K in range(len(rs2))]
+        q.local(torch.as_tensor(np.concatenate(kq), device="cuda"), src, mhm.SolveOpts(10, 1e-13, 0, 0))
+        torch.cuda.synchronize()
+        for K in idx:
+            for a, b in ((p.AK[K * NI * NI:(K + 1) * NI * NI], q.AK[K * NI * NI:(K + 1) * NI * NI]),
+                         (p.EK[K * NI:(K + 1) * NI], q.EK[K * NI:(K + 1) * NI])):
+                assert float((a - b).abs().max()) <= 1e-12 * float(b.abs().max()), (r, K)
