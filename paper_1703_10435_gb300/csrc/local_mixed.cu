@@ -94,6 +94,7 @@ struct MCtx {
     int col_fail;
     double red[kWarpsM];
     float epsred[2][32];          // level-Schur solve: per row-tile partial sums of g^T T g per column
+    uint32_t rmask[3][kWarpsM];   // level-Schur refinement: stencil directions each warp's rows use
     int64_t nextK;
     double mz[kMaxNI + 1];
     alignas(8) uint64_t bar[kMaxOpBufs];
@@ -869,9 +870,10 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
 // columns at a time before they are used, so that their loads are in flight
 // together.  Thread per node; `done` has bit col set for the columns to skip.
 __device__ __noinline__ void fused_residual(int PN, int nu, int R, const double* __restrict__ ah, const float* y,
-                                            double* __restrict__ Zh, double* __restrict__ Rh, uint64_t done) {
+                                            double* __restrict__ Zh, double* __restrict__ Rh, uint64_t done,
+                                            const uint32_t* rmask) {
     const uint32_t y_s = smem_u32(y);
-    for (int u = threadIdx.x; u < nu; u += kThreadsM) {
+    for (int u = threadIdx.x, rnd = 0; u < nu; u += kThreadsM, ++rnd) {
         int X, Y;
         lattice_of_unk(PN, u, &X, &Y);
         int v[7];
@@ -891,6 +893,9 @@ __device__ __noinline__ void fused_residual(int PN, int nu, int R, const double*
             if (v[d] < 0 || v[d] >= nu) { a[d] = 0.0; v[d] = u; }   // (weight zero there)
             if ((__double_as_longlong(a[d]) << 1) != 0) nz |= 1u << d;   // a[d] != 0 (either zero sign)
         }
+        // directions that no node of this warp's row set needs (the fine triangles' right
+        // angles give zero weights): skipped by a warp-uniform branch
+        const uint32_t any = rmask[rnd * kWarpsM + (threadIdx.x >> 5)];
         for (int c0 = 0; c0 < R; c0 += 8) {
             double zr[8], rr[8];
 #pragma unroll
@@ -909,7 +914,9 @@ __device__ __noinline__ void fused_residual(int PN, int nu, int R, const double*
                     double r = fma(-a[0], d0, rr[j]);
 #pragma unroll
                     for (int d = 1; d < 7; ++d)
-                        if (nz >> d & 1) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
+                        if (any >> d & 1) {
+                            if (nz >> d & 1) r = fma(-a[d], f2d_bits(lds1(y_s + 4u * (uint32_t)(v[d] * R + col))), r);
+                        }
                     Rh[(size_t)u * R + col] = r;
                 }
             }
@@ -1268,6 +1275,23 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
                 sc = scale;
                 ah = ahw;
             }
+            // per warp and round of the residual's node loop: the stencil directions with a
+            // non-zero weight at some node
+            for (int ub = 0, rnd = 0; ub < nu; ub += kThreadsM, ++rnd) {
+                const int u = ub + threadIdx.x;
+                uint32_t nz = 0;
+                if (u < nu) {
+                    int X, Y;
+                    lattice_of_unk(g.PN, u, &X, &Y);
+                    const int vv[7] = {u, unk(g.PN, X + 1, Y), unk(g.PN, X - 1, Y), unk(g.PN, X, Y + 1),
+                                       unk(g.PN, X, Y - 1), unk(g.PN, X + 1, Y - 1), unk(g.PN, X - 1, Y + 1)};
+#pragma unroll
+                    for (int d = 0; d < 7; ++d)
+                        if (vv[d] >= 0 && vv[d] < nu && !is_zero(ah[(size_t)d * nu + u])) nz |= 1u << d;
+                }
+                nz = __reduce_or_sync(0xffffffffu, nz);
+                if ((threadIdx.x & 31) == 0) c.rmask[rnd][threadIdx.x >> 5] = nz;
+            }
             // ---- right-hand sides Rh = S G (compatible loads, pinned DOF left out), S m, Zh = 0
             for (int u = threadIdx.x; u < nu; u += blockDim.x) {
                 int X, Y;
@@ -1325,7 +1349,7 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
                     uint64_t done = 0;
                     for (int col = 0; col < R; ++col)
                         if (c.col_done[col]) done |= 1ull << col;
-                    fused_residual(g.PN, nu, R, ah, y, Zh, Rh, done);
+                    fused_residual(g.PN, nu, R, ah, y, Zh, Rh, done, &c.rmask[0][0]);
                 }
                 ++pass;
                 __syncthreads();
