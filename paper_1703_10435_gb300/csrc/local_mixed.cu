@@ -483,6 +483,36 @@ __device__ __forceinline__ void tile_product(uint32_t aa, uint32_t ba, uint32_t 
     for (int e = 0; e < 4; ++e) c[e] = chh[e] + (chl[e] + clh[e]);
 }
 
+// tile_product with the k-steps in two halves, each with its own three accumulator chains
+// (six in all) summed at the end: the dependent chain of MMAs is half as long.
+template <int KT>
+__device__ __forceinline__ void tile_product_split(uint32_t aa, uint32_t ba, uint32_t bstep, float (&c)[4]) {
+    constexpr int H = (KT + 1) / 2;   // first half: k-steps 0 .. H-1; second: H .. KT-1
+    float x0[4] = {0.f, 0.f, 0.f, 0.f}, x1[4] = {0.f, 0.f, 0.f, 0.f}, x2[4] = {0.f, 0.f, 0.f, 0.f};
+    float y0[4] = {0.f, 0.f, 0.f, 0.f}, y1[4] = {0.f, 0.f, 0.f, 0.f}, y2[4] = {0.f, 0.f, 0.f, 0.f};
+    auto step = [&](int kt, float (&hh)[4], float (&hl)[4], float (&lh)[4]) {
+        const float4 av = lds4(aa + 512u * (uint32_t)kt);
+        const float2 bv = lds2(ba + bstep * (uint32_t)kt);
+        uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+        split_tf32(av.x, ah[0], al[0]);
+        split_tf32(av.y, ah[1], al[1]);
+        split_tf32(av.z, ah[2], al[2]);
+        split_tf32(av.w, ah[3], al[3]);
+        split_tf32(bv.x, bh0, bl0);
+        split_tf32(bv.y, bh1, bl1);
+        mma_tf32(hh, ah, bh0, bh1);
+        mma_tf32(hl, ah, bl0, bl1);
+        mma_tf32(lh, al, bh0, bh1);
+    };
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        step(i, x0, x1, x2);
+        if (i + H < KT) step(i + H, y0, y1, y2);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c[e] = (x0[e] + y0[e]) + ((x1[e] + x2[e]) + (y1[e] + y2[e]));
+}
+
 // Per solve step, built once per block: (b | bo << 8, ulev | uo << 16, unused,
 // operator offset in floats).
 __device__ __forceinline__ int4 solve_step_info(const LevelGeom& lg, int nlev, const int* opoff, const int* u0,
@@ -827,9 +857,9 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
             float cv[4];
             switch (KT) {
                 case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
-                case 2: tile_product<2>(aa, ba, bstep, KT, cv); break;
-                case 3: tile_product<3>(aa, ba, bstep, KT, cv); break;
-                default: tile_product<4>(aa, ba, bstep, KT, cv); break;
+                case 2: tile_product_split<2>(aa, ba, bstep, cv); break;
+                case 3: tile_product_split<3>(aa, ba, bstep, cv); break;
+                default: tile_product_split<4>(aa, ba, bstep, cv); break;
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -1066,13 +1096,13 @@ __device__ __noinline__ void solve_gen(const MixedArgs& g, const float* F, const
             float cv[4];
             switch (KT) {
                 case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
-                case 2: tile_product<2>(aa, ba, bstep, KT, cv); break;
-                case 3: tile_product<3>(aa, ba, bstep, KT, cv); break;
-                case 4: tile_product<4>(aa, ba, bstep, KT, cv); break;
-                case 5: tile_product<5>(aa, ba, bstep, KT, cv); break;
-                case 6: tile_product<6>(aa, ba, bstep, KT, cv); break;
-                case 7: tile_product<7>(aa, ba, bstep, KT, cv); break;
-                default: tile_product<8>(aa, ba, bstep, KT, cv); break;
+                case 2: tile_product_split<2>(aa, ba, bstep, cv); break;
+                case 3: tile_product_split<3>(aa, ba, bstep, cv); break;
+                case 4: tile_product_split<4>(aa, ba, bstep, cv); break;
+                case 5: tile_product_split<5>(aa, ba, bstep, cv); break;
+                case 6: tile_product_split<6>(aa, ba, bstep, cv); break;
+                case 7: tile_product_split<7>(aa, ba, bstep, cv); break;
+                default: tile_product_split<8>(aa, ba, bstep, cv); break;
             }
             // forward: y_lev = result; backward: y_lev -= result (columns still refining)
 #pragma unroll
