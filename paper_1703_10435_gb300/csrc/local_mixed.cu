@@ -99,6 +99,8 @@ struct MCtx {
     double mz[kMaxNI + 1];
     alignas(8) uint64_t bar[kMaxOpBufs];
     uint32_t phase[kMaxOpBufs];
+    alignas(8) uint64_t ebar[kMaxOpBufs];   // level-Schur solves by column groups: slot released
+    uint32_t ephase[kMaxOpBufs];
     int timeout;
 };
 
@@ -894,6 +896,156 @@ __device__ __noinline__ void solve_schur(const MixedArgs& g, const float* F, con
         for (int b = 0; b < kMaxOpBufs; ++b) c.phase[b] = (ph >> b) & 1u;
 }
 
+// The same solve with the column tiles decoupled (R <= 24: at most 3 tiles of 8
+// columns).  A column of the solve depends only on the same column at the other levels, so
+// each column tile runs its own chain of level steps in its own pair of warps (one per
+// 16-row tile), synchronised by a named barrier of those 64 threads instead of the whole
+// block; the groups drift against each other and hide one another's latencies.  The level
+// operators they share stream through the ring fed by a producer (lane 0 of the last warp,
+// which holds no tile): slot s mod nbuf is refilled once every group has released its step
+// s - nbuf (an mbarrier with one arrival per group).
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(64) : "memory");
+}
+
+__device__ __noinline__ void solve_schur_groups(const MixedArgs& g, const float* F, const int4* sinfo, float* y,
+                                                const float* cw, const double* Rh, float* opbuf, float* stage,
+                                                double* eps, MCtx& c) {
+    const int R = g.R, NT = (R + 7) >> 3, nu = g.nunk;
+    const int nsteps = 2 * g.nlev - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const int grp = warp >> 1, mt = warp & 1;          // column tile and row tile of this warp
+    const uint32_t y_s = smem_u32(y), op_s = smem_u32(opbuf), st_s = smem_u32(stage);
+    const float* cwS = cw + 2 * nu;
+    const float* cwSE = cw + 3 * nu;
+    const int nb = g.nbuf;
+    uint32_t fph = 0, eph = 0;   // bit b: parity of slot b's full / empty barrier at the solve's start
+    for (int b = 0; b < kMaxOpBufs; ++b) {
+        fph |= (c.phase[b] & 1u) << b;
+        eph |= (c.ephase[b] & 1u) << b;
+    }
+    uint64_t frozen = 0;
+    for (int col = 0; col < R; ++col)
+        if (c.col_frozen[col]) frozen |= 1ull << col;
+    const uint64_t pol = g.op_policy == 1 ? l2_policy_evict_first() : l2_policy_evict_last();
+    auto op_bytes = [&](int st) { return (uint32_t)frag_op_floats(sinfo[st].x & 0xff, sinfo[st].x & 0xff) * 4u; };
+    for (int t = threadIdx.x; t < g.stage_floats; t += kThreadsM) stage[t] = 0.0f;   // padding columns stay 0
+    for (int t = threadIdx.x; t < nu * R; t += kThreadsM) {
+        const int col = t % R;
+        if (!(frozen >> col & 1)) y[t] = d2f_bits(Rh[t]);
+    }
+    __syncthreads();
+    float eacc0 = 0.0f, eacc1 = 0.0f;
+    if (warp == kWarpsM - 1) {
+        if (lane == 0) {
+            // producer: the operator of every step into its slot, after the slot's last use
+            if (g.pf_all) {
+                const int l = nsteps / 2;
+                bulk_prefetch_l2(F, (uint32_t)(sinfo[l].w * 4u + op_bytes(l)));
+            }
+            for (int st = 0; st < nsteps; ++st) {
+                const int b = st % nb;
+                if (st >= nb) {
+                    const uint32_t k = (uint32_t)((st - nb) / nb);   // that use's index in this solve
+                    if (!mbar_wait_bounded(&c.ebar[b], ((eph >> b) ^ k) & 1u)) c.timeout = 1;
+                }
+                if (g.l2pf && !g.pf_all && st + g.l2pf < nsteps)
+                    bulk_prefetch_l2(F + sinfo[st + g.l2pf].w, op_bytes(st + g.l2pf));
+                const uint32_t bytes = op_bytes(st);
+                fence_proxy_async_shared();
+                mbar_arrive_expect_tx(&c.bar[b], bytes);
+                if (g.op_policy) bulk_copy_g2s_hint(opbuf + (size_t)b * g.opmax, F + sinfo[st].w, bytes, &c.bar[b], pol);
+                else bulk_copy_g2s(opbuf + (size_t)b * g.opmax, F + sinfo[st].w, bytes, &c.bar[b]);
+            }
+        }
+    } else if (grp < NT) {
+        const int t64 = threadIdx.x & 63, c8 = t64 & 7, i0 = t64 >> 3;
+        const int col = grp * 8 + c8;
+        for (int st = 0; st < nsteps; ++st) {
+            const int4 si = sinfo[st];
+            const int b = si.x & 0xff, dir = si.x >> 8;
+            const int ulev = si.y & 0xffff, uo = si.y >> 16;
+            const int bo = si.z & 0xffff, lev = si.z >> 16;
+            // this tile's columns of B (b x 8): forward r_lev - C_lev v_{lev-1}, backward
+            // C_{lev+1}^T x_{lev+1}
+            if (col < R) {
+                const int xo = lev == 0 ? 1 : 0;       // lattice x of position 0
+                const int off = lev == 1 ? 1 : 0;      // level below starts at x = 1
+                for (int i = i0; i < b; i += 8) {
+                    const int x = i + xo;
+                    float v;
+                    if (dir == 0) {
+                        v = lds1(y_s + 4u * (uint32_t)((ulev + i) * R + col));
+                        if (lev > 0) {
+                            const int ps = x - off, pse = x + 1 - off;
+                            float a = cwSE[ulev + i] * lds1(y_s + 4u * (uint32_t)((uo + pse) * R + col));
+                            if (ps >= 0) a = fmaf(cwS[ulev + i], lds1(y_s + 4u * (uint32_t)((uo + ps) * R + col)), a);
+                            v -= a;
+                        }
+                    } else {
+                        v = 0.0f;
+                        if (x < bo) v = cwS[uo + x] * lds1(y_s + 4u * (uint32_t)((uo + x) * R + col));
+                        if (x >= 1) v = fmaf(cwSE[uo + x - 1], lds1(y_s + 4u * (uint32_t)((uo + x - 1) * R + col)), v);
+                    }
+                    sts1(st_s + 4u * frag_b_pos(i, col, NT), v);
+                }
+            }
+            const int bu = st % nb;
+            const uint32_t k = (uint32_t)(st / nb);   // use of slot bu in this solve
+            if (!mbar_wait_bounded(&c.bar[bu], ((fph >> bu) ^ k) & 1u)) c.timeout = 1;
+            group_sync(1 + grp);
+            const int KT = (b + 7) >> 3, MT = (b + 15) >> 4;
+            if (mt < MT) {
+                const uint32_t op0 = op_s + (uint32_t)(bu * g.opmax) * 4u;
+                const uint32_t aa = op0 + (uint32_t)(((mt * KT) * 32 + lane) * 16);
+                const uint32_t ba = st_s + (uint32_t)((grp * 32 + lane) * 8);
+                const uint32_t bstep = (uint32_t)(NT * 32 * 8);
+                float cv[4];
+                switch (KT) {
+                    case 1: tile_product<1>(aa, ba, bstep, KT, cv); break;
+                    case 2: tile_product_split<2>(aa, ba, bstep, cv); break;
+                    case 3: tile_product_split<3>(aa, ba, bstep, cv); break;
+                    default: tile_product_split<4>(aa, ba, bstep, cv); break;
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = mt * 16 + gq + 8 * (e >> 1), cc = grp * 8 + 2 * tq + (e & 1);
+                    if (i < b && cc < R) {
+                        if (dir == 0) {
+                            const float gv = lds1(st_s + 4u * frag_b_pos(i, cc, NT)) * cv[e];
+                            if (e & 1) eacc1 += gv; else eacc0 += gv;
+                        }
+                        if (!(frozen >> cc & 1)) {
+                            const uint32_t ya = y_s + 4u * (uint32_t)((ulev + i) * R + cc);
+                            sts1(ya, dir == 0 ? cv[e] : lds1(ya) - cv[e]);
+                        }
+                    }
+                }
+            }
+            group_sync(1 + grp);
+            if (t64 == 0) mbar_arrive(&c.ebar[bu]);   // this group is done with the slot
+        }
+    }
+    // eps: sum over the 8 row lanes of each column (lanes with equal tq), then the two row tiles
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        eacc0 += __shfl_xor_sync(0xffffffffu, eacc0, o);
+        eacc1 += __shfl_xor_sync(0xffffffffu, eacc1, o);
+    }
+    if (grp < NT && warp < kWarpsM - 1 && gq == 0) {
+        c.epsred[mt][grp * 8 + 2 * tq] = eacc0;
+        c.epsred[mt][grp * 8 + 2 * tq + 1] = eacc1;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) eps[threadIdx.x] = (double)c.epsred[0][threadIdx.x] + (double)c.epsred[1][threadIdx.x];
+    if (threadIdx.x == 0)
+        for (int b = 0; b < kMaxOpBufs; ++b) {
+            const uint32_t uses = b < nb ? (uint32_t)((nsteps - b + nb - 1) / nb) : 0u;
+            c.phase[b] = ((fph >> b) ^ uses) & 1u;
+            c.ephase[b] = ((eph >> b) ^ uses) & 1u;
+        }
+}
+
 // One refinement pass of the level-Schur path, in scaled variables, for the columns
 // not done: Zh_u += y_u and Rh_u -= sum_v Ah_uv y_v over the stencil points v of u,
 // accumulated in FP64 (y widened on the integer pipe).  A node's entries are read 8
@@ -1176,6 +1328,8 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
         for (int b = 0; b < kMaxOpBufs; ++b) {
             mbar_init(&c.bar[b], 1);
             c.phase[b] = 0;
+            mbar_init(&c.ebar[b], (g.R + 7) >> 3);   // one release per column group
+            c.ephase[b] = 0;
         }
     }
     __syncthreads();
@@ -1360,7 +1514,8 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
             }
             __syncthreads();
             // ---- refinement (as in the generic path, in scaled variables)
-            solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.gamma, c);
+            if (R <= 24) solve_schur_groups(g, F, sinfo, y, cw, Rh, opbuf, stage, c.gamma, c);
+            else solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.gamma, c);
             __syncthreads();
             if (threadIdx.x == 0) {
                 int all = 1;
@@ -1394,7 +1549,8 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
                 }
                 __syncthreads();
                 if (c.all_done) break;
-                solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.eps, c);
+                if (R <= 24) solve_schur_groups(g, F, sinfo, y, cw, Rh, opbuf, stage, c.eps, c);
+                else solve_schur(g, F, sinfo, y, cw, Rh, opbuf, stage, c.eps, c);
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     int all = 1;
