@@ -1582,19 +1582,32 @@ __device__ __forceinline__ void mixed_blocks(const MixedArgs& g) {
                 float* gpart = y;
                 double* mpart = reinterpret_cast<double*>(y + gfl);
                 double* xbuf = reinterpret_cast<double*>(y + gfl + 2 * kWarpsM * R);
+                // two 32-float rows per warp, used in turn: a node's Rh row (FP32) goes through
+                // shared memory and is read back as 16-byte broadcasts
+                float* rowb = y + ((gfl + 2 * kWarpsM * R + 2 * R * R + 3) & ~3) + warp * 64;
                 float acc[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
                 double mzp = 0.0;
+                int par = 0;
                 for (int u = warp; u < nu; u += kWarpsM) {
                     const double zh = lc ? Zh[(size_t)u * R + lane] : 0.0;
                     const double rh = lc ? Rh[(size_t)u * R + lane] : 0.0;
                     mzp = fma(smass[u], zh, mzp);
-                    const float zf = d2f_bits(zh), rf = d2f_bits(rh);
+                    const float zf = d2f_bits(zh);
+                    float* rb = rowb + par * 32;
+                    par ^= 1;
+                    rb[lane] = d2f_bits(rh);
+                    __syncwarp();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float ri = __shfl_sync(0xffffffffu, rf, i);
-                        if (i < R) acc[i] = fmaf(zf, ri, acc[i]);
+                    for (int q = 0; q < 8; ++q) {
+                        if (4 * q < R) {
+                            const float4 r4 = *reinterpret_cast<const float4*>(rb + 4 * q);
+                            acc[4 * q] = fmaf(zf, r4.x, acc[4 * q]);
+                            if (4 * q + 1 < R) acc[4 * q + 1] = fmaf(zf, r4.y, acc[4 * q + 1]);
+                            if (4 * q + 2 < R) acc[4 * q + 2] = fmaf(zf, r4.z, acc[4 * q + 2]);
+                            if (4 * q + 3 < R) acc[4 * q + 3] = fmaf(zf, r4.w, acc[4 * q + 3]);
+                        }
                     }
                 }
                 if (lc) {
@@ -2479,7 +2492,7 @@ MixedLayout mixed_layout(const mhm_mesh* mesh, const Level& lv, bool split = tru
     if (yf < (size_t)2 * R * 64) yf = (size_t)2 * R * 64;   // also holds two R x 64 staging chunks
     L.ldr = (2 * bmax + 3) & ~3;
     if (L.mode == 0 && yf < (size_t)bmax * L.ldr) yf = (size_t)bmax * L.ldr;   // and the level right-hand sides while factoring
-    if (L.schur) yf = std::max(yf, (size_t)(10 * R * R + 16 * R + 8));      // and the output partials
+    if (L.schur) yf = std::max(yf, (size_t)(10 * R * R + 16 * R + 8 + 4 + kWarpsM * 64));   // and the output partials
     L.yfloats = (int)((yf + 3) & ~(size_t)3);
     size_t off = win * sizeof(float) + (size_t)L.yfloats * sizeof(float) + (size_t)(3 * L.nlev + 1) * sizeof(int);
     off = (off + 15) & ~(size_t)15;
