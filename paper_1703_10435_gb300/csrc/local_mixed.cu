@@ -648,39 +648,64 @@ constexpr int kSLd = kSchurMax + 1;
 // Row k travels through shared memory (rowbuf: 2 x 32 floats per warp, row k
 // published unscaled by lane k); every lane applies a[j] -= g_k r[j] with
 // g_k = a_ik / a_kk, or 1 - 1/a_kk in lane k (which turns its row into r / a_kk).
+// Pivots go in blocks of 8 with the register row rotated so that the block's pivot columns
+// sit at positions 0..7 (the row turns left by 8 after each block): every register index
+// stays static with a quarter of the fully unrolled code, and a chunk of 8 columns that
+// lies past b is skipped.  Each entry of the inverse sees the same operations in the same
+// order as in the unrotated elimination.
 __device__ __noinline__ void gauss_jordan_warp(const float* Sb, float* Tb, float* rowbuf, int b, int lev, int* bad) {
     const int lane = threadIdx.x & 31;
     float a[kSchurMax];
 #pragma unroll
     for (int j = 0; j < kSchurMax; ++j) a[j] = (lane < b && j < b) ? Sb[lane * kSLd + j] : (lane == j ? 1.0f : 0.0f);
+    const int nblk = (b + 7) >> 3;
+    for (int kb = 0; kb < nblk; ++kb) {
+        uint32_t cm = 0;   // chunk m (positions 8m..8m+7) holds columns 8 ((kb + m) mod 4) + 0..7
 #pragma unroll
-    for (int k = 0; k < kSchurMax; ++k) {
-        if (k < b) {
-            float* rb = rowbuf + (k & 1) * kSchurMax;
-            if (lane == k) {
+        for (int m = 0; m < kSchurMax / 8; ++m)
+            if ((((kb + m) & 3) << 3) < b) cm |= 1u << m;
 #pragma unroll
-                for (int j = 0; j < kSchurMax; j += 4)
-                    *reinterpret_cast<float4*>(rb + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = kb * 8 + kk;
+            if (k < b) {
+                float* rb = rowbuf + (k & 1) * kSchurMax;
+                if (lane == k) {
+#pragma unroll
+                    for (int j = 0; j < kSchurMax; j += 4)
+                        *reinterpret_cast<float4*>(rb + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+                }
+                __syncwarp();
+                const float piv = rb[kk];
+                if (lane == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
+                const float d = __frcp_rn(piv);
+                const float gk = lane == k ? 1.0f - d : a[kk] * d;
+#pragma unroll
+                for (int m = 0; m < kSchurMax / 8; ++m) {
+                    if (cm >> m & 1) {
+#pragma unroll
+                        for (int t = 0; t < 8; t += 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(rb + 8 * m + t);
+                            a[8 * m + t] = fmaf(-gk, v.x, a[8 * m + t]);
+                            a[8 * m + t + 1] = fmaf(-gk, v.y, a[8 * m + t + 1]);
+                            a[8 * m + t + 2] = fmaf(-gk, v.z, a[8 * m + t + 2]);
+                            a[8 * m + t + 3] = fmaf(-gk, v.w, a[8 * m + t + 3]);
+                        }
+                    }
+                }
+                a[kk] = lane == k ? d : -gk;
             }
-            __syncwarp();
-            float r[kSchurMax];
-#pragma unroll
-            for (int j = 0; j < kSchurMax; j += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(rb + j);
-                r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
-            }
-            const float piv = r[k];
-            if (lane == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
-            const float d = __frcp_rn(piv);
-            const float gk = lane == k ? 1.0f - d : a[k] * d;
-#pragma unroll
-            for (int j = 0; j < kSchurMax; ++j)
-                if (j < b) a[j] = fmaf(-gk, r[j], a[j]);
-            a[k] = lane == k ? d : -gk;
         }
-    }
+        float t8[8];
 #pragma unroll
-    for (int j = 0; j < kSchurMax; ++j) Tb[lane * kSLd + j] = a[j];
+        for (int j = 0; j < 8; ++j) t8[j] = a[j];
+#pragma unroll
+        for (int j = 0; j < kSchurMax - 8; ++j) a[j] = a[j + 8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[kSchurMax - 8 + j] = t8[j];
+    }
+    // position j now holds column (8 nblk + j) mod 32
+#pragma unroll
+    for (int j = 0; j < kSchurMax; ++j) Tb[lane * kSLd + ((8 * nblk + j) & (kSchurMax - 1))] = a[j];
 }
 
 // T (b x b, row-major ld kSLd in shared memory) to global memory in fragment order,
