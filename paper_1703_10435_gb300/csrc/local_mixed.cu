@@ -653,11 +653,9 @@ constexpr int kSLd = kSchurMax + 1;
 // stays static with a quarter of the fully unrolled code, and a chunk of 8 columns that
 // lies past b is skipped.  Each entry of the inverse sees the same operations in the same
 // order as in the unrotated elimination.
-__device__ __noinline__ void gauss_jordan_warp(const float* Sb, float* Tb, float* rowbuf, int b, int lev, int* bad) {
+__device__ __forceinline__ void gauss_jordan_regs(float (&a)[kSchurMax], float* Tb, float* rowbuf, int b, int lev,
+                                                  int* bad) {
     const int lane = threadIdx.x & 31;
-    float a[kSchurMax];
-#pragma unroll
-    for (int j = 0; j < kSchurMax; ++j) a[j] = (lane < b && j < b) ? Sb[lane * kSLd + j] : (lane == j ? 1.0f : 0.0f);
     const int nblk = (b + 7) >> 3;
     for (int kb = 0; kb < nblk; ++kb) {
         uint32_t cm = 0;   // chunk m (positions 8m..8m+7) holds columns 8 ((kb + m) mod 4) + 0..7
@@ -706,6 +704,58 @@ __device__ __noinline__ void gauss_jordan_warp(const float* Sb, float* Tb, float
     // position j now holds column (8 nblk + j) mod 32
 #pragma unroll
     for (int j = 0; j < kSchurMax; ++j) Tb[lane * kSLd + ((8 * nblk + j) & (kSchurMax - 1))] = a[j];
+}
+
+__device__ __noinline__ void gauss_jordan_warp(const float* Sb, float* Tb, float* rowbuf, int b, int lev, int* bad) {
+    const int lane = threadIdx.x & 31;
+    float a[kSchurMax];
+#pragma unroll
+    for (int j = 0; j < kSchurMax; ++j) a[j] = (lane < b && j < b) ? Sb[lane * kSLd + j] : (lane == j ? 1.0f : 0.0f);
+    gauss_jordan_regs(a, Tb, rowbuf, b, lev, bad);
+}
+
+// One level of the factor kernel in one warp: row p of S_lev (lane p; the same values as
+// schur_update, built in registers in chunks of 8 columns, identity past b) and its
+// inverse by gauss_jordan_regs, which leaves T_lev in Tb for the next level.
+__device__ __noinline__ void schur_level_warp(const float* cwE, const float* cwW, const float* cwS, const float* cwSE,
+                                              float* Tb, float* rowbuf, int lev, int b, int ul, int* bad) {
+    const int p = threadIdx.x & 31;
+    const int off = lev == 1 ? 1 : 0;   // level 0 starts at x = 1 (the pinned point)
+    const bool row = p < b;
+    const float cps = (row && lev > 0) ? cwS[ul + p] : 0.0f, cpse = (row && lev > 0) ? cwSE[ul + p] : 0.0f;
+    const float ce = row ? cwE[ul + p] : 0.0f, cwv = row ? cwW[ul + p] : 0.0f;
+    const int ps = p - off, pse = p + 1 - off;
+    float a[kSchurMax];
+#pragma unroll
+    for (int m = 0; m < kSchurMax / 8; ++m) {
+        if (8 * m < b) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int q = 8 * m + t;
+                float sv = p == q ? 1.0f : 0.0f;
+                if (row && q < b) {
+                    sv = p == q ? 1.0f : (q == p + 1 ? ce : (q == p - 1 ? cwv : 0.0f));
+                    if (lev > 0) {
+                        const int qs = q - off, qse = q + 1 - off;
+                        const float cqs = cwS[ul + q], cqse = cwSE[ul + q];
+                        float acc = cpse * Tb[pse * kSLd + qse] * cqse;
+                        if (qs >= 0) acc = fmaf(cpse * Tb[pse * kSLd + qs], cqs, acc);
+                        if (ps >= 0) {
+                            acc = fmaf(cps * Tb[ps * kSLd + qse], cqse, acc);
+                            if (qs >= 0) acc = fmaf(cps * Tb[ps * kSLd + qs], cqs, acc);
+                        }
+                        sv -= acc;
+                    }
+                }
+                a[q] = sv;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[8 * m + t] = p == 8 * m + t ? 1.0f : 0.0f;
+        }
+    }
+    __syncwarp();   // every lane has read T_{lev-1} before the elimination overwrites Tb
+    gauss_jordan_regs(a, Tb, rowbuf, b, lev, bad);
 }
 
 // T (b x b, row-major ld kSLd in shared memory) to global memory in fragment order,
@@ -2056,7 +2106,6 @@ __global__ void __launch_bounds__(kThreadsM, 3) k_local_mixed_levels(const __gri
 constexpr int kFactorWarps = 4;
 
 struct FactorSmem {   // per warp
-    float Sb[kSchurMax * kSLd];
     float Tb[kSchurMax * kSLd];
     alignas(16) float rowbuf[2 * kSchurMax];
     double Su[9], Sd[9];
@@ -2126,9 +2175,7 @@ __device__ __forceinline__ void schur_factor_block(const MixedArgs& g, int blk) 
     int ul = 0, o = 0;
     for (int lev = 0; lev < g.nlev; ++lev) {
         const int b = lg.size(lev);
-        schur_update(cw, cw + nu, cw + 2 * nu, cw + 3 * nu, fs.Tb, fs.Sb, lev, b, ul, lane, 0, 1);
-        __syncwarp();
-        gauss_jordan_warp(fs.Sb, fs.Tb, fs.rowbuf, b, lev, &fs.bad);
+        schur_level_warp(cw, cw + nu, cw + 2 * nu, cw + 3 * nu, fs.Tb, fs.rowbuf, lev, b, ul, &fs.bad);
         __syncwarp();
         write_frag_op(fs.Tb, b, T + o, warp, 1);
         __syncwarp();
