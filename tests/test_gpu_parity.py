@@ -151,13 +151,14 @@ def test_repeat_calls_identical():
 TOL_MIXED = 1e-9   # per-K blocks after FP64 refinement of the FP32 solves
 
 
-# (P1 with 37 right-hand sides and P2 with 49, the most a face's 16 multipliers give, run the
-# generic level-Schur path)
+# (P1 with 25 right-hand sides runs the level-Schur solve with all column tiles in step, up
+# to 24 in decoupled column groups; P1 with 37 and P2 with 49, the most a face's 16
+# multipliers give, run the generic level-Schur path)
 @pytest.mark.parametrize("P,r,m,l,nx,field", [(1, 3, 1, 1, 2, "one"), (1, 0, 1, 0, 1, "log_uniform"),
                                               (1, 2, 2, 1, 2, "log_uniform"), (1, 5, 2, 2, 1, "log_uniform"),
                                               (1, 5, 2, 2, 1, "grf4"), (2, 2, 3, 1, 2, "log_uniform"),
-                                              (2, 4, 3, 1, 1, "grf6"), (1, 4, 3, 3, 1, "grf4"),
-                                              (2, 3, 4, 3, 1, "log_uniform")])
+                                              (2, 4, 3, 1, 1, "grf6"), (1, 4, 2, 3, 1, "grf4"),
+                                              (1, 4, 3, 3, 1, "grf4"), (2, 3, 4, 3, 1, "log_uniform")])
 def test_mixed_blocks(P, r, m, l, nx, field):
     w = W.Workload("t", nx, nx, r, P, m, l, field, "sinsin", 1.0, 1.0, seed=5)
     p, kap = _run(w, mhm.MHM_MIXED, mhm.SolveOpts(10, 1e-13, 0, 0))
