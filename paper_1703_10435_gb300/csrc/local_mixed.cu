@@ -2202,11 +2202,11 @@ size_t factor_smem_bytes(int nunk) {
 
 // ---------------------------------------------------------------------------
 // The generic path's level-Schur factorisation (see solve_gen) as its own kernel, one
-// 64-thread block per coarse triangle, thread p holding row p of the level's matrix:
+// 128-thread block per coarse triangle, threads 2p and 2p + 1 holding row p of the level's matrix:
 // S_0 = Ah_00, S_lev = Ah_{lev,lev} - C_lev T_{lev-1} C_lev^T (on the leading first-row
 // block), T_lev = S_lev^-1 by Gauss-Jordan elimination in FP32, written with the coupling
 // tables into the element's operator block.
-constexpr int kGenThreads = 64;
+constexpr int kGenThreads = 128;
 constexpr int kGenLd = kGenMax + 4;    // tile row stride in floats (16-byte aligned rows)
 
 struct GenSmem {
@@ -2222,27 +2222,30 @@ struct GenSmem {
 };
 
 // T = S^-1 in place (b x b, b <= kGenMax, rows of stride kGenLd in shared memory) by
-// Gauss-Jordan elimination without pivoting (S is SPD); thread p holds row p in
-// registers.  Pivots go in blocks of 8 with the row array kept rotated so that the
-// block's pivot columns sit at positions 0..7 (the array turns left by 8 after each
-// block), which keeps every register index static.  Row k travels through shared
-// memory; each row applies a[j] -= g r[j] with g = a_pk / a_kk, or 1 - 1/a_kk in row
-// k (which turns it into r / a_kk), then a_pk = -g (1 / a_kk in row k).  Ends with a
-// block barrier.
+// Gauss-Jordan elimination without pivoting (S is SPD).  Row p is held in registers by the
+// two threads 2p (positions 0..31) and 2p + 1 (positions 32..63) of a warp pair.  Pivots go
+// in blocks of 8 with the row rotated so that the block's pivot columns sit at positions
+// 0..7 (the row turns left by 8 after each block, the halves trading 8 values by shuffles),
+// which keeps every register index static.  Row k travels through shared memory; each row
+// applies a[j] -= g r[j] with g = a_pk / a_kk, or 1 - 1/a_kk in row k (which turns it into
+// r / a_kk), then a_pk = -g (1 / a_kk in row k); a_pk reaches the second half by a shuffle.
+// Ends with a block barrier.
 __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b, int lev, int* bad) {
-    const int p = threadIdx.x;
-    float a[kGenMax];
+    constexpr int H = kGenMax / 2;   // positions per thread
+    const int p = threadIdx.x >> 1, h = threadIdx.x & 1;
+    const bool row = p < b;
+    float a[H];
 #pragma unroll
-    for (int j = 0; j < kGenMax; j += 4) {
-        const float4 v = p < b ? *reinterpret_cast<const float4*>(T + p * kGenLd + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < H; j += 4) {
+        const float4 v = row ? *reinterpret_cast<const float4*>(T + p * kGenLd + h * H + j) : make_float4(0.f, 0.f, 0.f, 0.f);
         a[j] = v.x; a[j + 1] = v.y; a[j + 2] = v.z; a[j + 3] = v.w;
     }
     const int nblk = (b + 7) >> 3;
     for (int kb = 0; kb < nblk; ++kb) {
-        uint32_t cm = 0;   // chunk m (positions 8m..8m+7) holds columns 8 ((kb + m) mod 8) + 0..7
+        uint32_t cm = 0;   // this half's chunk m (positions 8(m + 4h) ..) holds columns 8 ((kb + m + 4h) mod 8) + 0..7
 #pragma unroll
-        for (int m = 0; m < kGenMax / 8; ++m)
-            if ((((kb + m) & 7) << 3) < b) cm |= 1u << m;
+        for (int m = 0; m < H / 8; ++m)
+            if ((((kb + m + 4 * h) & 7) << 3) < b) cm |= 1u << m;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
             const int k = kb * 8 + kk;
@@ -2250,21 +2253,22 @@ __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b,
                 float* rb = rowbuf + (k & 1) * kGenMax;
                 if (p == k) {
 #pragma unroll
-                    for (int j = 0; j < kGenMax; j += 4)
-                        *reinterpret_cast<float4*>(rb + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+                    for (int j = 0; j < H; j += 4)
+                        *reinterpret_cast<float4*>(rb + h * H + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
                 }
                 __syncthreads();
-                if (p < b) {
+                const float apk = __shfl_sync(0xffffffffu, a[kk], threadIdx.x & 30);   // position kk: first half
+                if (row) {
                     const float piv = rb[kk];
-                    if (p == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
+                    if (threadIdx.x == 0 && !(piv > 0.0f) && *bad == 0) *bad = 1 + lev;
                     const float d = __frcp_rn(piv);
-                    const float gk = p == k ? 1.0f - d : a[kk] * d;
+                    const float gk = p == k ? 1.0f - d : apk * d;
 #pragma unroll
-                    for (int m = 0; m < kGenMax / 8; ++m) {
+                    for (int m = 0; m < H / 8; ++m) {
                         if (cm >> m & 1) {
 #pragma unroll
                             for (int t = 0; t < 8; t += 4) {
-                                const float4 r4 = *reinterpret_cast<const float4*>(rb + 8 * m + t);
+                                const float4 r4 = *reinterpret_cast<const float4*>(rb + h * H + 8 * m + t);
                                 a[8 * m + t] = fmaf(-gk, r4.x, a[8 * m + t]);
                                 a[8 * m + t + 1] = fmaf(-gk, r4.y, a[8 * m + t + 1]);
                                 a[8 * m + t + 2] = fmaf(-gk, r4.z, a[8 * m + t + 2]);
@@ -2272,24 +2276,25 @@ __device__ __forceinline__ void gauss_jordan_gen(float* T, float* rowbuf, int b,
                             }
                         }
                     }
-                    a[kk] = p == k ? d : -gk;
+                    if (h == 0) a[kk] = p == k ? d : -gk;
                 }
             }
         }
+        // turn the row left by 8: each half passes its first 8 positions to the other half's tail
         float t8[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) t8[j] = a[j];
+        for (int j = 0; j < 8; ++j) t8[j] = __shfl_xor_sync(0xffffffffu, a[j], 1);
 #pragma unroll
-        for (int j = 0; j < kGenMax - 8; ++j) a[j] = a[j + 8];
+        for (int j = 0; j < H - 8; ++j) a[j] = a[j + 8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) a[kGenMax - 8 + j] = t8[j];
+        for (int j = 0; j < 8; ++j) a[H - 8 + j] = t8[j];
     }
-    // position j now holds column (8 nblk + j) mod kGenMax
+    // position h H + j now holds column (8 nblk + h H + j) mod kGenMax
     __syncthreads();
-    if (p < b) {
+    if (row) {
 #pragma unroll
-        for (int j = 0; j < kGenMax; ++j) {
-            const int col = (8 * nblk + j) & (kGenMax - 1);
+        for (int j = 0; j < H; ++j) {
+            const int col = (8 * nblk + h * H + j) & (kGenMax - 1);
             if (col < b) T[p * kGenLd + col] = a[j];
         }
     }
