@@ -2126,8 +2126,8 @@ __device__ __forceinline__ void schur_factor_block(const MixedArgs& g, int blk) 
     const int64_t kk = ki - g.Kbase;
     float* cw = g.cwall + kk * 4 * (int64_t)nu;
     float* T = g.Tall + kk * (int64_t)g.t_stride;
-    if (lane == 0) {
-        // the two fine-triangle shapes (up and down) of the uniform refinement
+    if (lane < 2) {
+        // the two fine-triangle shapes of the uniform refinement: up (lane 0), down (lane 1)
         double V[3][2];
         for (int v = 0; v < 3; ++v) {
             V[v][0] = g.dm.geom[6 * K + 2 * v];
@@ -2139,9 +2139,9 @@ __device__ __forceinline__ void schur_factor_block(const MixedArgs& g, int blk) 
         const double Xd[3][2] = {{V[0][0] + e1x, V[0][1] + e1y},
                                  {V[0][0] + e1x + e2x, V[0][1] + e1y + e2y},
                                  {V[0][0] + e2x, V[0][1] + e2y}};
-        element_stiffness(1, Xu, fs.Su);
-        element_stiffness(1, Xd, fs.Sd);
-        fs.bad = 0;
+        if (lane == 0) element_stiffness(1, Xu, fs.Su);
+        else element_stiffness(1, Xd, fs.Sd);
+        if (lane == 0) fs.bad = 0;
     }
     __syncwarp();
     for (int u = lane; u < nu; u += 32) {
