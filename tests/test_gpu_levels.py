@@ -432,3 +432,38 @@ def test_mixed_levels_in_one_persistent_launch():
             for a, b in ((p.AK[K * NI * NI:(K + 1) * NI * NI], q.AK[K * NI * NI:(K + 1) * NI * NI]),
                          (p.EK[K * NI:(K + 1) * NI], q.EK[K * NI:(K + 1) * NI])):
                 assert float((a - b).abs().max()) <= 1e-12 * float(b.abs().max()), (r, K)
+
+
+def test_mixed_levels_launch_falls_back_to_fp64():
+    """The persistent launch across levels with a one-pass limit: the refinement of most
+    elements stops short, and each level's failed elements are solved again by the FP64 path
+    (status OK, iters -1, blocks equal to the FP64 path's); without the re-solve they keep
+    MHM_ERR_NOT_CONVERGED and the outcome word says so."""
+    from paper_1703_10435_gb300.pipeline import Pipeline
+    nx, ny, rs, kap = _levels_case()
+    keep = rs <= 5
+    rs2 = np.where(keep, rs, 5).astype(np.int8)
+    kap2 = [k if kp else 10.0 ** np.random.default_rng(K).uniform(-2, 2, 4 ** 5) for K, (k, kp) in
+            enumerate(zip(kap, keep))]
+    kd = torch.as_tensor(np.concatenate(kap2), device="cuda")
+    src = mhm.Source(mhm.MHM_SRC_CONST, 1.0, 1.0)
+    p = Pipeline(nx, ny, 0, 1, 1, 2, 0, mhm.MHM_MIXED, r_per_K=rs2)
+    q = Pipeline(nx, ny, 0, 1, 1, 2, 0, mhm.MHM_FP64, r_per_K=rs2)
+    mhm.mhm_set_timing(p.mesh, True)
+    p.local(kd, src, mhm.SolveOpts(1, 1e-13, 0, 0))
+    times = mhm.mhm_kernel_times(p.mesh)
+    assert times["k_local_mixed"][0] == 1, times
+    q.local(kd, src)
+    torch.cuda.synchronize()
+    assert set(p.status.cpu().tolist()) == {0}
+    failed = np.flatnonzero(p.iters.cpu().numpy() == -1)   # (the smallest levels may finish in one pass)
+    assert len(failed) >= len(rs2) // 2
+    NI = p.mesh.n_I
+    for K in failed:
+        assert torch.equal(p.AK[K * NI * NI:(K + 1) * NI * NI], q.AK[K * NI * NI:(K + 1) * NI * NI]), K
+        assert torch.equal(p.EK[K * NI:(K + 1) * NI], q.EK[K * NI:(K + 1) * NI]), K
+    p.local(kd, src, mhm.SolveOpts(1, 1e-13, 0, 0, 1))
+    torch.cuda.synchronize()
+    st = p.status.cpu().numpy()
+    assert set(st.tolist()) <= {0, mhm.MHM_ERR_NOT_CONVERGED} and (st[failed] == mhm.MHM_ERR_NOT_CONVERGED).all()
+    assert mhm.mhm_sync_status(p.mesh)[0] == mhm.MHM_ERR_NOT_CONVERGED
