@@ -237,10 +237,13 @@ mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes);
  * MHM_Q_KAPPA_OFFSET[K]), > 0.  workspace_dev: at least mhm_local_workspace_size
  * bytes (may be NULL when that size is 0).
  * stream: a cudaStream_t (NULL = legacy default stream).  On a mesh with several
- * refinement levels the levels run concurrently: the first on `stream`, the others
- * on library-owned side streams that wait for the work `stream` held when the call
- * was made, and `stream` waits for them before its later work (stream-ordered as a
- * whole; calls on the same mesh from several host threads must not interleave).
+ * refinement levels, MIXED puts its level-Schur levels (P1 levels of at most 32 points,
+ * each within one factor chunk, up to five of them) into one factor launch and one
+ * persistent solve launch that takes the levels as work buckets, largest first; that pair
+ * and the other levels run concurrently: the first on `stream`, the others on
+ * library-owned side streams that wait for the work `stream` held when the call was
+ * made, and `stream` waits for them before its later work (stream-ordered as a whole;
+ * calls on the same mesh from several host threads must not interleave).
  * Errors: INVALID_ARG (NULL pointers, bad options, workspace too small),
  * UNSUPPORTED, CUDA (launch failure). */
 mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
