@@ -10,7 +10,9 @@ mixed-precision path (FP32 factorisation and solves, FP64 residuals), the
 all-FP64 path is reported beside it, with the L2 difference of the
 multipliers and of the reconstructed u between the two, and a sample of
 coarse triangles checked against the FP64 oracle.  The 2048-element
-log-uniform workload is timed as a secondary line.  Prints one JSON line.
+log-uniform workload is timed as a secondary line, and the P2 (131072 elements) and
+uneven-level (8192 elements, levels 3..7) workloads in `more_configs` (3 warm-up and 3
+timed steps each, both paths).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
@@ -32,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "c3_grf_mixed"
 SECONDARY = "c2_hetero_fp64"
+MORE = "c5_p2_large,c4_channels"
 
 
 def algorithmic_fmas(P, N, R):
@@ -551,6 +554,24 @@ def run_ours(args, w, rank, world, local_rank):
                    "fp64_value": u2 / (r2["t_64"] * 1e-3), "mixed_over_fp64": r2["t_64"] / r2["t_mx"],
                    "ms_per_step": r2["t_mx"] / args.steps, "unit": "coarse elements/s"}
             del r2
+    more = []
+    for name in ([] if not args.more or args.more == "none" else args.more.split(",")):
+        if name in (w.name, args.secondary):
+            continue
+        w3 = W.WORKLOADS[name]
+        s3, ww3 = min(args.steps, 3), 3
+        r3 = run_workload(args, w3, rank, world, local_rank, dev, barrier, s3, ww3, flush, False)
+        if rank == 0:
+            u3 = world * w3.n_K * s3
+            it3 = r3["pmx"].iters.cpu().numpy()
+            a64, amx = r3["p64"].AK, r3["pmx"].AK
+            more.append({"workload": w3.name, "config": workload_config(w3), "steps": s3, "warmup": ww3,
+                         "value": u3 / (r3["t_mx"] * 1e-3), "fp64_value": u3 / (r3["t_64"] * 1e-3),
+                         "mixed_over_fp64": r3["t_64"] / r3["t_mx"], "ms_per_step": r3["t_mx"] / s3,
+                         "fp64_ms_per_step": r3["t_64"] / s3, "unit": "coarse elements/s",
+                         "refinement_passes_mean": float(it3[it3 > 0].mean()) if np.any(it3 > 0) else 0.0,
+                         "AK_rel_l2_mixed_vs_fp64": float(torch.linalg.norm(amx - a64) / torch.linalg.norm(a64))})
+        del r3
     if rank != 0:
         return
     p64, pmx, kern64, kernmx = r["p64"], r["pmx"], r["kern64"], r["kernmx"]
@@ -660,6 +681,7 @@ def run_ours(args, w, rank, world, local_rank):
         "clocks": clocks,
         "pipes_gflops": pipes,
         "secondary": sec,
+        "more_configs": more,
         "factor_reuse": None if "t_reuse" not in r else {
             "value": units / (r["t_reuse"] * 1e-3), "unit": "coarse elements/s",
             "ms_per_step": r["t_reuse"] / args.steps, "store_bytes": r["store_bytes"],
@@ -682,6 +704,7 @@ def main():
     ap.add_argument("--clocks-csv", default=None, help="file for the raw nvidia-smi samples (default: temp dir)")
     ap.add_argument("--no-solution-check", action="store_true")
     ap.add_argument("--secondary", default=SECONDARY, help="second workload timed beside the headline ('none': no second line)")
+    ap.add_argument("--more", default=MORE, help="further workloads timed briefly beside it, comma-separated ('none': none)")
     ap.add_argument("--oracle-sample", type=int, default=12, help="coarse triangles checked against the oracle")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
