@@ -251,8 +251,9 @@ def workload_config(w):
 
 
 def mixed_level(w, r):
-    """True where the mixed path runs level r in mixed precision (P1 levels wider than
-    32 points, and P2 levels of r >= 5, run on the FP64 path)."""
+    """True where the mixed path runs level r by level-Schur refinement (P1 levels of at
+    most 32 points, P2 levels of r <= 4).  Wider P1 levels run FP64 conjugate gradients
+    preconditioned by the FP32 factor, P2 levels of r >= 5 the FP64 path."""
     return (1 << r) <= 32 if w.degree == 1 else r <= 4
 
 

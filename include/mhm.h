@@ -229,8 +229,11 @@ mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes);
  *   BK_dev[K*N_I + j]             = (s psi_j, 1)_{dK}
  *   FK_dev[K]                     = (f, 1)_K
  *   status_dev[K]                 = 0, or MHM_ERR_NOT_CONVERGED (MIXED refinement
- *                                   hit it_max), or MHM_ERR_INVALID_ARG (non-positive pivot)
- *   iters_dev[K]                  = refinement passes taken (1 for FP64; -1: MIXED
+ *                                   hit it_max), or MHM_ERR_INVALID_ARG (non-positive pivot),
+ *                                   or MHM_ERR_UNSUPPORTED (MIXED, wide level, pinned DOF
+ *                                   on lattice row 1: left to the FP64 re-solve; zero blocks)
+ *   iters_dev[K]                  = refinement passes taken (1 for FP64; conjugate-gradient
+ *                                   iterations on the wide MIXED levels; -1: MIXED
  *                                   refinement failed and K was solved again in FP64); may be NULL
  * Arrays are indexed by absolute K; entries outside the range are untouched.
  * kappa_dev: n_K * 4^r doubles (with a level per K: 4^r_K from
@@ -244,6 +247,14 @@ mhm_status mhm_factor_store_size(const mhm_mesh* mesh, size_t* bytes);
  * library-owned side streams that wait for the work `stream` held when the call was
  * made, and `stream` waits for them before its later work (stream-ordered as a whole;
  * calls on the same mesh from several host threads must not interleave).
+ * MIXED on the wide P1 levels (r = 6, 7: lattice rows of 64 and 128 points, at most 16
+ * right-hand sides): the FP32 level-Schur factor of the diagonally scaled pinned matrix
+ * preconditions conjugate gradients in FP64 (it_max and tol then bound its iterations;
+ * the error estimate r^T M r is the refinement's), one persistent launch per level with
+ * a workspace slot per resident block (Sec. 3: per-element factorisations, then only
+ * products with them).  Elements whose CG fails, and those whose pinned DOF lies on
+ * lattice row 1 (a level 0 one point wider than the kernel's rows), are solved again by
+ * the FP64 path unless opts->no_fallback.
  * Errors: INVALID_ARG (NULL pointers, bad options, workspace too small),
  * UNSUPPORTED, CUDA (launch failure). */
 mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* kappa_dev, const mhm_source* f,
@@ -382,7 +393,9 @@ mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa_dev, const 
  * of failures without reading the per-K status array:
  *   bit (1u << c)  some element finished with the final per-K status c: MHM_ERR_NOT_CONVERGED
  *                  (refinement hit it_max), MHM_ERR_INVALID_ARG (non-positive pivot),
- *                  MHM_ERR_TIMEOUT (a bounded wait for the staged operators ran out);
+ *                  MHM_ERR_TIMEOUT (a bounded wait for the staged operators ran out),
+ *                  MHM_ERR_UNSUPPORTED (a wide-level element left to an FP64 re-solve
+ *                  that was turned off);
  *                  with the default FP64 re-solve of failed mixed elements, only the
  *                  outcome of the re-solve counts;
  *   MHM_STATUS_REFINED_IN_FP64  some elements whose mixed refinement failed were solved
@@ -392,7 +405,8 @@ mhm_status mhm_reconstruct(const mhm_mesh* mesh, const double* kappa_dev, const 
 /* Waits for the work queued on `stream` (a cudaStream_t, NULL = legacy default stream),
  * reads the mesh's outcome word into *word_out (may be NULL) and clears it.  Returns the
  * most severe final code recorded since the last read (MHM_ERR_TIMEOUT, then
- * MHM_ERR_INVALID_ARG, then MHM_ERR_NOT_CONVERGED), MHM_OK if none; the calls of the
+ * MHM_ERR_INVALID_ARG, then MHM_ERR_UNSUPPORTED, then MHM_ERR_NOT_CONVERGED), MHM_OK if
+ * none; the calls of the
  * recorded solves must have been issued on `stream` or ordered before its current work.
  * Errors: INVALID_ARG (NULL or host-only mesh), CUDA. */
 mhm_status mhm_sync_status(const mhm_mesh* mesh, void* stream, uint32_t* word_out);

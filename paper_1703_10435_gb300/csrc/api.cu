@@ -8,6 +8,7 @@
 #include <string>
 
 #include "mhm_internal.h"
+#include "mixed_wide.h"
 
 namespace mhm {
 
@@ -68,9 +69,15 @@ bool fp64_level(const mhm_mesh* mesh, const Level& lv) {
     return fp64_window_rows(mesh, lv) > 128;
 }
 
+// MIXED: wide P1 levels (r = 6, 7) run the level-Schur factor with CG (local_mixed_wide.cu)
+bool wide_level(const mhm_mesh* mesh, const Level& lv, int32_t precision) {
+    return precision == MHM_MIXED && wide_mixed_level(mesh, lv);
+}
+
 size_t level_workspace_bytes(const mhm_mesh* mesh, const Level& lv, int32_t precision) {
-    const size_t b = (precision == MHM_FP64 || fp64_level(mesh, lv)) ? fp64_level_workspace(mesh, lv)
-                                                                       : mixed_level_workspace(mesh, lv);
+    const size_t b = wide_level(mesh, lv, precision) ? wide_mixed_workspace(mesh, lv)
+                     : (precision == MHM_FP64 || fp64_level(mesh, lv)) ? fp64_level_workspace(mesh, lv)
+                                                                         : mixed_level_workspace(mesh, lv);
     return (b + 255) & ~(size_t)255;
 }
 
@@ -253,7 +260,10 @@ extern "C" mhm_status mhm_local_solve_batch(const mhm_mesh* mesh, const double* 
             const Level& lv = *run[i];
             const size_t need = level_workspace_bytes(mesh, lv, precision);
             void* region = need ? (char*)workspace + level_region_offset(mesh, lv, precision) : nullptr;
-            if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
+            if (wide_level(mesh, lv, precision)) {
+                st = launch_local_mixed_wide(mesh, lv, kappa, *f, o, r0[i], r1[i], AK, EK, BK, FK, status, iters,
+                                             region, need, si);
+            } else if (precision == MHM_FP64 || fp64_level(mesh, lv)) {
                 st = launch_local_fp64(mesh, lv, kappa, *f, r0[i], r1[i], AK, EK, BK, FK, status, iters, region, need,
                                        si);
             } else {
@@ -430,7 +440,7 @@ extern "C" mhm_status mhm_sync_status(const mhm_mesh* mesh, void* stream, uint32
     MHM_CUDA_TRY(cudaMemsetAsync(mesh->d_sword, 0, sizeof(uint32_t), s));
     MHM_CUDA_TRY(cudaStreamSynchronize(s));
     if (word_out) *word_out = w;
-    for (int c : {MHM_ERR_TIMEOUT, MHM_ERR_INVALID_ARG, MHM_ERR_NOT_CONVERGED})
+    for (int c : {MHM_ERR_TIMEOUT, MHM_ERR_INVALID_ARG, MHM_ERR_UNSUPPORTED, MHM_ERR_NOT_CONVERGED})
         if (w & (1u << c)) return c;
     return MHM_OK;
 }

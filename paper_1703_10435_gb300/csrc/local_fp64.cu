@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "local_common.cuh"
+#include "mixed_wide.h"
 
 namespace mhm {
 
@@ -518,6 +519,14 @@ mhm_status launch_local_fp64(const mhm_mesh* mesh, const Level& lv, const double
     // K0, K1: launch indices within the level (its K list, or K itself on a uniform mesh)
     return launch_fp64(mesh, lv, kappa, f, K0, K1, AK, EK, BK, FK, status, iters, nullptr, nullptr, ws, ws_bytes,
                        stream);
+}
+
+mhm_status launch_local_fp64_list_ws(const mhm_mesh* mesh, const Level& lv, const double* kappa,
+                                     const mhm_source& f, const int32_t* list, const int32_t* count, int64_t max_n,
+                                     double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                                     int32_t* iters, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    // re-solves of failed elements of a wide mixed level: the window may need the workspace
+    return launch_fp64(mesh, lv, kappa, f, 0, max_n, AK, EK, BK, FK, status, iters, list, count, ws, ws_bytes, stream);
 }
 
 mhm_status launch_local_fp64_list(const mhm_mesh* mesh, const Level& lv, const double* kappa, const mhm_source& f,

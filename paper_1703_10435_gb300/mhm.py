@@ -316,8 +316,8 @@ def mhm_sync_status(mesh: Mesh, stream=None):
     work on `stream` and clears the word.  The code is returned, not raised."""
     w = ctypes.c_uint32(0)
     code = lib().mhm_sync_status(mesh.handle, _stream(stream), ctypes.byref(w))
-    if code not in (MHM_OK, MHM_ERR_NOT_CONVERGED, MHM_ERR_INVALID_ARG, MHM_ERR_TIMEOUT) or (
-            code == MHM_ERR_INVALID_ARG and not w.value):
+    if code not in (MHM_OK, MHM_ERR_NOT_CONVERGED, MHM_ERR_INVALID_ARG, MHM_ERR_TIMEOUT, MHM_ERR_UNSUPPORTED) or (
+            code in (MHM_ERR_INVALID_ARG, MHM_ERR_UNSUPPORTED) and not w.value):
         _check(code)
     return code, int(w.value)
 

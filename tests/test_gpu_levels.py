@@ -316,11 +316,29 @@ def test_channel_workload_full_size():
         out[prec] = p.AK.view(w.n_K, -1)
         if prec == mhm.MHM_MIXED:
             # levels 3..5 converge in FP32 + refinement; the 64- and 128-wide levels 6
-            # and 7 run on the FP64 path (one pass)
+            # and 7 in FP64 conjugate gradients preconditioned by the FP32 factor (a few
+            # elements whose pinned DOF lies on lattice row 1 are solved in FP64: -1)
             it = p.iters.cpu().numpy()
-            assert np.all(it[rk <= 5] >= 2) and np.all(it[rk >= 6] == 1)
-    d = (torch.linalg.norm(out[mhm.MHM_MIXED] - out[mhm.MHM_FP64], dim=1) / torch.linalg.norm(out[mhm.MHM_FP64], dim=1)).max()
-    assert float(d) < 1e-9
+            assert np.all(it[rk <= 5] >= 2)
+            w67 = it[rk >= 6]
+            assert np.all((w67 == -1) | ((w67 >= 1) & (w67 <= 8))) and np.mean(w67 == -1) < 0.01
+            assert float(w67[w67 > 0].mean()) <= 4.0
+    d = (torch.linalg.norm(out[mhm.MHM_MIXED] - out[mhm.MHM_FP64], dim=1) /
+         torch.linalg.norm(out[mhm.MHM_FP64], dim=1)).cpu().numpy()
+    # levels 3..5: the same pinned solution to 1e-9.  Levels 6, 7: the two paths reach it by
+    # different FP64 arithmetic (Cholesky Gram form; CG residuals and the corrected bilinear
+    # form), each to about 10 u cond(A): on the element where they differ most, twice that
+    # bound (cond from the oracle's matrix) holds.
+    assert float(d[rk <= 5].max()) < 1e-9
+    Kw = int(np.flatnonzero(rk >= 6)[np.argmax(d[rk >= 6])])
+    from oracle.fem import Submesh
+    from oracle.local import assemble_stiffness
+    import scipy.sparse.linalg as sla
+    kw = W.kappa_levels(w, [Kw])[0]
+    A = assemble_stiffness(Submesh(W.coarse_vertices(w.nx, w.ny)[Kw], int(rk[Kw]), 1), kw)
+    hi = float(sla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0])
+    lo = float(np.sort(sla.eigsh(A, k=2, sigma=-1e-6 * hi, which="LM", return_eigenvectors=False))[1])
+    assert float(d[Kw]) < 2 * max(1e-10, 10 * 2.0 ** -53 * hi / lo), (Kw, float(d[Kw]), hi / lo)
     # Per level: the median element and the first element crossing a channel (kappa 1 and
     # 1e4 inside it), each path against the oracle.  The bound is 1e-10, or the FP64
     # error bound 10 u cond(A) (u = 2^-53, cond on the mean-zero space) where that is
