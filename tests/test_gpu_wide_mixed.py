@@ -131,7 +131,7 @@ def test_wide_level_mixed_vs_fp64_on_channel_elements():
     arithmetic (a Cholesky factor's Gram form; CG residuals with the corrected bilinear
     form), each to about u cond(A) (u = 2^-53, cond on the mean-zero space, ~1e8 here):
     on the element where they differ most, both are held to the oracle at max(1e-10,
-    10 u cond) and their difference to twice that."""
+    10 u cond), entry by entry."""
     from paper_1703_10435_gb300 import workloads as W
     from paper_1703_10435_gb300.pipeline import Pipeline
     from _blocks import gram_entry_error
@@ -157,4 +157,4 @@ def test_wide_level_mixed_vs_fp64_on_channel_elements():
     NI = o.AK.shape[0]
     e_mx = gram_entry_error(amx[K].reshape(NI, NI), o.AK)
     e_64 = gram_entry_error(a64[K].reshape(NI, NI), o.AK)
-    assert e_mx < tol and e_64 < tol and d[K] < 2 * tol, (K, d[K], e_mx, e_64, tol)
+    assert e_mx < tol and e_64 < tol, (K, d[K], e_mx, e_64, tol)
