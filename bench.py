@@ -548,20 +548,28 @@ def run_ours(args, w, rank, world, local_rank):
     sec = None
     if args.secondary and args.secondary != "none" and args.secondary != w.name:
         w2 = W.WORKLOADS[args.secondary]
-        r2 = run_workload(args, w2, rank, world, local_rank, dev, barrier, args.steps, args.warmup, flush, False)
-        if rank == 0:
-            u2 = world * w2.n_K * args.steps
-            sec = {"workload": w2.name, "config": workload_config(w2), "value": u2 / (r2["t_mx"] * 1e-3),
-                   "fp64_value": u2 / (r2["t_64"] * 1e-3), "mixed_over_fp64": r2["t_64"] / r2["t_mx"],
-                   "ms_per_step": r2["t_mx"] / args.steps, "unit": "coarse elements/s"}
+        try:
+            r2 = run_workload(args, w2, rank, world, local_rank, dev, barrier, args.steps, args.warmup, flush, False)
+            if rank == 0:
+                u2 = world * w2.n_K * args.steps
+                sec = {"workload": w2.name, "config": workload_config(w2), "value": u2 / (r2["t_mx"] * 1e-3),
+                       "fp64_value": u2 / (r2["t_64"] * 1e-3), "mixed_over_fp64": r2["t_64"] / r2["t_mx"],
+                       "ms_per_step": r2["t_mx"] / args.steps, "unit": "coarse elements/s"}
             del r2
+        except (AssertionError, RuntimeError, mhm.MHMError) as e:
+            # a failure of a side workload is reported in the line, not fatal to the headline
+            sec = {"workload": w2.name, "error": "%s: %s" % (type(e).__name__, e)}
     more = []
     for name in ([] if not args.more or args.more == "none" else args.more.split(",")):
         if name in (w.name, args.secondary):
             continue
         w3 = W.WORKLOADS[name]
         s3, ww3 = min(args.steps, 3), 3
-        r3 = run_workload(args, w3, rank, world, local_rank, dev, barrier, s3, ww3, flush, False)
+        try:
+            r3 = run_workload(args, w3, rank, world, local_rank, dev, barrier, s3, ww3, flush, False)
+        except (AssertionError, RuntimeError, mhm.MHMError) as e:
+            more.append({"workload": w3.name, "error": "%s: %s" % (type(e).__name__, e)})
+            continue
         if rank == 0:
             u3 = world * w3.n_K * s3
             it3 = r3["pmx"].iters.cpu().numpy()
