@@ -24,7 +24,11 @@ It follows the paper's statement of the method literally, in FP64:
                   (psi_j, eta_f) by quadrature of traces;
 * ``globalsys``   reduceLocalProblems: assembly and direct solve of the
                   saddle-point system (Eq. "mat_global");
-* ``reconstruct`` computeSolution (Eq. "u_Hh") and error norms.
+* ``reconstruct`` computeSolution (Eq. "u_Hh") and error norms;
+* ``tet3d``       the same four steps in three dimensions, on the paper's
+                  experiment (Sec. 5): tetrahedral coarse mesh of the unit
+                  cube, structured tetrahedral submeshes, Lagrange P1/P2
+                  locals and l = 0 multipliers on m = 4^s subfaces per face.
 
 Every function cites the passage it follows.  The readings of points where
 the paper is silent (numbering, orientation, basis of Lambda_H^{m,l},

@@ -43,3 +43,25 @@ def dirichlet_moment(mesh, e, q, p, m, gold):
     gk = (a0 + a1 * c + a2 * c * c, (a1 + 2.0 * a2 * c) * h, a2 * h * h)
     mom = lambda k: gold["moments"].get((k, p), 0.0)
     return float(np.linalg.norm(d)) * h * sum(gk[k] * mom(k) for k in range(3))
+
+
+def reference_tet_golden():
+    """The closed forms of tests/golden/reference_elements_3d.txt: the P1 stiffness of the
+    reference tetrahedron (times 6), the P2 basis integrals over |T| and the monomial
+    moments {(a, b, c): int x^a y^b z^c}."""
+    sec, out = None, {"p1_stiffness": [], "p2_mass": {}, "moments": {}}
+    for line in open(os.path.join(GOLDEN, "reference_elements_3d.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        if line.startswith("["):
+            sec = line[1:line.index("]")]
+            continue
+        tok = line.split()
+        if sec == "p1_stiffness":
+            out["p1_stiffness"].append([float(t) for t in tok])
+        elif sec == "p2_mass":
+            out["p2_mass"][tok[0]] = _frac(tok[1])
+        elif sec == "moments":
+            out["moments"][(int(tok[0]), int(tok[1]), int(tok[2]))] = _frac(tok[3])
+    out["p1_stiffness"] = np.asarray(out["p1_stiffness"]) / 6.0
+    return out
