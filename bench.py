@@ -12,7 +12,9 @@ multipliers and of the reconstructed u between the two, and a sample of
 coarse triangles checked against the FP64 oracle.  The 2048-element
 log-uniform workload is timed as a secondary line, and the P2 (131072 elements) and
 uneven-level (8192 elements, levels 3..7) workloads in `more_configs` (3 warm-up and 3
-timed steps each, both paths).  Prints one JSON line.
+timed steps each, both paths).  The three-dimensional form of the paper's experiment
+(Sec. 5: 12288 and 1536 coarse tetrahedra of the unit cube, P2 locals, l = 0 multipliers
+on 4 or 16 subfaces) is timed last, FP64, in `three_d`.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
@@ -529,6 +531,81 @@ def solution_errors(args, w, p64, pmx, kap, src):
     return out
 
 
+THREE_D = [(8, 2, 2, 4), (4, 2, 2, 16)]   # (nc, r, k, m): 12288 and 1536 coarse tetrahedra
+
+
+def local3d_flops(n, R):
+    """FP64 flops of one 3-D local solve: Cholesky of the pinned n - 1 unknowns
+    ((n-1)^3 / 3) and the forward and backward substitutions of R right-hand sides
+    (2 (n-1)^2 R)."""
+    n1 = n - 1
+    return n1 ** 3 / 3.0 + 2.0 * n1 * n1 * R
+
+
+def run_three_d(dev, flush, peak64, steps=5, warmup=3, n_check=2):
+    """The paper's three-dimensional experiment (Sec. 5: kappa = 1, f = 12 pi^2 sin sin sin
+    on the unit cube; 24 nc^3 coarse tetrahedra with 8^r sub-tetrahedra, k = 2, l = 0
+    multipliers on m subfaces): FP64 local solves + skeleton gather per step, CUDA events
+    on the launching stream, L2 flushed between steps, and a few elements against the
+    oracle."""
+    import torch
+    from paper_1703_10435_gb300 import mhm
+    stream = torch.cuda.current_stream()
+    out = []
+    for nc, r, P, m in THREE_D:
+        M = mhm.Mesh3D(nc, r, P, m, device=dev.index)
+        kap = torch.ones(M.n_K * M.n_sub, dtype=torch.float64, device=dev)
+        src = mhm.Source3D(mhm.MHM3D_SRC_SINSINSIN, 1.0, 2.0)
+        AK = torch.empty(M.n_K, M.n_I, M.n_I, dtype=torch.float64, device=dev)
+        EK = torch.empty(M.n_K, M.n_I, dtype=torch.float64, device=dev)
+        BK = torch.empty_like(EK)
+        FK = torch.empty(M.n_K, dtype=torch.float64, device=dev)
+        st = torch.empty(M.n_K, dtype=torch.int32, device=dev)
+        vals = torch.empty(M.nnz, dtype=torch.float64, device=dev)
+        E = torch.empty(M.n_lambda, dtype=torch.float64, device=dev)
+
+        def step():
+            mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st)
+            mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st)
+            ev[s][1].record(stream)
+            mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
+            ev[s][2].record(stream)
+        torch.cuda.synchronize()
+        t_step = sum(a.elapsed_time(c) for a, b, c in ev) / steps
+        t_local = sum(a.elapsed_time(b) for a, b, c in ev) / steps
+        assert int(st.abs().sum()) == 0, "3-D local solve status nonzero"
+        fl = local3d_flops(M.n_local, M.n_I + 1) * M.n_K
+        # a few elements against the oracle (kappa = 1, the same source)
+        from oracle import tet3d as T
+        o = T.build_mesh3d(nc, m)
+        f = T.source3d_fn("sinsinsin", 1.0, 2.0)
+        err = 0.0
+        for K in (0, M.n_K - 1)[:n_check]:
+            loc = T.solve_local3d(o, K, r, P, np.ones(M.n_sub), f)
+            d = np.sqrt(np.abs(np.diag(loc.AK)))
+            err = max(err, float((np.abs(AK[K].cpu().numpy() - loc.AK) / np.outer(d, d)).max()))
+        out.append({"workload": "cube_%dx%dx%d_tets%d_sub%d_k%d_m%d" % (nc, nc, nc, M.n_K, M.n_sub, P, m),
+                    "n_K": M.n_K, "local_dofs": M.n_local, "n_I": M.n_I, "lambda_unknowns": M.n_lambda,
+                    "value": M.n_K / (t_step * 1e-3), "unit": "coarse elements/s", "ms_per_step": t_step,
+                    "local_ms": t_local, "skeleton_ms": t_step - t_local, "dtype": "f64",
+                    "roofline": {"kernel": "k_local3d", "bound": "alu", "pipe": "fp64",
+                                 "flops_per_step": fl, "achieved": fl / (t_local * 1e-3) / 1e12, "peak": peak64,
+                                 "unit": "TFLOP/s", "frac": fl / (t_local * 1e-3) / 1e12 / peak64},
+                    "AK_gram_err_vs_oracle_%d_elements" % n_check: err,
+                    "inputs": "kappa = 1, f = 12 pi^2 sin(2 pi x) sin(2 pi y) sin(2 pi z) (the paper's model problem)"})
+        del M
+    return out
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -666,6 +743,13 @@ def run_ours(args, w, rank, world, local_rank):
                "sample": "%d coarse triangles of the workload (K = 0..%d), local solves, best of 3 runs"
                          % (n_sample, n_sample - 1)}
 
+    three_d = None
+    if world == 1 and not args.no_three_d:
+        try:
+            three_d = run_three_d(dev, flush, peak64)
+        except (AssertionError, RuntimeError, ValueError, mhm.MHMError) as e:
+            three_d = {"error": "%s: %s" % (type(e).__name__, e)}
+
     line = {
         "metric": "coarse elements/s (local solves + skeleton assembly)",
         "value": value, "unit": "coarse elements/s", "n_gpus": world, "steps": args.steps,
@@ -698,6 +782,7 @@ def run_ours(args, w, rank, world, local_rank):
             "what": "mixed local solves + skeleton with the level-Schur factors kept from an earlier call "
                     "(mhm_solve_opts.factor_store, factor_reuse = 1) and a new source f; L2 flushed between steps"},
         "tuning": r.get("tuning"),
+        "three_d": three_d,
     }
     print(json.dumps(line), flush=True)
 
@@ -716,6 +801,7 @@ def main():
     ap.add_argument("--secondary", default=SECONDARY, help="second workload timed beside the headline ('none': no second line)")
     ap.add_argument("--more", default=MORE, help="further workloads timed briefly beside it, comma-separated ('none': none)")
     ap.add_argument("--oracle-sample", type=int, default=12, help="coarse triangles checked against the oracle")
+    ap.add_argument("--no-three-d", action="store_true", help="skip the three-dimensional workloads")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

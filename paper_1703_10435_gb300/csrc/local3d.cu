@@ -1,0 +1,553 @@
+// Three-dimensional local problems (the paper's experiment, Sec. 5) in FP64 on the GPU:
+// solveLocalProblem for every coarse tetrahedron (Sec. 3, Eqs. "etaf", "etai") and the
+// gather of the skeleton system (Eq. "mat_global").  Conventions in mhm3d.h.
+//
+// k_local3d: one block of kThreads threads per coarse element, everything in shared
+// memory:
+//   1. one element matrix per class of congruent sub-tetrahedra (the Freudenthal
+//      refinement has six: its sub-tetrahedra of one permutation class are translates),
+//      from the closed forms of the P1 / P2 Lagrange stiffness in barycentric gradients;
+//   2. assembly of kappa_T S_class into the packed lower triangle of the stiffness with
+//      local DOF 0 pinned (shared-memory atomics), the mass vector int phi_w, the
+//      multiplier loads -s (psi_j, phi_w) from the face table (a fine face triangle
+//      puts a third of its area on each load node) and the source load;
+//   3. the compatibility projection g - (1^T g / |K|) m of every right-hand side;
+//   4. a right-looking Cholesky factorisation of the pinned matrix with the forward
+//      substitution of all right-hand sides fused in, then the backward substitution;
+//   5. the projection onto int_K eta = 0 and the face integrals (s psi_j, eta_i) from the
+//      same face table, symmetrised.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "mhm3d_internal.h"
+
+namespace mhm3 {
+
+namespace {
+
+struct Local3DArgs {
+    const double* geom;
+    const int8_t* signs;
+    const int8_t* perm;
+    const int32_t* sub_dofs;
+    const int8_t* sub_cls;
+    const int8_t* sub_base;
+    const int32_t* ftab_off;
+    const int16_t* ftab_node;
+    const int8_t* ftab_cnt;
+    const double* quad;
+    const double* kappa;
+    int src_kind;
+    double src_value, src_freq;
+    int64_t K0;
+    int N, P, n, nb, nsub, m, NI, R;
+    double* AK;
+    double* EK;
+    double* BK;
+    double* FK;
+    int32_t* status;
+};
+
+__constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+__constant__ int c_edges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+// packed lower triangle, row i >= column j
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// shared-memory layout (doubles), in this order
+struct Smem3 {
+    int T, Y, mass, S6, G6, J6, invd, red, misc, total;
+};
+
+__host__ __device__ inline Smem3 smem_layout(int n, int NI, int nb) {
+    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2;
+    Smem3 s{};
+    int o = 0;
+    s.T = o;    o += npk > NI * R ? npk : NI * R;   // the pinned factor, later the face integrals
+    s.Y = o;    o += n * R;                         // right-hand sides, then solutions
+    s.mass = o; o += n;
+    s.S6 = o;   o += 6 * nb * nb;                   // element matrix per class
+    s.G6 = o;   o += 6 * 12;                        // barycentric gradients per class
+    s.J6 = o;   o += 6 * 9;                         // edge vectors per class (columns)
+    s.invd = o; o += n1;                            // 1 / L_kk
+    s.red = o;  o += R;
+    s.misc = o; o += 16;                            // |K|, |face a| / N^2 (4), V_sub, F_K, pivot flag
+    s.total = o;
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
+    extern __shared__ double sm[];
+    const Smem3 L = smem_layout(g.n, g.NI, g.nb);
+    double* Lp = sm + L.T;
+    double* Y = sm + L.Y;
+    double* mass = sm + L.mass;
+    double* S6 = sm + L.S6;
+    double* G6 = sm + L.G6;
+    double* J6 = sm + L.J6;
+    double* invd = sm + L.invd;
+    double* red = sm + L.red;
+    double* misc = sm + L.misc;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int64_t K = g.K0 + blockIdx.x;
+    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI, nb = g.nb, m = g.m, N = g.N;
+    const double* V = g.geom + 12 * K;   // v0..v3
+    const double* kap = g.kappa + K * (int64_t)g.nsub;
+
+    // ---- zero the factor, right-hand sides and mass; geometry scalars
+    for (int i = tid; i < L.S6; i += nthr) sm[i] = 0.0;
+    if (tid == 0) {
+        double e[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 3; ++k) e[k][c] = V[3 * (k + 1) + c] - V[c];
+        const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                           e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        misc[0] = fabs(det) / 6.0;
+        misc[5] = misc[0] / ((double)N * N * N);
+        misc[6] = 0.0;
+        misc[7] = 0.0;
+    }
+    if (tid < 4) {   // area of local face a over N^2
+        int b[3], k = 0;
+        for (int v = 0; v < 4; ++v)
+            if (v != tid) b[k++] = v;
+        double u[3], w[3];
+        for (int c = 0; c < 3; ++c) u[c] = V[3 * b[1] + c] - V[3 * b[0] + c], w[c] = V[3 * b[2] + c] - V[3 * b[0] + c];
+        const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+        misc[1 + tid] = 0.5 * sqrt(cx * cx + cy * cy + cz * cz) / ((double)N * N);
+    }
+    if (tid < 6) {   // class tid: edge vectors X_v - X_0 = D p_v / N and barycentric gradients
+        double D[3][3];   // columns: v1 - v0, v2 - v1, v3 - v2
+        for (int c = 0; c < 3; ++c) {
+            D[c][0] = V[3 + c] - V[c];
+            D[c][1] = V[6 + c] - V[3 + c];
+            D[c][2] = V[9 + c] - V[6 + c];
+        }
+        int p[3] = {0, 0, 0};
+        double J[3][3];   // J[c][v]: component c of edge vector v
+        for (int v = 0; v < 3; ++v) {
+            p[c_perm[tid][v]] += 1;
+            for (int c = 0; c < 3; ++c) J[c][v] = (D[c][0] * p[0] + D[c][1] * p[1] + D[c][2] * p[2]) / N;
+        }
+        for (int c = 0; c < 3; ++c)
+            for (int v = 0; v < 3; ++v) J6[tid * 9 + 3 * c + v] = J[c][v];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        const double id = 1.0 / det;
+        // rows of J^{-1} are the gradients of the barycentrics l1, l2, l3
+        double Ji[3][3];
+        Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * id;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+        Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * id;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+        Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * id;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+        double* G = G6 + tid * 12;
+        for (int c = 0; c < 3; ++c) {
+            G[3 + c] = Ji[0][c], G[6 + c] = Ji[1][c], G[9 + c] = Ji[2][c];
+            G[c] = -(Ji[0][c] + Ji[1][c] + Ji[2][c]);
+        }
+    }
+    __syncthreads();
+
+    // ---- element matrix of each class (closed forms; Vs the common volume)
+    const double Vs = misc[5];
+    for (int it = tid; it < 6 * nb * nb; it += nthr) {
+        const int c = it / (nb * nb), a = (it / nb) % nb, b = it % nb;
+        const double* G = G6 + c * 12;
+        auto d = [&](int i, int j) { return G[3 * i] * G[3 * j] + G[3 * i + 1] * G[3 * j + 1] + G[3 * i + 2] * G[3 * j + 2]; };
+        double v;
+        if (g.P == 1) {
+            v = Vs * d(a, b);
+        } else if (a < 4 && b < 4) {
+            v = Vs * d(a, b) * (a == b ? 0.6 : -0.2);
+        } else if (a < 4 || b < 4) {
+            const int x = a < 4 ? a : b, e = (a < 4 ? b : a) - 4;
+            const int j = c_edges[e][0], k = c_edges[e][1];
+            const double cj = x == j ? 0.15 : -0.05, ck = x == k ? 0.15 : -0.05;
+            v = 4.0 * Vs * (d(x, k) * cj + d(x, j) * ck);
+        } else {
+            const int i = c_edges[a - 4][0], j = c_edges[a - 4][1], k = c_edges[b - 4][0], l = c_edges[b - 4][1];
+            v = 0.8 * Vs * (d(j, l) * (1 + (i == k)) + d(j, k) * (1 + (i == l)) + d(i, l) * (1 + (j == k)) +
+                            d(i, k) * (1 + (j == l)));
+        }
+        S6[it] = v;
+    }
+    __syncthreads();
+
+    // ---- assembly (pinned DOF 0 dropped, lower triangle), mass vector
+    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
+        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
+        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
+        if (da == 0 || db == 0 || da < db) continue;
+        atomicAdd(&Lp[pk(da - 1, db - 1)], kap[t] * S6[g.sub_cls[t] * nb * nb + ab]);
+    }
+    for (int it = tid; it < g.nsub * nb; it += nthr) {
+        const int a = it % nb;
+        const double c = g.P == 1 ? 0.25 : (a < 4 ? -0.05 : 0.2);
+        atomicAdd(&mass[g.sub_dofs[it]], c * Vs);
+    }
+    // multiplier loads: column a m + q, -s |fine face| / 3 per load node and fine triangle
+    for (int it = tid; it < 4 * m; it += nthr) {
+        const int a = it / m, q = it % m;
+        const int p = g.perm[4 * K + a];
+        const double w = -(double)g.signs[4 * K + a] * misc[1 + a] / 3.0;
+        const int base = (a * 6 + p) * (m + 1) + q;
+        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e)
+            Y[g.ftab_node[e] * R + it] = w * g.ftab_cnt[e];
+    }
+    // source load (f, phi_w)_K: sin sin sin by the collapsed Gauss rule of every sub-tetrahedron
+    if (g.src_kind == MHM3D_SRC_SINSINSIN) {
+        const double* qp = g.quad;
+        const double* qphi = g.quad + 4 * kQuad;
+        const double w6 = 6.0 * Vs;
+        const double kf = g.src_freq * M_PI, amp = g.src_value * 3.0 * kf * kf;
+        double fk = 0.0;
+        const int items = g.nsub * kQuad;
+        for (int it0 = 0; it0 < items; it0 += nthr) {
+            const int it = it0 + tid;
+            double wf = 0.0;
+            if (it < items) {
+                const int t = it / kQuad, q = it % kQuad;
+                const double* Jc = J6 + 9 * g.sub_cls[t];
+                const int zA = g.sub_base[3 * t], zB = g.sub_base[3 * t + 1], zC = g.sub_base[3 * t + 2];
+                double x[3];
+                for (int c = 0; c < 3; ++c) {
+                    const double x0 = V[c] + ((V[3 + c] - V[c]) * zA + (V[6 + c] - V[3 + c]) * zB +
+                                              (V[9 + c] - V[6 + c]) * zC) / N;
+                    x[c] = x0 + Jc[3 * c] * qp[4 * q] + Jc[3 * c + 1] * qp[4 * q + 1] + Jc[3 * c + 2] * qp[4 * q + 2];
+                }
+                const double fv = amp * sin(kf * x[0]) * sin(kf * x[1]) * sin(kf * x[2]);
+                wf = qp[4 * q + 3] * w6 * fv;
+                for (int a = 0; a < nb; ++a) atomicAdd(&Y[g.sub_dofs[t * nb + a] * R + NI], wf * qphi[q * nb + a]);
+            }
+            fk += wf;
+        }
+        fk = warp_sum(fk);
+        if (lane == 0) atomicAdd(&misc[6], fk);
+    }
+    __syncthreads();
+    if (g.src_kind == MHM3D_SRC_CONST) {
+        for (int w = tid; w < n; w += nthr) Y[w * R + NI] = g.src_value * mass[w];
+        if (tid == 0) misc[6] = g.src_value * misc[0];
+        __syncthreads();
+    }
+
+    // ---- compatibility projection g - (1^T g / |K|) m
+    const double volK = misc[0];
+    for (int r = warp; r < R; r += nwarp) {
+        double s = 0.0;
+        for (int w = lane; w < n; w += 32) s += Y[w * R + r];
+        s = warp_sum(s);
+        if (lane == 0) red[r] = s / volK;
+    }
+    __syncthreads();
+    for (int it = tid; it < n * R; it += nthr) Y[it] -= red[it % R] * mass[it / R];
+    __syncthreads();
+
+    // ---- Cholesky of the pinned matrix (rows 1..n-1), forward substitution fused
+    for (int k = 0; k < n1; ++k) {
+        double d = Lp[pk(k, k)];
+        if (!(d > 0.0)) {
+            d = 1.0;
+            if (tid == 0) misc[7] = 1.0;
+        }
+        const double inv = 1.0 / sqrt(d);
+        for (int i = k + 1 + tid; i < n1; i += nthr) Lp[pk(i, k)] *= inv;
+        for (int r = tid; r < R; r += nthr) Y[(k + 1) * R + r] *= inv;
+        if (tid == 0) invd[k] = inv;
+        __syncthreads();
+        for (int i = k + 1 + warp; i < n1; i += nwarp) {
+            const double lik = Lp[pk(i, k)];
+            double* row = Lp + pk(i, 0);
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * Lp[pk(j, k)];
+            for (int r = lane; r < R; r += 32) Y[(i + 1) * R + r] -= lik * Y[(k + 1) * R + r];
+        }
+        __syncthreads();
+    }
+    // ---- backward substitution L^T z = y
+    for (int k = n1 - 1; k >= 0; --k) {
+        for (int r = tid; r < R; r += nthr) Y[(k + 1) * R + r] *= invd[k];
+        __syncthreads();
+        for (int i = warp; i < k; i += nwarp) {
+            const double lki = Lp[pk(k, i)];
+            for (int r = lane; r < R; r += 32) Y[(i + 1) * R + r] -= lki * Y[(k + 1) * R + r];
+        }
+        __syncthreads();
+    }
+    // pinned DOF 0, then the projection onto int_K eta = 0
+    for (int r = tid; r < R; r += nthr) Y[r] = 0.0;
+    __syncthreads();
+    for (int r = warp; r < R; r += nwarp) {
+        double s = 0.0;
+        for (int w = lane; w < n; w += 32) s += mass[w] * Y[w * R + r];
+        s = warp_sum(s);
+        if (lane == 0) red[r] = s / volK;
+    }
+    __syncthreads();
+    for (int it = tid; it < n * R; it += nthr) Y[it] -= red[it % R];
+    __syncthreads();
+
+    // ---- face integrals T[j][r] = (s psi_j, eta_r)_{dK} (the factor's storage reused)
+    double* Tf = Lp;
+    for (int it = tid; it < NI * R; it += nthr) {
+        const int j = it / R, r = it % R, a = j / m, q = j % m;
+        const int p = g.perm[4 * K + a];
+        const int base = (a * 6 + p) * (m + 1) + q;
+        double s = 0.0;
+        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) s += g.ftab_cnt[e] * Y[g.ftab_node[e] * R + r];
+        Tf[it] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * s;
+    }
+    __syncthreads();
+    double* AK = g.AK + K * (int64_t)NI * NI;
+    for (int it = tid; it < NI * NI; it += nthr) {
+        const int j = it / NI, i = it % NI;
+        AK[it] = 0.5 * (Tf[j * R + i] + Tf[i * R + j]);
+    }
+    for (int j = tid; j < NI; j += nthr) {
+        const int a = j / m, q = j % m;
+        const int p = g.perm[4 * K + a];
+        const int base = (a * 6 + p) * (m + 1) + q;
+        int c = 0;
+        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) c += g.ftab_cnt[e];
+        g.EK[K * NI + j] = -Tf[j * R + NI];
+        g.BK[K * NI + j] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * c;
+    }
+    if (tid == 0) {
+        g.FK[K] = misc[6];
+        g.status[K] = misc[7] != 0.0 ? MHM_ERR_INVALID_ARG : MHM_OK;
+    }
+}
+
+// skeleton values: one thread per entry of a neighbour block
+__global__ void k_skeleton3d_A(const Nbr3* nbrs, int64_t nblocks, const int32_t* rowptr, int m, int NI,
+                               const double* AK, double* vals) {
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nblocks * mm;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const Nbr3 b = nbrs[it / mm];
+        const int q = (int)((it % mm) / m), q2 = (int)(it % m);
+        double v = AK[((int64_t)b.K0 * NI + b.a0 * m + q) * NI + b.b0 * m + q2];
+        if (b.K1 >= 0) v += AK[((int64_t)b.K1 * NI + b.a1 * m + q) * NI + b.b1 * m + q2];
+        vals[rowptr[(int64_t)b.f * m + q] + b.col_off + q2] = v;
+    }
+}
+
+__global__ void k_skeleton3d_E(const int32_t* face_ka, int64_t nlam, int m, int NI, const double* EK, double* E) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nlam; l += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = l / m;
+        const int q = (int)(l % m);
+        const int32_t* k = face_ka + 4 * f;
+        double v = EK[(int64_t)k[0] * NI + k[1] * m + q];
+        if (k[2] >= 0) v += EK[(int64_t)k[2] * NI + k[3] * m + q];
+        E[l] = v;
+    }
+}
+
+template <typename T>
+mhm_status upload3(const std::vector<T>& h, T** d) {
+    if (h.empty()) {
+        *d = nullptr;
+        return MHM_OK;
+    }
+    cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) return mhm::fail(MHM_ERR_OOM, "cudaMalloc failed for 3-D mesh tables");
+    if (e != cudaSuccess) return mhm::cuda_fail(e, "cudaMalloc");
+    e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return mhm::cuda_fail(e, "cudaMemcpy");
+    return MHM_OK;
+}
+
+void free_device(mhm_mesh3d* m) {
+    void* ptrs[] = {m->d_geom, m->d_signs, m->d_perm, m->d_sub_dofs, m->d_sub_cls, m->d_sub_base, m->d_ftab_off,
+                    m->d_ftab_node, m->d_ftab_cnt, m->d_quad, m->d_rowptr, m->d_nbrs, m->d_face_ka};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+size_t local3d_smem(int n, int NI, int nb) { return (size_t)smem_layout(n, NI, nb).total * sizeof(double); }
+
+}  // namespace mhm3
+
+using namespace mhm3;
+
+extern "C" mhm_status mhm3d_create_mesh(const mhm3d_mesh_desc* desc, int32_t device, mhm3d_mesh** out) {
+    if (!desc || !out) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: NULL argument");
+    *out = nullptr;
+    const mhm3d_mesh_desc d = *desc;
+    if (d.nc < 1 || d.nc > 64 || d.r < 0 || d.r > 4 || (d.degree != 1 && d.degree != 2))
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: need 1 <= nc <= 64, 0 <= r <= 4, degree 1 or 2");
+    int s = 0;
+    while ((1 << (2 * s)) < d.m && s < 8) ++s;
+    if (d.m < 1 || (1 << (2 * s)) != d.m || s > d.r)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: m must be 4^s with s <= r");
+    if (d.degree == 1 && (1 << d.r) < 2 * (1 << s))
+        return mhm::fail(MHM_ERR_INVALID_ARG,
+                         "mhm3d_create_mesh: degree 1 needs 2^r >= 2 sqrt(m) (the local traces must outnumber "
+                         "the multipliers, else A_K is singular)");
+    const int PN = d.degree << d.r;
+    const int64_t n = (int64_t)(PN + 1) * (PN + 2) * (PN + 3) / 6;
+    const int64_t nK = 24LL * d.nc * d.nc * d.nc;
+    if (nK * 16LL * d.m * d.m > INT32_MAX * 8LL)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: mesh too large");
+    if (device >= 0) {
+        if (!mhm::device_supported(device))
+            return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_create_mesh: device is not an sm_103 GPU");
+        if (n > kMaxLocal || d.m > kMaxM || local3d_smem((int)n, 4 * d.m, d.degree == 1 ? 4 : 10) > 227 * 1024)
+            return mhm::fail(MHM_ERR_UNSUPPORTED,
+                             "mhm3d_create_mesh: the local factor and right-hand sides exceed shared memory "
+                             "(degree 2: r <= 2, degree 1: r <= 3, m <= 16)");
+    }
+    mhm_mesh3d* m = new mhm_mesh3d();
+    m->device = device;
+    m->desc = d;
+    m->s = s;
+    const std::string err = build_mesh3d_host(m);
+    if (!err.empty()) {
+        delete m;
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: " + err);
+    }
+    if (device >= 0) {
+        cudaError_t ce = cudaSetDevice(device);
+        if (ce != cudaSuccess) {
+            delete m;
+            return mhm::cuda_fail(ce, "cudaSetDevice");
+        }
+        mhm_status st = MHM_OK;
+        if (!st) st = upload3(m->geom, &m->d_geom);
+        if (!st) st = upload3(m->signs, &m->d_signs);
+        if (!st) st = upload3(m->perm, &m->d_perm);
+        if (!st) st = upload3(m->sub_dofs, &m->d_sub_dofs);
+        if (!st) st = upload3(m->sub_cls, &m->d_sub_cls);
+        if (!st) st = upload3(m->sub_base, &m->d_sub_base);
+        if (!st) st = upload3(m->ftab_off, &m->d_ftab_off);
+        if (!st) st = upload3(m->ftab_node, &m->d_ftab_node);
+        if (!st) st = upload3(m->ftab_cnt, &m->d_ftab_cnt);
+        if (!st) st = upload3(m->quad, &m->d_quad);
+        if (!st) st = upload3(m->rowptr, &m->d_rowptr);
+        if (!st) st = upload3(m->nbrs, &m->d_nbrs);
+        if (!st) st = upload3(m->face_ka, &m->d_face_ka);
+        if (st) {
+            free_device(m);
+            delete m;
+            return st;
+        }
+        ce = cudaFuncSetAttribute(k_local3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)local3d_smem((int)m->n, (int)m->NI, m->nb));
+        if (ce != cudaSuccess) {
+            free_device(m);
+            delete m;
+            return mhm::cuda_fail(ce, "cudaFuncSetAttribute(k_local3d)");
+        }
+    }
+    *out = m;
+    return MHM_OK;
+}
+
+extern "C" void mhm3d_destroy_mesh(mhm3d_mesh* mesh) {
+    if (!mesh) return;
+    if (mesh->device >= 0) {
+        cudaSetDevice(mesh->device);
+        free_device(mesh);
+    }
+    delete mesh;
+}
+
+extern "C" mhm_status mhm3d_mesh_query(const mhm3d_mesh* m, int32_t what, void* host_out, size_t bytes) {
+    if (!m || !host_out) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_mesh_query: NULL argument");
+    auto copy = [&](const void* src, size_t n) -> mhm_status {
+        if (bytes < n) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_mesh_query: output buffer too small");
+        if (n) std::memcpy(host_out, src, n);
+        return MHM_OK;
+    };
+    switch (what) {
+        case MHM3D_Q_SIZES: {
+            const int64_t s[8] = {m->nK, m->nf, m->nv, m->nlam, m->n, m->NI, m->nsub, m->nnz};
+            return copy(s, sizeof(s));
+        }
+        case MHM3D_Q_TETS: return copy(m->tets.data(), m->tets.size() * 4);
+        case MHM3D_Q_TET_FACES: return copy(m->tet_faces.data(), m->tet_faces.size() * 4);
+        case MHM3D_Q_TET_SIGNS: return copy(m->signs.data(), m->signs.size());
+        case MHM3D_Q_FACES: return copy(m->faces.data(), m->faces.size() * 4);
+        case MHM3D_Q_VERTICES: return copy(m->verts.data(), m->verts.size() * 8);
+        case MHM3D_Q_NORMALS: return copy(m->normals.data(), m->normals.size() * 8);
+        case MHM3D_Q_CSR_ROWPTR: return copy(m->rowptr.data(), m->rowptr.size() * 4);
+        case MHM3D_Q_CSR_COLS: return copy(m->cols.data(), m->cols.size() * 4);
+        case MHM3D_Q_SUB_DOFS: return copy(m->sub_dofs.data(), m->sub_dofs.size() * 4);
+        case MHM3D_Q_NODES: return copy(m->nodes.data(), m->nodes.size() * 4);
+        case MHM3D_Q_FACE_PERM: return copy(m->perm.data(), m->perm.size());
+        case MHM3D_Q_FTAB_OFF: return copy(m->ftab_off.data(), m->ftab_off.size() * 4);
+        case MHM3D_Q_FTAB_NODE: return copy(m->ftab_node.data(), m->ftab_node.size() * 2);
+        case MHM3D_Q_FTAB_COUNT: return copy(m->ftab_cnt.data(), m->ftab_cnt.size());
+        case MHM3D_Q_QUAD: return copy(m->quad.data(), m->quad.size() * 8);
+        default: return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_mesh_query: unknown query");
+    }
+}
+
+extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double* kappa, const mhm3d_source* f,
+                                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK,
+                                              double* FK, int32_t* status, void* stream) {
+    if (!m) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL mesh");
+    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_local_solve_batch: host-only mesh");
+    if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL pointer argument");
+    if (f->kind != MHM3D_SRC_CONST && f->kind != MHM3D_SRC_SINSINSIN)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: unknown source kind");
+    if (K1 <= 0) K1 = m->nK;
+    if (K0 < 0 || K1 > m->nK || K0 > K1) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: K range");
+    if (K1 == K0) return MHM_OK;
+    MHM_CUDA_TRY(cudaSetDevice(m->device));
+    Local3DArgs g{};
+    g.geom = m->d_geom, g.signs = m->d_signs, g.perm = m->d_perm;
+    g.sub_dofs = m->d_sub_dofs, g.sub_cls = m->d_sub_cls, g.sub_base = m->d_sub_base;
+    g.ftab_off = m->d_ftab_off, g.ftab_node = m->d_ftab_node, g.ftab_cnt = m->d_ftab_cnt;
+    g.quad = m->d_quad, g.kappa = kappa;
+    g.src_kind = f->kind, g.src_value = f->value, g.src_freq = f->freq;
+    g.K0 = K0;
+    g.N = m->N, g.P = m->desc.degree, g.n = (int)m->n, g.nb = m->nb, g.nsub = (int)m->nsub, g.m = m->desc.m;
+    g.NI = (int)m->NI, g.R = (int)m->NI + 1;
+    g.AK = AK, g.EK = EK, g.BK = BK, g.FK = FK, g.status = status;
+    const size_t smem = local3d_smem(g.n, g.NI, g.nb);
+    // the attribute is per kernel, not per mesh: set it for this mesh's size every call
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_local3d<<<(unsigned)(K1 - K0), kThreads, smem, (cudaStream_t)stream>>>(g);
+    MHM_CUDA_TRY(cudaGetLastError());
+    return MHM_OK;
+}
+
+extern "C" mhm_status mhm3d_assemble_skeleton(const mhm3d_mesh* m, const double* AK, const double* EK,
+                                              double* A_vals, double* E, void* stream) {
+    if (!m) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_assemble_skeleton: NULL mesh");
+    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_assemble_skeleton: host-only mesh");
+    if (!AK || !EK || !A_vals || !E) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_assemble_skeleton: NULL pointer");
+    MHM_CUDA_TRY(cudaSetDevice(m->device));
+    const int64_t nblocks = (int64_t)m->nbrs.size();
+    const int64_t items = nblocks * m->desc.m * m->desc.m;
+    const int threads = 256;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    const int64_t want = (items + threads - 1) / threads;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    k_skeleton3d_A<<<grid, threads, 0, (cudaStream_t)stream>>>(m->d_nbrs, nblocks, m->d_rowptr, m->desc.m,
+                                                               (int)m->NI, AK, A_vals);
+    MHM_CUDA_TRY(cudaGetLastError());
+    const int64_t want_e = (m->nlam + threads - 1) / threads;
+    const unsigned grid_e = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want_e, (int64_t)sms * 8));
+    k_skeleton3d_E<<<grid_e, threads, 0, (cudaStream_t)stream>>>(m->d_face_ka, m->nlam, m->desc.m, (int)m->NI, EK, E);
+    MHM_CUDA_TRY(cudaGetLastError());
+    return MHM_OK;
+}

@@ -161,6 +161,7 @@ def lib():
                      "mhm_solve_global", "mhm_reconstruct", "mhm_set_timing", "mhm_kernel_times",
                      "mhm_local_solve_waves"):
             getattr(L, name).restype = i32
+        _bind3d(L)
         _lib = L
     return _lib
 
@@ -338,3 +339,77 @@ def mhm_autotune(mesh: Mesh, kappa, source: Source, opts: SolveOpts | None, AK, 
     _check(lib().mhm_autotune(mesh.handle, _ptr(kappa), ctypes.byref(source), None if opts is None else ctypes.byref(opts),
                               _ptr(AK), _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters), _ptr(workspace),
                               ws_bytes, None if cache_path is None else str(cache_path).encode(), _stream(stream)))
+
+
+# ---------------------------------------------------------------- include/mhm3d.h
+# The three-dimensional local problems (the paper's experiment, Sec. 5).
+
+MHM3D_SRC_CONST = 0
+MHM3D_SRC_SINSINSIN = 1
+Q3_SIZES, Q3_TETS, Q3_TET_FACES, Q3_TET_SIGNS, Q3_FACES, Q3_VERTICES, Q3_NORMALS, Q3_CSR_ROWPTR, \
+    Q3_CSR_COLS, Q3_SUB_DOFS, Q3_NODES, Q3_FACE_PERM, Q3_FTAB_OFF, Q3_FTAB_NODE, Q3_FTAB_COUNT, Q3_QUAD = range(16)
+EXPORTED_3D = ["mhm3d_create_mesh", "mhm3d_destroy_mesh", "mhm3d_mesh_query", "mhm3d_local_solve_batch",
+               "mhm3d_assemble_skeleton"]
+
+
+class Mesh3DDesc(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int32), ("r", ctypes.c_int32), ("degree", ctypes.c_int32), ("m", ctypes.c_int32)]
+
+
+class Source3D(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("freq", ctypes.c_double)]
+
+
+def _bind3d(L):
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    L.mhm3d_create_mesh.argtypes = [ctypes.POINTER(Mesh3DDesc), i32, ctypes.POINTER(vp)]
+    L.mhm3d_destroy_mesh.argtypes = [vp]
+    L.mhm3d_destroy_mesh.restype = None
+    L.mhm3d_mesh_query.argtypes = [vp, i32, vp, sz]
+    L.mhm3d_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source3D), i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mhm3d_assemble_skeleton.argtypes = [vp, vp, vp, vp, vp, vp]
+    for name in ("mhm3d_create_mesh", "mhm3d_mesh_query", "mhm3d_local_solve_batch", "mhm3d_assemble_skeleton"):
+        getattr(L, name).restype = i32
+
+
+class Mesh3D:
+    """Owning handle of an mhm3d_mesh (splitProblem on the unit cube)."""
+
+    def __init__(self, nc, r, degree, m, device: int = 0):
+        self.desc = Mesh3DDesc(nc, r, degree, m)
+        h = ctypes.c_void_p()
+        _check(lib().mhm3d_create_mesh(ctypes.byref(self.desc), device, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+        (self.n_K, self.n_faces, self.n_vertices, self.n_lambda, self.n_local, self.n_I, self.n_sub,
+         self.nnz) = [int(v) for v in self.query(Q3_SIZES, np.int64, 8)]
+
+    def query(self, what, dtype, count):
+        out = np.empty(count, dtype=dtype)
+        _check(lib().mhm3d_mesh_query(self.handle, what, out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+        return out
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            _lib.mhm3d_destroy_mesh(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mhm3d_create_mesh(nc, r, degree, m, device: int = 0) -> Mesh3D:
+    return Mesh3D(nc, r, degree, m, device)
+
+
+def mhm3d_local_solve_batch(mesh: Mesh3D, kappa, source: Source3D, AK, EK, BK, FK, status, K0=0, K1=0,
+                            stream=None):
+    _check(lib().mhm3d_local_solve_batch(mesh.handle, _ptr(kappa), ctypes.byref(source), K0, K1, _ptr(AK),
+                                         _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _stream(stream)))
+
+
+def mhm3d_assemble_skeleton(mesh: Mesh3D, AK, EK, A_vals, E, stream=None):
+    _check(lib().mhm3d_assemble_skeleton(mesh.handle, _ptr(AK), _ptr(EK), _ptr(A_vals), _ptr(E), _stream(stream)))

@@ -28,6 +28,11 @@ def test_exports_every_declared_symbol(lib):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(mhm.EXPORTED) <= declared
+    hdr3 = open(os.path.join(ROOT, "include", "mhm3d.h")).read()
+    declared3 = set(re.findall(r"\b(mhm3d_[a-z_0-9]+)\s*\(", hdr3))
+    assert declared3 == set(mhm.EXPORTED_3D)
+    for name in declared3:
+        assert hasattr(lib, name), name
 
 
 def _host_mesh(nx, ny, r=2, P=1, m=2, l=1):
