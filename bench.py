@@ -534,12 +534,12 @@ def solution_errors(args, w, p64, pmx, kap, src):
 THREE_D = [(8, 2, 2, 4), (4, 2, 2, 16)]   # (nc, r, k, m): 12288 and 1536 coarse tetrahedra
 
 
-def local3d_flops(n, R):
+def local3d_flops(n, NI):
     """FP64 flops of one 3-D local solve: Cholesky of the pinned n - 1 unknowns
-    ((n-1)^3 / 3) and the forward and backward substitutions of R right-hand sides
-    (2 (n-1)^2 R)."""
+    ((n-1)^3 / 3), the forward substitution of N_I + 1 right-hand sides ((n-1)^2 (N_I + 1))
+    and the Gram products of the face integrals (2 (n-1) (N_I (N_I + 1) / 2 + N_I))."""
     n1 = n - 1
-    return n1 ** 3 / 3.0 + 2.0 * n1 * n1 * R
+    return n1 ** 3 / 3.0 + n1 * n1 * (NI + 1.0) + 2.0 * n1 * (NI * (NI + 1) / 2.0 + NI)
 
 
 def run_three_d(dev, flush, peak64, steps=5, warmup=3, n_check=2):
@@ -583,7 +583,7 @@ def run_three_d(dev, flush, peak64, steps=5, warmup=3, n_check=2):
         t_step = sum(a.elapsed_time(c) for a, b, c in ev) / steps
         t_local = sum(a.elapsed_time(b) for a, b, c in ev) / steps
         assert int(st.abs().sum()) == 0, "3-D local solve status nonzero"
-        fl = local3d_flops(M.n_local, M.n_I + 1) * M.n_K
+        fl = local3d_flops(M.n_local, M.n_I) * M.n_K
         # a few elements against the oracle (kappa = 1, the same source)
         from oracle import tet3d as T
         o = T.build_mesh3d(nc, m)

@@ -116,9 +116,11 @@ typedef struct {
  * congruent sub-tetrahedra, the loads N_i = -(s psi_i, phi_w)_{dK} and
  * (f, phi_w)_K (a collapsed 4x4x4 Gauss rule per sub-tetrahedron for the
  * non-constant f), the compatibility projection, a Cholesky factorisation
- * with local DOF 0 pinned, the N_I + 1 solves and the projection onto
- * int_K eta = 0.  Outputs (device, caller-owned, indexed by K):
- *   AK_dev[K][j][i] = (s psi_j, eta_i)_{dK}  (N_I x N_I, symmetrised)
+ * with local DOF 0 pinned and the forward substitution of the N_I + 1
+ * right-hand sides; the face integrals of the zero-mean solutions follow in
+ * Gram form, (s psi_j, eta_i)_{dK} = -Y_j . Y_i with Y = L^{-1} times the
+ * projected loads.  Outputs (device, caller-owned, indexed by K):
+ *   AK_dev[K][j][i] = (s psi_j, eta_i)_{dK}  (N_I x N_I, symmetric)
  *   EK_dev[K][j]    = -(s psi_j, eta_f)_{dK}
  *   BK_dev[K][j]    = (s psi_j, 1)_{dK}
  *   FK_dev[K]       = (f, 1)_K

@@ -13,9 +13,9 @@
 //      puts a third of its area on each load node) and the source load;
 //   3. the compatibility projection g - (1^T g / |K|) m of every right-hand side;
 //   4. a right-looking Cholesky factorisation of the pinned matrix with the forward
-//      substitution of all right-hand sides fused in, then the backward substitution;
-//   5. the projection onto int_K eta = 0 and the face integrals (s psi_j, eta_i) from the
-//      same face table, symmetrised.
+//      substitution of all right-hand sides fused in;
+//   5. the face integrals in Gram form, (s psi_j, eta_i)_{dK} = -Y_j . Y_i with Y = L^{-1}
+//      times the projected loads (symmetric by construction), and E_K = Y_j . y_f.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -63,20 +63,19 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // shared-memory layout (doubles), in this order
 struct Smem3 {
-    int T, Y, mass, S6, G6, J6, invd, red, misc, total;
+    int T, Y, mass, S6, G6, J6, red, misc, total;
 };
 
 __host__ __device__ inline Smem3 smem_layout(int n, int NI, int nb) {
     const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2;
     Smem3 s{};
     int o = 0;
-    s.T = o;    o += npk > NI * R ? npk : NI * R;   // the pinned factor, later the face integrals
+    s.T = o;    o += npk;                           // the pinned factor (packed lower triangle)
     s.Y = o;    o += n * R;                         // right-hand sides, then solutions
     s.mass = o; o += n;
     s.S6 = o;   o += 6 * nb * nb;                   // element matrix per class
     s.G6 = o;   o += 6 * 12;                        // barycentric gradients per class
     s.J6 = o;   o += 6 * 9;                         // edge vectors per class (columns)
-    s.invd = o; o += n1;                            // 1 / L_kk
     s.red = o;  o += R;
     s.misc = o; o += 16;                            // |K|, |face a| / N^2 (4), V_sub, F_K, pivot flag
     s.total = o;
@@ -92,7 +91,6 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     double* S6 = sm + L.S6;
     double* G6 = sm + L.G6;
     double* J6 = sm + L.J6;
-    double* invd = sm + L.invd;
     double* red = sm + L.red;
     double* misc = sm + L.misc;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -267,7 +265,6 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         const double inv = 1.0 / sqrt(d);
         for (int i = k + 1 + tid; i < n1; i += nthr) Lp[pk(i, k)] *= inv;
         for (int r = tid; r < R; r += nthr) Y[(k + 1) * R + r] *= inv;
-        if (tid == 0) invd[k] = inv;
         __syncthreads();
         for (int i = k + 1 + warp; i < n1; i += nwarp) {
             const double lik = Lp[pk(i, k)];
@@ -277,52 +274,30 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         }
         __syncthreads();
     }
-    // ---- backward substitution L^T z = y
-    for (int k = n1 - 1; k >= 0; --k) {
-        for (int r = tid; r < R; r += nthr) Y[(k + 1) * R + r] *= invd[k];
-        __syncthreads();
-        for (int i = warp; i < k; i += nwarp) {
-            const double lki = Lp[pk(k, i)];
-            for (int r = lane; r < R; r += 32) Y[(i + 1) * R + r] -= lki * Y[(k + 1) * R + r];
-        }
-        __syncthreads();
-    }
-    // pinned DOF 0, then the projection onto int_K eta = 0
-    for (int r = tid; r < R; r += nthr) Y[r] = 0.0;
-    __syncthreads();
-    for (int r = warp; r < R; r += nwarp) {
-        double s = 0.0;
-        for (int w = lane; w < n; w += 32) s += mass[w] * Y[w * R + r];
-        s = warp_sum(s);
-        if (lane == 0) red[r] = s / volK;
-    }
-    __syncthreads();
-    for (int it = tid; it < n * R; it += nthr) Y[it] -= red[it % R];
-    __syncthreads();
-
-    // ---- face integrals T[j][r] = (s psi_j, eta_r)_{dK} (the factor's storage reused)
-    double* Tf = Lp;
-    for (int it = tid; it < NI * R; it += nthr) {
-        const int j = it / R, r = it % R, a = j / m, q = j % m;
-        const int p = g.perm[4 * K + a];
-        const int base = (a * 6 + p) * (m + 1) + q;
-        double s = 0.0;
-        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) s += g.ftab_cnt[e] * Y[g.ftab_node[e] * R + r];
-        Tf[it] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * s;
-    }
-    __syncthreads();
+    // ---- face integrals by the Gram form.  With Y = L^{-1} g~ over the pinned rows,
+    // (s psi_j, eta_i)_{dK} = -N_j^T eta_i = -N~_j^T z_i = -Y_j . Y_i: the zero-mean shift of
+    // eta_i cancels against the compatibility projection of N_j (N~_j^T 1 = 0), and z_i
+    // vanishes on the pinned DOF.  Likewise -(s psi_j, eta_f)_{dK} = Y_j . y_f.  No backward
+    // substitution is needed.
     double* AK = g.AK + K * (int64_t)NI * NI;
-    for (int it = tid; it < NI * NI; it += nthr) {
-        const int j = it / NI, i = it % NI;
-        AK[it] = 0.5 * (Tf[j * R + i] + Tf[i * R + j]);
+    for (int it = tid; it < NI * R; it += nthr) {
+        const int j = it / R, i = it % R;
+        if (i < NI && i > j) continue;   // each pair once; the E_K column i = NI for every j
+        double s = 0.0;
+        for (int w = 1; w < n; ++w) s += Y[w * R + j] * Y[w * R + i];
+        if (i == NI) {
+            g.EK[K * NI + j] = s;
+        } else {
+            AK[j * NI + i] = -s;
+            AK[i * NI + j] = -s;
+        }
     }
-    for (int j = tid; j < NI; j += nthr) {
+    for (int j = tid; j < NI; j += nthr) {   // B_K[j] = (s psi_j, 1) = s |subface j|
         const int a = j / m, q = j % m;
         const int p = g.perm[4 * K + a];
         const int base = (a * 6 + p) * (m + 1) + q;
         int c = 0;
         for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) c += g.ftab_cnt[e];
-        g.EK[K * NI + j] = -Tf[j * R + NI];
         g.BK[K * NI + j] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * c;
     }
     if (tid == 0) {
