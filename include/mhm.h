@@ -145,9 +145,10 @@ typedef struct {
     int32_t no_fallback;  /* MIXED: 0 (default): elements whose refinement fails (not
                            * converged in it_max passes, FP32 pivot breakdown) are solved
                            * again by the FP64 path, their iters entry set to -1;
-                           * 1: they keep their failure status.  MIXED runs P1
-                           * levels wider than 32 points (r >= 6) and P2 levels of
-                           * r >= 5 on the FP64 path. */
+                           * 1: they keep their failure status.  MIXED runs P2
+                           * levels of r >= 5 on the FP64 path, and P1 levels of
+                           * r = 6, 7 on the wide mixed path (FP32-preconditioned
+                           * FP64 conjugate gradients, see mhm_local_solve_batch). */
     /* MIXED, P1 levels of at most 32 points and P2 levels of r <= 4: keep the local
      * factorisations across calls
      * (the paper factors each local matrix once and reuses it while kappa does not change,
