@@ -110,27 +110,49 @@ typedef struct {
     double freq;
 } mhm3d_source;
 
-/* solveLocalProblem for the elements K0 <= K < K1 (K1 <= 0: n_K), in FP64
- * (Sec. 3, Eqs. "etaf", "etai"): the stiffness a(u,w)_K = (kappa grad u,
- * grad w)_K assembled on the submesh from one element matrix per class of
- * congruent sub-tetrahedra, the loads N_i = -(s psi_i, phi_w)_{dK} and
- * (f, phi_w)_K (a collapsed 4x4x4 Gauss rule per sub-tetrahedron for the
- * non-constant f), the compatibility projection, a Cholesky factorisation
- * with local DOF 0 pinned and the forward substitution of the N_I + 1
- * right-hand sides; the face integrals of the zero-mean solutions follow in
- * Gram form, (s psi_j, eta_i)_{dK} = -Y_j . Y_i with Y = L^{-1} times the
- * projected loads.  Outputs (device, caller-owned, indexed by K):
+/* Options of mhm3d_local_solve_batch (NULL: the defaults in brackets). */
+typedef struct {
+    int32_t it_max;       /* MIXED: refinement passes, >= 1 [8] */
+    double tol;           /* MIXED: a column is done when |S r| <= tol |S g~| (S = diag^-1/2 of
+                             the pinned matrix, r = g~ - A z its FP64 residual) [1e-9] */
+    int32_t no_fallback;  /* MIXED: 0 [default]: elements whose FP32 factor breaks down or whose
+                             refinement does not converge are solved again in FP64 (iters -1);
+                             1: they keep MHM_ERR_NOT_CONVERGED */
+} mhm3d_opts;
+
+/* solveLocalProblem for the elements K0 <= K < K1 (K1 <= 0: n_K) (Sec. 3, Eqs.
+ * "etaf", "etai"): the stiffness a(u,w)_K = (kappa grad u, grad w)_K assembled on
+ * the submesh from one element matrix per class of congruent sub-tetrahedra, the
+ * loads N_i = -(s psi_i, phi_w)_{dK} and (f, phi_w)_K (a collapsed 4x4x4 Gauss
+ * rule per sub-tetrahedron for the non-constant f), the compatibility
+ * projection, and the face integrals of the zero-mean solutions.
+ *   MHM_FP64: a Cholesky factorisation with local DOF 0 pinned and the forward
+ *     substitution of the N_I + 1 right-hand sides, the face integrals in Gram
+ *     form (s psi_j, eta_i)_{dK} = -Y_j . Y_i with Y = L^{-1} times the
+ *     projected loads.
+ *   MHM_MIXED (N_I <= 16, i.e. m <= 4; larger m runs MHM_FP64): the pinned
+ *     matrix scaled by its diagonal is factored once in FP32 (Sec. 3: factor once,
+ *     then only products with the factor), the solutions are refined in FP64
+ *     against the matrix-free FP64 residual, and the face integrals use the
+ *     corrected bilinear form -(g~_j . z_i + z_j . r_i), second order in the
+ *     solution error.
+ * Outputs (device, caller-owned, indexed by K):
  *   AK_dev[K][j][i] = (s psi_j, eta_i)_{dK}  (N_I x N_I, symmetric)
  *   EK_dev[K][j]    = -(s psi_j, eta_f)_{dK}
  *   BK_dev[K][j]    = (s psi_j, 1)_{dK}
  *   FK_dev[K]       = (f, 1)_K
- *   status_dev[K]   = 0, or MHM_ERR_INVALID_ARG for a non-positive pivot.
+ *   status_dev[K]   = 0, MHM_ERR_INVALID_ARG (FP64: non-positive pivot), or
+ *                     MHM_ERR_NOT_CONVERGED (MIXED with no_fallback: FP32 breakdown or
+ *                     it_max passes without convergence)
+ *   iters_dev[K]    = refinement passes (1 for FP64; -1: solved again in FP64 after
+ *                     the mixed refinement failed); may be NULL.
  * kappa_dev: 8^r values per K (sub-tetrahedron order above), > 0.
- * Errors: INVALID_ARG (NULL pointers, range, source kind), UNSUPPORTED
- * (host-only mesh), CUDA (launch). */
+ * Errors: INVALID_ARG (NULL pointers, range, source kind, precision, options),
+ * UNSUPPORTED (host-only mesh), CUDA (launch). */
 mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* mesh, const double* kappa_dev, const mhm3d_source* f,
-                                   int64_t K0, int64_t K1, double* AK_dev, double* EK_dev, double* BK_dev,
-                                   double* FK_dev, int32_t* status_dev, void* stream);
+                                   int32_t precision, const mhm3d_opts* opts, int64_t K0, int64_t K1,
+                                   double* AK_dev, double* EK_dev, double* BK_dev, double* FK_dev,
+                                   int32_t* status_dev, int32_t* iters_dev, void* stream);
 
 /* reduceLocalProblems' gather (Eq. "mat_global"): A_vals_dev[nnz] of the
  * skeleton matrix A_ij = sum_K (s psi_j, eta_i)_{dK} on the CSR pattern of

@@ -48,6 +48,10 @@ struct Local3DArgs {
     double* BK;
     double* FK;
     int32_t* status;
+    int32_t* iters;       // may be NULL
+    int only_failed;      // FP64 kernel: solve only the elements whose status is nonzero (iters -1)
+    int it_max;           // mixed kernel: refinement passes
+    double tol;           // mixed kernel: scaled residual target per column
 };
 
 __constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
@@ -61,7 +65,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// shared-memory layout (doubles), in this order
+__device__ __forceinline__ float warp_sumf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// shared-memory layout of the FP64 kernel (doubles), in this order
 struct Smem3 {
     int T, Y, mass, S6, G6, J6, red, misc, total;
 };
@@ -77,30 +86,47 @@ __host__ __device__ inline Smem3 smem_layout(int n, int NI, int nb) {
     s.G6 = o;   o += 6 * 12;                        // barycentric gradients per class
     s.J6 = o;   o += 6 * 9;                         // edge vectors per class (columns)
     s.red = o;  o += R;
-    s.misc = o; o += 16;                            // |K|, |face a| / N^2 (4), V_sub, F_K, pivot flag
+    s.misc = o; o += 16;                            // |K|, |face a| / N^2 (4), V_sub, F_K, pivot flag, done flag
     s.total = o;
     return s;
 }
 
-__global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
-    extern __shared__ double sm[];
-    const Smem3 L = smem_layout(g.n, g.NI, g.nb);
-    double* Lp = sm + L.T;
-    double* Y = sm + L.Y;
-    double* mass = sm + L.mass;
-    double* S6 = sm + L.S6;
-    double* G6 = sm + L.G6;
-    double* J6 = sm + L.J6;
-    double* red = sm + L.red;
-    double* misc = sm + L.misc;
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-    const int64_t K = g.K0 + blockIdx.x;
-    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI, nb = g.nb, m = g.m, N = g.N;
-    const double* V = g.geom + 12 * K;   // v0..v3
-    const double* kap = g.kappa + K * (int64_t)g.nsub;
+// shared-memory layout of the mixed kernel (doubles; the FP32 factor and solve vectors
+// take half a double per value)
+struct Smem3M {
+    int Lf, G, Z, Rr, W, sc, dg, invf, mass, S6, G6, J6, red, gn, misc, total;
+};
 
-    // ---- zero the factor, right-hand sides and mass; geometry scalars
-    for (int i = tid; i < L.S6; i += nthr) sm[i] = 0.0;
+__host__ __device__ inline Smem3M smem_layout_mixed(int n, int NI, int nb) {
+    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2;
+    Smem3M s{};
+    int o = 0;
+    s.Lf = o;   o += (npk + 1) / 2;                 // FP32 factor of the scaled pinned matrix
+    s.G = o;    o += n * R;                         // projected loads g~ (FP64)
+    s.Z = o;    o += n * R;                         // solutions (FP64)
+    s.Rr = o;   o += n * R;                         // residuals g~ - A z (FP64)
+    s.W = o;    o += (n1 * R + 1) / 2;              // FP32 preconditioner solves
+    s.sc = o;   o += n1;                            // 1 / sqrt(diag) of the pinned matrix
+    s.dg = o;   o += n;                             // FP64 diagonal
+    s.invf = o; o += (n1 + 1) / 2;                  // FP32 1 / L_kk
+    s.mass = o; o += n;
+    s.S6 = o;   o += 6 * nb * nb;
+    s.G6 = o;   o += 6 * 12;
+    s.J6 = o;   o += 6 * 9;
+    s.red = o;  o += R;
+    s.gn = o;   o += R;                             // |S g~|^2 per column
+    s.misc = o; o += 16;
+    s.total = o;
+    return s;
+}
+
+// Geometry of element K into shared memory: misc[0] = |K|, misc[1 + a] = |face a| / N^2,
+// misc[5] = |sub-tetrahedron|, misc[6] = F_K accumulator, misc[7] = failure flag,
+// misc[8] = done flag; per class c: edge vectors J6[9c + 3 comp + v] and the gradients of
+// the four barycentrics G6[12c + 3 l + comp].  No barrier.
+__device__ __forceinline__ void element_geometry(const Local3DArgs& g, const double* V, double* misc, double* G6,
+                                                 double* J6) {
+    const int tid = threadIdx.x, N = g.N;
     if (tid == 0) {
         double e[3][3];
         for (int c = 0; c < 3; ++c)
@@ -112,6 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         misc[5] = misc[0] / ((double)N * N * N);
         misc[6] = 0.0;
         misc[7] = 0.0;
+        misc[8] = 0.0;
     }
     if (tid < 4) {   // area of local face a over N^2
         int b[3], k = 0;
@@ -158,11 +185,13 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
             G[c] = -(Ji[0][c] + Ji[1][c] + Ji[2][c]);
         }
     }
-    __syncthreads();
+}
 
-    // ---- element matrix of each class (closed forms; Vs the common volume)
-    const double Vs = misc[5];
-    for (int it = tid; it < 6 * nb * nb; it += nthr) {
+// Element matrix of each class from the closed forms in the barycentric gradients
+// (Vs the common volume of the sub-tetrahedra).  No barrier.
+__device__ __forceinline__ void class_matrices(const Local3DArgs& g, double Vs, const double* G6, double* S6) {
+    const int nb = g.nb;
+    for (int it = threadIdx.x; it < 6 * nb * nb; it += blockDim.x) {
         const int c = it / (nb * nb), a = (it / nb) % nb, b = it % nb;
         const double* G = G6 + c * 12;
         auto d = [&](int i, int j) { return G[3 * i] * G[3 * j] + G[3 * i + 1] * G[3 * j + 1] + G[3 * i + 2] * G[3 * j + 2]; };
@@ -183,21 +212,22 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         }
         S6[it] = v;
     }
-    __syncthreads();
+}
 
-    // ---- assembly (pinned DOF 0 dropped, lower triangle), mass vector
-    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
-        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
-        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
-        if (da == 0 || db == 0 || da < db) continue;
-        atomicAdd(&Lp[pk(da - 1, db - 1)], kap[t] * S6[g.sub_cls[t] * nb * nb + ab]);
-    }
+// The mass vector, the multiplier loads -s |fine face| / 3 per load node and fine face
+// triangle (columns a m + q of Y, n x R), and a sin sin sin source by the collapsed Gauss
+// rule of every sub-tetrahedron (column N_I, F_K into misc[6]).  Y and mass zeroed by the
+// caller.  No barrier.
+__device__ __forceinline__ void element_loads(const Local3DArgs& g, int64_t K, const double* V, double* Y,
+                                              double* mass, const double* J6, double* misc) {
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    const int nb = g.nb, m = g.m, R = g.R, NI = g.NI, N = g.N;
+    const double Vs = misc[5];
     for (int it = tid; it < g.nsub * nb; it += nthr) {
         const int a = it % nb;
         const double c = g.P == 1 ? 0.25 : (a < 4 ? -0.05 : 0.2);
         atomicAdd(&mass[g.sub_dofs[it]], c * Vs);
     }
-    // multiplier loads: column a m + q, -s |fine face| / 3 per load node and fine triangle
     for (int it = tid; it < 4 * m; it += nthr) {
         const int a = it / m, q = it % m;
         const int p = g.perm[4 * K + a];
@@ -206,7 +236,6 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e)
             Y[g.ftab_node[e] * R + it] = w * g.ftab_cnt[e];
     }
-    // source load (f, phi_w)_K: sin sin sin by the collapsed Gauss rule of every sub-tetrahedron
     if (g.src_kind == MHM3D_SRC_SINSINSIN) {
         const double* qp = g.quad;
         const double* qphi = g.quad + 4 * kQuad;
@@ -236,14 +265,19 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         fk = warp_sum(fk);
         if (lane == 0) atomicAdd(&misc[6], fk);
     }
-    __syncthreads();
+}
+
+// After the loads' barrier: a constant source, then the compatibility projection
+// g - (1^T g / |K|) m of every column.  Ends with a barrier.
+__device__ __forceinline__ void const_source_and_projection(const Local3DArgs& g, double* Y, const double* mass,
+                                                            double* red, double* misc) {
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int n = g.n, R = g.R, NI = g.NI;
     if (g.src_kind == MHM3D_SRC_CONST) {
         for (int w = tid; w < n; w += nthr) Y[w * R + NI] = g.src_value * mass[w];
         if (tid == 0) misc[6] = g.src_value * misc[0];
         __syncthreads();
     }
-
-    // ---- compatibility projection g - (1^T g / |K|) m
     const double volK = misc[0];
     for (int r = warp; r < R; r += nwarp) {
         double s = 0.0;
@@ -254,6 +288,62 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     __syncthreads();
     for (int it = tid; it < n * R; it += nthr) Y[it] -= red[it % R] * mass[it / R];
     __syncthreads();
+}
+
+// B_K[j] = (s psi_j, 1)_{dK} = s |subface j| from the face-load table, F_K, status.
+__device__ __forceinline__ void element_tail(const Local3DArgs& g, int64_t K, const double* misc, int32_t code,
+                                            int32_t iters) {
+    const int m = g.m, NI = g.NI;
+    for (int j = threadIdx.x; j < NI; j += blockDim.x) {
+        const int a = j / m, q = j % m;
+        const int p = g.perm[4 * K + a];
+        const int base = (a * 6 + p) * (m + 1) + q;
+        int c = 0;
+        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) c += g.ftab_cnt[e];
+        g.BK[K * NI + j] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * c;
+    }
+    if (threadIdx.x == 0) {
+        g.FK[K] = misc[6];
+        g.status[K] = code;
+        if (g.iters) g.iters[K] = iters;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
+    extern __shared__ double sm[];
+    const Smem3 L = smem_layout(g.n, g.NI, g.nb);
+    double* Lp = sm + L.T;
+    double* Y = sm + L.Y;
+    double* mass = sm + L.mass;
+    double* S6 = sm + L.S6;
+    double* G6 = sm + L.G6;
+    double* J6 = sm + L.J6;
+    double* red = sm + L.red;
+    double* misc = sm + L.misc;
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, nwarp = nthr >> 5, lane = tid & 31;
+    const int64_t K = g.K0 + blockIdx.x;
+    if (g.only_failed && g.status[K] == MHM_OK) return;   // the whole block, before any barrier
+    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI, nb = g.nb;
+    const double* V = g.geom + 12 * K;   // v0..v3
+    const double* kap = g.kappa + K * (int64_t)g.nsub;
+
+    // ---- zero the factor, right-hand sides and mass; geometry; class matrices
+    for (int i = tid; i < L.S6; i += nthr) sm[i] = 0.0;
+    element_geometry(g, V, misc, G6, J6);
+    __syncthreads();
+    class_matrices(g, misc[5], G6, S6);
+    __syncthreads();
+
+    // ---- assembly (pinned DOF 0 dropped, lower triangle), loads
+    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
+        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
+        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
+        if (da == 0 || db == 0 || da < db) continue;
+        atomicAdd(&Lp[pk(da - 1, db - 1)], kap[t] * S6[g.sub_cls[t] * nb * nb + ab]);
+    }
+    element_loads(g, K, V, Y, mass, J6, misc);
+    __syncthreads();
+    const_source_and_projection(g, Y, mass, red, misc);
 
     // ---- Cholesky of the pinned matrix (rows 1..n-1), forward substitution fused
     for (int k = 0; k < n1; ++k) {
@@ -292,18 +382,192 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
             AK[i * NI + j] = -s;
         }
     }
-    for (int j = tid; j < NI; j += nthr) {   // B_K[j] = (s psi_j, 1) = s |subface j|
-        const int a = j / m, q = j % m;
-        const int p = g.perm[4 * K + a];
-        const int base = (a * 6 + p) * (m + 1) + q;
-        int c = 0;
-        for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e) c += g.ftab_cnt[e];
-        g.BK[K * NI + j] = (double)g.signs[4 * K + a] * misc[1 + a] / 3.0 * c;
+    element_tail(g, K, misc, misc[7] != 0.0 ? MHM_ERR_INVALID_ARG : MHM_OK, g.only_failed ? -1 : 1);
+}
+
+// Mixed precision (Sec. 3: the local matrix is factored once and each further solve is
+// only products with the factor): the pinned matrix, scaled by its diagonal, is factored
+// in FP32 (Cholesky, shared memory); the N_I + 1 solutions are refined in FP64 against
+// the matrix-free FP64 residual r = g~ - A z (element matrices of the six classes times
+// kappa), each pass one FP32 forward and backward substitution per column (a warp per
+// column), until every column's scaled residual |S r| <= tol |S g~| or it_max passes.  The
+// face integrals use the corrected bilinear form
+//   (s psi_j, eta_i)_{dK} = -(g~_j . z_i + z_j . r_i),
+// whose error is the product of the two solution errors in the energy norm (second order),
+// averaged with its transpose.  An element whose FP32 factor breaks down or that does not
+// converge gets MHM_ERR_NOT_CONVERGED (the host then re-solves it in FP64 unless asked not to).
+__global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
+    extern __shared__ double sm[];
+    const Smem3M L = smem_layout_mixed(g.n, g.NI, g.nb);
+    float* Lf = reinterpret_cast<float*>(sm + L.Lf);
+    double* G = sm + L.G;
+    double* Z = sm + L.Z;
+    double* Rr = sm + L.Rr;
+    float* W = reinterpret_cast<float*>(sm + L.W);
+    double* sc = sm + L.sc;
+    double* dg = sm + L.dg;
+    float* invf = reinterpret_cast<float*>(sm + L.invf);
+    double* mass = sm + L.mass;
+    double* S6 = sm + L.S6;
+    double* G6 = sm + L.G6;
+    double* J6 = sm + L.J6;
+    double* red = sm + L.red;
+    double* gn = sm + L.gn;
+    double* misc = sm + L.misc;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int64_t K = g.K0 + blockIdx.x;
+    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI, nb = g.nb, npk = n1 * (n1 + 1) / 2;
+    const double* V = g.geom + 12 * K;
+    const double* kap = g.kappa + K * (int64_t)g.nsub;
+
+    // ---- zero the factor, loads, solutions, residuals, diagonal and mass; geometry; classes
+    for (int i = tid; i < L.sc; i += nthr) sm[i] = 0.0;
+    for (int i = L.dg + tid; i < L.invf; i += nthr) sm[i] = 0.0;
+    for (int i = L.mass + tid; i < L.S6; i += nthr) sm[i] = 0.0;
+    element_geometry(g, V, misc, G6, J6);
+    __syncthreads();
+    class_matrices(g, misc[5], G6, S6);
+    __syncthreads();
+
+    // ---- FP32 assembly of the pinned lower triangle, its FP64 diagonal, loads
+    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
+        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
+        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
+        if (da == 0 || db == 0 || da < db) continue;
+        const double v = kap[t] * S6[g.sub_cls[t] * nb * nb + ab];
+        atomicAdd(&Lf[pk(da - 1, db - 1)], (float)v);
+        if (da == db) atomicAdd(&dg[da], v);
     }
-    if (tid == 0) {
-        g.FK[K] = misc[6];
-        g.status[K] = misc[7] != 0.0 ? MHM_ERR_INVALID_ARG : MHM_OK;
+    element_loads(g, K, V, G, mass, J6, misc);
+    __syncthreads();
+    const_source_and_projection(g, G, mass, red, misc);
+
+    // ---- diagonal scaling S A S (S = diag^-1/2), then the FP32 Cholesky
+    for (int i = tid; i < n1; i += nthr) {
+        const double d = dg[i + 1];
+        if (!(d > 0.0)) misc[7] = 1.0;
+        sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
     }
+    __syncthreads();
+    for (int it = tid; it < npk; it += nthr) {
+        int i = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);   // row of packed entry it
+        while (i * (i + 1) / 2 > it) --i;
+        while ((i + 1) * (i + 2) / 2 <= it) ++i;
+        const int j = it - i * (i + 1) / 2;
+        Lf[it] = (float)((double)Lf[it] * sc[i] * sc[j]);
+    }
+    __syncthreads();
+    for (int k = 0; k < n1; ++k) {
+        float d = Lf[pk(k, k)];
+        if (!(d > 0.0f)) {
+            d = 1.0f;
+            if (tid == 0) misc[7] = 1.0;
+        }
+        const float inv = 1.0f / sqrtf(d);
+        for (int i = k + 1 + tid; i < n1; i += nthr) Lf[pk(i, k)] *= inv;
+        if (tid == 0) invf[k] = inv;
+        __syncthreads();
+        for (int i = k + 1 + warp; i < n1; i += nwarp) {
+            const float lik = Lf[pk(i, k)];
+            float* row = Lf + pk(i, 0);
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * Lf[pk(j, k)];
+        }
+        __syncthreads();
+    }
+
+    // ---- FP64 refinement: z = 0, r = g~; |S g~|^2 per column
+    for (int it = tid; it < n * R; it += nthr) Rr[it] = it < R ? 0.0 : G[it];
+    for (int c = warp; c < R; c += nwarp) {
+        double s = 0.0;
+        for (int i = lane; i < n1; i += 32) s += (sc[i] * G[(i + 1) * R + c]) * (sc[i] * G[(i + 1) * R + c]);
+        s = warp_sum(s);
+        if (lane == 0) gn[c] = s;
+    }
+    __syncthreads();
+    int passes = 0;
+    const double tol2 = g.tol * g.tol;
+    for (int pass = 0; pass < g.it_max && misc[7] == 0.0; ++pass) {
+        // w = S r (FP32), then L^-1 and L^-T by a warp per column
+        for (int it = tid; it < n1 * R; it += nthr) {
+            const int i = it / R, c = it % R;
+            W[it] = (float)(sc[i] * Rr[(i + 1) * R + c]);
+        }
+        __syncthreads();
+        for (int c = warp; c < R; c += nwarp) {
+            for (int k = 0; k < n1; ++k) {
+                const float xk = W[k * R + c] * invf[k];
+                __syncwarp();
+                for (int i = k + 1 + lane; i < n1; i += 32) W[i * R + c] -= Lf[pk(i, k)] * xk;
+                if (lane == 0) W[k * R + c] = xk;
+                __syncwarp();
+            }
+            for (int k = n1 - 1; k >= 0; --k) {
+                float s = 0.0f;
+                for (int i = k + 1 + lane; i < n1; i += 32) s += Lf[pk(i, k)] * W[i * R + c];
+                s = warp_sumf(s);
+                const float xk = (W[k * R + c] - s) * invf[k];
+                __syncwarp();
+                if (lane == 0) W[k * R + c] = xk;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // z += S w; r = g~ on the pinned rows, then r -= A z element by element
+        for (int it = tid; it < n1 * R; it += nthr) {
+            const int i = it / R, c = it % R;
+            Z[(i + 1) * R + c] += sc[i] * (double)W[it];
+            Rr[(i + 1) * R + c] = G[(i + 1) * R + c];
+        }
+        __syncthreads();
+        for (int it = tid; it < g.nsub * nb * R; it += nthr) {
+            const int t = it / (nb * R), a = (it / R) % nb, c = it % R;
+            const int da = g.sub_dofs[t * nb + a];
+            if (da == 0) continue;
+            const double* Sa = S6 + (g.sub_cls[t] * nb + a) * nb;
+            double s = 0.0;
+            for (int b = 0; b < nb; ++b) s += Sa[b] * Z[g.sub_dofs[t * nb + b] * R + c];
+            atomicAdd(&Rr[da * R + c], -kap[t] * s);
+        }
+        __syncthreads();
+        // converged when every column's |S r|^2 <= tol^2 |S g~|^2
+        for (int c = warp; c < R; c += nwarp) {
+            double s = 0.0;
+            for (int i = lane; i < n1; i += 32) s += (sc[i] * Rr[(i + 1) * R + c]) * (sc[i] * Rr[(i + 1) * R + c]);
+            s = warp_sum(s);
+            if (lane == 0) red[c] = s;
+        }
+        __syncthreads();
+        passes = pass + 1;
+        bool done = true;
+        for (int c = 0; c < R; ++c) done = done && red[c] <= tol2 * gn[c];
+        if (done) break;   // the same decision in every thread (read after the barrier)
+        __syncthreads();   // red is rewritten in the next pass
+    }
+    const bool converged = misc[7] == 0.0 && passes > 0 && [&] {
+        bool ok = true;
+        for (int c = 0; c < R; ++c) ok = ok && red[c] <= tol2 * gn[c];
+        return ok;
+    }();
+
+    // ---- corrected face integrals T_ji = -(g~_j . z_i + z_j . r_i), averaged with T_ij
+    double* AK = g.AK + K * (int64_t)NI * NI;
+    for (int it = tid; it < NI * R; it += nthr) {
+        const int j = it / R, i = it % R;
+        if (i < NI && i > j) continue;
+        double a1 = 0.0, a2 = 0.0;
+        for (int w = 1; w < n; ++w) {
+            a1 += G[w * R + j] * Z[w * R + i] + Z[w * R + j] * Rr[w * R + i];
+            a2 += G[w * R + i] * Z[w * R + j] + Z[w * R + i] * Rr[w * R + j];
+        }
+        const double v = 0.5 * (a1 + a2);
+        if (i == NI) {
+            g.EK[K * NI + j] = v;
+        } else {
+            AK[j * NI + i] = -v;
+            AK[i * NI + j] = -v;
+        }
+    }
+    element_tail(g, K, misc, converged ? MHM_OK : MHM_ERR_NOT_CONVERGED, passes);
 }
 
 // skeleton values: one thread per entry of a neighbour block
@@ -355,6 +619,9 @@ void free_device(mhm_mesh3d* m) {
 }  // namespace
 
 size_t local3d_smem(int n, int NI, int nb) { return (size_t)smem_layout(n, NI, nb).total * sizeof(double); }
+size_t local3d_smem_mixed(int n, int NI, int nb) {
+    return (size_t)smem_layout_mixed(n, NI, nb).total * sizeof(double);
+}
 
 }  // namespace mhm3
 
@@ -421,13 +688,6 @@ extern "C" mhm_status mhm3d_create_mesh(const mhm3d_mesh_desc* desc, int32_t dev
             delete m;
             return st;
         }
-        ce = cudaFuncSetAttribute(k_local3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)local3d_smem((int)m->n, (int)m->NI, m->nb));
-        if (ce != cudaSuccess) {
-            free_device(m);
-            delete m;
-            return mhm::cuda_fail(ce, "cudaFuncSetAttribute(k_local3d)");
-        }
     }
     *out = m;
     return MHM_OK;
@@ -474,14 +734,21 @@ extern "C" mhm_status mhm3d_mesh_query(const mhm3d_mesh* m, int32_t what, void* 
 }
 
 extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double* kappa, const mhm3d_source* f,
-                                              int64_t K0, int64_t K1, double* AK, double* EK, double* BK,
-                                              double* FK, int32_t* status, void* stream) {
+                                              int32_t precision, const mhm3d_opts* opts, int64_t K0, int64_t K1,
+                                              double* AK, double* EK, double* BK, double* FK, int32_t* status,
+                                              int32_t* iters, void* stream) {
     if (!m) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL mesh");
     if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_local_solve_batch: host-only mesh");
     if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL pointer argument");
     if (f->kind != MHM3D_SRC_CONST && f->kind != MHM3D_SRC_SINSINSIN)
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: unknown source kind");
+    if (precision != MHM_FP64 && precision != MHM_MIXED)
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: precision must be MHM_FP64 or MHM_MIXED");
+    mhm3d_opts o{8, 1e-9, 0};
+    if (opts) o = *opts;
+    if (o.it_max < 1 || !(o.tol > 0.0))
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: it_max >= 1 and tol > 0 required");
     if (K1 <= 0) K1 = m->nK;
     if (K0 < 0 || K1 > m->nK || K0 > K1) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: K range");
     if (K1 == K0) return MHM_OK;
@@ -495,11 +762,23 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
     g.K0 = K0;
     g.N = m->N, g.P = m->desc.degree, g.n = (int)m->n, g.nb = m->nb, g.nsub = (int)m->nsub, g.m = m->desc.m;
     g.NI = (int)m->NI, g.R = (int)m->NI + 1;
-    g.AK = AK, g.EK = EK, g.BK = BK, g.FK = FK, g.status = status;
-    const size_t smem = local3d_smem(g.n, g.NI, g.nb);
-    // the attribute is per kernel, not per mesh: set it for this mesh's size every call
-    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_local3d<<<(unsigned)(K1 - K0), kThreads, smem, (cudaStream_t)stream>>>(g);
+    g.AK = AK, g.EK = EK, g.BK = BK, g.FK = FK, g.status = status, g.iters = iters;
+    g.it_max = o.it_max, g.tol = o.tol;
+    const unsigned grid = (unsigned)(K1 - K0);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the shared-memory attribute is per kernel, not per mesh: set it for this mesh every call
+    const size_t smem64 = local3d_smem(g.n, g.NI, g.nb);
+    const size_t smemmx = local3d_smem_mixed(g.n, g.NI, g.nb);
+    const bool mixed = precision == MHM_MIXED && smemmx <= 227 * 1024;
+    if (mixed) {
+        MHM_CUDA_TRY(cudaFuncSetAttribute(k_local3d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemmx));
+        k_local3d_mixed<<<grid, kThreads, smemmx, s>>>(g);
+        MHM_CUDA_TRY(cudaGetLastError());
+        if (o.no_fallback) return MHM_OK;
+        g.only_failed = 1;   // the elements the refinement could not finish, again in FP64
+    }
+    MHM_CUDA_TRY(cudaFuncSetAttribute(k_local3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
+    k_local3d<<<grid, kThreads, smem64, s>>>(g);
     MHM_CUDA_TRY(cudaGetLastError());
     return MHM_OK;
 }

@@ -29,8 +29,9 @@ struct Nbr3 {
     int32_t K1, a1, b1;   // K1 = -1: one contribution
 };
 
-// shared memory bytes of one local-solve block
+// shared memory bytes of one local-solve block (FP64 and mixed kernels)
 size_t local3d_smem(int n, int NI, int nb);
+size_t local3d_smem_mixed(int n, int NI, int nb);
 
 // rule on [0,1] (Newton on the Legendre polynomial)
 void gauss01(int n, double* x, double* w);

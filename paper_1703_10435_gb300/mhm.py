@@ -360,13 +360,19 @@ class Source3D(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("value", ctypes.c_double), ("freq", ctypes.c_double)]
 
 
+class Opts3D(ctypes.Structure):
+    """mhm3d_opts: MIXED refinement passes, scaled residual target, no FP64 re-solve."""
+    _fields_ = [("it_max", ctypes.c_int32), ("tol", ctypes.c_double), ("no_fallback", ctypes.c_int32)]
+
+
 def _bind3d(L):
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     L.mhm3d_create_mesh.argtypes = [ctypes.POINTER(Mesh3DDesc), i32, ctypes.POINTER(vp)]
     L.mhm3d_destroy_mesh.argtypes = [vp]
     L.mhm3d_destroy_mesh.restype = None
     L.mhm3d_mesh_query.argtypes = [vp, i32, vp, sz]
-    L.mhm3d_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source3D), i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mhm3d_local_solve_batch.argtypes = [vp, vp, ctypes.POINTER(Source3D), i32, ctypes.POINTER(Opts3D), i64, i64,
+                                          vp, vp, vp, vp, vp, vp, vp]
     L.mhm3d_assemble_skeleton.argtypes = [vp, vp, vp, vp, vp, vp]
     for name in ("mhm3d_create_mesh", "mhm3d_mesh_query", "mhm3d_local_solve_batch", "mhm3d_assemble_skeleton"):
         getattr(L, name).restype = i32
@@ -406,9 +412,10 @@ def mhm3d_create_mesh(nc, r, degree, m, device: int = 0) -> Mesh3D:
 
 
 def mhm3d_local_solve_batch(mesh: Mesh3D, kappa, source: Source3D, AK, EK, BK, FK, status, K0=0, K1=0,
-                            stream=None):
-    _check(lib().mhm3d_local_solve_batch(mesh.handle, _ptr(kappa), ctypes.byref(source), K0, K1, _ptr(AK),
-                                         _ptr(EK), _ptr(BK), _ptr(FK), _ptr(status), _stream(stream)))
+                            precision=MHM_FP64, opts: Opts3D | None = None, iters=None, stream=None):
+    _check(lib().mhm3d_local_solve_batch(mesh.handle, _ptr(kappa), ctypes.byref(source), precision,
+                                         None if opts is None else ctypes.byref(opts), K0, K1, _ptr(AK), _ptr(EK),
+                                         _ptr(BK), _ptr(FK), _ptr(status), _ptr(iters), _stream(stream)))
 
 
 def mhm3d_assemble_skeleton(mesh: Mesh3D, AK, EK, A_vals, E, stream=None):
