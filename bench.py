@@ -542,14 +542,23 @@ def local3d_flops(n, NI):
     return n1 ** 3 / 3.0 + n1 * n1 * (NI + 1.0) + 2.0 * n1 * (NI * (NI + 1) / 2.0 + NI)
 
 
+def local3d_mixed_fp64_flops(n, NI, n_sub, nb, passes):
+    """FP64 flops of one mixed 3-D local solve: per refinement pass the matrix-free
+    residual (n_sub nb^2 R multiply-adds), and the corrected face integrals (four dot
+    products of length n - 1 per pair (j <= i) and per E_K entry)."""
+    R = NI + 1
+    return 2.0 * passes * n_sub * nb * nb * R + 8.0 * (n - 1) * (NI * (NI + 1) / 2.0 + NI)
+
+
 def run_three_d(dev, flush, peak64, steps=5, warmup=3, n_check=2):
     """The paper's three-dimensional experiment (Sec. 5: kappa = 1, f = 12 pi^2 sin sin sin
     on the unit cube; 24 nc^3 coarse tetrahedra with 8^r sub-tetrahedra, k = 2, l = 0
-    multipliers on m subfaces): FP64 local solves + skeleton gather per step, CUDA events
-    on the launching stream, L2 flushed between steps, and a few elements against the
-    oracle."""
+    multipliers on m subfaces): local solves + skeleton gather per step in FP64 and (m <= 4)
+    mixed precision, CUDA events on the launching stream, L2 flushed between steps, and a
+    few elements of each path against the oracle."""
     import torch
     from paper_1703_10435_gb300 import mhm
+    from oracle import tet3d as T
     stream = torch.cuda.current_stream()
     out = []
     for nc, r, P, m in THREE_D:
@@ -561,51 +570,75 @@ def run_three_d(dev, flush, peak64, steps=5, warmup=3, n_check=2):
         BK = torch.empty_like(EK)
         FK = torch.empty(M.n_K, dtype=torch.float64, device=dev)
         st = torch.empty(M.n_K, dtype=torch.int32, device=dev)
+        it = torch.empty(M.n_K, dtype=torch.int32, device=dev)
         vals = torch.empty(M.nnz, dtype=torch.float64, device=dev)
         E = torch.empty(M.n_lambda, dtype=torch.float64, device=dev)
-
-        def step():
-            mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st)
-            mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
-        for _ in range(warmup):
-            step()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for s in range(steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st)
-            ev[s][1].record(stream)
-            mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
-            ev[s][2].record(stream)
-        torch.cuda.synchronize()
-        t_step = sum(a.elapsed_time(c) for a, b, c in ev) / steps
-        t_local = sum(a.elapsed_time(b) for a, b, c in ev) / steps
-        assert int(st.abs().sum()) == 0, "3-D local solve status nonzero"
-        fl = local3d_flops(M.n_local, M.n_I) * M.n_K
-        # a few elements against the oracle (kappa = 1, the same source)
-        from oracle import tet3d as T
         o = T.build_mesh3d(nc, m)
         f = T.source3d_fn("sinsinsin", 1.0, 2.0)
-        err = 0.0
-        t0 = time.perf_counter()
-        for K in (0, M.n_K - 1)[:n_check]:
-            loc = T.solve_local3d(o, K, r, P, np.ones(M.n_sub), f)
-            d = np.sqrt(np.abs(np.diag(loc.AK)))
-            err = max(err, float((np.abs(AK[K].cpu().numpy() - loc.AK) / np.outer(d, d)).max()))
-        t_oracle = (time.perf_counter() - t0) / n_check
-        out.append({"workload": "cube_%dx%dx%d_tets%d_sub%d_k%d_m%d" % (nc, nc, nc, M.n_K, M.n_sub, P, m),
-                    "n_K": M.n_K, "local_dofs": M.n_local, "n_I": M.n_I, "lambda_unknowns": M.n_lambda,
-                    "value": M.n_K / (t_step * 1e-3), "unit": "coarse elements/s", "ms_per_step": t_step,
-                    "local_ms": t_local, "skeleton_ms": t_step - t_local, "dtype": "f64",
-                    "roofline": {"kernel": "k_local3d", "bound": "alu", "pipe": "fp64",
-                                 "flops_per_step": fl, "achieved": fl / (t_local * 1e-3) / 1e12, "peak": peak64,
-                                 "unit": "TFLOP/s", "frac": fl / (t_local * 1e-3) / 1e12 / peak64},
-                    "AK_gram_err_vs_oracle_%d_elements" % n_check: err,
-                    "cpu_oracle": {"value": 1.0 / t_oracle, "unit": "coarse elements/s", "cores": 1,
-                                   "kind": "oracle", "sample": "the %d checked elements, local solves" % n_check},
-                    "inputs": "kappa = 1, f = 12 pi^2 sin(2 pi x) sin(2 pi y) sin(2 pi z) (the paper's model problem)"})
+        nb = 4 if P == 1 else 10
+
+        def timed(precision):
+            def local():
+                mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st, precision=precision, iters=it)
+            for _ in range(warmup):
+                local()
+                mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                   torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for s_ in range(steps):
+                flush.zero_()
+                ev[s_][0].record(stream)
+                local()
+                ev[s_][1].record(stream)
+                mhm.mhm3d_assemble_skeleton(M, AK, EK, vals, E)
+                ev[s_][2].record(stream)
+            torch.cuda.synchronize()
+            assert int(st.abs().sum()) == 0, "3-D local solve status nonzero"
+            t_step = sum(a.elapsed_time(c) for a, b, c in ev) / steps
+            t_local = sum(a.elapsed_time(b) for a, b, c in ev) / steps
+            err = 0.0
+            t0 = time.perf_counter()
+            for K in (0, M.n_K - 1)[:n_check]:
+                loc = T.solve_local3d(o, K, r, P, np.ones(M.n_sub), f)
+                d = np.sqrt(np.abs(np.diag(loc.AK)))
+                err = max(err, float((np.abs(AK[K].cpu().numpy() - loc.AK) / np.outer(d, d)).max()))
+            t_or = (time.perf_counter() - t0) / n_check
+            itv = it.cpu().numpy()
+            return t_step, t_local, err, t_or, itv
+
+        t64, l64, e64, t_or, _ = timed(mhm.MHM_FP64)
+        fl64 = local3d_flops(M.n_local, M.n_I) * M.n_K
+        entry = {"workload": "cube_%dx%dx%d_tets%d_sub%d_k%d_m%d" % (nc, nc, nc, M.n_K, M.n_sub, P, m),
+                 "n_K": M.n_K, "local_dofs": M.n_local, "n_I": M.n_I, "lambda_unknowns": M.n_lambda,
+                 "unit": "coarse elements/s",
+                 "fp64": {"value": M.n_K / (t64 * 1e-3), "ms_per_step": t64, "local_ms": l64,
+                          "skeleton_ms": t64 - l64,
+                          "roofline": {"kernel": "k_local3d", "bound": "alu", "pipe": "fp64",
+                                       "flops_per_step": fl64, "achieved": fl64 / (l64 * 1e-3) / 1e12,
+                                       "peak": peak64, "unit": "TFLOP/s",
+                                       "frac": fl64 / (l64 * 1e-3) / 1e12 / peak64},
+                          "AK_gram_err_vs_oracle_%d_elements" % n_check: e64},
+                 "cpu_oracle": {"value": 1.0 / t_or, "unit": "coarse elements/s", "cores": 1, "kind": "oracle",
+                                "sample": "the %d checked elements, local solves" % n_check},
+                 "inputs": "kappa = 1, f = 12 pi^2 sin(2 pi x) sin(2 pi y) sin(2 pi z) (the paper's model problem)"}
+        entry["value"], entry["ms_per_step"], entry["dtype"] = entry["fp64"]["value"], t64, "f64"
+        if M.n_I <= 16:
+            tmx, lmx, emx, _, itv = timed(mhm.MHM_MIXED)
+            passes = float(itv[itv > 0].mean()) if np.any(itv > 0) else 0.0
+            flmx = local3d_mixed_fp64_flops(M.n_local, M.n_I, M.n_sub, nb, passes) * M.n_K
+            entry["mixed"] = {"value": M.n_K / (tmx * 1e-3), "ms_per_step": tmx, "local_ms": lmx,
+                              "skeleton_ms": tmx - lmx, "refinement_passes_mean": passes,
+                              "fp64_resolved_elements": int(np.sum(itv < 0)),
+                              "roofline": {"kernel": "k_local3d_mixed", "bound": "alu",
+                                           "pipe": "fp64 (residuals and corrected face integrals)",
+                                           "flops_per_step": flmx, "achieved": flmx / (lmx * 1e-3) / 1e12,
+                                           "peak": peak64, "unit": "TFLOP/s",
+                                           "frac": flmx / (lmx * 1e-3) / 1e12 / peak64},
+                              "AK_gram_err_vs_oracle_%d_elements" % n_check: emx}
+            entry["mixed_over_fp64"] = t64 / tmx
+            entry["value"], entry["ms_per_step"], entry["dtype"] = entry["mixed"]["value"], tmx, "f32+f64"
+        out.append(entry)
         del M
     return out
 
