@@ -34,6 +34,8 @@ struct Local3DArgs {
     const int32_t* sub_dofs;
     const int8_t* sub_cls;
     const int8_t* sub_base;
+    const int32_t* inc_off;   // per local DOF, its slots t nb + a (ascending)
+    const int32_t* inc_ent;
     const int32_t* ftab_off;
     const int16_t* ftab_node;
     const int8_t* ftab_cnt;
@@ -52,6 +54,7 @@ struct Local3DArgs {
     int only_failed;      // FP64 kernel: solve only the elements whose status is nonzero (iters -1)
     int it_max;           // mixed kernel: refinement passes
     double tol;           // mixed kernel: scaled residual target per column
+    int qs;               // the source's quadrature points of a sub-tetrahedron in qs groups of 64/qs
 };
 
 __constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
@@ -75,11 +78,15 @@ struct Smem3 {
     int T, Y, mass, S6, G6, J6, red, misc, total;
 };
 
-__host__ __device__ inline Smem3 smem_layout(int n, int NI, int nb) {
-    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2;
+// doubles of the source's partial loads: per group of quadrature points of every
+// sub-tetrahedron, its nb loads and its part of F_K
+__host__ __device__ inline int partial_loads(int nsub, int nb, int qs) { return qs * nsub * (nb + 1); }
+
+__host__ __device__ inline Smem3 smem_layout(int n, int NI, int nb, int nsub, int qs) {
+    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2, pl = partial_loads(nsub, nb, qs);
     Smem3 s{};
     int o = 0;
-    s.T = o;    o += npk;                           // the pinned factor (packed lower triangle)
+    s.T = o;    o += npk > pl ? npk : pl;           // the source's partial loads, then the pinned factor
     s.Y = o;    o += n * R;                         // right-hand sides, then solutions
     s.mass = o; o += n;
     s.S6 = o;   o += 6 * nb * nb;                   // element matrix per class
@@ -97,14 +104,14 @@ struct Smem3M {
     int Lf, G, Z, Rr, W, sc, dg, invf, mass, S6, G6, J6, red, gn, misc, total;
 };
 
-__host__ __device__ inline Smem3M smem_layout_mixed(int n, int NI, int nb) {
-    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2;
+__host__ __device__ inline Smem3M smem_layout_mixed(int n, int NI, int nb, int nsub, int qs) {
+    const int R = NI + 1, n1 = n - 1, npk = n1 * (n1 + 1) / 2, pl = partial_loads(nsub, nb, qs);
     Smem3M s{};
     int o = 0;
     s.Lf = o;   o += (npk + 1) / 2;                 // FP32 factor of the scaled pinned matrix
     s.G = o;    o += n * R;                         // projected loads g~ (FP64)
     s.Z = o;    o += n * R;                         // solutions (FP64)
-    s.Rr = o;   o += n * R;                         // residuals g~ - A z (FP64)
+    s.Rr = o;   o += n * R > pl ? n * R : pl;       // the source's partial loads, then residuals g~ - A z
     s.W = o;    o += (n1 * R + 1) / 2;              // FP32 preconditioner solves
     s.sc = o;   o += n1;                            // 1 / sqrt(diag) of the pinned matrix
     s.dg = o;   o += n;                             // FP64 diagonal
@@ -214,19 +221,62 @@ __device__ __forceinline__ void class_matrices(const Local3DArgs& g, double Vs, 
     }
 }
 
-// The mass vector, the multiplier loads -s |fine face| / 3 per load node and fine face
-// triangle (columns a m + q of Y, n x R), and a sin sin sin source by the collapsed Gauss
-// rule of every sub-tetrahedron (column N_I, F_K into misc[6]).  Y and mass zeroed by the
-// caller.  No barrier.
-__device__ __forceinline__ void element_loads(const Local3DArgs& g, int64_t K, const double* V, double* Y,
-                                              double* mass, const double* J6, double* misc) {
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
-    const int nb = g.nb, m = g.m, R = g.R, NI = g.NI, N = g.N;
+// The source's partial loads (sin sin sin by the collapsed Gauss rule of every
+// sub-tetrahedron, its 64 points in qs groups): PL[(t qs + grp) nb + a] and, after the
+// qs nsub nb loads, the group's part of F_K.  No barrier.
+__device__ __forceinline__ void source_partials(const Local3DArgs& g, const double* V, const double* J6,
+                                                const double* misc, double* PL) {
+    if (g.src_kind != MHM3D_SRC_SINSINSIN) return;
+    const int nb = g.nb, N = g.N, qs = g.qs, per = kQuad / qs;
+    const double* qp = g.quad;
+    const double* qphi = g.quad + 4 * kQuad;
+    const double w6 = 6.0 * misc[5];
+    const double kf = g.src_freq * M_PI, amp = g.src_value * 3.0 * kf * kf;
+    for (int it = threadIdx.x; it < g.nsub * qs; it += blockDim.x) {
+        const int t = it / qs, grp = it % qs;
+        const double* Jc = J6 + 9 * g.sub_cls[t];
+        const int zA = g.sub_base[3 * t], zB = g.sub_base[3 * t + 1], zC = g.sub_base[3 * t + 2];
+        double x0[3];
+        for (int c = 0; c < 3; ++c)
+            x0[c] = V[c] + ((V[3 + c] - V[c]) * zA + (V[6 + c] - V[3 + c]) * zB + (V[9 + c] - V[6 + c]) * zC) / N;
+        double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, fk = 0.0;
+        for (int q = grp * per; q < (grp + 1) * per; ++q) {
+            double x[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = x0[c] + Jc[3 * c] * qp[4 * q] + Jc[3 * c + 1] * qp[4 * q + 1] + Jc[3 * c + 2] * qp[4 * q + 2];
+            const double wf = qp[4 * q + 3] * w6 * amp * sin(kf * x[0]) * sin(kf * x[1]) * sin(kf * x[2]);
+            fk += wf;
+#pragma unroll
+            for (int a = 0; a < 10; ++a)
+                if (a < nb) acc[a] += wf * qphi[q * nb + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+            if (a < nb) PL[(size_t)it * nb + a] = acc[a];
+        PL[(size_t)g.nsub * qs * nb + it] = fk;
+    }
+}
+
+// After the partial loads' barrier: per local DOF, in the fixed order of its incidence
+// list, the mass int phi_w and the source load (f, phi_w)_K (column N_I of Y, n x R); the
+// multiplier loads -s |fine face| / 3 per load node and fine face triangle (columns
+// a m + q of Y, zeroed by the caller); F_K into misc[6] (thread 0, in order).  No barrier.
+__device__ __forceinline__ void element_loads(const Local3DArgs& g, int64_t K, double* Y, double* mass,
+                                              const double* PL, double* misc) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nb = g.nb, m = g.m, R = g.R, NI = g.NI, qs = g.qs;
     const double Vs = misc[5];
-    for (int it = tid; it < g.nsub * nb; it += nthr) {
-        const int a = it % nb;
-        const double c = g.P == 1 ? 0.25 : (a < 4 ? -0.05 : 0.2);
-        atomicAdd(&mass[g.sub_dofs[it]], c * Vs);
+    const bool src = g.src_kind == MHM3D_SRC_SINSINSIN;
+    for (int w = tid; w < g.n; w += nthr) {
+        double ms = 0.0, ld = 0.0;
+        for (int e = g.inc_off[w]; e < g.inc_off[w + 1]; ++e) {
+            const int slot = g.inc_ent[e], t = slot / nb, a = slot % nb;
+            ms += (g.P == 1 ? 0.25 : (a < 4 ? -0.05 : 0.2)) * Vs;
+            if (src)
+                for (int grp = 0; grp < qs; ++grp) ld += PL[(size_t)(t * qs + grp) * nb + a];
+        }
+        mass[w] = ms;
+        if (src) Y[w * R + NI] = ld;
     }
     for (int it = tid; it < 4 * m; it += nthr) {
         const int a = it / m, q = it % m;
@@ -236,35 +286,36 @@ __device__ __forceinline__ void element_loads(const Local3DArgs& g, int64_t K, c
         for (int e = g.ftab_off[base]; e < g.ftab_off[base + 1]; ++e)
             Y[g.ftab_node[e] * R + it] = w * g.ftab_cnt[e];
     }
-    if (g.src_kind == MHM3D_SRC_SINSINSIN) {
-        const double* qp = g.quad;
-        const double* qphi = g.quad + 4 * kQuad;
-        const double w6 = 6.0 * Vs;
-        const double kf = g.src_freq * M_PI, amp = g.src_value * 3.0 * kf * kf;
+    if (src && tid == 0) {
         double fk = 0.0;
-        const int items = g.nsub * kQuad;
-        for (int it0 = 0; it0 < items; it0 += nthr) {
-            const int it = it0 + tid;
-            double wf = 0.0;
-            if (it < items) {
-                const int t = it / kQuad, q = it % kQuad;
-                const double* Jc = J6 + 9 * g.sub_cls[t];
-                const int zA = g.sub_base[3 * t], zB = g.sub_base[3 * t + 1], zC = g.sub_base[3 * t + 2];
-                double x[3];
-                for (int c = 0; c < 3; ++c) {
-                    const double x0 = V[c] + ((V[3 + c] - V[c]) * zA + (V[6 + c] - V[3 + c]) * zB +
-                                              (V[9 + c] - V[6 + c]) * zC) / N;
-                    x[c] = x0 + Jc[3 * c] * qp[4 * q] + Jc[3 * c + 1] * qp[4 * q + 1] + Jc[3 * c + 2] * qp[4 * q + 2];
-                }
-                const double fv = amp * sin(kf * x[0]) * sin(kf * x[1]) * sin(kf * x[2]);
-                wf = qp[4 * q + 3] * w6 * fv;
-                for (int a = 0; a < nb; ++a) atomicAdd(&Y[g.sub_dofs[t * nb + a] * R + NI], wf * qphi[q * nb + a]);
-            }
-            fk += wf;
-        }
-        fk = warp_sum(fk);
-        if (lane == 0) atomicAdd(&misc[6], fk);
+        for (int i = 0; i < g.nsub * qs; ++i) fk += PL[(size_t)g.nsub * qs * nb + i];
+        misc[6] = fk;
     }
+}
+
+// Row w of the pinned lower triangle (DOF w >= 1, pinned row w - 1), gathered from the
+// element matrices of the sub-tetrahedra at w in the fixed order of its incidence list;
+// one thread owns the row (no atomics).  TL: double (FP64 factor) or float (FP32 factor).
+template <typename TL>
+__device__ __forceinline__ void assemble_row(const Local3DArgs& g, int w, const double* kap, const double* S6,
+                                             TL* Lrow, double* diag) {
+    const int nb = g.nb;
+    for (int j = 0; j < w; ++j) Lrow[j] = (TL)0;
+    double dsum = 0.0;
+    for (int e = g.inc_off[w]; e < g.inc_off[w + 1]; ++e) {
+        const int slot = g.inc_ent[e], t = slot / nb, a = slot % nb;
+        const double kt = kap[t];
+        const double* Sa = S6 + (g.sub_cls[t] * nb + a) * nb;
+        const int32_t* dofs = g.sub_dofs + t * nb;
+        for (int b = 0; b < nb; ++b) {
+            const int col = dofs[b];
+            if (col < 1 || col > w) continue;
+            const double v = kt * Sa[b];
+            Lrow[col - 1] += (TL)v;
+            if (col == w) dsum += v;
+        }
+    }
+    if (diag) *diag = dsum;
 }
 
 // After the loads' barrier: a constant source, then the compatibility projection
@@ -311,7 +362,7 @@ __device__ __forceinline__ void element_tail(const Local3DArgs& g, int64_t K, co
 
 __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     extern __shared__ double sm[];
-    const Smem3 L = smem_layout(g.n, g.NI, g.nb);
+    const Smem3 L = smem_layout(g.n, g.NI, g.nb, g.nsub, g.qs);
     double* Lp = sm + L.T;
     double* Y = sm + L.Y;
     double* mass = sm + L.mass;
@@ -327,22 +378,18 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     const double* V = g.geom + 12 * K;   // v0..v3
     const double* kap = g.kappa + K * (int64_t)g.nsub;
 
-    // ---- zero the factor, right-hand sides and mass; geometry; class matrices
-    for (int i = tid; i < L.S6; i += nthr) sm[i] = 0.0;
+    // ---- zero the right-hand sides; geometry; class matrices; the source's partial loads
+    for (int i = L.Y + tid; i < L.mass; i += nthr) sm[i] = 0.0;
     element_geometry(g, V, misc, G6, J6);
     __syncthreads();
     class_matrices(g, misc[5], G6, S6);
+    source_partials(g, V, J6, misc, Lp);
     __syncthreads();
-
-    // ---- assembly (pinned DOF 0 dropped, lower triangle), loads
-    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
-        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
-        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
-        if (da == 0 || db == 0 || da < db) continue;
-        atomicAdd(&Lp[pk(da - 1, db - 1)], kap[t] * S6[g.sub_cls[t] * nb * nb + ab]);
-    }
-    element_loads(g, K, V, Y, mass, J6, misc);
+    // ---- loads and mass per DOF, then the pinned lower triangle row by row (pinned DOF 0
+    // dropped), over the partial loads once they are summed: no atomics, a fixed order
+    element_loads(g, K, Y, mass, Lp, misc);
     __syncthreads();
+    for (int w = 1 + tid; w < n; w += nthr) assemble_row<double>(g, w, kap, S6, Lp + pk(w - 1, 0), nullptr);
     const_source_and_projection(g, Y, mass, red, misc);
 
     // ---- Cholesky of the pinned matrix (rows 1..n-1), forward substitution fused
@@ -398,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
 // converge gets MHM_ERR_NOT_CONVERGED (the host then re-solves it in FP64 unless asked not to).
 __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
     extern __shared__ double sm[];
-    const Smem3M L = smem_layout_mixed(g.n, g.NI, g.nb);
+    const Smem3M L = smem_layout_mixed(g.n, g.NI, g.nb, g.nsub, g.qs);
     float* Lf = reinterpret_cast<float*>(sm + L.Lf);
     double* G = sm + L.G;
     double* Z = sm + L.Z;
@@ -420,25 +467,17 @@ __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
     const double* V = g.geom + 12 * K;
     const double* kap = g.kappa + K * (int64_t)g.nsub;
 
-    // ---- zero the factor, loads, solutions, residuals, diagonal and mass; geometry; classes
-    for (int i = tid; i < L.sc; i += nthr) sm[i] = 0.0;
-    for (int i = L.dg + tid; i < L.invf; i += nthr) sm[i] = 0.0;
-    for (int i = L.mass + tid; i < L.S6; i += nthr) sm[i] = 0.0;
+    // ---- zero the loads and solutions; geometry; classes; the source's partial loads
+    for (int i = L.G + tid; i < L.Rr; i += nthr) sm[i] = 0.0;
     element_geometry(g, V, misc, G6, J6);
     __syncthreads();
     class_matrices(g, misc[5], G6, S6);
+    source_partials(g, V, J6, misc, Rr);
     __syncthreads();
-
-    // ---- FP32 assembly of the pinned lower triangle, its FP64 diagonal, loads
-    for (int it = tid; it < g.nsub * nb * nb; it += nthr) {
-        const int t = it / (nb * nb), ab = it % (nb * nb), a = ab / nb, b = ab % nb;
-        const int da = g.sub_dofs[t * nb + a], db = g.sub_dofs[t * nb + b];
-        if (da == 0 || db == 0 || da < db) continue;
-        const double v = kap[t] * S6[g.sub_cls[t] * nb * nb + ab];
-        atomicAdd(&Lf[pk(da - 1, db - 1)], (float)v);
-        if (da == db) atomicAdd(&dg[da], v);
-    }
-    element_loads(g, K, V, G, mass, J6, misc);
+    // ---- loads and mass per DOF; the pinned lower triangle in FP32 row by row with its
+    // diagonal in FP64 (no atomics, a fixed order)
+    element_loads(g, K, G, mass, Rr, misc);
+    for (int w = 1 + tid; w < n; w += nthr) assemble_row<float>(g, w, kap, S6, Lf + pk(w - 1, 0), dg + w);
     __syncthreads();
     const_source_and_projection(g, G, mass, red, misc);
 
@@ -512,21 +551,25 @@ __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
             }
         }
         __syncthreads();
-        // z += S w; r = g~ on the pinned rows, then r -= A z element by element
+        // z += S w; then r = g~ - A z on the pinned rows, gathered per DOF from the element
+        // matrices at it (z vanishes on the pinned DOF)
         for (int it = tid; it < n1 * R; it += nthr) {
             const int i = it / R, c = it % R;
             Z[(i + 1) * R + c] += sc[i] * (double)W[it];
-            Rr[(i + 1) * R + c] = G[(i + 1) * R + c];
         }
         __syncthreads();
-        for (int it = tid; it < g.nsub * nb * R; it += nthr) {
-            const int t = it / (nb * R), a = (it / R) % nb, c = it % R;
-            const int da = g.sub_dofs[t * nb + a];
-            if (da == 0) continue;
-            const double* Sa = S6 + (g.sub_cls[t] * nb + a) * nb;
+        for (int it = tid; it < n1 * R; it += nthr) {
+            const int w = it / R + 1, c = it % R;
             double s = 0.0;
-            for (int b = 0; b < nb; ++b) s += Sa[b] * Z[g.sub_dofs[t * nb + b] * R + c];
-            atomicAdd(&Rr[da * R + c], -kap[t] * s);
+            for (int e = g.inc_off[w]; e < g.inc_off[w + 1]; ++e) {
+                const int slot = g.inc_ent[e], t = slot / nb, a = slot % nb;
+                const double* Sa = S6 + (g.sub_cls[t] * nb + a) * nb;
+                const int32_t* dofs = g.sub_dofs + t * nb;
+                double sa = 0.0;
+                for (int b = 0; b < nb; ++b) sa += Sa[b] * Z[dofs[b] * R + c];
+                s += kap[t] * sa;
+            }
+            Rr[w * R + c] = G[w * R + c] - s;
         }
         __syncthreads();
         // converged when every column's |S r|^2 <= tol^2 |S g~|^2
@@ -611,16 +654,24 @@ mhm_status upload3(const std::vector<T>& h, T** d) {
 
 void free_device(mhm_mesh3d* m) {
     void* ptrs[] = {m->d_geom, m->d_signs, m->d_perm, m->d_sub_dofs, m->d_sub_cls, m->d_sub_base, m->d_ftab_off,
-                    m->d_ftab_node, m->d_ftab_cnt, m->d_quad, m->d_rowptr, m->d_nbrs, m->d_face_ka};
+                    m->d_ftab_node, m->d_ftab_cnt, m->d_quad, m->d_rowptr, m->d_nbrs, m->d_face_ka, m->d_inc_off,
+                    m->d_inc_ent};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
 
 }  // namespace
 
-size_t local3d_smem(int n, int NI, int nb) { return (size_t)smem_layout(n, NI, nb).total * sizeof(double); }
-size_t local3d_smem_mixed(int n, int NI, int nb) {
-    return (size_t)smem_layout_mixed(n, NI, nb).total * sizeof(double);
+int local3d_qsplit(int nsub) {
+    int qs = 8;   // groups of the 64 points: as many as keep one item per thread
+    while (qs > 1 && qs * nsub > kThreads) qs >>= 1;
+    return qs;
+}
+size_t local3d_smem(int n, int NI, int nb, int nsub) {
+    return (size_t)smem_layout(n, NI, nb, nsub, local3d_qsplit(nsub)).total * sizeof(double);
+}
+size_t local3d_smem_mixed(int n, int NI, int nb, int nsub) {
+    return (size_t)smem_layout_mixed(n, NI, nb, nsub, local3d_qsplit(nsub)).total * sizeof(double);
 }
 
 }  // namespace mhm3
@@ -649,7 +700,8 @@ extern "C" mhm_status mhm3d_create_mesh(const mhm3d_mesh_desc* desc, int32_t dev
     if (device >= 0) {
         if (!mhm::device_supported(device))
             return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_create_mesh: device is not an sm_103 GPU");
-        if (n > kMaxLocal || d.m > kMaxM || local3d_smem((int)n, 4 * d.m, d.degree == 1 ? 4 : 10) > 227 * 1024)
+        if (n > kMaxLocal || d.m > kMaxM ||
+            local3d_smem((int)n, 4 * d.m, d.degree == 1 ? 4 : 10, 1 << (3 * d.r)) > 227 * 1024)
             return mhm::fail(MHM_ERR_UNSUPPORTED,
                              "mhm3d_create_mesh: the local factor and right-hand sides exceed shared memory "
                              "(degree 2: r <= 2, degree 1: r <= 3, m <= 16)");
@@ -676,6 +728,8 @@ extern "C" mhm_status mhm3d_create_mesh(const mhm3d_mesh_desc* desc, int32_t dev
         if (!st) st = upload3(m->sub_dofs, &m->d_sub_dofs);
         if (!st) st = upload3(m->sub_cls, &m->d_sub_cls);
         if (!st) st = upload3(m->sub_base, &m->d_sub_base);
+        if (!st) st = upload3(m->inc_off, &m->d_inc_off);
+        if (!st) st = upload3(m->inc_ent, &m->d_inc_ent);
         if (!st) st = upload3(m->ftab_off, &m->d_ftab_off);
         if (!st) st = upload3(m->ftab_node, &m->d_ftab_node);
         if (!st) st = upload3(m->ftab_cnt, &m->d_ftab_cnt);
@@ -756,6 +810,7 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
     Local3DArgs g{};
     g.geom = m->d_geom, g.signs = m->d_signs, g.perm = m->d_perm;
     g.sub_dofs = m->d_sub_dofs, g.sub_cls = m->d_sub_cls, g.sub_base = m->d_sub_base;
+    g.inc_off = m->d_inc_off, g.inc_ent = m->d_inc_ent;
     g.ftab_off = m->d_ftab_off, g.ftab_node = m->d_ftab_node, g.ftab_cnt = m->d_ftab_cnt;
     g.quad = m->d_quad, g.kappa = kappa;
     g.src_kind = f->kind, g.src_value = f->value, g.src_freq = f->freq;
@@ -767,8 +822,9 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
     const unsigned grid = (unsigned)(K1 - K0);
     cudaStream_t s = (cudaStream_t)stream;
     // the shared-memory attribute is per kernel, not per mesh: set it for this mesh every call
-    const size_t smem64 = local3d_smem(g.n, g.NI, g.nb);
-    const size_t smemmx = local3d_smem_mixed(g.n, g.NI, g.nb);
+    g.qs = local3d_qsplit(g.nsub);
+    const size_t smem64 = local3d_smem(g.n, g.NI, g.nb, g.nsub);
+    const size_t smemmx = local3d_smem_mixed(g.n, g.NI, g.nb, g.nsub);
     const bool mixed = precision == MHM_MIXED && smemmx <= 227 * 1024;
     if (mixed) {
         MHM_CUDA_TRY(cudaFuncSetAttribute(k_local3d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemmx));

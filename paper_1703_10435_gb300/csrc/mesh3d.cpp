@@ -244,6 +244,16 @@ std::string build_mesh3d_host(mhm_mesh3d* m) {
                 }
     m->nsub = (int64_t)sub_lat.size();
     if (m->nsub != (int64_t)N * N * N) return "internal: Freudenthal refinement count";
+    // incidence of the local DOFs: the slots t nb + a of the sub-tetrahedra that hold each
+    // DOF, ascending (the kernels gather per DOF in this fixed order: no atomics)
+    m->inc_off.assign(m->n + 1, 0);
+    for (int32_t d : m->sub_dofs) ++m->inc_off[d + 1];
+    for (int64_t w = 0; w < m->n; ++w) m->inc_off[w + 1] += m->inc_off[w];
+    m->inc_ent.assign(m->sub_dofs.size(), 0);
+    {
+        std::vector<int32_t> fill(m->inc_off.begin(), m->inc_off.end() - 1);
+        for (size_t slot = 0; slot < m->sub_dofs.size(); ++slot) m->inc_ent[fill[m->sub_dofs[slot]]++] = (int32_t)slot;
+    }
 
     // ---- face-load table: for local face a and permutation code p, per subface q the
     // local DOFs that carry the face load of its fine triangles (P1: vertices, P2: edge

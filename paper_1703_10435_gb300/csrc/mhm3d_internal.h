@@ -30,8 +30,9 @@ struct Nbr3 {
 };
 
 // shared memory bytes of one local-solve block (FP64 and mixed kernels)
-size_t local3d_smem(int n, int NI, int nb);
-size_t local3d_smem_mixed(int n, int NI, int nb);
+int local3d_qsplit(int nsub);
+size_t local3d_smem(int n, int NI, int nb, int nsub);
+size_t local3d_smem_mixed(int n, int NI, int nb, int nsub);
 
 // rule on [0,1] (Newton on the Legendre polynomial)
 void gauss01(int n, double* x, double* w);
@@ -58,6 +59,8 @@ struct mhm_mesh3d {
     std::vector<int32_t> sub_dofs;    // nsub*nb
     std::vector<int8_t> sub_cls;      // nsub: permutation class
     std::vector<int8_t> sub_base;     // nsub*3: base point z
+    std::vector<int32_t> inc_off;     // n+1: sub-tetrahedron slots t nb + a holding each local DOF
+    std::vector<int32_t> inc_ent;     // nsub*nb, ascending per DOF
     std::vector<int32_t> ftab_off;    // 24*(m+1): entries of subface q of local face a under perm p
     std::vector<int16_t> ftab_node;   // local DOF
     std::vector<int8_t> ftab_cnt;     // fine face triangles of the subface that hold the DOF as a load node
@@ -72,6 +75,8 @@ struct mhm_mesh3d {
     int32_t* d_sub_dofs = nullptr;
     int8_t* d_sub_cls = nullptr;
     int8_t* d_sub_base = nullptr;
+    int32_t* d_inc_off = nullptr;
+    int32_t* d_inc_ent = nullptr;
     int32_t* d_ftab_off = nullptr;
     int16_t* d_ftab_node = nullptr;
     int8_t* d_ftab_cnt = nullptr;

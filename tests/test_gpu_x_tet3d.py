@@ -106,10 +106,8 @@ def test_mixed_fallback_and_no_fallback():
     ref = _run(M, kappa, src)
     fb = _run(M, kappa, src, precision=mhm.MHM_MIXED, opts=mhm.Opts3D(1, 1e-300, 0))
     assert np.all(fb["status"] == 0) and np.all(fb["iters"] == -1)
-    for k in ("AK", "EK", "BK"):
-        assert np.abs(fb[k] - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max(), k
-    # F_K is a sum with cancellation (small next to int |f|): held on the scale amp |K|
-    assert np.abs(fb["FK"] - ref["FK"]).max() <= 1e-13 * 12 * math.pi ** 2 / M.n_K
+    for k in ("AK", "EK", "BK", "FK"):   # the FP64 kernel again: bit for bit
+        assert np.array_equal(fb[k], ref[k]), k
     nf = _run(M, kappa, src, precision=mhm.MHM_MIXED, opts=mhm.Opts3D(1, 1e-300, 1))
     assert np.all(nf["status"] == mhm.MHM_ERR_NOT_CONVERGED) and np.all(nf["iters"] == 1)
     with pytest.raises(mhm.MHMError) as e:
@@ -117,21 +115,32 @@ def test_mixed_fallback_and_no_fallback():
     assert e.value.code == mhm.MHM_ERR_INVALID_ARG
 
 
-def test_k_range_matches_full_call():
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_k_range_matches_full_call(precision):
     M = mhm.Mesh3D(1, 2, 2, 4, device=0)
     rng = np.random.default_rng(3)
     kappa = 10.0 ** rng.uniform(-1, 1, (M.n_K, 64))
     src = mhm.Source3D(mhm.MHM3D_SRC_SINSINSIN, 1.0, 2.0)
-    full = _run(M, kappa, src)
-    part = _run(M, kappa, src, 5, 17)
+    full = _run(M, kappa, src, precision=precision)
+    part = _run(M, kappa, src, 5, 17, precision=precision)
     assert np.all(part["status"][:5] == -7) and np.all(part["status"][17:] == -7)
-    # the same elements up to the shared-memory atomics' summation order (F_K, a sum with
-    # cancellation, on the scale amp |K|)
+    # the same elements bit for bit (every sum in the kernels runs in a fixed order)
     for k in ("AK", "EK", "BK", "FK"):
-        a, b = part[k][5:17], full[k][5:17]
-        scale = 12 * math.pi ** 2 / M.n_K if k == "FK" else np.abs(b).max()
-        assert np.abs(a - b).max() <= 1e-11 * scale, k
+        assert np.array_equal(part[k][5:17], full[k][5:17]), k
         assert not np.any(part[k][17:])
+
+
+@pytest.mark.parametrize("precision", [mhm.MHM_FP64, mhm.MHM_MIXED])
+def test_repeated_calls_bit_identical(precision):
+    """No atomics: assembly, loads and residuals are gathered per DOF in a fixed order."""
+    M = mhm.Mesh3D(1, 2, 2, 4, device=0)
+    rng = np.random.default_rng(12)
+    kappa = 10.0 ** rng.uniform(-2, 2, (M.n_K, 64))
+    src = mhm.Source3D(mhm.MHM3D_SRC_SINSINSIN, 1.0, 2.0)
+    a = _run(M, kappa, src, precision=precision)
+    b = _run(M, kappa, src, precision=precision)
+    for k in ("AK", "EK", "BK", "FK", "status", "iters"):
+        assert np.array_equal(a[k], b[k]), k
 
 
 def test_skeleton_matches_oracle_assembly():
