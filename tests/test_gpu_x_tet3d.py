@@ -202,14 +202,15 @@ def test_exact_linear_recovery_through_gpu_blocks():
     assert np.abs(lam - np.repeat(-(o.normals @ grad), m)).max() < 1e-10
 
 
-def test_full_size_sampled_parity_and_properties():
-    """The paper's first configuration (Sec. 5: 12288 coarse tetrahedra, m = 4, k = 2;
-    here 64 sub-tetrahedra per element for TetGen's 59), kappa = 1 and f = 12 pi^2 sin sin sin
-    as in the paper (FP64 and MIXED), then a log-uniform kappa (MIXED): sampled elements
-    against the oracle, and at
+@pytest.mark.parametrize("nc,m", [(8, 4), (4, 16)])
+def test_full_size_sampled_parity_and_properties(nc, m):
+    """The paper's configurations (Sec. 5, k = 2, here 64 sub-tetrahedra per element for
+    TetGen's 59): 12288 coarse tetrahedra with m = 4 and 1536 with m = 16 (MIXED runs the FP64
+    kernel there), kappa = 1 and f = 12 pi^2 sin sin sin as in the paper (FP64 and MIXED), then
+    a log-uniform kappa (MIXED): sampled elements against the oracle, and at
     every element B_K = s |face| / m, a symmetric negative semidefinite A_K (checked on 256
     elements) and status 0."""
-    nc, r, P, m = 8, 2, 2, 4
+    r, P = 2, 2
     M = mhm.Mesh3D(nc, r, P, m, device=0)
     o = T.build_mesh3d(nc, m)
     src = mhm.Source3D(mhm.MHM3D_SRC_SINSINSIN, 1.0, 2.0)
