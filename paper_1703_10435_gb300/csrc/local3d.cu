@@ -1,21 +1,26 @@
-// Three-dimensional local problems (the paper's experiment, Sec. 5) in FP64 on the GPU:
-// solveLocalProblem for every coarse tetrahedron (Sec. 3, Eqs. "etaf", "etai") and the
-// gather of the skeleton system (Eq. "mat_global").  Conventions in mhm3d.h.
+// Three-dimensional local problems (the paper's experiment, Sec. 5) on the GPU:
+// solveLocalProblem for every coarse tetrahedron (Sec. 3, Eqs. "etaf", "etai") in FP64
+// or mixed precision, and the gather of the skeleton system (Eq. "mat_global").
+// Conventions in mhm3d.h.
 //
-// k_local3d: one block of kThreads threads per coarse element, everything in shared
-// memory:
+// Both local kernels run one block of kThreads threads per coarse element, everything in
+// shared memory, with no atomics (every sum in a fixed order: repeated calls are
+// bit-identical):
 //   1. one element matrix per class of congruent sub-tetrahedra (the Freudenthal
 //      refinement has six: its sub-tetrahedra of one permutation class are translates),
 //      from the closed forms of the P1 / P2 Lagrange stiffness in barycentric gradients;
-//   2. assembly of kappa_T S_class into the packed lower triangle of the stiffness with
-//      local DOF 0 pinned (shared-memory atomics), the mass vector int phi_w, the
-//      multiplier loads -s (psi_j, phi_w) from the face table (a fine face triangle
-//      puts a third of its area on each load node) and the source load;
+//   2. per local DOF, over the sub-tetrahedra that hold it: its row of the pinned lower
+//      triangle (local DOF 0 removed), its mass int phi_w and its source load; the
+//      multiplier loads -s (psi_j, phi_w) from the face table (a fine face triangle puts
+//      a third of its area on each load node);
 //   3. the compatibility projection g - (1^T g / |K|) m of every right-hand side;
+// then k_local3d (FP64):
 //   4. a right-looking Cholesky factorisation of the pinned matrix with the forward
 //      substitution of all right-hand sides fused in;
 //   5. the face integrals in Gram form, (s psi_j, eta_i)_{dK} = -Y_j . Y_i with Y = L^{-1}
-//      times the projected loads (symmetric by construction), and E_K = Y_j . y_f.
+//      times the projected loads (symmetric by construction), and E_K = Y_j . y_f;
+// or k_local3d_mixed: an FP32 factor of the diagonally scaled matrix, FP64 refinement
+// against the matrix-free residual, and the corrected bilinear form (see the kernel).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -695,8 +700,8 @@ extern "C" mhm_status mhm3d_create_mesh(const mhm3d_mesh_desc* desc, int32_t dev
     const int PN = d.degree << d.r;
     const int64_t n = (int64_t)(PN + 1) * (PN + 2) * (PN + 3) / 6;
     const int64_t nK = 24LL * d.nc * d.nc * d.nc;
-    if (nK * 16LL * d.m * d.m > INT32_MAX * 8LL)
-        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: mesh too large");
+    if (nK * 16LL * d.m * d.m > (1LL << 34))   // A_K alone: n_K N_I^2 doubles
+        return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_create_mesh: the per-element blocks would exceed 2^34 values");
     if (device >= 0) {
         if (!mhm::device_supported(device))
             return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_create_mesh: device is not an sm_103 GPU");
