@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     double* J6 = sm + L.J6;
     double* red = sm + L.red;
     double* misc = sm + L.misc;
-    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, nwarp = nthr >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t K = g.K0 + blockIdx.x;
     if (g.only_failed && g.status[K] == MHM_OK) return;   // the whole block, before any barrier
-    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI, nb = g.nb;
+    const int n = g.n, n1 = n - 1, R = g.R, NI = g.NI;
     const double* V = g.geom + 12 * K;   // v0..v3
     const double* kap = g.kappa + K * (int64_t)g.nsub;
 
@@ -408,11 +408,20 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         for (int i = k + 1 + tid; i < n1; i += nthr) Lp[pk(i, k)] *= inv;
         for (int r = tid; r < R; r += nthr) Y[(k + 1) * R + r] *= inv;
         __syncthreads();
-        for (int i = k + 1 + warp; i < n1; i += nwarp) {
-            const double lik = Lp[pk(i, k)];
-            double* row = Lp + pk(i, 0);
-            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * Lp[pk(j, k)];
-            for (int r = lane; r < R; r += 32) Y[(i + 1) * R + r] -= lik * Y[(k + 1) * R + r];
+        // trailing update of the triangle below pivot k and of the right-hand sides, as one
+        // flat list of items over all threads (every lane busy: the FP64 pipe is the limit)
+        const int mt = n1 - k - 1, tri = mt * (mt + 1) / 2, items = tri + mt * R;
+        for (int t = tid; t < items; t += nthr) {
+            if (t < tri) {
+                int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // row of entry t
+                while (ii * (ii + 1) / 2 > t) --ii;
+                while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+                const int i = k + 1 + ii, j = k + 1 + (t - ii * (ii + 1) / 2);
+                Lp[pk(i, j)] -= Lp[pk(i, k)] * Lp[pk(j, k)];
+            } else {
+                const int u = t - tri, i = k + 1 + u / R, r = u % R;
+                Y[(i + 1) * R + r] -= Lp[pk(i, k)] * Y[(k + 1) * R + r];
+            }
         }
         __syncthreads();
     }
