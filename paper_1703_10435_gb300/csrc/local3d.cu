@@ -78,6 +78,14 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
+// Row of entry t of a packed lower triangle (t = row (row + 1) / 2 + col, col <= row).
+__device__ __forceinline__ int tri_row(int t) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    return r;
+}
+
 // shared-memory layout of the FP64 kernel (doubles), in this order
 struct Smem3 {
     int T, Y, mass, S6, G6, J6, red, misc, total;
@@ -413,9 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
         const int mt = n1 - k - 1, tri = mt * (mt + 1) / 2, items = tri + mt * R;
         for (int t = tid; t < items; t += nthr) {
             if (t < tri) {
-                int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // row of entry t
-                while (ii * (ii + 1) / 2 > t) --ii;
-                while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+                const int ii = tri_row(t);
                 const int i = k + 1 + ii, j = k + 1 + (t - ii * (ii + 1) / 2);
                 Lp[pk(i, j)] -= Lp[pk(i, k)] * Lp[pk(j, k)];
             } else {
@@ -431,9 +437,9 @@ __global__ void __launch_bounds__(kThreads) k_local3d(Local3DArgs g) {
     // vanishes on the pinned DOF.  Likewise -(s psi_j, eta_f)_{dK} = Y_j . y_f.  No backward
     // substitution is needed.
     double* AK = g.AK + K * (int64_t)NI * NI;
-    for (int it = tid; it < NI * R; it += nthr) {
-        const int j = it / R, i = it % R;
-        if (i < NI && i > j) continue;   // each pair once; the E_K column i = NI for every j
+    const int pairs = NI * (NI + 1) / 2;   // each pair i <= j once, then the E_K entries (i = N_I)
+    for (int it = tid; it < pairs + NI; it += nthr) {
+        const int j = it < pairs ? tri_row(it) : it - pairs, i = it < pairs ? it - j * (j + 1) / 2 : NI;
         double s = 0.0;
         for (int w = 1; w < n; ++w) s += Y[w * R + j] * Y[w * R + i];
         if (i == NI) {
@@ -503,10 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
     }
     __syncthreads();
     for (int it = tid; it < npk; it += nthr) {
-        int i = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);   // row of packed entry it
-        while (i * (i + 1) / 2 > it) --i;
-        while ((i + 1) * (i + 2) / 2 <= it) ++i;
-        const int j = it - i * (i + 1) / 2;
+        const int i = tri_row(it), j = it - i * (i + 1) / 2;
         Lf[it] = (float)((double)Lf[it] * sc[i] * sc[j]);
     }
     __syncthreads();
@@ -608,9 +611,9 @@ __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
 
     // ---- corrected face integrals T_ji = -(g~_j . z_i + z_j . r_i), averaged with T_ij
     double* AK = g.AK + K * (int64_t)NI * NI;
-    for (int it = tid; it < NI * R; it += nthr) {
-        const int j = it / R, i = it % R;
-        if (i < NI && i > j) continue;
+    const int pairs = NI * (NI + 1) / 2;   // each pair i <= j once, then the E_K entries (i = N_I)
+    for (int it = tid; it < pairs + NI; it += nthr) {
+        const int j = it < pairs ? tri_row(it) : it - pairs, i = it < pairs ? it - j * (j + 1) / 2 : NI;
         double a1 = 0.0, a2 = 0.0;
         for (int w = 1; w < n; ++w) {
             a1 += G[w * R + j] * Z[w * R + i] + Z[w * R + j] * Rr[w * R + i];
