@@ -16,6 +16,12 @@ kappa field sampled at that level), e.g. the 256-row level windows of r = 7:
 
     python -m paper_1703_10435_gb300.profile_case --workload c4_channels --level 7 \
         --precision fp64 --n-k 152
+
+--cube nc runs the three-dimensional local solves instead (the unit cube of the paper's
+experiment, Sec. 5: 24 nc^3 tetrahedra, P2 on 64 sub-tetrahedra, m subfaces per face,
+kappa = 1, f = 12 pi^2 sin sin sin), e.g. the 1536 elements of nc = 4 in mixed precision:
+
+    python -m paper_1703_10435_gb300.profile_case --cube 4 --m 4 --precision mixed
 """
 from __future__ import annotations
 
@@ -28,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--n-k", type=int, default=152, help="coarse triangles K = 0 .. n_k - 1")
     ap.add_argument("--level", type=int, default=None, help="uniform refinement level r for every K")
+    ap.add_argument("--cube", type=int, default=None, help="3-D: cubes per side of the unit cube")
+    ap.add_argument("--m", type=int, default=4, help="3-D: subfaces per face (4 or 16)")
     args = ap.parse_args(argv)
 
     import torch
@@ -36,6 +44,25 @@ def main(argv=None):
     from .pipeline import Pipeline, source_of
 
     build.build()
+    if args.cube is not None:
+        M = mhm.Mesh3D(args.cube, 2, 2, args.m, device=0)
+        dev = torch.device("cuda", 0)
+        kap = torch.ones(M.n_K * M.n_sub, dtype=torch.float64, device=dev)
+        AK = torch.empty(M.n_K, M.n_I, M.n_I, dtype=torch.float64, device=dev)
+        EK = torch.empty(M.n_K, M.n_I, dtype=torch.float64, device=dev)
+        BK, FK = torch.empty_like(EK), torch.empty(M.n_K, dtype=torch.float64, device=dev)
+        st = torch.empty(M.n_K, dtype=torch.int32, device=dev)
+        prec = mhm.MHM_MIXED if args.precision == "mixed" else mhm.MHM_FP64
+        src = mhm.Source3D(mhm.MHM3D_SRC_SINSINSIN, 1.0, 2.0)
+        for _ in range(2):
+            mhm.mhm3d_local_solve_batch(M, kap, src, AK, EK, BK, FK, st, precision=prec)
+        torch.cuda.synchronize()
+        bad = int(st.abs().sum())
+        print("profile case: cube %d, m %d, %s, %d tetrahedra, status sum %d"
+              % (args.cube, args.m, args.precision, M.n_K, bad))
+        if bad:
+            raise SystemExit(1)
+        return
     w = W.WORKLOADS[args.workload]
     if args.level is not None:
         import dataclasses
