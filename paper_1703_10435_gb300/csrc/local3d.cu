@@ -523,10 +523,11 @@ __global__ void __launch_bounds__(kThreads) k_local3d_mixed(Local3DArgs g) {
         for (int i = k + 1 + tid; i < n1; i += nthr) Lf[pk(i, k)] *= inv;
         if (tid == 0) invf[k] = inv;
         __syncthreads();
-        for (int i = k + 1 + warp; i < n1; i += nwarp) {
-            const float lik = Lf[pk(i, k)];
-            float* row = Lf + pk(i, 0);
-            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * Lf[pk(j, k)];
+        const int mt = n1 - k - 1, tri = mt * (mt + 1) / 2;   // the trailing triangle, one flat list
+        for (int t = tid; t < tri; t += nthr) {
+            const int ii = tri_row(t);
+            const int i = k + 1 + ii, j = k + 1 + (t - ii * (ii + 1) / 2);
+            Lf[pk(i, j)] -= Lf[pk(i, k)] * Lf[pk(j, k)];
         }
         __syncthreads();
     }
