@@ -13,7 +13,6 @@ torch = pytest.importorskip("torch")
 from oracle import globalsys
 from oracle import tet3d as T
 from paper_1703_10435_gb300 import mhm
-from paper_1703_10435_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
