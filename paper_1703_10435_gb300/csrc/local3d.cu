@@ -809,8 +809,8 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
                                               int32_t precision, const mhm3d_opts* opts, int64_t K0, int64_t K1,
                                               double* AK, double* EK, double* BK, double* FK, int32_t* status,
                                               int32_t* iters, void* stream) {
+    // every argument is checked before the device: a host-only mesh reports argument errors too
     if (!m) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL mesh");
-    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_local_solve_batch: host-only mesh");
     if (!kappa || !f || !AK || !EK || !BK || !FK || !status)
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: NULL pointer argument");
     if (f->kind != MHM3D_SRC_CONST && f->kind != MHM3D_SRC_SINSINSIN)
@@ -823,6 +823,7 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
         return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: it_max >= 1 and tol > 0 required");
     if (K1 <= 0) K1 = m->nK;
     if (K0 < 0 || K1 > m->nK || K0 > K1) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_local_solve_batch: K range");
+    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_local_solve_batch: host-only mesh");
     if (K1 == K0) return MHM_OK;
     MHM_CUDA_TRY(cudaSetDevice(m->device));
     Local3DArgs g{};
@@ -860,8 +861,8 @@ extern "C" mhm_status mhm3d_local_solve_batch(const mhm3d_mesh* m, const double*
 extern "C" mhm_status mhm3d_assemble_skeleton(const mhm3d_mesh* m, const double* AK, const double* EK,
                                               double* A_vals, double* E, void* stream) {
     if (!m) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_assemble_skeleton: NULL mesh");
-    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_assemble_skeleton: host-only mesh");
     if (!AK || !EK || !A_vals || !E) return mhm::fail(MHM_ERR_INVALID_ARG, "mhm3d_assemble_skeleton: NULL pointer");
+    if (m->device < 0) return mhm::fail(MHM_ERR_UNSUPPORTED, "mhm3d_assemble_skeleton: host-only mesh");
     MHM_CUDA_TRY(cudaSetDevice(m->device));
     const int64_t nblocks = (int64_t)m->nbrs.size();
     const int64_t items = nblocks * m->desc.m * m->desc.m;

@@ -105,6 +105,29 @@ def test_refusals(lib, nc, r, P, m):
     assert e.value.code == mhm.MHM_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("case", ["kind", "precision", "it_max", "tol", "range", "null"])
+def test_local_solve_argument_errors(lib, case):
+    """Arguments are checked before the device: refusals on a host-only mesh (no pointer is
+    dereferenced on the host)."""
+    import torch
+    M = mhm.Mesh3D(1, 1, 2, 4, device=-1)
+    t = torch.zeros(8)
+    st = torch.zeros(8, dtype=torch.int32)
+    src = mhm.Source3D(7 if case == "kind" else mhm.MHM3D_SRC_CONST, 1.0, 2.0)
+    kw = dict(stream=type("S", (), {"cuda_stream": 0})())
+    if case == "precision":
+        kw["precision"] = 5
+    if case == "it_max":
+        kw["opts"] = mhm.Opts3D(0, 1e-9, 0)
+    if case == "tol":
+        kw["opts"] = mhm.Opts3D(4, 0.0, 0)
+    if case == "range":
+        kw["K0"], kw["K1"] = 3, M.n_K + 1
+    with pytest.raises(mhm.MHMError) as e:
+        mhm.mhm3d_local_solve_batch(M, None if case == "null" else t, src, t, t, t, t, st, **kw)
+    assert e.value.code == mhm.MHM_ERR_INVALID_ARG
+
+
 def test_host_only_mesh_has_no_compute(lib):
     import torch
     M = mhm.Mesh3D(1, 1, 2, 4, device=-1)
