@@ -216,9 +216,11 @@ def test_full_size_sampled_parity_and_properties(nc, m):
     f = T.source3d_fn("sinsinsin", 1.0, 2.0)
     amp = 12.0 * math.pi ** 2
     rng = np.random.default_rng(2026)
+    runs = []
     for kappa, precision in ((np.ones((M.n_K, 64)), mhm.MHM_FP64), (np.ones((M.n_K, 64)), mhm.MHM_MIXED),
                              (10.0 ** rng.uniform(-1, 1, (M.n_K, 64)), mhm.MHM_MIXED)):
         got = _run(M, kappa, src, precision=precision)
+        runs.append(got)
         assert np.all(got["status"] == 0)
         sample = [0, M.n_K - 1] + [int(k) for k in rng.choice(M.n_K, 4, replace=False)]
         for K in sample:
@@ -235,6 +237,11 @@ def test_full_size_sampled_parity_and_properties(nc, m):
         for K in rng.choice(M.n_K, 256, replace=False):
             ev = np.linalg.eigvalsh(got["AK"][K])
             assert ev.max() <= 1e-12 * np.abs(ev).max()
+    # every element: the two precisions on the same input agree on the Gram scale
+    a64, amx = runs[0]["AK"], runs[1]["AK"]
+    d = np.sqrt(np.abs(np.einsum("kii->ki", a64)))
+    assert float((np.abs(amx - a64) / np.maximum(d[:, :, None] * d[:, None, :], 1e-300)).max()) < 1e-10
+    assert float(np.abs(runs[1]["EK"] - runs[0]["EK"]).max()) <= 1e-10 * float(np.abs(runs[0]["EK"]).max())
 
 
 def test_device_refusals():
